@@ -1,0 +1,280 @@
+// Oracle: plain, single-threaded CPU definition of the k-mer counting result.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+// benchmark's CPU-baseline leg may load this file's library.  It shares no
+// code with the GPU library: it reads ASCII reads (never the 2-bit packed
+// format), encodes each window from its characters, and keeps counts in a
+// std::unordered_map.
+//
+// What it computes (the exact result the GPU path must reproduce bit for bit):
+//
+//  1. k-mers of a read of length M are its M-k+1 substrings of length k
+//     (Section II-A).  A window that contains any character other than
+//     A/C/G/T is skipped: the reads' quality screen (Section III-A) is read
+//     as "drop windows over unknown bases".
+//  2. Each base takes 2 bits, A=0 C=1 G=2 T=3, first base most significant, so
+//     a k-mer is one 64-bit word (Section II-A, "64 bits per k-mer -- 2 bits
+//     per each base") and numeric order equals lexicographic order.
+//  3. A k-mer and its reverse complement are the same key: key = min(fwd, rc),
+//     rc being the encoding of the reversed, complemented string.  (The paper
+//     does not discuss strands; canonical keys are this library's reading.)
+//  4. count[key][sample] = number of valid windows with that key, per sample.
+//  5. The result keeps the keys whose count summed over samples is at least
+//     min_count: k-mers seen only once are dropped (Section II-B, Count unit;
+//     Section III, Prune), and Bloom false positives are removed (Section III,
+//     Unify).  Keys are listed in ascending order.
+//  6. The Bloom filter is the OR over every valid window of the window key's
+//     bit pattern placed in one 64-bit word (a word-blocked filter):
+//        h = mixer64(key), g = mixer64(h)
+//        word   = h >> (64 - log2(bloom_bits / 64))
+//        bit i  = (g >> 6i) & 63 for i < n_hashes   (colliding bits merge)
+//     mixer64 is the SplitMix64 output function (Steele, Lea & Flood,
+//     "Fast splittable pseudorandom number generators", OOPSLA 2014): add the
+//     golden-ratio increment, then two xor-shift/multiply rounds and a final
+//     xor-shift.  The paper names no hash function; this is the library's.
+//
+// Partition-restricted runs (for inputs too large to count in full here):
+// when a keep-set over the top q bits of h is given, windows whose key falls
+// outside the set are counted in the window total but not otherwise.
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+int base_code(char c) {
+    switch (c) {
+        case 'A': return 0;
+        case 'C': return 1;
+        case 'G': return 2;
+        case 'T': return 3;
+        default: return -1;
+    }
+}
+
+char complement_base(char c) {
+    switch (c) {
+        case 'A': return 'T';
+        case 'C': return 'G';
+        case 'G': return 'C';
+        case 'T': return 'A';
+        default: return 'N';
+    }
+}
+
+uint64_t mixer64(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Encode k characters starting at s, first character most significant.
+uint64_t encode(const char* s, int k) {
+    uint64_t v = 0;
+    for (int t = 0; t < k; ++t) v = v * 4 + (uint64_t)base_code(s[t]);
+    return v;
+}
+
+int log2_exact(uint64_t x) {
+    int r = 0;
+    while ((1ull << r) < x) ++r;
+    return r;
+}
+
+struct Oracle {
+    int k;
+    int n_samples;
+    uint64_t bloom_bits;
+    int n_hashes;
+    uint32_t min_count;
+    int log2_words;
+
+    int restrict_bits = 0;           // 0 = count every key
+    std::vector<uint8_t> keep;       // 2^restrict_bits flags
+
+    uint64_t windows = 0;            // valid windows seen, all samples
+    uint64_t counted = 0;            // windows whose key was counted
+    std::unordered_map<uint64_t, std::vector<uint32_t>> counts;
+    std::vector<uint64_t> bloom;                    // full filter (unrestricted)
+    std::unordered_map<uint64_t, uint64_t> bloom_words;  // touched words (restricted)
+
+    uint64_t word_of(uint64_t key) const {
+        uint64_t h = mixer64(key);
+        return log2_words == 0 ? 0 : h >> (64 - log2_words);
+    }
+
+    uint64_t pattern_of(uint64_t key) const {
+        uint64_t g = mixer64(mixer64(key));
+        uint64_t p = 0;
+        for (int i = 0; i < n_hashes; ++i) {
+            int bit = (int)((g >> (6 * i)) & 63);
+            p |= 1ull << bit;
+        }
+        return p;
+    }
+
+    bool kept(uint64_t key) const {
+        if (restrict_bits == 0) return true;
+        return keep[mixer64(key) >> (64 - restrict_bits)] != 0;
+    }
+
+    void bloom_insert(uint64_t key) {
+        uint64_t w = word_of(key);
+        uint64_t g = mixer64(mixer64(key));
+        for (int i = 0; i < n_hashes; ++i) {
+            int bit = (int)((g >> (6 * i)) & 63);
+            if (restrict_bits == 0)
+                bloom[w] |= 1ull << bit;
+            else
+                bloom_words[w] |= 1ull << bit;
+        }
+    }
+
+    void add_read(int sample, const char* s, uint64_t len) {
+        if (len < (uint64_t)k) return;
+        std::vector<char> rc_buf((size_t)k);
+        for (uint64_t j = 0; j + (uint64_t)k <= len; ++j) {
+            bool valid = true;
+            for (int t = 0; t < k; ++t)
+                if (base_code(s[j + t]) < 0) {
+                    valid = false;
+                    break;
+                }
+            if (!valid) continue;
+            ++windows;
+            uint64_t fwd = encode(s + j, k);
+            for (int t = 0; t < k; ++t) rc_buf[t] = complement_base(s[j + k - 1 - t]);
+            uint64_t rc = encode(rc_buf.data(), k);
+            uint64_t key = std::min(fwd, rc);
+            if (!kept(key)) continue;
+            ++counted;
+            auto& c = counts[key];
+            if (c.empty()) c.assign((size_t)n_samples, 0u);
+            if (c[sample] != 0xffffffffu) ++c[sample];
+            bloom_insert(key);
+        }
+    }
+
+    std::vector<uint64_t> result_keys() const {
+        std::vector<uint64_t> keys;
+        for (const auto& kv : counts) {
+            uint64_t total = 0;
+            for (uint32_t c : kv.second) total += c;
+            if (total >= min_count) keys.push_back(kv.first);
+        }
+        std::sort(keys.begin(), keys.end());
+        return keys;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+// Returns nullptr on invalid arguments (same ranges as the GPU library).
+void* orc_create(int k, int n_samples, uint64_t bloom_bits, int n_hashes, uint32_t min_count) {
+    if (k < 1 || k > 31 || n_samples < 1 || n_samples > 2 || n_hashes < 1 || n_hashes > 10 || min_count < 1)
+        return nullptr;
+    if (bloom_bits < 4096 || (bloom_bits & (bloom_bits - 1)) != 0) return nullptr;
+    Oracle* o = new Oracle();
+    o->k = k;
+    o->n_samples = n_samples;
+    o->bloom_bits = bloom_bits;
+    o->n_hashes = n_hashes;
+    o->min_count = min_count;
+    o->log2_words = log2_exact(bloom_bits / 64);
+    return o;
+}
+
+// Restrict counting to keys whose top q bits of mixer64(key) are flagged in
+// keep[0 .. 2^q).  Must be called before the first orc_add_reads.
+int orc_restrict(void* h, int q, const uint8_t* keep) {
+    Oracle* o = (Oracle*)h;
+    if (!o || q < 1 || q > 24 || !keep || o->windows != 0) return -1;
+    o->restrict_bits = q;
+    o->keep.assign(keep, keep + (1ull << q));
+    return 0;
+}
+
+// Add n_reads ASCII reads of one sample; read r = ascii[offsets[r] .. offsets[r+1]).
+int orc_add_reads(void* h, int sample, const char* ascii, const uint64_t* offsets, uint64_t n_reads) {
+    Oracle* o = (Oracle*)h;
+    if (!o || sample < 0 || sample >= o->n_samples || (!ascii && n_reads) || !offsets) return -1;
+    if (o->restrict_bits == 0 && o->bloom.empty()) o->bloom.assign(o->bloom_bits / 64, 0ull);
+    for (uint64_t r = 0; r < n_reads; ++r) {
+        if (offsets[r + 1] < offsets[r]) return -2;
+        o->add_read(sample, ascii + offsets[r], offsets[r + 1] - offsets[r]);
+    }
+    return 0;
+}
+
+uint64_t orc_windows(void* h) { return ((Oracle*)h)->windows; }
+uint64_t orc_counted(void* h) { return ((Oracle*)h)->counted; }
+uint64_t orc_distinct(void* h) { return ((Oracle*)h)->counts.size(); }
+
+// Number of keys in the result (count summed over samples >= min_count).
+uint64_t orc_result_size(void* h) { return ((Oracle*)h)->result_keys().size(); }
+
+// Write the result in ascending key order: keys[i], counts[i*n_samples + s].
+int64_t orc_result(void* h, uint64_t* keys, uint32_t* counts, uint64_t capacity) {
+    Oracle* o = (Oracle*)h;
+    std::vector<uint64_t> ks = o->result_keys();
+    if (ks.size() > capacity) return -1;
+    for (size_t i = 0; i < ks.size(); ++i) {
+        keys[i] = ks[i];
+        const auto& c = o->counts.at(ks[i]);
+        for (int s = 0; s < o->n_samples; ++s) counts[i * o->n_samples + s] = c[s];
+    }
+    return (int64_t)ks.size();
+}
+
+// Copy Bloom words [first, first + n) (words never set read as 0).
+int orc_bloom(void* h, uint64_t* out, uint64_t first, uint64_t n) {
+    Oracle* o = (Oracle*)h;
+    uint64_t nw = o->bloom_bits / 64;
+    if (first > nw || n > nw - first) return -1;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (o->restrict_bits == 0) {
+            out[i] = o->bloom.empty() ? 0 : o->bloom[first + i];
+        } else {
+            auto it = o->bloom_words.find(first + i);
+            out[i] = it == o->bloom_words.end() ? 0 : it->second;
+        }
+    }
+    return 0;
+}
+
+// 1 if every bit of key's pattern is set in its word (membership query).
+int orc_bloom_query(void* h, uint64_t key) {
+    Oracle* o = (Oracle*)h;
+    uint64_t w = o->word_of(key), p = o->pattern_of(key);
+    uint64_t word = 0;
+    if (o->restrict_bits == 0) {
+        word = o->bloom.empty() ? 0 : o->bloom[w];
+    } else {
+        auto it = o->bloom_words.find(w);
+        word = it == o->bloom_words.end() ? 0 : it->second;
+    }
+    return (word & p) == p ? 1 : 0;
+}
+
+uint64_t orc_bloom_word_index(void* h, uint64_t key) { return ((Oracle*)h)->word_of(key); }
+uint64_t orc_bloom_pattern(void* h, uint64_t key) { return ((Oracle*)h)->pattern_of(key); }
+uint64_t orc_mixer64(uint64_t x) { return mixer64(x); }
+
+// Canonical key of the k characters at s, or ~0 if any is not A/C/G/T.
+uint64_t orc_canonical(const char* s, int k) {
+    for (int t = 0; t < k; ++t)
+        if (base_code(s[t]) < 0) return ~0ull;
+    std::vector<char> rc((size_t)k);
+    for (int t = 0; t < k; ++t) rc[t] = complement_base(s[k - 1 - t]);
+    return std::min(encode(s, k), encode(rc.data(), k));
+}
+
+void orc_destroy(void* h) { delete (Oracle*)h; }
+
+}  // extern "C"
