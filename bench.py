@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""Benchmark: canonical k-mers counted per second on one GB300 (plain path).
+
+A step is one whole counting job on the "mid" workload: a 5 Mbp i.i.d.
+uniform genome sequenced at 30x as 1,000,000 x 150 bp reads from both strands
+with 0.5 % substitutions and 0.05 % N; k = 31, a 2^30-bit filter with 4 bits
+per key, a 2^24-slot table, min_count 2.  The step is reset (filter and table
+zeroed), ingest, pass 1 (filter + candidate claims), finalize (exact recount,
+compaction, sort) and dump.  The unit of work is one valid window (an N-free
+k-window inside one read).
+
+  value  device-resident inputs, CUDA events on the library's stream
+  e2e    the same step through the C ABI from pinned host buffers, the host to
+         device copy of the reads and the device to host copy of the result
+         inside the timed region (wall clock)
+
+With N ranks (torchrun) every rank counts its own job (independent read set),
+no collective is on the data path, and value = all ranks' windows / the
+slowest rank's time ("weak" scaling).
+
+--impl reference times the CPU oracle (single thread, as it stands) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "canonical k-mers counted/s per GB300 (plain vs batched/served); p99 job latency"
+UNIT = "k-mers/s"
+WORKLOAD = ("mid: 5 Mbp uniform ACGT genome, 1,000,000 x 150 bp reads from both strands (30x), "
+            "0.5% substitutions, 0.05% N; k=31 canonical uint64 keys, Bloom 2^30 bits with 4 hashes, "
+            "2^24-slot open-addressing table, exact uint32 counts of k-mers seen >= 2 times")
+MID_SEED = 2
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ---------------------------------------------------------------- distributed
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def shard_seed(rank: int) -> int:
+    """Seed of the read set counted by a rank (rank 0: the canonical workload)."""
+    return MID_SEED + 7919 * rank
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(x: float, dist, device) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, dist, device) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+
+
+def _smi_id(local: int) -> str:
+    """nvidia-smi id of CUDA device `local` (its UUID, robust to CUDA_VISIBLE_DEVICES)."""
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:  # older torch without the uuid property
+        return str(local)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [l.strip().split(",") for l in self.out if l.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- roofline
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1712_03254_gb300", "csrc")
+    for f in ("kc_device.cuh", "kc_kernels.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != _kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- workloads
+
+
+def make_inputs(rank: int):
+    import synth
+
+    w = synth.mid(seed=shard_seed(rank))
+    return w
+
+
+def oracle_rate(w, n_reads: int):
+    """Windows/s of the oracle on the first n_reads reads (single thread)."""
+    import oracle
+
+    rs = w.samples[0].slice(0, n_reads)
+    o = oracle.Oracle(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count)
+    t = time.perf_counter()
+    o.add_reads(0, rs)
+    o.result()
+    dt = time.perf_counter() - t
+    return o.windows, dt
+
+
+def pick_sample_reads(w, seconds: float) -> int:
+    win, dt = oracle_rate(w, 5000)
+    per_read = max(1.0, win / 5000.0)
+    rate = win / max(dt, 1e-6)
+    return int(max(5000, min(w.samples[0].n_reads, seconds * rate / per_read)))
+
+
+# ---------------------------------------------------------------- kc arm
+
+
+def run_kc(args):
+    import numpy as np
+    import torch
+
+    import paper_1712_03254_gb300 as kc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    stream = torch.cuda.current_stream()
+
+    w = make_inputs(rank)
+    rs = w.samples[0]
+    packed, mask = kc.pack_ascii(rs.ascii)
+    offsets = np.ascontiguousarray(rs.offsets, dtype=np.uint64)
+    # pinned host copies (e2e) and device-resident copies (value)
+    h_packed = torch.from_numpy(packed.view(np.int64)).pin_memory()
+    h_mask = torch.from_numpy(mask.view(np.int64)).pin_memory()
+    h_off = torch.from_numpy(offsets.view(np.int64)).pin_memory()
+    d_packed = h_packed.to(dev)
+    d_mask = h_mask.to(dev)
+    d_off = h_off.to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots, timing=True,
+                       stream=stream)
+
+    # size result buffers with one untimed job
+    c.add_reads(0, d_packed, d_off, d_mask)
+    c.finalize()
+    n_res = c.result_size()
+    d_keys = torch.empty(n_res, dtype=torch.int64, device=dev)
+    d_counts = torch.empty((n_res, 1), dtype=torch.int32, device=dev)
+    h_keys = torch.empty(n_res, dtype=torch.int64).pin_memory()
+    h_counts = torch.empty((n_res, 1), dtype=torch.int32).pin_memory()
+
+    def job(p, o, m, keys, counts):
+        c.reset()
+        c.add_reads(0, p, o, m)
+        c.finalize()
+        c.dump(keys, counts)
+
+    # warm-up
+    for _ in range(args.warmup):
+        job(d_packed, d_off, d_mask, d_keys, d_counts)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(_smi_id(local))
+    clocks.start()
+    time.sleep(0.3)
+    phases = {"ingest": [], "pass1": [], "pass2": [], "compact": [], "sort": []}
+    launches = 0
+    windows = None
+    step_ms = []
+    barrier(dist)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()  # write 256 MiB between steps: the next step starts with a cold L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        job(d_packed, d_off, d_mask, d_keys, d_counts)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = c.stats()
+        for k in phases:
+            phases[k].append(st["ms_" + k])
+        launches += st["launches"]
+        windows = st["windows"]
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+
+    total_ms = sum(step_ms)
+    max_total_ms = reduce_max(total_ms, dist, dev)
+    all_windows = reduce_sum(float(windows * args.steps), dist, dev)
+    value = all_windows / (max_total_ms / 1e3)
+
+    # e2e: pinned host inputs and outputs through the C ABI, wall clock
+    h2d = int(h_packed.numel() * 8 + h_mask.numel() * 8 + h_off.numel() * 8)
+    d2h = int(n_res * 8 + n_res * 4)
+    for _ in range(max(1, args.warmup)):
+        job(h_packed, h_off, h_mask, h_keys, h_counts)
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        job(h_packed, h_off, h_mask, h_keys, h_counts)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = reduce_max(e2e_s, dist, dev)
+    e2e_value = all_windows / e2e_s
+    # the e2e result must be the device result
+    assert np.array_equal(h_keys.numpy(), d_keys.cpu().numpy()), "e2e and device dumps differ"
+
+    # roofline of the dominant kernel (per-launch means over the timed steps)
+    st = c.stats()
+    read_bytes = (2 * (rs.n_bases + 63) // 64 + 2) * 8 + ((rs.n_bases + 63) // 64) * 8  # packed + valid bits
+    bloom_bytes = w.bloom_bits // 8
+    claimed = st["table_keys"]
+    algo = {
+        "k_pass1": read_bytes + 2 * bloom_bytes + 2 * 16 * claimed,
+        "k_pass2": read_bytes + 2 * 16 * claimed,
+    }
+    mean = {k: statistics.mean(v) for k, v in phases.items()}
+    dom = "k_pass1" if mean["pass1"] >= mean["pass2"] else "k_pass2"
+    dom_ms = mean["pass1"] if dom == "k_pass1" else mean["pass2"]
+    peak, peak_kind = measured_hbm_peak()
+    achieved = algo[dom] / (dom_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": ncu_traffic(dom), "algorithmic_bytes": int(algo[dom]),
+                "ms_per_launch": round(dom_ms, 4)}
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s = pick_sample_reads(w, args.cpu_seconds)
+        win, dt = oracle_rate(w, n_s)
+        cpu = {"value": round(win / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {n_s:,} of {rs.n_reads:,} reads of the mid workload ({win:,} windows, "
+                         f"{dt:.1f} s, single-threaded C++ oracle, {os.cpu_count()} host cores present)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(max_total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded genome and reads)",
+            "config": {"workload": WORKLOAD, "windows_per_job": windows, "result_keys": n_res,
+                       "l2": "256 MiB written between timed steps (outside the step events)",
+                       "parallelism": f"{world} independent jobs, one per GPU" if world > 1 else "1 GPU"},
+            "phase_ms": {k: round(v, 4) for k, v in mean.items()},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3 / args.steps, 4)},
+            "clocks": clk,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    c.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = make_inputs(0)
+    budget_s = 150.0
+    per_step = budget_s / max(1, args.steps + args.warmup)
+    n_s = pick_sample_reads(w, per_step)
+    for _ in range(args.warmup):
+        oracle_rate(w, n_s)
+    times, wins = [], 0
+    for _ in range(args.steps):
+        win, dt = oracle_rate(w, n_s)
+        times.append(dt)
+        wins = win
+    total = sum(times)
+    value = wins * args.steps / total
+    sample = (f"first {n_s:,} of {w.samples[0].n_reads:,} reads of the mid workload per step ({wins:,} windows), "
+              f"single-threaded C++ oracle, {os.cpu_count()} host cores present")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded genome and reads)", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["kc", "reference"], default="kc")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_kc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * kc.h -- C ABI of libkc, a GB300 (sm_103a) k-mer frequency counter.
+ *
+ * The library counts canonical k-mers of DNA reads per sample, drops k-mers
+ * seen only once with a Bloom filter, and returns the exact counts of the
+ * survivors in ascending key order.  This is the counting step of the
+ * reference-free variant caller described in "Accelerating K-mer Frequency
+ * Counting with GPU and Non-Volatile Memory" (Cadenelli, Polo, Carrera):
+ *   - k-mers of a read: its M-k+1 substrings of length k (Section II-A);
+ *   - 2-bit, 64-bit encoding of a k-mer (Section II-A);
+ *   - singleton removal through a Bloom filter that answers "seen before"
+ *     (Section III, Prune unit), exact counts per sample (Section II-B, Count
+ *     unit; Section III-D, 16-byte k-mer items), false positives removed
+ *     before output (Section III, Unify unit).
+ *
+ * Definitions used throughout (the exact result; readings of the paper that
+ * it leaves open are marked "library"):
+ *   base codes      A=0 C=1 G=2 T=3; a window over any other character is
+ *                   skipped (library reading of the reads' quality check).
+ *   key             min(forward, reverse complement), each the 2k-bit number
+ *                   whose most significant 2 bits are the window's first base
+ *                   (library: canonical keys), so 1 <= k <= 31 fits a uint64.
+ *   result          keys whose count summed over samples is >= min_count,
+ *                   ascending, with one uint32 count per sample.
+ *   Bloom filter    bloom_bits / 64 words; key sets n_hashes bits of ONE word
+ *                   (library: word-blocked, so a single atomic decides whether
+ *                   a key was seen before):
+ *                     h = mixer64(key), g = mixer64(h)
+ *                     word = h >> (64 - log2(bloom_bits / 64))
+ *                     bit i = (g >> 6i) & 63, i < n_hashes
+ *                   mixer64 = SplitMix64 output function (Steele, Lea &
+ *                   Flood, OOPSLA 2014).
+ *
+ * Packed read format (what kc_add_reads consumes):
+ *   packed_reads  base i of the caller's base stream is bits
+ *                 [63-2(i%32) .. 62-2(i%32)] of packed_reads[i/32] (first base
+ *                 in the most significant bits).  An N base may hold any code.
+ *   n_mask        bit 63-(i%64) of n_mask[i/64] is 1 iff base i is unknown
+ *                 (any character other than A, C, G, T).
+ *   offsets       n_reads+1 non-decreasing base indices; read r covers bases
+ *                 [offsets[r], offsets[r+1]).  offsets[0] may be > 0; only the
+ *                 words that cover [offsets[0], offsets[n_reads]) are read.
+ *
+ * Pointers: every array argument may be host memory (pageable or pinned) or
+ * device memory of the handle's device; the library detects which.  The caller
+ * owns its arrays; the library owns the filter, the table, its copy of the
+ * reads and the result.  All functions return a kc_status; none aborts, exits
+ * or traps.  After an error the handle stays valid; if device state may be
+ * inconsistent it is poisoned and every later call except kc_destroy,
+ * kc_reset and kc_last_error returns KC_ERR_STATE.
+ *
+ * Threading: a handle is used by one thread at a time.  kc_last_error is
+ * per thread.
+ */
+#ifndef KC_H
+#define KC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kc_ctx* kc_handle;
+
+typedef enum kc_status {
+    KC_OK = 0,
+    KC_ERR_ARG = 1,        /* invalid argument (range, format, offsets)          */
+    KC_ERR_STATE = 2,      /* call not allowed now, or handle poisoned           */
+    KC_ERR_OOM_DEVICE = 3, /* device allocation failed                          */
+    KC_ERR_OOM_HOST = 4,   /* host allocation failed                            */
+    KC_ERR_CUDA = 5,       /* CUDA runtime error (message in kc_last_error)      */
+    KC_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                      */
+    KC_ERR_CAPACITY = 7,   /* table full, count overflow or output too small     */
+    KC_ERR_INTERNAL = 8    /* library bug detected by a self-check               */
+} kc_status;
+
+/* Tuning and resource knobs; zero means "library default" everywhere. */
+typedef struct kc_config {
+    uint32_t struct_size;         /* sizeof(kc_config), for ABI growth             */
+    uint32_t block_threads;       /* threads per CTA of the streaming kernels       */
+    uint32_t ctas_per_sm;         /* resident CTAs per SM for grid sizing           */
+    uint32_t part_bits;           /* the table is processed as 2^part_bits hash-
+                                     prefix partitions, one after another          */
+    uint64_t table_slots;         /* open-addressing slots (power of two) of the
+                                     table for one partition                        */
+    uint32_t spill;               /* 1: each finished partition's result is copied
+                                     to pinned host memory on a side stream         */
+    uint32_t timing;              /* 1: record CUDA events around every phase on
+                                     the handle's stream (see kc_stats.ms_*)        */
+    uint64_t reserved[6];
+} kc_config;
+
+/* Counters of one job (valid after kc_finalize unless noted). */
+typedef struct kc_stats {
+    uint64_t windows;         /* valid windows added so far, all samples         */
+    uint64_t bases;           /* bases added so far                              */
+    uint64_t candidates;      /* windows the filter reported as seen before      */
+    uint64_t table_keys;      /* distinct keys held in the table (all partitions) */
+    uint64_t result_keys;     /* keys in the result                              */
+    uint64_t spilled_bytes;   /* result bytes copied to pinned host memory       */
+    uint32_t partitions;      /* hash-prefix partitions used                     */
+    uint32_t table_log2;      /* log2 of table slots per partition               */
+    uint64_t device_bytes;    /* device memory held by the handle                */
+    uint64_t launches;        /* kernels launched since create / reset           */
+    /* Device time per phase since create / reset, from CUDA events on the
+     * handle's stream (zero unless kc_config.timing = 1; complete after
+     * kc_finalize): ingest = read-start and valid-window bits; pass1 = filter
+     * update and candidate claims; pass2 = exact recount; compact = survivor
+     * compaction; sort = bucketing and bucket sorts. */
+    double ms_ingest, ms_pass1, ms_pass2, ms_compact, ms_sort;
+} kc_stats;
+
+/* Fill *cfg with the defaults (struct_size set). */
+void kc_default_config(kc_config* cfg);
+
+/*
+ * Create a counting job on the current CUDA device.
+ *   k          window length, 1..31
+ *   n_samples  1 or 2 (2: joint normal/tumour table, Section III-D layout of
+ *              one key with two counts)
+ *   bloom_bits power of two, >= 4096
+ *   n_hashes   bits per key in its filter word, 1..10
+ *   min_count  keys whose count summed over samples is below this are dropped
+ *              (2 drops the k-mers seen only once; 1 keeps every key)
+ * Returns KC_ERR_ARG on out-of-range arguments.
+ */
+kc_status kc_create(int k, int n_samples, uint64_t bloom_bits, int n_hashes, uint32_t min_count,
+                    kc_handle* out);
+
+/*
+ * As kc_create, with tuning knobs (cfg may be NULL) and a CUDA stream
+ * (a cudaStream_t passed as void*; NULL = the library creates its own) on
+ * which every device operation of the handle is ordered.
+ */
+kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, uint32_t min_count,
+                       const kc_config* cfg, void* stream, kc_handle* out);
+
+/*
+ * Add n_reads reads of one sample (0 <= sample < n_samples) in the packed
+ * format above.  The library copies what it needs before returning, so the
+ * caller may reuse its arrays at once; device work continues asynchronously
+ * on the handle's stream.  Reads shorter than k add no windows.  Offsets that
+ * decrease give KC_ERR_ARG (checked on the host for host offsets, on the
+ * device for device offsets, where the error surfaces at kc_finalize).
+ * Not allowed after kc_finalize (KC_ERR_STATE).
+ */
+kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, const uint64_t* offsets,
+                       const uint64_t* n_mask, uint64_t n_reads);
+
+/* Finish the job: exact recount, singleton and false-positive removal, sort.
+ * Blocks until the result is ready on the device. */
+kc_status kc_finalize(kc_handle h);
+
+/*
+ * Copy the result: keys[i] ascending, counts[i * n_samples + s].  With
+ * keys == NULL only *n_out is written (size query).  capacity is in keys;
+ * a smaller capacity than the result gives KC_ERR_CAPACITY and *n_out = size.
+ */
+kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capacity, uint64_t* n_out);
+
+/* Copy filter words [first_word, first_word + n_words) (for parity checks and
+ * checkpoints).  Allowed at any time; blocks until pending work is done. */
+kc_status kc_export_bloom(kc_handle h, uint64_t* words, uint64_t first_word, uint64_t n_words);
+
+kc_status kc_stats_get(kc_handle h, kc_stats* out);
+
+/* Forget all reads and results but keep the allocations, for a new job with
+ * the same parameters. */
+kc_status kc_reset(kc_handle h);
+
+void kc_destroy(kc_handle h);
+
+/* Message of the last error on this thread ("" if none). */
+const char* kc_last_error(void);
+
+/* Name of a status code. */
+const char* kc_status_string(kc_status s);
+
+/*
+ * Host helper: pack n_bases ASCII characters into the packed format above
+ * (packed: ceil(n_bases/32) words, n_mask: ceil(n_bases/64) words, both
+ * written in full, unused tail bits zero).  Any byte other than 'A','C','G','T'
+ * is an unknown base.
+ */
+kc_status kc_pack_ascii(const char* ascii, uint64_t n_bases, uint64_t* packed, uint64_t* n_mask);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KC_H */

@@ -62,6 +62,8 @@ def _load():
         lib.orc_bloom_pattern.restype = u64
         lib.orc_mixer64.argtypes = [u64]
         lib.orc_mixer64.restype = u64
+        lib.orc_partitions.argtypes = [p, u64, i, p]
+        lib.orc_partitions.restype = i
         lib.orc_canonical.argtypes = [ctypes.c_char_p, i]
         lib.orc_canonical.restype = u64
         lib.orc_destroy.argtypes = [p]
@@ -72,6 +74,16 @@ def _load():
 
 def mixer64(x: int) -> int:
     return int(_load().orc_mixer64(x))
+
+
+def partitions(keys: np.ndarray, q: int) -> np.ndarray:
+    """Top q bits of mixer64(key) for every key (which partition a key is in)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    out = np.empty(keys.size, dtype=np.uint32)
+    if _load().orc_partitions(keys.ctypes.data if keys.size else None, keys.size, q,
+                              out.ctypes.data if keys.size else None) != 0:
+        raise ValueError("oracle: partitions")
+    return out
 
 
 def canonical(s: str) -> int | None:

@@ -266,6 +266,13 @@ uint64_t orc_bloom_word_index(void* h, uint64_t key) { return ((Oracle*)h)->word
 uint64_t orc_bloom_pattern(void* h, uint64_t key) { return ((Oracle*)h)->pattern_of(key); }
 uint64_t orc_mixer64(uint64_t x) { return mixer64(x); }
 
+// Partition (top q bits of mixer64) of each of n keys, for restricted comparisons.
+int orc_partitions(const uint64_t* keys, uint64_t n, int q, uint32_t* out) {
+    if (q < 1 || q > 24 || (!keys && n) || (!out && n)) return -1;
+    for (uint64_t i = 0; i < n; ++i) out[i] = (uint32_t)(mixer64(keys[i]) >> (64 - q));
+    return 0;
+}
+
 // Canonical key of the k characters at s, or ~0 if any is not A/C/G/T.
 uint64_t orc_canonical(const char* s, int k) {
     for (int t = 0; t < k; ++t)

@@ -1,0 +1,209 @@
+"""GB300 k-mer frequency counting: Python binding of libkc (include/kc.h).
+
+The binding only marshals arguments: every step of the counting path runs in
+the library's CUDA kernels.  There is no CPU fallback; if libkc.so is missing
+and cannot be built, loading fails with an error.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); the
+library detects where each pointer lives.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["KmerCounter", "KcError", "pack_ascii", "lib", "build", "Config", "Stats"]
+
+_lock = threading.Lock()
+_lib = None
+
+STATUS = ["KC_OK", "KC_ERR_ARG", "KC_ERR_STATE", "KC_ERR_OOM_DEVICE", "KC_ERR_OOM_HOST", "KC_ERR_CUDA",
+          "KC_ERR_TIMEOUT", "KC_ERR_CAPACITY", "KC_ERR_INTERNAL"]
+
+
+class KcError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        self.name = STATUS[status] if 0 <= status < len(STATUS) else f"status {status}"
+        super().__init__(f"{where}: {self.name}: {message}")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("part_bits", ctypes.c_uint32),
+                ("table_slots", ctypes.c_uint64), ("spill", ctypes.c_uint32), ("timing", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint64 * 6)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("windows", ctypes.c_uint64), ("bases", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
+                ("table_keys", ctypes.c_uint64), ("result_keys", ctypes.c_uint64),
+                ("spilled_bytes", ctypes.c_uint64), ("partitions", ctypes.c_uint32),
+                ("table_log2", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("ms_ingest", ctypes.c_double), ("ms_pass1", ctypes.c_double), ("ms_pass2", ctypes.c_double),
+                ("ms_compact", ctypes.c_double), ("ms_sort", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def lib():
+    """Load libkc.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            p, u64, u32, i, st = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int
+            L.kc_default_config.argtypes = [ctypes.POINTER(Config)]
+            L.kc_default_config.restype = None
+            L.kc_create.argtypes = [i, i, u64, i, u32, ctypes.POINTER(p)]
+            L.kc_create.restype = st
+            L.kc_create_ex.argtypes = [i, i, u64, i, u32, ctypes.POINTER(Config), p, ctypes.POINTER(p)]
+            L.kc_create_ex.restype = st
+            L.kc_add_reads.argtypes = [p, i, p, p, p, u64]
+            L.kc_add_reads.restype = st
+            L.kc_finalize.argtypes = [p]
+            L.kc_finalize.restype = st
+            L.kc_dump.argtypes = [p, p, p, u64, ctypes.POINTER(u64)]
+            L.kc_dump.restype = st
+            L.kc_export_bloom.argtypes = [p, p, u64, u64]
+            L.kc_export_bloom.restype = st
+            L.kc_stats_get.argtypes = [p, ctypes.POINTER(Stats)]
+            L.kc_stats_get.restype = st
+            L.kc_reset.argtypes = [p]
+            L.kc_reset.restype = st
+            L.kc_destroy.argtypes = [p]
+            L.kc_destroy.restype = None
+            L.kc_last_error.argtypes = []
+            L.kc_last_error.restype = ctypes.c_char_p
+            L.kc_status_string.argtypes = [st]
+            L.kc_status_string.restype = ctypes.c_char_p
+            L.kc_pack_ascii.argtypes = [p, u64, p, p]
+            L.kc_pack_ascii.restype = st
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise KcError(status, where, lib().kc_last_error().decode(errors="replace"))
+
+
+def _ptr(a) -> int | None:
+    """Raw pointer of a numpy array or torch tensor (None for None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def pack_ascii(ascii: np.ndarray):
+    """Pack ASCII bases into (packed words, N-mask words) on the host."""
+    ascii = np.ascontiguousarray(ascii, dtype=np.uint8)
+    n = ascii.size
+    packed = np.zeros((n + 31) // 32, dtype=np.uint64)
+    mask = np.zeros((n + 63) // 64, dtype=np.uint64)
+    if n:
+        _check(lib().kc_pack_ascii(ascii.ctypes.data, n, packed.ctypes.data, mask.ctypes.data), "kc_pack_ascii")
+    return packed, mask
+
+
+class KmerCounter:
+    """One counting job: add reads per sample, finalize, dump sorted counts."""
+
+    def __init__(self, k: int, n_samples: int, bloom_bits: int, n_hashes: int = 4, min_count: int = 2,
+                 table_slots: int = 0, part_bits: int = 0, spill: bool = False, ctas_per_sm: int = 0,
+                 timing: bool = False, stream=None):
+        L = lib()
+        cfg = Config()
+        L.kc_default_config(ctypes.byref(cfg))
+        cfg.table_slots = table_slots
+        cfg.part_bits = part_bits
+        cfg.spill = 1 if spill else 0
+        cfg.ctas_per_sm = ctas_per_sm
+        cfg.timing = 1 if timing else 0
+        h = ctypes.c_void_p()
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        _check(L.kc_create_ex(k, n_samples, bloom_bits, n_hashes, min_count, ctypes.byref(cfg), stream,
+                              ctypes.byref(h)), "kc_create_ex")
+        self._h = h
+        self._L = L
+        self.k, self.n_samples, self.bloom_bits = k, n_samples, bloom_bits
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.kc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_reads(self, sample: int, packed, offsets, n_mask):
+        n_reads = (offsets.numel() if hasattr(offsets, "numel") else len(offsets)) - 1
+        _check(self._L.kc_add_reads(self._h, sample, _ptr(packed), _ptr(offsets), _ptr(n_mask), max(0, n_reads)),
+               "kc_add_reads")
+
+    def add_readset(self, sample: int, readset):
+        """Pack a synth.ReadSet-like object (ascii + offsets) on the host and add it."""
+        packed, mask = pack_ascii(readset.ascii)
+        self.add_reads(sample, packed, np.ascontiguousarray(readset.offsets, dtype=np.uint64), mask)
+
+    def finalize(self):
+        _check(self._L.kc_finalize(self._h), "kc_finalize")
+
+    def result_size(self) -> int:
+        n = ctypes.c_uint64()
+        _check(self._L.kc_dump(self._h, None, None, 0, ctypes.byref(n)), "kc_dump")
+        return n.value
+
+    def dump(self, keys=None, counts=None):
+        """Return (keys uint64[n], counts uint32[n, n_samples]) as numpy, or fill given buffers."""
+        n = self.result_size()
+        if keys is None:
+            keys = np.empty(n, dtype=np.uint64)
+            counts = np.empty((n, self.n_samples), dtype=np.uint32)
+        got = ctypes.c_uint64()
+        cap = keys.numel() if hasattr(keys, "numel") else len(keys)
+        _check(self._L.kc_dump(self._h, _ptr(keys), _ptr(counts), cap, ctypes.byref(got)), "kc_dump")
+        return keys[: got.value], counts[: got.value]
+
+    def export_bloom(self, first: int = 0, n: int | None = None, out=None):
+        nw = self.bloom_bits // 64
+        if n is None:
+            n = nw - first
+        if out is None:
+            out = np.empty(n, dtype=np.uint64)
+        _check(self._L.kc_export_bloom(self._h, _ptr(out), first, n), "kc_export_bloom")
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._L.kc_stats_get(self._h, ctypes.byref(s)), "kc_stats_get")
+        return s.as_dict()
+
+    def reset(self):
+        _check(self._L.kc_reset(self._h), "kc_reset")

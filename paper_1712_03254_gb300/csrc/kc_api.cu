@@ -1,0 +1,581 @@
+// C ABI of libkc: handle lifecycle, ingest, finalize, dump (see include/kc.h).
+//
+// Device memory of one job:
+//   filter       bloom_bits / 8 bytes, 64-bit words
+//   table        table_slots x 16-byte items (key + 1, two uint32 counts), the
+//                Count unit's k-mer layout of Section III-D without its padding
+//   read store   per kc_add_reads call: 2-bit packed words (padded to whole
+//                64-base units) and one valid-window-start bit per base, kept
+//                for the exact recount of kc_finalize
+//   result       sorted keys and per-sample counts after kc_finalize
+// Transient buffers (N mask, read starts, offsets, sort buckets) come from the
+// stream-ordered pool (cudaMallocAsync) and are released on the same stream.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/kc.h"
+#include "kc_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+kc_status fail(kc_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+kc_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? KC_ERR_OOM_DEVICE : KC_ERR_CUDA;
+}
+
+#define KC_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+int log2_exact(uint64_t x) {
+    int r = 0;
+    while ((1ull << r) < x) ++r;
+    return r;
+}
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Batch {
+    uint64_t* pw = nullptr;  // packed words, 2 * n_units + 2
+    uint64_t* vw = nullptr;  // valid-window-start words, n_units
+    uint64_t n_units = 0;
+    int sample = 0;
+};
+
+enum class State { Open, Finalized, Poisoned };
+
+}  // namespace
+
+struct kc_ctx {
+    int k = 0, n_samples = 0, n_hashes = 0;
+    uint64_t bloom_bits = 0;
+    uint32_t min_count = 0;
+    kc_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev_copy = nullptr, ev_main = nullptr;
+    kc::Grid grid;
+    int log2_words = 0, log2_slots = 0;
+    uint64_t n_slots = 0;
+
+    uint64_t* bloom = nullptr;
+    kc::Slot* table = nullptr;
+    kc::DevCounters* ctr = nullptr;
+    std::vector<Batch> batches;
+    uint64_t bases = 0;
+
+    uint64_t* res_keys = nullptr;
+    uint64_t* res_vals = nullptr;
+    uint64_t n_result = 0;
+    uint64_t res_cap = 0;
+
+    kc::DevCounters host_ctr{};
+    State state = State::Open;
+    size_t fixed_bytes = 0;
+
+    // Phase timing (kc_config.timing): event pairs recorded on the stream,
+    // turned into milliseconds after the next synchronisation.
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<Mark> marks;
+    double ms[5] = {0, 0, 0, 0, 0};
+    uint64_t launches = 0;
+
+    kc::PassParams params(int sample) const {
+        kc::PassParams p{};
+        p.k = k;
+        p.rc_shift = 64 - 2 * k;
+        p.kmask = (1ull << (2 * k)) - 1ull;
+        p.bloom_shift = 64 - log2_words;
+        p.n_hashes = n_hashes;
+        p.table_shift = 64 - log2_slots;
+        p.table_mask = n_slots - 1;
+        p.all_candidates = min_count <= 1 ? 1 : 0;
+        p.sample = sample;
+        return p;
+    }
+};
+
+namespace {
+
+enum Phase { kIngest = 0, kPass1 = 1, kPass2 = 2, kCompact = 3, kSort = 4 };
+
+cudaEvent_t phase_begin(kc_handle h) {
+    if (!h->cfg.timing) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (!h->ev_pool.empty()) {
+        e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaEventRecord(e, h->stream);
+    return e;
+}
+
+void phase_end(kc_handle h, int phase, cudaEvent_t a) {
+    if (!a) return;
+    cudaEvent_t b = phase_begin(h);
+    if (!b) {
+        h->ev_pool.push_back(a);
+        return;
+    }
+    h->marks.push_back({phase, a, b});
+}
+
+// Call after the stream has been synchronised.
+void phase_collect(kc_handle h) {
+    for (const auto& m : h->marks) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) h->ms[m.phase] += t;
+        else cudaGetLastError();
+        h->ev_pool.push_back(m.a);
+        h->ev_pool.push_back(m.b);
+    }
+    h->marks.clear();
+}
+
+kc_status check_open(kc_handle h) {
+    if (!h) return fail(KC_ERR_ARG, "null handle");
+    if (h->state == State::Poisoned) return fail(KC_ERR_STATE, "handle poisoned by an earlier error; call kc_reset");
+    return KC_OK;
+}
+
+void free_batches(kc_handle h) {
+    for (auto& b : h->batches) {
+        cudaFreeAsync(b.pw, h->stream);
+        cudaFreeAsync(b.vw, h->stream);
+    }
+    h->batches.clear();
+}
+
+void free_result(kc_handle h) {
+    if (h->res_keys) cudaFreeAsync(h->res_keys, h->stream);
+    if (h->res_vals) cudaFreeAsync(h->res_vals, h->stream);
+    h->res_keys = h->res_vals = nullptr;
+    h->n_result = h->res_cap = 0;
+}
+
+kc_status read_counters(kc_handle h) {
+    KC_CUDA(cudaMemcpyAsync(&h->host_ctr, h->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, h->stream));
+    KC_CUDA(cudaStreamSynchronize(h->stream));
+    return KC_OK;
+}
+
+kc_status device_errors(kc_handle h) {
+    const unsigned e = h->host_ctr.err;
+    if (e & kc::DERR_OFFSETS) {
+        h->state = State::Poisoned;
+        return fail(KC_ERR_ARG, "read offsets decrease");
+    }
+    if (e & kc::DERR_TABLE_FULL) {
+        h->state = State::Poisoned;
+        return fail(KC_ERR_CAPACITY, "counting table full: raise kc_config.table_slots");
+    }
+    if (e & kc::DERR_COUNT_OVERFLOW) {
+        h->state = State::Poisoned;
+        return fail(KC_ERR_CAPACITY, "a per-sample count exceeded 2^32-1");
+    }
+    return KC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void kc_default_config(kc_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->struct_size = sizeof(kc_config);
+}
+
+const char* kc_last_error(void) { return g_last_error.c_str(); }
+
+const char* kc_status_string(kc_status s) {
+    switch (s) {
+        case KC_OK: return "KC_OK";
+        case KC_ERR_ARG: return "KC_ERR_ARG";
+        case KC_ERR_STATE: return "KC_ERR_STATE";
+        case KC_ERR_OOM_DEVICE: return "KC_ERR_OOM_DEVICE";
+        case KC_ERR_OOM_HOST: return "KC_ERR_OOM_HOST";
+        case KC_ERR_CUDA: return "KC_ERR_CUDA";
+        case KC_ERR_TIMEOUT: return "KC_ERR_TIMEOUT";
+        case KC_ERR_CAPACITY: return "KC_ERR_CAPACITY";
+        case KC_ERR_INTERNAL: return "KC_ERR_INTERNAL";
+    }
+    return "KC_ERR_UNKNOWN";
+}
+
+kc_status kc_create(int k, int n_samples, uint64_t bloom_bits, int n_hashes, uint32_t min_count, kc_handle* out) {
+    return kc_create_ex(k, n_samples, bloom_bits, n_hashes, min_count, nullptr, nullptr, out);
+}
+
+kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, uint32_t min_count,
+                       const kc_config* cfg, void* stream, kc_handle* out) {
+    g_last_error.clear();
+    if (!out) return fail(KC_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (k < 1 || k > 31) return fail(KC_ERR_ARG, "k must be in 1..31");
+    if (n_samples < 1 || n_samples > 2) return fail(KC_ERR_ARG, "n_samples must be 1 or 2");
+    if (!is_pow2(bloom_bits) || bloom_bits < 4096) return fail(KC_ERR_ARG, "bloom_bits must be a power of two >= 4096");
+    if (n_hashes < 1 || n_hashes > 10) return fail(KC_ERR_ARG, "n_hashes must be in 1..10");
+    if (min_count < 1) return fail(KC_ERR_ARG, "min_count must be >= 1");
+    kc_config c;
+    kc_default_config(&c);
+    if (cfg) {
+        if (cfg->struct_size < offsetof(kc_config, timing)) return fail(KC_ERR_ARG, "kc_config.struct_size");
+        std::memcpy(&c, cfg, std::min<size_t>(cfg->struct_size, sizeof(c)));
+        c.struct_size = sizeof(c);
+    }
+    uint64_t slots = c.table_slots ? c.table_slots : std::max<uint64_t>(1ull << 12, bloom_bits / 32);
+    if (!is_pow2(slots) || slots < 1024) return fail(KC_ERR_ARG, "table_slots must be a power of two >= 1024");
+    if (c.block_threads && c.block_threads != 256) return fail(KC_ERR_ARG, "block_threads must be 256");
+
+    kc_ctx* h = new (std::nothrow) kc_ctx();
+    if (!h) return fail(KC_ERR_OOM_HOST, "host allocation");
+    h->k = k;
+    h->n_samples = n_samples;
+    h->bloom_bits = bloom_bits;
+    h->n_hashes = n_hashes;
+    h->min_count = min_count;
+    h->cfg = c;
+    h->log2_words = log2_exact(bloom_bits / 64);
+    h->n_slots = slots;
+    h->log2_slots = log2_exact(slots);
+
+    auto bail = [&](kc_status s) {
+        kc_destroy(h);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->grid.sm_count = sms > 0 ? sms : 152;
+    h->grid.ctas_per_sm = c.ctas_per_sm ? (int)c.ctas_per_sm : 8;
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+        h->own_stream = true;
+    }
+    if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(cuda_fail(e, "stream/event create"));
+    const size_t bloom_bytes = bloom_bits / 8, table_bytes = slots * sizeof(kc::Slot);
+    if ((e = cudaMalloc(&h->bloom, bloom_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(filter)"));
+    if ((e = cudaMalloc(&h->table, table_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(table)"));
+    if ((e = cudaMalloc(&h->ctr, sizeof(kc::DevCounters))) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMalloc(counters)"));
+    h->fixed_bytes = bloom_bytes + table_bytes + sizeof(kc::DevCounters);
+    kc_status s = kc_reset(h);
+    if (s != KC_OK) return bail(s);
+    *out = h;
+    return KC_OK;
+}
+
+kc_status kc_reset(kc_handle h) {
+    if (!h) return fail(KC_ERR_ARG, "null handle");
+    free_batches(h);
+    free_result(h);
+    KC_CUDA(cudaMemsetAsync(h->bloom, 0, h->bloom_bits / 8, h->stream));
+    KC_CUDA(cudaMemsetAsync(h->table, 0, h->n_slots * sizeof(kc::Slot), h->stream));
+    KC_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(kc::DevCounters), h->stream));
+    h->bases = 0;
+    std::memset(&h->host_ctr, 0, sizeof(h->host_ctr));
+    for (const auto& m : h->marks) {
+        h->ev_pool.push_back(m.a);
+        h->ev_pool.push_back(m.b);
+    }
+    h->marks.clear();
+    for (double& x : h->ms) x = 0.0;
+    h->launches = 0;
+    h->state = State::Open;
+    return KC_OK;
+}
+
+void kc_destroy(kc_handle h) {
+    if (!h) return;
+    if (h->stream) {
+        free_batches(h);
+        free_result(h);
+        cudaStreamSynchronize(h->stream);
+    }
+    if (h->bloom) cudaFree(h->bloom);
+    if (h->table) cudaFree(h->table);
+    if (h->ctr) cudaFree(h->ctr);
+    for (const auto& m : h->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->ev_copy) cudaEventDestroy(h->ev_copy);
+    if (h->ev_main) cudaEventDestroy(h->ev_main);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, const uint64_t* offsets,
+                       const uint64_t* n_mask, uint64_t n_reads) {
+    kc_status s = check_open(h);
+    if (s != KC_OK) return s;
+    if (h->state != State::Open) return fail(KC_ERR_STATE, "kc_add_reads after kc_finalize");
+    if (sample < 0 || sample >= h->n_samples) return fail(KC_ERR_ARG, "sample out of range");
+    if (n_reads == 0) return KC_OK;
+    if (!offsets) return fail(KC_ERR_ARG, "offsets is null");
+
+    const bool off_dev = is_device_ptr(offsets);
+    uint64_t b0, b1;
+    if (off_dev) {
+        uint64_t ends[2];
+        KC_CUDA(cudaMemcpyAsync(&ends[0], offsets, 8, cudaMemcpyDeviceToHost, h->stream));
+        KC_CUDA(cudaMemcpyAsync(&ends[1], offsets + n_reads, 8, cudaMemcpyDeviceToHost, h->stream));
+        KC_CUDA(cudaStreamSynchronize(h->stream));
+        b0 = ends[0];
+        b1 = ends[1];
+    } else {
+        for (uint64_t r = 0; r < n_reads; ++r)
+            if (offsets[r + 1] < offsets[r]) return fail(KC_ERR_ARG, "read offsets decrease");
+        b0 = offsets[0];
+        b1 = offsets[n_reads];
+    }
+    if (b1 < b0) return fail(KC_ERR_ARG, "read offsets decrease");
+    if (b1 == b0) return KC_OK;
+    if (!packed_reads || !n_mask) return fail(KC_ERR_ARG, "packed_reads or n_mask is null");
+
+    const uint64_t B = (b0 / 64) * 64;
+    const uint64_t n_local = b1 - B;
+    const uint64_t n_units = (n_local + 63) / 64;
+    const uint64_t n_pwords_src = (n_local + 31) / 32;
+    const uint64_t n_pwords = 2 * n_units + 2;
+    const bool data_dev = is_device_ptr(packed_reads);
+    const bool mask_dev = is_device_ptr(n_mask);
+
+    Batch b;
+    b.n_units = n_units;
+    b.sample = sample;
+    uint64_t *nm = nullptr, *bd = nullptr, *doff = nullptr;
+    cudaStream_t st = h->stream;
+    // Host inputs are copied on the copy stream (allocated there too), so the
+    // copy overlaps kernels already queued on the handle's stream; device
+    // inputs are copied on the handle's stream, after the work queued there.
+    const bool any_host = !(data_dev && mask_dev && off_dev);
+    cudaStream_t cs = any_host ? h->copy_stream : st;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&b.pw, n_pwords * 8, cs)) != cudaSuccess ||
+        (e = cudaMallocAsync(&b.vw, n_units * 8, cs)) != cudaSuccess ||
+        (e = cudaMallocAsync(&nm, n_units * 8, cs)) != cudaSuccess ||
+        (e = cudaMallocAsync(&bd, n_units * 8, cs)) != cudaSuccess ||
+        (e = cudaMallocAsync(&doff, (n_reads + 1) * 8, cs)) != cudaSuccess) {
+        cudaFreeAsync(b.pw, cs);
+        cudaFreeAsync(b.vw, cs);
+        cudaFreeAsync(nm, cs);
+        cudaFreeAsync(bd, cs);
+        cudaFreeAsync(doff, cs);
+        return cuda_fail(e, "cudaMallocAsync(read store)");
+    }
+    KC_CUDA(cudaMemcpyAsync(b.pw, packed_reads + B / 32, n_pwords_src * 8, cudaMemcpyDefault, cs));
+    KC_CUDA(cudaMemsetAsync(b.pw + n_pwords_src, 0, (n_pwords - n_pwords_src) * 8, cs));
+    KC_CUDA(cudaMemcpyAsync(nm, n_mask + B / 64, n_units * 8, cudaMemcpyDefault, cs));
+    KC_CUDA(cudaMemcpyAsync(doff, offsets, (n_reads + 1) * 8, cudaMemcpyDefault, cs));
+    if (any_host) {
+        KC_CUDA(cudaEventRecord(h->ev_copy, cs));
+        KC_CUDA(cudaStreamWaitEvent(st, h->ev_copy, 0));
+    }
+    cudaEvent_t t0 = phase_begin(h);
+    KC_CUDA(cudaMemsetAsync(bd, 0, n_units * 8, st));
+    kc::launch_mark_read_starts(doff, n_reads, B, n_local, bd, h->ctr, st);
+    kc::launch_build_valid(nm, bd, n_units, b0 - B, n_local, h->k, b.vw, h->ctr, h->grid, st);
+    phase_end(h, kIngest, t0);
+    t0 = phase_begin(h);
+    kc::launch_pass1(b.pw, b.vw, n_units, h->params(sample), h->bloom, h->table, h->ctr, h->grid, st);
+    phase_end(h, kPass1, t0);
+    h->launches += 3;
+    KC_CUDA(cudaGetLastError());
+    cudaFreeAsync(nm, st);
+    cudaFreeAsync(bd, st);
+    cudaFreeAsync(doff, st);
+    h->batches.push_back(b);
+    h->bases += b1 - b0;
+    if (any_host) KC_CUDA(cudaEventSynchronize(h->ev_copy));  // caller may reuse its arrays
+    return KC_OK;
+}
+
+kc_status kc_finalize(kc_handle h) {
+    kc_status s = check_open(h);
+    if (s != KC_OK) return s;
+    if (h->state == State::Finalized) return KC_OK;
+    cudaStream_t st = h->stream;
+    cudaEvent_t t0 = phase_begin(h);
+    for (const auto& b : h->batches)
+        kc::launch_pass2(b.pw, b.vw, b.n_units, h->params(b.sample), h->table, h->ctr, h->grid, st);
+    phase_end(h, kPass2, t0);
+    h->launches += h->batches.size();
+    KC_CUDA(cudaGetLastError());
+    if ((s = read_counters(h)) != KC_OK) return s;
+    if ((s = device_errors(h)) != KC_OK) return s;
+
+    // Sort buckets: top B bits of the 2k-bit key, about 512 survivors each.
+    const uint64_t cap = std::max<uint64_t>(1, h->host_ctr.claimed);
+    int bits = 0;
+    while (bits < 22 && bits < 2 * h->k && (cap >> bits) > 512) ++bits;
+    const uint64_t n_buckets = 1ull << bits;
+    const int prefix_shift = 2 * h->k - bits;
+
+    uint64_t *tk = nullptr, *tv = nullptr, *starts = nullptr, *cursor = nullptr;
+    uint32_t* hist = nullptr;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&tk, cap * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&tv, cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&hist, n_buckets * 4, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&starts, (n_buckets + 1) * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&cursor, n_buckets * 8, st)) != cudaSuccess) {
+        cudaFreeAsync(tk, st);
+        cudaFreeAsync(tv, st);
+        cudaFreeAsync(hist, st);
+        cudaFreeAsync(starts, st);
+        cudaFreeAsync(cursor, st);
+        free_result(h);
+        return cuda_fail(e, "cudaMallocAsync(sort buffers)");
+    }
+    h->res_cap = cap;
+    KC_CUDA(cudaMemsetAsync(hist, 0, n_buckets * 4, st));
+    KC_CUDA(cudaMemsetAsync(&h->ctr->survivors, 0, 8, st));
+    t0 = phase_begin(h);
+    kc::launch_compact(h->table, h->n_slots, h->n_samples, h->min_count, tk, tv, h->ctr, hist, prefix_shift, h->grid,
+                       st);
+    phase_end(h, kCompact, t0);
+    t0 = phase_begin(h);
+    kc::launch_scan(hist, n_buckets, starts, cursor, st);
+    kc::launch_scatter(tk, tv, h->ctr, prefix_shift, cursor, h->res_keys, h->res_vals, h->grid, st);
+    kc::launch_bucket_sort(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, st);
+    phase_end(h, kSort, t0);
+    h->launches += 4;
+    KC_CUDA(cudaGetLastError());
+    if ((s = read_counters(h)) != KC_OK) return s;
+    if (h->host_ctr.err & kc::DERR_SORT_BUCKET) {
+        // Rare: a bucket larger than the shared-memory tile; sort it in global memory.
+        std::vector<uint64_t> hs(n_buckets + 1);
+        KC_CUDA(cudaMemcpyAsync(hs.data(), starts, (n_buckets + 1) * 8, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        const uint64_t capb = (uint64_t)kc::bucket_sort_capacity();
+        for (uint64_t i = 0; i < n_buckets; ++i)
+            if (hs[i + 1] - hs[i] > capb) {
+                uint64_t n = hs[i + 1] - hs[i], n2 = 1, steps = 0;
+                while (n2 < n) n2 <<= 1;
+                for (uint64_t size = 2; size <= n2; size <<= 1)
+                    for (uint64_t stride = size >> 1; stride > 0; stride >>= 1) ++steps;
+                kc::launch_bitonic_global(h->res_keys + hs[i], h->res_vals + hs[i], n, st);
+                h->launches += steps;
+            }
+        unsigned zero = 0;
+        KC_CUDA(cudaMemcpyAsync(&h->ctr->err, &zero, 4, cudaMemcpyHostToDevice, st));
+        KC_CUDA(cudaGetLastError());
+    }
+    cudaFreeAsync(tk, st);
+    cudaFreeAsync(tv, st);
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(starts, st);
+    cudaFreeAsync(cursor, st);
+    KC_CUDA(cudaStreamSynchronize(st));
+    phase_collect(h);
+    h->n_result = h->host_ctr.survivors;
+    h->state = State::Finalized;
+    return KC_OK;
+}
+
+kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capacity, uint64_t* n_out) {
+    kc_status s = check_open(h);
+    if (s != KC_OK) return s;
+    if (h->state != State::Finalized) return fail(KC_ERR_STATE, "kc_dump before kc_finalize");
+    if (n_out) *n_out = h->n_result;
+    if (!keys) return KC_OK;
+    if (capacity < h->n_result) return fail(KC_ERR_CAPACITY, "dump capacity smaller than the result");
+    if (h->n_result == 0) return KC_OK;
+    cudaStream_t st = h->stream;
+    KC_CUDA(cudaMemcpyAsync(keys, h->res_keys, h->n_result * 8, cudaMemcpyDefault, st));
+    if (counts) {
+        if (h->n_samples == 2) {
+            KC_CUDA(cudaMemcpyAsync(counts, h->res_vals, h->n_result * 8, cudaMemcpyDefault, st));
+        } else {
+            uint32_t* narrow = nullptr;
+            KC_CUDA(cudaMallocAsync(&narrow, h->n_result * 4, st));
+            kc::launch_counts_narrow(h->res_vals, h->n_result, narrow, st);
+            h->launches += 1;
+            KC_CUDA(cudaMemcpyAsync(counts, narrow, h->n_result * 4, cudaMemcpyDefault, st));
+            cudaFreeAsync(narrow, st);
+        }
+    }
+    KC_CUDA(cudaStreamSynchronize(st));
+    return KC_OK;
+}
+
+kc_status kc_export_bloom(kc_handle h, uint64_t* words, uint64_t first_word, uint64_t n_words) {
+    if (!h) return fail(KC_ERR_ARG, "null handle");
+    const uint64_t nw = h->bloom_bits / 64;
+    if (!words || first_word > nw || n_words > nw - first_word) return fail(KC_ERR_ARG, "filter range");
+    KC_CUDA(cudaMemcpyAsync(words, h->bloom + first_word, n_words * 8, cudaMemcpyDefault, h->stream));
+    KC_CUDA(cudaStreamSynchronize(h->stream));
+    return KC_OK;
+}
+
+kc_status kc_stats_get(kc_handle h, kc_stats* out) {
+    if (!h || !out) return fail(KC_ERR_ARG, "null argument");
+    kc_status s = read_counters(h);
+    if (s != KC_OK) return s;
+    phase_collect(h);
+    std::memset(out, 0, sizeof(*out));
+    out->windows = h->host_ctr.windows;
+    out->bases = h->bases;
+    out->candidates = h->host_ctr.candidates;
+    out->table_keys = h->host_ctr.claimed;
+    out->result_keys = h->state == State::Finalized ? h->n_result : 0;
+    out->partitions = 1;
+    out->table_log2 = (uint32_t)h->log2_slots;
+    size_t bytes = h->fixed_bytes + h->res_cap * 16;
+    for (const auto& b : h->batches) bytes += (2 * b.n_units + 2) * 8 + b.n_units * 8;
+    out->device_bytes = bytes;
+    out->launches = h->launches;
+    out->ms_ingest = h->ms[kIngest];
+    out->ms_pass1 = h->ms[kPass1];
+    out->ms_pass2 = h->ms[kPass2];
+    out->ms_compact = h->ms[kCompact];
+    out->ms_sort = h->ms[kSort];
+    return KC_OK;
+}
+
+}  // extern "C"

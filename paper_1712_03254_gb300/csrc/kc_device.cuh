@@ -1,0 +1,156 @@
+// Device-side building blocks of the k-mer counting path (sm_103a).
+//
+// Reads are kept on the device as 2-bit codes, 32 bases per 64-bit word,
+// first base in the most significant bits, plus one "valid window start" bit
+// per base (V).  A window of k <= 31 bases starting inside a 64-base unit
+// never reaches past the first word of the next unit, so a lane that owns one
+// unit (two packed words, one V word) only needs the next lane's first word,
+// which it gets with a warp shuffle.
+#pragma once
+
+#include <cstdint>
+
+namespace kc {
+
+struct __align__(16) Slot {
+    unsigned long long key1;  // key + 1; 0 marks an empty slot
+    unsigned int cnt[2];      // per-sample counts (cnt[1] unused with one sample)
+};
+static_assert(sizeof(Slot) == 16, "a table item is 8 bytes of key and 8 of counts (Section III-D)");
+
+// Device-wide counters and error bits of one job.
+struct DevCounters {
+    unsigned long long windows;     // valid windows (V bits) of all batches
+    unsigned long long candidates;  // windows whose filter bits were all set already
+    unsigned long long claimed;     // keys inserted into the table
+    unsigned long long survivors;   // keys written by the compaction
+    unsigned int err;               // DERR_* bits
+    unsigned int pad[7];
+};
+
+enum : unsigned int {
+    DERR_TABLE_FULL = 1u,      // a probe sequence visited every slot
+    DERR_COUNT_OVERFLOW = 2u,  // a per-sample count passed 2^32 - 1
+    DERR_OFFSETS = 4u,         // decreasing read offsets
+    DERR_SORT_BUCKET = 8u,     // a sort bucket exceeded the shared-memory tile
+};
+
+// Parameters shared by the extraction passes.
+struct PassParams {
+    int k;
+    int rc_shift;            // 64 - 2k
+    unsigned long long kmask;  // 2k low bits
+    int bloom_shift;         // 64 - log2(words)
+    int n_hashes;
+    int table_shift;         // 64 - log2(slots)
+    unsigned long long table_mask;
+    int all_candidates;      // min_count <= 1: every window goes to the table
+    int sample;
+};
+
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014): golden-ratio
+// increment, then two xor-shift-multiply rounds and a closing xor-shift.
+__device__ __forceinline__ uint64_t mixer64(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Reverse the order of the 32 two-bit groups of x.
+__device__ __forceinline__ uint64_t reverse_pairs(uint64_t x) {
+    x = __brevll(x);
+    return ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+}
+
+// Forward 2k-bit code of the window starting at base j (0..63) of a unit whose
+// words are w0, w1 and the following word w2.
+__device__ __forceinline__ uint64_t window_code(uint64_t w0, uint64_t w1, uint64_t w2, int j, int rc_shift) {
+    const bool second = j >= 32;
+    const uint64_t hi = second ? w1 : w0;
+    const uint64_t lo = second ? w2 : w1;
+    const int off = 2 * (j & 31);
+    const uint64_t x = off ? (hi << off) | (lo >> (64 - off)) : hi;
+    return x >> rc_shift;
+}
+
+// Canonical key: the smaller of the forward code and the code of the reverse
+// complement (complement = code ^ 3, then reverse the base order).
+__device__ __forceinline__ uint64_t canonical_key(uint64_t fwd, const PassParams& p) {
+    const uint64_t rc = reverse_pairs(fwd ^ p.kmask) >> p.rc_shift;
+    return fwd < rc ? fwd : rc;
+}
+
+// Bits of one key in its filter word: bit (g >> 6i) & 63 for i < n_hashes.
+__device__ __forceinline__ uint64_t bloom_pattern(uint64_t g, int n_hashes) {
+    uint64_t pat = 0;
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+        if (i < n_hashes) pat |= 1ull << ((g >> (6 * i)) & 63);
+    return pat;
+}
+
+// Load the unit's words; lanes of a warp hold consecutive units, so the word
+// after the unit comes from the next lane (the last lane loads it itself).
+// The packed buffer is padded to 2 * n_units + 2 zero-filled words, so every
+// unit has both of its words and a successor word in bounds.
+struct UnitWords {
+    uint64_t w0, w1, w2, v;
+};
+
+__device__ __forceinline__ UnitWords load_unit(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw,
+                                               uint64_t u, uint64_t n_units, int lane) {
+    UnitWords r{0, 0, 0, 0};
+    const bool in = u < n_units;
+    if (in) {
+        r.v = __ldg(vw + u);
+        const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(pw) + u);
+        r.w0 = p.x;
+        r.w1 = p.y;
+    }
+    r.w2 = __shfl_down_sync(0xffffffffu, r.w0, 1);
+    if (lane == 31 && in) r.w2 = __ldg(pw + 2 * u + 2);
+    return r;
+}
+
+// Insert key (stored as key + 1) by linear probing.  Returns 1 if this call
+// claimed a new slot.  A probe sequence that wraps the whole table sets
+// DERR_TABLE_FULL and gives up.
+__device__ __forceinline__ int table_claim(Slot* __restrict__ table, uint64_t mask, uint64_t s, uint64_t stored,
+                                           DevCounters* ctr) {
+    for (uint64_t i = 0; i <= mask; ++i) {
+        const unsigned long long cur = __ldcg(&table[s].key1);
+        if (cur == stored) return 0;
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(&table[s].key1, 0ull, (unsigned long long)stored);
+            if (prev == 0ull) return 1;
+            if (prev == stored) return 0;
+        }
+        s = (s + 1) & mask;
+    }
+    atomicOr(&ctr->err, DERR_TABLE_FULL);
+    return 0;
+}
+
+// Add one occurrence of key to its slot if the key is in the table.
+__device__ __forceinline__ void table_count(Slot* __restrict__ table, uint64_t mask, uint64_t s, uint64_t stored,
+                                            int sample, DevCounters* ctr) {
+    for (uint64_t i = 0; i <= mask; ++i) {
+        const unsigned long long cur = __ldcg(&table[s].key1);
+        if (cur == stored) {
+            const unsigned int old = atomicAdd(&table[s].cnt[sample], 1u);
+            if (old == 0xffffffffu) atomicOr(&ctr->err, DERR_COUNT_OVERFLOW);
+            return;
+        }
+        if (cur == 0ull) return;
+        s = (s + 1) & mask;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace kc

@@ -157,9 +157,9 @@ def tiny(scale: float = 1.0) -> Workload:
     return Workload("tiny", [rs], k=31, bloom_bits=1 << 24, n_hashes=4, min_count=2)
 
 
-def mid(scale: float = 1.0) -> Workload:
-    g = genome(2, 5_000_000)
-    rs = reads(2, g, _scaled(1_000_000, scale), 150, 150, 0.005, 0.0005)
+def mid(scale: float = 1.0, seed: int = 2) -> Workload:
+    g = genome(seed, 5_000_000)
+    rs = reads(seed, g, _scaled(1_000_000, scale), 150, 150, 0.005, 0.0005)
     return Workload("mid", [rs], k=31, bloom_bits=1 << 30, n_hashes=4, min_count=2, table_slots=1 << 24)
 
 

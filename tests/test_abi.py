@@ -1,0 +1,98 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+declared symbol, validates arguments before touching the GPU, and packs reads
+in the documented format."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1712_03254_gb300 as kc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def _declared_functions():
+    names = set()
+    for f in os.listdir(INCLUDE):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(INCLUDE, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(kc_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    path = kc.build()
+    declared = _declared_functions()
+    assert "kc_create" in declared and "kc_add_reads" in declared and "kc_dump" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+    L = ctypes.CDLL(path)
+    for n in declared:
+        assert getattr(L, n) is not None
+
+
+def test_status_strings_and_default_config():
+    L = kc.lib()
+    assert L.kc_status_string(0) == b"KC_OK"
+    assert L.kc_status_string(7) == b"KC_ERR_CAPACITY"
+    cfg = kc.Config()
+    L.kc_default_config(ctypes.byref(cfg))
+    assert cfg.struct_size == ctypes.sizeof(kc.Config)
+    assert cfg.table_slots == 0 and cfg.part_bits == 0
+
+
+@pytest.mark.parametrize("args", [
+    (0, 1, 1 << 20, 4, 2), (32, 1, 1 << 20, 4, 2), (31, 0, 1 << 20, 4, 2), (31, 3, 1 << 20, 4, 2),
+    (31, 1, 3 << 20, 4, 2), (31, 1, 2048, 4, 2), (31, 1, 1 << 20, 0, 2), (31, 1, 1 << 20, 11, 2),
+    (31, 1, 1 << 20, 4, 0),
+])
+def test_create_rejects_bad_arguments_before_cuda(args):
+    L = kc.lib()
+    h = ctypes.c_void_p()
+    assert L.kc_create(*args, ctypes.byref(h)) == 1  # KC_ERR_ARG
+    assert not h.value
+    assert L.kc_last_error()
+
+
+def test_null_handle_calls_fail_cleanly():
+    L = kc.lib()
+    n = ctypes.c_uint64()
+    assert L.kc_finalize(None) == 1
+    assert L.kc_dump(None, None, None, 0, ctypes.byref(n)) == 1
+    assert L.kc_add_reads(None, 0, None, None, None, 0) == 1
+    L.kc_destroy(None)
+
+
+def _pack_reference(ascii: bytes):
+    """The packed format of include/kc.h, bit by bit."""
+    n = len(ascii)
+    packed = [0] * ((n + 31) // 32)
+    mask = [0] * ((n + 63) // 64)
+    code = {ord("A"): 0, ord("C"): 1, ord("G"): 2, ord("T"): 3}
+    for i, c in enumerate(ascii):
+        if c in code:
+            packed[i // 32] |= code[c] << (63 - 2 * (i % 32) - 1)
+        else:
+            mask[i // 64] |= 1 << (63 - i % 64)
+    return np.array(packed, dtype=np.uint64), np.array(mask, dtype=np.uint64)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 63, 64, 65, 127, 1000, 70001])
+def test_pack_ascii_matches_format(n):
+    rng = np.random.default_rng(n)
+    ascii = rng.choice(np.frombuffer(b"ACGTNacgRY", dtype=np.uint8), size=n,
+                       p=[0.22, 0.22, 0.22, 0.22, 0.04, 0.02, 0.02, 0.02, 0.02, 0.0])
+    packed, mask = kc.pack_ascii(ascii)
+    ref_p, ref_m = _pack_reference(ascii.tobytes())
+    assert np.array_equal(packed, ref_p)
+    assert np.array_equal(mask, ref_m)

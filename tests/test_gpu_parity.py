@@ -1,0 +1,220 @@
+"""GPU parity: libkc through its C ABI against the CPU oracle, bit for bit.
+
+Count tables (keys and per-sample counts) and Bloom filter words must match
+the oracle exactly: everything on this path is integer work.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import synth
+import paper_1712_03254_gb300 as kc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    kc.lib()
+
+
+def gpu_count(w, batches=1, **kw):
+    c = kc.KmerCounter(w.k, len(w.samples), w.bloom_bits, w.n_hashes, w.min_count,
+                       table_slots=w.table_slots, **kw)
+    for s, rs in enumerate(w.samples):
+        if batches == 1:
+            c.add_readset(s, rs)
+        else:
+            cuts = np.linspace(0, rs.n_reads, batches + 1).astype(int)
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                c.add_readset(s, rs.slice(a, b))
+    c.finalize()
+    return c
+
+
+def assert_same_result(c, o):
+    gk, gc = c.dump()
+    ok, oc = o.result()
+    assert gk.shape == ok.shape, (gk.shape, ok.shape)
+    assert np.array_equal(gk, ok)
+    assert np.array_equal(gc, oc)
+
+
+def assert_same_bloom(c, o):
+    assert np.array_equal(c.export_bloom(), o.bloom())
+
+
+def test_tiny_full_parity(oracle_mod):
+    """20,000 x 100 bp reads, k=31, 2^24-bit filter, 4 hashes, min_count 2."""
+    w = synth.tiny()
+    o = oracle_mod.count(w)
+    c = gpu_count(w)
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    st = c.stats()
+    assert st["windows"] == o.windows
+    assert st["result_keys"] == len(o.result()[0])
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 8, 16, 25, 31])
+@pytest.mark.parametrize("min_count", [1, 2, 3])
+def test_ragged_random_reads(oracle_mod, k, min_count):
+    """Read lengths 0..300 (shorter than k, exactly k, across word boundaries), 2 % N."""
+    rng = random.Random(31 * k + min_count)
+    g = "".join(rng.choice("ACGT") for _ in range(3000))
+    reads = []
+    for _ in range(700):
+        L = rng.choice([0, 1, k - 1, k, k + 1, 31, 32, 33, 63, 64, 65, rng.randint(0, 300)])
+        L = max(0, min(L, len(g)))
+        s = rng.randint(0, len(g) - L)
+        r = list(g[s : s + L])
+        for i in range(L):
+            if rng.random() < 0.02:
+                r[i] = "N"
+        reads.append("".join(r))
+    w = synth.Workload("ragged", [synth.ReadSet.from_strings(reads)], k, 1 << 16, 3, min_count)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, table_slots=1 << 16)
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    assert c.stats()["windows"] == o.windows
+
+
+def test_n_at_every_position(oracle_mod):
+    k = 7
+    base = "ACGTTGCAACGTAGGCTAAC"
+    reads = [base[:i] + "N" + base[i + 1 :] for i in range(len(base))] + [base, "N" * 40, "NACGTACGN"]
+    w = synth.Workload("nmask", [synth.ReadSet.from_strings(reads)], k, 1 << 12, 2, 1)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, table_slots=1 << 12)
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+def test_empty_and_degenerate_inputs(oracle_mod):
+    for reads in ([], [""], ["", "", ""], ["ACG"], ["NNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNN"]):
+        w = synth.Workload("empty", [synth.ReadSet.from_strings(reads)], 5, 1 << 12, 4, 1)
+        o = oracle_mod.count(w)
+        c = gpu_count(w, table_slots=1 << 12)
+        assert_same_result(c, o)
+        assert c.result_size() == 0
+        assert_same_bloom(c, o)
+
+
+def test_several_batches_and_offset_base(oracle_mod):
+    """Reads added in uneven batches, with offsets not starting at 0 (unaligned base)."""
+    w = synth.tiny(scale=0.2)
+    o = oracle_mod.count(w)
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count)
+    rs = w.samples[0]
+    packed, mask = kc.pack_ascii(rs.ascii)
+    cuts = [0, 1, 7, 500, 1333, 2000, rs.n_reads]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        # the whole packed stream is passed; offsets select the batch's reads
+        c.add_reads(0, packed, np.ascontiguousarray(rs.offsets[a : b + 1]), mask)
+    c.finalize()
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+def test_two_samples_joint_table(oracle_mod):
+    w = synth.paired(scale=0.002)
+    o = oracle_mod.count(w)
+    c = gpu_count(w)
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    gk, gc = c.dump()
+    assert gc.shape[1] == 2 and gc[:, 0].sum() > 0 and gc[:, 1].sum() > 0
+
+
+def test_device_resident_inputs(oracle_mod):
+    torch = pytest.importorskip("torch")
+    w = synth.tiny(scale=0.3)
+    o = oracle_mod.count(w)
+    rs = w.samples[0]
+    packed, mask = kc.pack_ascii(rs.ascii)
+    dp = torch.from_numpy(packed.view(np.int64)).cuda()
+    dm = torch.from_numpy(mask.view(np.int64)).cuda()
+    do = torch.from_numpy(rs.offsets.view(np.int64)).cuda()
+    torch.cuda.synchronize()
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count)
+    c.add_reads(0, dp, do, dm)
+    c.finalize()
+    n = c.result_size()
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    counts = torch.empty((n, 1), dtype=torch.int32, device="cuda")
+    c.dump(keys, counts)
+    ok, oc = o.result()
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), ok)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32), oc)
+    bloom = torch.empty(w.bloom_bits // 64, dtype=torch.int64, device="cuda")
+    c.export_bloom(out=bloom)
+    assert np.array_equal(bloom.cpu().numpy().view(np.uint64), o.bloom())
+
+
+def test_reset_reuses_handle(oracle_mod):
+    w = synth.tiny(scale=0.25)
+    o = oracle_mod.count(w)
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count)
+    for _ in range(3):
+        c.add_readset(0, w.samples[0])
+        c.finalize()
+        assert_same_result(c, o)
+        assert_same_bloom(c, o)
+        c.reset()
+
+
+def test_errors_are_reported_not_faulted(oracle_mod):
+    w = synth.tiny(scale=0.2)
+    # table far too small: probes are bounded, the job reports KC_ERR_CAPACITY
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=1024)
+    c.add_readset(0, w.samples[0])
+    with pytest.raises(kc.KcError) as e:
+        c.finalize()
+    assert e.value.name == "KC_ERR_CAPACITY"
+    with pytest.raises(kc.KcError) as e:
+        c.finalize()
+    assert e.value.name == "KC_ERR_STATE"
+    c.reset()
+    # decreasing offsets are rejected on the host
+    packed, mask = kc.pack_ascii(np.frombuffer(b"ACGT" * 40, dtype=np.uint8))
+    with pytest.raises(kc.KcError) as e:
+        c.add_reads(0, packed, np.array([0, 100, 50, 160], dtype=np.uint64), mask)
+    assert e.value.name == "KC_ERR_ARG"
+    # dump before finalize, and into a buffer that is too small
+    with pytest.raises(kc.KcError):
+        c.dump()
+    c.add_readset(0, w.samples[0])
+    c.finalize()
+    n = c.result_size()
+    assert n > 10
+    with pytest.raises(kc.KcError) as e:
+        c.dump(np.empty(n - 1, dtype=np.uint64), np.empty((n - 1, 1), dtype=np.uint32))
+    assert e.value.name == "KC_ERR_CAPACITY"
+
+
+def test_mid_full_size_sampled_partitions(oracle_mod):
+    """1,000,000 x 150 bp, 2^30-bit filter, 2^24 slots: the configuration the
+    benchmark times.  The oracle counts four of 64 hash partitions in full;
+    the GPU result restricted to them, and their filter words, must match."""
+    w = synth.mid()
+    q, parts = 6, [0, 17, 42, 63]
+    o = oracle_mod.count(w, restrict=(q, parts))
+    c = gpu_count(w)
+    gk, gc = c.dump()
+    sel = np.isin(oracle_mod.partitions(gk, q), parts)
+    ok, oc = o.result()
+    assert np.array_equal(gk[sel], ok)
+    assert np.array_equal(gc[sel], oc)
+    assert np.all(np.diff(gk.astype(np.uint64)) > 0)  # strictly ascending everywhere
+    nw = w.bloom_bits // 64
+    per = nw >> q
+    for p in parts:
+        assert np.array_equal(c.export_bloom(p * per, per), o.bloom(p * per, per))
+    st = c.stats()
+    assert st["windows"] == o.windows
