@@ -200,6 +200,40 @@ def ncu_traffic(kernel: str):
     return e.get("dram_bytes_per_launch")
 
 
+def roofline_of(st, phases, rs, w):
+    """Roofline entry for the phase that takes the most device time.
+
+    Algorithmic bytes are compulsory traffic only (measurement):
+      reads      2 bits (packed base) + 1 bit (valid-window bit) per base
+      direct     pass1: reads + filter read and written once + 32 B per claimed
+                 key; pass2: reads + 32 B per claimed key (slot read, counts
+                 written)
+      partitioned bucketing (count + scatter): reads twice + 8 B hash written
+                 per window; consumer: 8 B hash read per window + filter
+                 written once + 16 B per result key
+    """
+    import statistics as _st
+
+    W = st["windows"]
+    read_bytes = (rs.n_bases * 3 + 7) // 8
+    bloom_bytes = w.bloom_bits // 8
+    mean = {k: _st.mean(v) for k, v in phases.items()}
+    if st["strategy"] == 1:
+        table = {"pass1": ("k_pass1", read_bytes + 2 * bloom_bytes + 32 * st["table_keys"]),
+                 "pass2": ("k_pass2", read_bytes + 32 * st["table_keys"])}
+    else:
+        table = {"pass1": ("k_bucket_pass (count + scatter)", 2 * read_bytes + 8 * W),
+                 "pass2": ("k_part_consume", 8 * W + bloom_bytes + 16 * st["result_keys"])}
+    phase = max(table, key=lambda k: mean[k])
+    kernel, algo = table[phase]
+    ms = mean[phase]
+    peak, peak_kind = measured_hbm_peak()
+    achieved = algo / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": ncu_traffic(kernel), "algorithmic_bytes": int(algo), "ms_per_launch": round(ms, 4)}
+
+
 # ---------------------------------------------------------------- workloads
 
 
@@ -260,7 +294,7 @@ def run_kc(args):
     torch.cuda.synchronize()
 
     c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots, timing=True,
-                       stream=stream)
+                       strategy=args.strategy, stream=stream)
 
     # size result buffers with one untimed job
     c.add_reads(0, d_packed, d_off, d_mask)
@@ -333,22 +367,8 @@ def run_kc(args):
 
     # roofline of the dominant kernel (per-launch means over the timed steps)
     st = c.stats()
-    read_bytes = (2 * (rs.n_bases + 63) // 64 + 2) * 8 + ((rs.n_bases + 63) // 64) * 8  # packed + valid bits
-    bloom_bytes = w.bloom_bits // 8
-    claimed = st["table_keys"]
-    algo = {
-        "k_pass1": read_bytes + 2 * bloom_bytes + 2 * 16 * claimed,
-        "k_pass2": read_bytes + 2 * 16 * claimed,
-    }
-    mean = {k: statistics.mean(v) for k, v in phases.items()}
-    dom = "k_pass1" if mean["pass1"] >= mean["pass2"] else "k_pass2"
-    dom_ms = mean["pass1"] if dom == "k_pass1" else mean["pass2"]
-    peak, peak_kind = measured_hbm_peak()
-    achieved = algo[dom] / (dom_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": ncu_traffic(dom), "algorithmic_bytes": int(algo[dom]),
-                "ms_per_launch": round(dom_ms, 4)}
+    roofline = roofline_of(st, phases, rs, w)
+    strategy = {1: "direct", 2: "partitioned"}.get(st["strategy"], "?")
 
     # CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
     cpu = None
@@ -367,7 +387,8 @@ def run_kc(args):
             "config": {"workload": WORKLOAD, "windows_per_job": windows, "result_keys": n_res,
                        "l2": "256 MiB written between timed steps (outside the step events)",
                        "parallelism": f"{world} independent jobs, one per GPU" if world > 1 else "1 GPU"},
-            "phase_ms": {k: round(v, 4) for k, v in mean.items()},
+            "strategy": strategy,
+            "phase_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -422,6 +443,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["kc", "reference"], default="kc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--strategy", choices=["auto", "direct", "partitioned"], default="auto")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -80,16 +80,37 @@ typedef struct kc_config {
     uint32_t struct_size;         /* sizeof(kc_config), for ABI growth             */
     uint32_t block_threads;       /* threads per CTA of the streaming kernels       */
     uint32_t ctas_per_sm;         /* resident CTAs per SM for grid sizing           */
-    uint32_t part_bits;           /* the table is processed as 2^part_bits hash-
-                                     prefix partitions, one after another          */
-    uint64_t table_slots;         /* open-addressing slots (power of two) of the
-                                     table for one partition                        */
+    uint32_t part_bits;           /* partitioned: log2 of the number of hash-prefix
+                                     partitions (1..14)                             */
+    uint64_t table_slots;         /* direct: open-addressing slots (power of two)
+                                     of the global table                            */
     uint32_t spill;               /* 1: each finished partition's result is copied
                                      to pinned host memory on a side stream         */
     uint32_t timing;              /* 1: record CUDA events around every phase on
                                      the handle's stream (see kc_stats.ms_*)        */
-    uint64_t reserved[6];
+    uint32_t strategy;            /* KC_STRATEGY_*                                  */
+    uint32_t smem_table_log2;     /* partitioned: log2 shared-memory table slots of
+                                     one partition (10..13)                         */
+    uint64_t reserved[5];
 } kc_config;
+
+/*
+ * Strategies.  Both compute the same result and filter bit for bit.
+ *   DIRECT       kc_add_reads updates the global filter with one 64-bit
+ *                atomicOr per window and claims candidates in a global
+ *                open-addressing table; kc_finalize recounts every window
+ *                against that table.
+ *   PARTITIONED  kc_add_reads stores each window's 64-bit hash grouped by
+ *                2^part_bits hash-prefix partitions (counting-sort shuffle, as
+ *                the paper's Encode / Prefix-sum / Broker kernels group k-mers
+ *                by consumer, Section III-B); kc_finalize gives each partition
+ *                to one CTA that keeps the partition's filter words and table
+ *                in shared memory (filter update, candidate claims, exact
+ *                recount, compaction).  The filter is built at kc_finalize.
+ *   AUTO         PARTITIONED when the filter slices fit shared memory, else
+ *                DIRECT.
+ */
+enum { KC_STRATEGY_AUTO = 0, KC_STRATEGY_DIRECT = 1, KC_STRATEGY_PARTITIONED = 2 };
 
 /* Counters of one job (valid after kc_finalize unless noted). */
 typedef struct kc_stats {
@@ -105,10 +126,15 @@ typedef struct kc_stats {
     uint64_t launches;        /* kernels launched since create / reset           */
     /* Device time per phase since create / reset, from CUDA events on the
      * handle's stream (zero unless kc_config.timing = 1; complete after
-     * kc_finalize): ingest = read-start and valid-window bits; pass1 = filter
-     * update and candidate claims; pass2 = exact recount; compact = survivor
-     * compaction; sort = bucketing and bucket sorts. */
+     * kc_finalize): ingest = read-start and valid-window bits; sort = key-
+     * prefix bucketing and bucket sorts.  DIRECT: pass1 = filter update and
+     * candidate claims, pass2 = exact recount, compact = survivor compaction.
+     * PARTITIONED: pass1 = hash bucketing (count and scatter), pass2 = the
+     * shared-memory partition consumer (filter, claims, recount, compaction),
+     * compact = fallback partitions. */
     double ms_ingest, ms_pass1, ms_pass2, ms_compact, ms_sort;
+    uint32_t strategy;              /* KC_STRATEGY_DIRECT or KC_STRATEGY_PARTITIONED */
+    uint32_t fallback_partitions;   /* partitions whose table left shared memory    */
 } kc_stats;
 
 /* Fill *cfg with the defaults (struct_size set). */
@@ -160,7 +186,8 @@ kc_status kc_finalize(kc_handle h);
 kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capacity, uint64_t* n_out);
 
 /* Copy filter words [first_word, first_word + n_words) (for parity checks and
- * checkpoints).  Allowed at any time; blocks until pending work is done. */
+ * checkpoints).  Blocks until pending work is done.  With the partitioned
+ * strategy the filter is built by kc_finalize (all zero before). */
 kc_status kc_export_bloom(kc_handle h, uint64_t* words, uint64_t first_word, uint64_t n_words);
 
 kc_status kc_stats_get(kc_handle h, kc_stats* out);

@@ -203,7 +203,8 @@ int orc_restrict(void* h, int q, const uint8_t* keep) {
 // Add n_reads ASCII reads of one sample; read r = ascii[offsets[r] .. offsets[r+1]).
 int orc_add_reads(void* h, int sample, const char* ascii, const uint64_t* offsets, uint64_t n_reads) {
     Oracle* o = (Oracle*)h;
-    if (!o || sample < 0 || sample >= o->n_samples || (!ascii && n_reads) || !offsets) return -1;
+    if (!o || sample < 0 || sample >= o->n_samples || !offsets) return -1;
+    if (!ascii && n_reads && offsets[n_reads] != offsets[0]) return -1;
     if (o->restrict_bits == 0 && o->bloom.empty()) o->bloom.assign(o->bloom_bits / 64, 0ull);
     for (uint64_t r = 0; r < n_reads; ++r) {
         if (offsets[r + 1] < offsets[r]) return -2;

@@ -37,7 +37,8 @@ class Config(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("part_bits", ctypes.c_uint32),
                 ("table_slots", ctypes.c_uint64), ("spill", ctypes.c_uint32), ("timing", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint64 * 6)]
+                ("strategy", ctypes.c_uint32), ("smem_table_log2", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint64 * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -46,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("spilled_bytes", ctypes.c_uint64), ("partitions", ctypes.c_uint32),
                 ("table_log2", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("ms_ingest", ctypes.c_double), ("ms_pass1", ctypes.c_double), ("ms_pass2", ctypes.c_double),
-                ("ms_compact", ctypes.c_double), ("ms_sort", ctypes.c_double)]
+                ("ms_compact", ctypes.c_double), ("ms_sort", ctypes.c_double), ("strategy", ctypes.c_uint32),
+                ("fallback_partitions", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -130,7 +132,7 @@ class KmerCounter:
 
     def __init__(self, k: int, n_samples: int, bloom_bits: int, n_hashes: int = 4, min_count: int = 2,
                  table_slots: int = 0, part_bits: int = 0, spill: bool = False, ctas_per_sm: int = 0,
-                 timing: bool = False, stream=None):
+                 timing: bool = False, strategy: str = "auto", smem_table_log2: int = 0, stream=None):
         L = lib()
         cfg = Config()
         L.kc_default_config(ctypes.byref(cfg))
@@ -139,6 +141,8 @@ class KmerCounter:
         cfg.spill = 1 if spill else 0
         cfg.ctas_per_sm = ctas_per_sm
         cfg.timing = 1 if timing else 0
+        cfg.strategy = {"auto": 0, "direct": 1, "partitioned": 2}[strategy]
+        cfg.smem_table_log2 = smem_table_log2
         h = ctypes.c_void_p()
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream

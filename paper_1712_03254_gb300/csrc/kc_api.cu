@@ -61,10 +61,15 @@ bool is_device_ptr(const void* p) {
 }
 
 struct Batch {
+    int sample = 0;
+    // direct strategy: the resident reads, rescanned by the recount
     uint64_t* pw = nullptr;  // packed words, 2 * n_units + 2
     uint64_t* vw = nullptr;  // valid-window-start words, n_units
     uint64_t n_units = 0;
-    int sample = 0;
+    // partitioned strategy: window hashes grouped by partition
+    uint64_t* hdata = nullptr;    // capacity: one per base of the batch
+    uint64_t* hstarts = nullptr;  // partition starts, 2^part_bits + 1
+    uint64_t hcap = 0;
 };
 
 enum class State { Open, Finalized, Poisoned };
@@ -83,6 +88,9 @@ struct kc_ctx {
     kc::Grid grid;
     int log2_words = 0, log2_slots = 0;
     uint64_t n_slots = 0;
+    int strategy = KC_STRATEGY_DIRECT;
+    int part_bits = 0;   // partitioned: 2^part_bits partitions
+    int slice_log2 = 0;  // partitioned: filter words per partition
 
     uint64_t* bloom = nullptr;
     kc::Slot* table = nullptr;
@@ -109,6 +117,7 @@ struct kc_ctx {
     std::vector<Mark> marks;
     double ms[5] = {0, 0, 0, 0, 0};
     uint64_t launches = 0;
+    uint32_t fallback_partitions = 0;
 
     kc::PassParams params(int sample) const {
         kc::PassParams p{};
@@ -173,8 +182,10 @@ kc_status check_open(kc_handle h) {
 
 void free_batches(kc_handle h) {
     for (auto& b : h->batches) {
-        cudaFreeAsync(b.pw, h->stream);
-        cudaFreeAsync(b.vw, h->stream);
+        if (b.pw) cudaFreeAsync(b.pw, h->stream);
+        if (b.vw) cudaFreeAsync(b.vw, h->stream);
+        if (b.hdata) cudaFreeAsync(b.hdata, h->stream);
+        if (b.hstarts) cudaFreeAsync(b.hstarts, h->stream);
     }
     h->batches.clear();
 }
@@ -207,6 +218,331 @@ kc_status device_errors(kc_handle h) {
         return fail(KC_ERR_CAPACITY, "a per-sample count exceeded 2^32-1");
     }
     return KC_OK;
+}
+
+// Partitioned strategy, ingest: group the batch's window hashes by partition
+// (count pass, per-partition prefix over CTAs, scan, scatter pass).
+kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st) {
+    const int a = h->part_bits;
+    const uint64_t P = 1ull << a;
+    const int max_ctas = h->grid.sm_count * 2;
+    const uint64_t upc = std::max<uint64_t>(1, (b.n_units + max_ctas - 1) / max_ctas);
+    const int n_ctas = (int)((b.n_units + upc - 1) / upc);
+    uint32_t* counts = nullptr;
+    uint32_t* total = nullptr;
+    uint64_t *rel = nullptr, *cursor = nullptr;
+    b.hcap = n_local;  // at most one window per base
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&counts, (size_t)n_ctas * P * 4, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&rel, (size_t)n_ctas * P * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&total, P * 4, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&cursor, P * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&b.hstarts, (P + 1) * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, b.hcap) * 8, st)) != cudaSuccess) {
+        cudaFreeAsync(counts, st);
+        cudaFreeAsync(rel, st);
+        cudaFreeAsync(total, st);
+        cudaFreeAsync(cursor, st);
+        if (b.hstarts) cudaFreeAsync(b.hstarts, st);
+        if (b.hdata) cudaFreeAsync(b.hdata, st);
+        b.hstarts = b.hdata = nullptr;
+        return cuda_fail(e, "cudaMallocAsync(partition buckets)");
+    }
+    const kc::PassParams p = h->params(b.sample);
+    kc::launch_bucket_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, st);
+    kc::launch_bucket_offsets(counts, n_ctas, a, rel, total, st);
+    kc::launch_scan(total, P, b.hstarts, cursor, st);
+    kc::launch_bucket_base(rel, b.hstarts, n_ctas, a, st);
+    kc::launch_bucket_scatter(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, rel, b.hdata, st);
+    cudaFreeAsync(counts, st);
+    cudaFreeAsync(rel, st);
+    cudaFreeAsync(total, st);
+    cudaFreeAsync(cursor, st);
+    return KC_OK;
+}
+
+// Sort the survivors held in tk/tv (count in host_ctr.survivors, already
+// read back) into res_keys/res_vals: bucket by the top bits of the 2k-bit
+// key (about 512 keys a bucket), then sort every bucket in shared memory.
+kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
+    cudaStream_t st = h->stream;
+    const uint64_t n = h->host_ctr.survivors;
+    const uint64_t cap = std::max<uint64_t>(1, n);
+    int bits = 0;
+    while (bits < 22 && bits < 2 * h->k && (cap >> bits) > 512) ++bits;
+    const uint64_t n_buckets = 1ull << bits;
+    const int prefix_shift = 2 * h->k - bits;
+    uint64_t *starts = nullptr, *cursor = nullptr;
+    uint32_t* hist = nullptr;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&hist, n_buckets * 4, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&starts, (n_buckets + 1) * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&cursor, n_buckets * 8, st)) != cudaSuccess) {
+        if (hist) cudaFreeAsync(hist, st);
+        if (starts) cudaFreeAsync(starts, st);
+        free_result(h);
+        return cuda_fail(e, "cudaMallocAsync(sort buffers)");
+    }
+    h->res_cap = cap;
+    cudaEvent_t t0 = phase_begin(h);
+    KC_CUDA(cudaMemsetAsync(hist, 0, n_buckets * 4, st));
+    kc::launch_prefix_hist(tk, h->ctr, n, prefix_shift, n_buckets, hist, h->grid, st);
+    kc::launch_scan(hist, n_buckets, starts, cursor, st);
+    kc::launch_scatter(tk, tv, h->ctr, n, prefix_shift, n_buckets, cursor, h->res_keys, h->res_vals, h->grid, st);
+    kc::launch_bucket_sort(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, st);
+    phase_end(h, kSort, t0);
+    h->launches += 4;
+    KC_CUDA(cudaGetLastError());
+    kc_status s = read_counters(h);
+    if (s != KC_OK) return s;
+    if (h->host_ctr.err & kc::DERR_INTERNAL) {
+        h->state = State::Poisoned;
+        return fail(KC_ERR_INTERNAL, "sort: key outside its bucket range");
+    }
+    if (h->host_ctr.err & kc::DERR_SORT_BUCKET) {
+        // Rare: a bucket larger than the shared-memory tile; sort it in global memory.
+        std::vector<uint64_t> hs(n_buckets + 1);
+        KC_CUDA(cudaMemcpyAsync(hs.data(), starts, (n_buckets + 1) * 8, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        const uint64_t capb = (uint64_t)kc::bucket_sort_capacity();
+        for (uint64_t i = 0; i < n_buckets; ++i)
+            if (hs[i + 1] - hs[i] > capb) {
+                uint64_t m = hs[i + 1] - hs[i], m2 = 1, steps = 0;
+                while (m2 < m) m2 <<= 1;
+                for (uint64_t size = 2; size <= m2; size <<= 1)
+                    for (uint64_t stride = size >> 1; stride > 0; stride >>= 1) ++steps;
+                kc::launch_bitonic_global(h->res_keys + hs[i], h->res_vals + hs[i], m, st);
+                h->launches += steps;
+            }
+        unsigned zero = 0;
+        KC_CUDA(cudaMemcpyAsync(&h->ctr->err, &zero, 4, cudaMemcpyHostToDevice, st));
+        KC_CUDA(cudaGetLastError());
+    }
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(starts, st);
+    cudaFreeAsync(cursor, st);
+    KC_CUDA(cudaStreamSynchronize(st));
+    phase_collect(h);
+    h->n_result = n;
+    return KC_OK;
+}
+
+kc_status finalize_direct(kc_handle h) {
+    cudaStream_t st = h->stream;
+    cudaEvent_t t0 = phase_begin(h);
+    for (const auto& b : h->batches)
+        kc::launch_pass2(b.pw, b.vw, b.n_units, h->params(b.sample), h->table, h->ctr, h->grid, st);
+    phase_end(h, kPass2, t0);
+    h->launches += h->batches.size();
+    KC_CUDA(cudaGetLastError());
+    kc_status s = read_counters(h);
+    if (s != KC_OK) return s;
+    if ((s = device_errors(h)) != KC_OK) return s;
+    const uint64_t cap = std::max<uint64_t>(1, h->host_ctr.claimed);
+    uint64_t *tk = nullptr, *tv = nullptr;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&tk, cap * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&tv, cap * 8, st)) != cudaSuccess) {
+        if (tk) cudaFreeAsync(tk, st);
+        return cuda_fail(e, "cudaMallocAsync(compaction)");
+    }
+    KC_CUDA(cudaMemsetAsync(&h->ctr->survivors, 0, 8, st));
+    t0 = phase_begin(h);
+    kc::launch_compact(h->table, h->n_slots, h->n_samples, h->min_count, tk, tv, h->ctr, nullptr, 0, h->grid, st);
+    phase_end(h, kCompact, t0);
+    h->launches += 1;
+    KC_CUDA(cudaGetLastError());
+    if ((s = read_counters(h)) != KC_OK) return s;
+    s = sort_result(h, tk, tv);
+    cudaFreeAsync(tk, st);
+    cudaFreeAsync(tv, st);
+    return s;
+}
+
+// Fallback for partitions whose shared-memory table overflowed: the
+// partition's filter slice is rebuilt from zero and its keys are counted in a
+// global table sized for every window of the partition.
+kc_status fallback_partitions(kc_handle h, const std::vector<uint32_t>& failed, const std::vector<uint64_t>& hs,
+                              const kc::ConsumeArgs& A, uint64_t*& tk, uint64_t*& tv, uint64_t& out_cap) {
+    cudaStream_t st = h->stream;
+    const uint64_t P = 1ull << h->part_bits;
+    const size_t nb = h->batches.size();
+    auto windows_of = [&](uint32_t p) {
+        uint64_t w = 0;
+        for (size_t b = 0; b < nb; ++b) w += hs[b * (P + 1) + p + 1] - hs[b * (P + 1) + p];
+        return w;
+    };
+    uint64_t extra = 0;
+    for (uint32_t p : failed) extra += windows_of(p);
+    kc_status s = read_counters(h);
+    if (s != KC_OK) return s;
+    const uint64_t need = h->host_ctr.survivors + extra;
+    if (need > out_cap) {  // grow the survivor arrays, keeping what is there
+        uint64_t *nk = nullptr, *nv = nullptr;
+        cudaError_t e;
+        if ((e = cudaMallocAsync(&nk, need * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&nv, need * 8, st)) != cudaSuccess) {
+            if (nk) cudaFreeAsync(nk, st);
+            return cuda_fail(e, "cudaMallocAsync(fallback survivors)");
+        }
+        const uint64_t have = std::min<uint64_t>(h->host_ctr.survivors, out_cap);
+        KC_CUDA(cudaMemcpyAsync(nk, tk, have * 8, cudaMemcpyDeviceToDevice, st));
+        KC_CUDA(cudaMemcpyAsync(nv, tv, have * 8, cudaMemcpyDeviceToDevice, st));
+        cudaFreeAsync(tk, st);
+        cudaFreeAsync(tv, st);
+        tk = nk;
+        tv = nv;
+        out_cap = need;
+    }
+    const uint64_t n_sw = 1ull << h->slice_log2;
+    for (uint32_t p : failed) {
+        const uint64_t w = windows_of(p);
+        uint64_t slots = 1024;
+        while (slots < 2 * w) slots <<= 1;
+        kc::Slot* table = nullptr;
+        cudaError_t e = cudaMallocAsync(&table, slots * sizeof(kc::Slot), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(fallback table)");
+        KC_CUDA(cudaMemsetAsync(table, 0, slots * sizeof(kc::Slot), st));
+        KC_CUDA(cudaMemsetAsync(h->bloom + p * n_sw, 0, n_sw * 8, st));
+        kc::FallbackArgs F{};
+        F.data = A.data;
+        F.starts = A.starts;
+        F.samples = A.samples;
+        F.part = p;
+        F.part_bits = h->part_bits;
+        F.bloom_shift = A.bloom_shift;
+        F.n_hashes = h->n_hashes;
+        F.n_samples = h->n_samples;
+        F.all_candidates = A.all_candidates;
+        F.min_count = h->min_count;
+        F.bloom = reinterpret_cast<unsigned long long*>(h->bloom);
+        F.table = table;
+        F.table_mask = slots - 1;
+        F.out_keys = tk;
+        F.out_vals = tv;
+        F.out_cap = out_cap;
+        F.n_out = &h->ctr->survivors;
+        F.ctr = h->ctr;
+        for (size_t b = 0; b < nb; ++b) kc::launch_fb_claim(F, (int)b, st);
+        for (size_t b = 0; b < nb; ++b) kc::launch_fb_recount(F, (int)b, st);
+        kc::launch_fb_compact(F, st);
+        h->launches += 2 * nb + 1;
+        KC_CUDA(cudaGetLastError());
+        cudaFreeAsync(table, st);
+    }
+    return KC_OK;
+}
+
+kc_status finalize_partitioned(kc_handle h) {
+    cudaStream_t st = h->stream;
+    const int a = h->part_bits;
+    const uint64_t P = 1ull << a;
+    const size_t nb = h->batches.size();
+    // partition sizes over all batches
+    std::vector<uint64_t> hs(nb * (P + 1));
+    for (size_t b = 0; b < nb; ++b)
+        KC_CUDA(cudaMemcpyAsync(hs.data() + b * (P + 1), h->batches[b].hstarts, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
+    kc_status s = read_counters(h);
+    if (s != KC_OK) return s;
+    if ((s = device_errors(h)) != KC_OK) return s;
+    uint64_t max_w = 0, total_w = 0;
+    for (uint64_t p = 0; p < P; ++p) {
+        uint64_t w = 0;
+        for (size_t b = 0; b < nb; ++b) w += hs[b * (P + 1) + p + 1] - hs[b * (P + 1) + p];
+        max_w = std::max(max_w, w);
+        total_w += w;
+    }
+    // Shared-memory table: about one slot per 8 windows of the largest
+    // partition (keys seen at least twice, at half load), 1024..8192 slots.
+    int tl = (int)h->cfg.smem_table_log2;
+    if (!tl) {
+        tl = 10;
+        while (tl < 13 && (1ull << tl) < max_w / 8) ++tl;
+    }
+    int max_optin = 0, max_sm = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+    while (tl > 10 && kc::consume_smem(h->slice_log2, tl, h->n_samples) + 1024 > (size_t)max_optin) --tl;
+    const size_t smem = kc::consume_smem(h->slice_log2, tl, h->n_samples);
+    if (smem + 1024 > (size_t)max_optin) return fail(KC_ERR_INTERNAL, "partition does not fit shared memory");
+    const int per_sm = std::max(1, std::min(4, max_sm / (int)(smem + 2048)));
+    const int n_ctas = (int)std::min<uint64_t>(P, (uint64_t)h->grid.sm_count * per_sm);
+
+    uint64_t out_cap = std::max<uint64_t>(1, std::min<uint64_t>(P << tl, total_w));
+    uint64_t *tk = nullptr, *tv = nullptr;
+    uint32_t* failed = nullptr;
+    void* meta = nullptr;
+    const size_t meta_bytes = std::max<size_t>(16, nb * 16 + nb * 4);
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&tk, out_cap * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&tv, out_cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&failed, (P + 1) * 4, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&meta, meta_bytes, st)) != cudaSuccess) {
+        if (tk) cudaFreeAsync(tk, st);
+        if (tv) cudaFreeAsync(tv, st);
+        if (failed) cudaFreeAsync(failed, st);
+        return cuda_fail(e, "cudaMallocAsync(partition consumer)");
+    }
+    std::vector<unsigned char> hmeta(meta_bytes, 0);
+    for (size_t b = 0; b < nb; ++b) {
+        const uint64_t dp = (uint64_t)(uintptr_t)h->batches[b].hdata, sp = (uint64_t)(uintptr_t)h->batches[b].hstarts;
+        const int smp = h->batches[b].sample;
+        std::memcpy(hmeta.data() + b * 8, &dp, 8);
+        std::memcpy(hmeta.data() + nb * 8 + b * 8, &sp, 8);
+        std::memcpy(hmeta.data() + nb * 16 + b * 4, &smp, 4);
+    }
+    KC_CUDA(cudaMemcpyAsync(meta, hmeta.data(), meta_bytes, cudaMemcpyHostToDevice, st));
+    KC_CUDA(cudaMemsetAsync(failed + P, 0, 4, st));
+    KC_CUDA(cudaMemsetAsync(&h->ctr->survivors, 0, 8, st));
+
+    kc::ConsumeArgs A{};
+    A.data = reinterpret_cast<const uint64_t* const*>(meta);
+    A.starts = reinterpret_cast<const uint64_t* const*>(static_cast<char*>(meta) + nb * 8);
+    A.samples = reinterpret_cast<const int*>(static_cast<char*>(meta) + nb * 16);
+    A.n_batches = (int)nb;
+    A.part_bits = a;
+    A.slice_log2 = h->slice_log2;
+    A.table_log2 = tl;
+    A.bloom_shift = 64 - h->log2_words;
+    A.n_hashes = h->n_hashes;
+    A.n_samples = h->n_samples;
+    A.all_candidates = h->min_count <= 1 ? 1 : 0;
+    A.min_count = h->min_count;
+    A.bloom = reinterpret_cast<unsigned long long*>(h->bloom);
+    A.out_keys = tk;
+    A.out_vals = tv;
+    A.out_cap = out_cap;
+    A.n_out = &h->ctr->survivors;
+    A.failed = failed;
+    A.n_failed = failed + P;
+    A.ctr = h->ctr;
+    cudaEvent_t t0 = phase_begin(h);
+    if (kc::launch_part_consume(A, n_ctas, st) != 0) {
+        cudaGetLastError();
+        return fail(KC_ERR_CUDA, "partition consumer launch configuration");
+    }
+    phase_end(h, kPass2, t0);
+    h->launches += 1;
+    KC_CUDA(cudaGetLastError());
+    uint32_t n_failed = 0;
+    KC_CUDA(cudaMemcpyAsync(&n_failed, failed + P, 4, cudaMemcpyDeviceToHost, st));
+    if ((s = read_counters(h)) != KC_OK) return s;
+    if (n_failed) {
+        std::vector<uint32_t> fl(n_failed);
+        KC_CUDA(cudaMemcpyAsync(fl.data(), failed, n_failed * 4, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        t0 = phase_begin(h);
+        s = fallback_partitions(h, fl, hs, A, tk, tv, out_cap);
+        phase_end(h, kCompact, t0);
+        if (s == KC_OK) s = read_counters(h);
+        if (s == KC_OK) s = device_errors(h);
+    }
+    h->fallback_partitions = n_failed;
+    if (s == KC_OK) s = sort_result(h, tk, tv);
+    cudaFreeAsync(tk, st);
+    cudaFreeAsync(tv, st);
+    cudaFreeAsync(failed, st);
+    cudaFreeAsync(meta, st);
+    return s;
 }
 
 }  // namespace
@@ -260,6 +596,20 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     uint64_t slots = c.table_slots ? c.table_slots : std::max<uint64_t>(1ull << 12, bloom_bits / 32);
     if (!is_pow2(slots) || slots < 1024) return fail(KC_ERR_ARG, "table_slots must be a power of two >= 1024");
     if (c.block_threads && c.block_threads != 256) return fail(KC_ERR_ARG, "block_threads must be 256");
+    if (c.strategy > KC_STRATEGY_PARTITIONED) return fail(KC_ERR_ARG, "unknown strategy");
+    if (c.part_bits > 14) return fail(KC_ERR_ARG, "part_bits must be <= 14");
+    if (c.smem_table_log2 && (c.smem_table_log2 < 10 || c.smem_table_log2 > 13))
+        return fail(KC_ERR_ARG, "smem_table_log2 must be in 10..13");
+    // Partitions: filter slices of 4096 words (32 KiB) unless set; the
+    // partitioned strategy needs a slice of at most 8192 words in shared memory.
+    const int lw = log2_exact(bloom_bits / 64);
+    int pb = c.part_bits ? (int)c.part_bits : std::min(14, std::max(1, lw - 12));
+    pb = std::min(pb, lw);
+    const bool part_ok = lw - pb <= 13 && pb >= 1;
+    int strategy = (int)c.strategy;
+    if (strategy == KC_STRATEGY_AUTO) strategy = part_ok ? KC_STRATEGY_PARTITIONED : KC_STRATEGY_DIRECT;
+    if (strategy == KC_STRATEGY_PARTITIONED && !part_ok)
+        return fail(KC_ERR_ARG, "partitioned strategy: filter slice per partition exceeds 8192 words");
 
     kc_ctx* h = new (std::nothrow) kc_ctx();
     if (!h) return fail(KC_ERR_OOM_HOST, "host allocation");
@@ -270,8 +620,12 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     h->min_count = min_count;
     h->cfg = c;
     h->log2_words = log2_exact(bloom_bits / 64);
+    h->strategy = strategy;
+    h->part_bits = pb;
+    h->slice_log2 = lw - pb;
+    if (strategy == KC_STRATEGY_PARTITIONED) slots = 0;
     h->n_slots = slots;
-    h->log2_slots = log2_exact(slots);
+    h->log2_slots = slots ? log2_exact(slots) : 0;
 
     auto bail = [&](kc_status s) {
         kc_destroy(h);
@@ -294,9 +648,16 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
         (e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming)) != cudaSuccess)
         return bail(cuda_fail(e, "stream/event create"));
+    // Keep freed stream-ordered allocations cached for the next job.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     const size_t bloom_bytes = bloom_bits / 8, table_bytes = slots * sizeof(kc::Slot);
     if ((e = cudaMalloc(&h->bloom, bloom_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(filter)"));
-    if ((e = cudaMalloc(&h->table, table_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(table)"));
+    if (table_bytes && (e = cudaMalloc(&h->table, table_bytes)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMalloc(table)"));
     if ((e = cudaMalloc(&h->ctr, sizeof(kc::DevCounters))) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMalloc(counters)"));
     h->fixed_bytes = bloom_bytes + table_bytes + sizeof(kc::DevCounters);
@@ -311,7 +672,7 @@ kc_status kc_reset(kc_handle h) {
     free_batches(h);
     free_result(h);
     KC_CUDA(cudaMemsetAsync(h->bloom, 0, h->bloom_bits / 8, h->stream));
-    KC_CUDA(cudaMemsetAsync(h->table, 0, h->n_slots * sizeof(kc::Slot), h->stream));
+    if (h->table) KC_CUDA(cudaMemsetAsync(h->table, 0, h->n_slots * sizeof(kc::Slot), h->stream));
     KC_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(kc::DevCounters), h->stream));
     h->bases = 0;
     std::memset(&h->host_ctr, 0, sizeof(h->host_ctr));
@@ -322,6 +683,7 @@ kc_status kc_reset(kc_handle h) {
     h->marks.clear();
     for (double& x : h->ms) x = 0.0;
     h->launches = 0;
+    h->fallback_partitions = 0;
     h->state = State::Open;
     return KC_OK;
 }
@@ -421,13 +783,30 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     kc::launch_build_valid(nm, bd, n_units, b0 - B, n_local, h->k, b.vw, h->ctr, h->grid, st);
     phase_end(h, kIngest, t0);
     t0 = phase_begin(h);
-    kc::launch_pass1(b.pw, b.vw, n_units, h->params(sample), h->bloom, h->table, h->ctr, h->grid, st);
+    if (h->strategy == KC_STRATEGY_DIRECT) {
+        kc::launch_pass1(b.pw, b.vw, n_units, h->params(sample), h->bloom, h->table, h->ctr, h->grid, st);
+        h->launches += 3;
+    } else {
+        s = bucket_batch(h, b, n_local, st);
+        if (s != KC_OK) {
+            cudaFreeAsync(nm, st);
+            cudaFreeAsync(bd, st);
+            cudaFreeAsync(doff, st);
+            return s;
+        }
+        h->launches += 7;
+    }
     phase_end(h, kPass1, t0);
-    h->launches += 3;
     KC_CUDA(cudaGetLastError());
     cudaFreeAsync(nm, st);
     cudaFreeAsync(bd, st);
     cudaFreeAsync(doff, st);
+    if (h->strategy != KC_STRATEGY_DIRECT) {
+        // the hashes replace the reads: nothing rescans them
+        cudaFreeAsync(b.pw, st);
+        cudaFreeAsync(b.vw, st);
+        b.pw = b.vw = nullptr;
+    }
     h->batches.push_back(b);
     h->bases += b1 - b0;
     if (any_host) KC_CUDA(cudaEventSynchronize(h->ev_copy));  // caller may reuse its arrays
@@ -438,82 +817,8 @@ kc_status kc_finalize(kc_handle h) {
     kc_status s = check_open(h);
     if (s != KC_OK) return s;
     if (h->state == State::Finalized) return KC_OK;
-    cudaStream_t st = h->stream;
-    cudaEvent_t t0 = phase_begin(h);
-    for (const auto& b : h->batches)
-        kc::launch_pass2(b.pw, b.vw, b.n_units, h->params(b.sample), h->table, h->ctr, h->grid, st);
-    phase_end(h, kPass2, t0);
-    h->launches += h->batches.size();
-    KC_CUDA(cudaGetLastError());
-    if ((s = read_counters(h)) != KC_OK) return s;
-    if ((s = device_errors(h)) != KC_OK) return s;
-
-    // Sort buckets: top B bits of the 2k-bit key, about 512 survivors each.
-    const uint64_t cap = std::max<uint64_t>(1, h->host_ctr.claimed);
-    int bits = 0;
-    while (bits < 22 && bits < 2 * h->k && (cap >> bits) > 512) ++bits;
-    const uint64_t n_buckets = 1ull << bits;
-    const int prefix_shift = 2 * h->k - bits;
-
-    uint64_t *tk = nullptr, *tv = nullptr, *starts = nullptr, *cursor = nullptr;
-    uint32_t* hist = nullptr;
-    cudaError_t e;
-    if ((e = cudaMallocAsync(&tk, cap * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&tv, cap * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&hist, n_buckets * 4, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&starts, (n_buckets + 1) * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&cursor, n_buckets * 8, st)) != cudaSuccess) {
-        cudaFreeAsync(tk, st);
-        cudaFreeAsync(tv, st);
-        cudaFreeAsync(hist, st);
-        cudaFreeAsync(starts, st);
-        cudaFreeAsync(cursor, st);
-        free_result(h);
-        return cuda_fail(e, "cudaMallocAsync(sort buffers)");
-    }
-    h->res_cap = cap;
-    KC_CUDA(cudaMemsetAsync(hist, 0, n_buckets * 4, st));
-    KC_CUDA(cudaMemsetAsync(&h->ctr->survivors, 0, 8, st));
-    t0 = phase_begin(h);
-    kc::launch_compact(h->table, h->n_slots, h->n_samples, h->min_count, tk, tv, h->ctr, hist, prefix_shift, h->grid,
-                       st);
-    phase_end(h, kCompact, t0);
-    t0 = phase_begin(h);
-    kc::launch_scan(hist, n_buckets, starts, cursor, st);
-    kc::launch_scatter(tk, tv, h->ctr, prefix_shift, cursor, h->res_keys, h->res_vals, h->grid, st);
-    kc::launch_bucket_sort(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, st);
-    phase_end(h, kSort, t0);
-    h->launches += 4;
-    KC_CUDA(cudaGetLastError());
-    if ((s = read_counters(h)) != KC_OK) return s;
-    if (h->host_ctr.err & kc::DERR_SORT_BUCKET) {
-        // Rare: a bucket larger than the shared-memory tile; sort it in global memory.
-        std::vector<uint64_t> hs(n_buckets + 1);
-        KC_CUDA(cudaMemcpyAsync(hs.data(), starts, (n_buckets + 1) * 8, cudaMemcpyDeviceToHost, st));
-        KC_CUDA(cudaStreamSynchronize(st));
-        const uint64_t capb = (uint64_t)kc::bucket_sort_capacity();
-        for (uint64_t i = 0; i < n_buckets; ++i)
-            if (hs[i + 1] - hs[i] > capb) {
-                uint64_t n = hs[i + 1] - hs[i], n2 = 1, steps = 0;
-                while (n2 < n) n2 <<= 1;
-                for (uint64_t size = 2; size <= n2; size <<= 1)
-                    for (uint64_t stride = size >> 1; stride > 0; stride >>= 1) ++steps;
-                kc::launch_bitonic_global(h->res_keys + hs[i], h->res_vals + hs[i], n, st);
-                h->launches += steps;
-            }
-        unsigned zero = 0;
-        KC_CUDA(cudaMemcpyAsync(&h->ctr->err, &zero, 4, cudaMemcpyHostToDevice, st));
-        KC_CUDA(cudaGetLastError());
-    }
-    cudaFreeAsync(tk, st);
-    cudaFreeAsync(tv, st);
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(starts, st);
-    cudaFreeAsync(cursor, st);
-    KC_CUDA(cudaStreamSynchronize(st));
-    phase_collect(h);
-    h->n_result = h->host_ctr.survivors;
+    s = h->strategy == KC_STRATEGY_DIRECT ? finalize_direct(h) : finalize_partitioned(h);
+    if (s != KC_OK) return s;
     h->state = State::Finalized;
     return KC_OK;
 }
@@ -564,10 +869,15 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->candidates = h->host_ctr.candidates;
     out->table_keys = h->host_ctr.claimed;
     out->result_keys = h->state == State::Finalized ? h->n_result : 0;
-    out->partitions = 1;
+    out->partitions = h->strategy == KC_STRATEGY_DIRECT ? 1u : (1u << h->part_bits);
     out->table_log2 = (uint32_t)h->log2_slots;
+    out->fallback_partitions = h->fallback_partitions;
+    out->strategy = (uint32_t)h->strategy;
     size_t bytes = h->fixed_bytes + h->res_cap * 16;
-    for (const auto& b : h->batches) bytes += (2 * b.n_units + 2) * 8 + b.n_units * 8;
+    for (const auto& b : h->batches) {
+        if (b.pw) bytes += (2 * b.n_units + 2) * 8 + b.n_units * 8;
+        if (b.hdata) bytes += b.hcap * 8 + ((1ull << h->part_bits) + 1) * 8;
+    }
     out->device_bytes = bytes;
     out->launches = h->launches;
     out->ms_ingest = h->ms[kIngest];

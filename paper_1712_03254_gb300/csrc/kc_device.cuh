@@ -33,6 +33,7 @@ enum : unsigned int {
     DERR_COUNT_OVERFLOW = 2u,  // a per-sample count passed 2^32 - 1
     DERR_OFFSETS = 4u,         // decreasing read offsets
     DERR_SORT_BUCKET = 8u,     // a sort bucket exceeded the shared-memory tile
+    DERR_INTERNAL = 16u,       // a self-check failed (index out of range)
 };
 
 // Parameters shared by the extraction passes.
@@ -56,6 +57,20 @@ __device__ __forceinline__ uint64_t mixer64(uint64_t x) {
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
     return z ^ (z >> 31);
 }
+
+// Inverse of mixer64: undo the closing xor-shift, the two multiplies (by the
+// multipliers' inverses modulo 2^64) and xor-shifts, then the increment.
+// x ^= x >> s is undone by x ^ (x >> s) ^ (x >> 2s) ^ ... while the shift fits.
+__device__ __forceinline__ uint64_t unmixer64(uint64_t z) {
+    z ^= (z >> 31) ^ (z >> 62);
+    z *= 0x319642b2d24d8ec3ull;  // inverse of 0x94d049bb133111eb
+    z ^= (z >> 27) ^ (z >> 54);
+    z *= 0x96de1b173f119089ull;  // inverse of 0xbf58476d1ce4e5b9
+    z ^= (z >> 30) ^ (z >> 60);
+    return z - 0x9e3779b97f4a7c15ull;
+}
+static_assert(0x319642b2d24d8ec3ull * 0x94d049bb133111ebull == 1ull, "multiplier inverse");
+static_assert(0x96de1b173f119089ull * 0xbf58476d1ce4e5b9ull == 1ull, "multiplier inverse");
 
 // Reverse the order of the 32 two-bit groups of x.
 __device__ __forceinline__ uint64_t reverse_pairs(uint64_t x) {
@@ -98,10 +113,13 @@ struct UnitWords {
     uint64_t w0, w1, w2, v;
 };
 
+// Units at or beyond u_end are inactive (zero words); the last active lane
+// loads its successor word itself, since that unit may belong to another
+// lane group or CTA.  All 32 lanes must call this together.
 __device__ __forceinline__ UnitWords load_unit(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw,
-                                               uint64_t u, uint64_t n_units, int lane) {
+                                               uint64_t u, uint64_t u_end, int lane) {
     UnitWords r{0, 0, 0, 0};
-    const bool in = u < n_units;
+    const bool in = u < u_end;
     if (in) {
         r.v = __ldg(vw + u);
         const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(pw) + u);
@@ -109,7 +127,7 @@ __device__ __forceinline__ UnitWords load_unit(const uint64_t* __restrict__ pw, 
         r.w1 = p.y;
     }
     r.w2 = __shfl_down_sync(0xffffffffu, r.w0, 1);
-    if (lane == 31 && in) r.w2 = __ldg(pw + 2 * u + 2);
+    if (in && (lane == 31 || u + 1 >= u_end)) r.w2 = __ldg(pw + 2 * u + 2);
     return r;
 }
 

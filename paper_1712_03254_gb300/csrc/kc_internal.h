@@ -36,8 +36,11 @@ void launch_compact(const Slot* table, uint64_t n_slots, int n_samples, uint32_t
                     cudaStream_t st);
 // starts[0..n] = exclusive scan of hist[0..n); cursor[0..n) = starts[0..n).
 void launch_scan(const uint32_t* hist, uint64_t n, uint64_t* starts, uint64_t* cursor, cudaStream_t st);
-void launch_scatter(const uint64_t* keys, const uint64_t* vals, const DevCounters* ctr, int prefix_shift,
-                    uint64_t* cursor, uint64_t* out_keys, uint64_t* out_vals, const Grid& g, cudaStream_t st);
+// Scatter survivors (at most cap of them) into their buckets; keys whose
+// bucket or position would fall outside the arrays set DERR_INTERNAL.
+void launch_scatter(const uint64_t* keys, const uint64_t* vals, DevCounters* ctr, uint64_t cap, int prefix_shift,
+                    uint64_t n_buckets, uint64_t* cursor, uint64_t* out_keys, uint64_t* out_vals, const Grid& g,
+                    cudaStream_t st);
 // Sort every bucket in place; buckets larger than the shared-memory tile set
 // DERR_SORT_BUCKET and are left for launch_bitonic_global.
 void launch_bucket_sort(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets,
@@ -46,5 +49,68 @@ int bucket_sort_capacity();
 void launch_bitonic_global(uint64_t* keys, uint64_t* vals, uint64_t n, cudaStream_t st);
 
 void launch_counts_narrow(const uint64_t* vals, uint64_t n, uint32_t* out, cudaStream_t st);
+
+// ---- partitioned strategy (kc_partition.cu) --------------------------------
+
+struct ConsumeArgs {
+    const uint64_t* const* data;    // per batch: window hashes grouped by bucket
+    const uint64_t* const* starts;  // per batch: bucket starts, 2^part_bits + 1
+    const int* samples;             // per batch: sample index
+    int n_batches;
+    int part_bits;                  // partitions = 2^part_bits (top bits of h)
+    int slice_log2;                 // filter words per partition
+    int table_log2;                 // shared-memory table slots per partition
+    int bloom_shift;                // 64 - log2(filter words)
+    int n_hashes;
+    int n_samples;
+    int all_candidates;
+    uint32_t min_count;
+    unsigned long long* bloom;
+    uint64_t* out_keys;
+    uint64_t* out_vals;
+    uint64_t out_cap;
+    unsigned long long* n_out;
+    uint32_t* failed;               // partitions left to the fallback
+    uint32_t* n_failed;
+    DevCounters* ctr;
+};
+
+struct FallbackArgs {
+    const uint64_t* const* data;
+    const uint64_t* const* starts;
+    const int* samples;
+    uint32_t part;
+    int part_bits;
+    int bloom_shift;
+    int n_hashes;
+    int n_samples;
+    int all_candidates;
+    uint32_t min_count;
+    unsigned long long* bloom;
+    Slot* table;
+    uint64_t table_mask;
+    uint64_t* out_keys;
+    uint64_t* out_vals;
+    uint64_t out_cap;
+    unsigned long long* n_out;
+    DevCounters* ctr;
+};
+
+size_t bucket_pass_smem(int a);
+void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
+                         int n_ctas, const PassParams& p, int a, uint32_t* counts, cudaStream_t st);
+void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, uint64_t* rel, uint32_t* total,
+                           cudaStream_t st);
+void launch_bucket_base(uint64_t* rel, const uint64_t* starts, int n_ctas, int a, cudaStream_t st);
+void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
+                           int n_ctas, const PassParams& p, int a, const uint64_t* base, uint64_t* out,
+                           cudaStream_t st);
+size_t consume_smem(int slice_log2, int table_log2, int n_samples);
+int launch_part_consume(const ConsumeArgs& A, int n_ctas, cudaStream_t st);
+void launch_fb_claim(const FallbackArgs& F, int bt, cudaStream_t st);
+void launch_fb_recount(const FallbackArgs& F, int bt, cudaStream_t st);
+void launch_fb_compact(const FallbackArgs& F, cudaStream_t st);
+void launch_prefix_hist(const uint64_t* keys, DevCounters* ctr, uint64_t cap, int shift, uint64_t n_buckets,
+                        uint32_t* hist, const Grid& g, cudaStream_t st);
 
 }  // namespace kc

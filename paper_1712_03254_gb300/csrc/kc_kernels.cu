@@ -102,17 +102,24 @@ __global__ void __launch_bounds__(256) k_pass1(const uint64_t* __restrict__ pw, 
     for (uint64_t base = warp * 32; base < n_units; base += n_warps * 32) {
         const UnitWords uw = load_unit(pw, vw, base + lane, n_units, lane);
         uint64_t vm = uw.v;
-        while (vm) {
-            const int j = __clzll(vm);
-            vm &= ~(0x8000000000000000ull >> j);
-            const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
-            const uint64_t h = mixer64(key);
-            const uint64_t pat = bloom_pattern(mixer64(h), p.n_hashes);
-            const unsigned long long old = atomicOr(bloom + (h >> p.bloom_shift), (unsigned long long)pat);
-            if (p.all_candidates || (old & pat) == pat) {
-                ++cand;
-                claimed += table_claim(table, p.table_mask, h >> p.table_shift, key + 1, ctr);
+        // Warp-uniform trip count with a reconvergence point per window, so
+        // the lanes stay together instead of splitting into sub-warps at the
+        // candidate branch.
+        const int n_iter = __reduce_max_sync(kFull, (unsigned)__popcll(vm));
+        for (int it = 0; it < n_iter; ++it) {
+            if (vm) {
+                const int j = __clzll(vm);
+                vm &= ~(0x8000000000000000ull >> j);
+                const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
+                const uint64_t h = mixer64(key);
+                const uint64_t pat = bloom_pattern(mixer64(h), p.n_hashes);
+                const unsigned long long old = atomicOr(bloom + (h >> p.bloom_shift), (unsigned long long)pat);
+                if (p.all_candidates || (old & pat) == pat) {
+                    ++cand;
+                    claimed += table_claim(table, p.table_mask, h >> p.table_shift, key + 1, ctr);
+                }
             }
+            __syncwarp();
         }
     }
     cand = warp_sum(cand);
@@ -132,12 +139,16 @@ __global__ void __launch_bounds__(256) k_pass2(const uint64_t* __restrict__ pw, 
     for (uint64_t base = warp * 32; base < n_units; base += n_warps * 32) {
         const UnitWords uw = load_unit(pw, vw, base + lane, n_units, lane);
         uint64_t vm = uw.v;
-        while (vm) {
-            const int j = __clzll(vm);
-            vm &= ~(0x8000000000000000ull >> j);
-            const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
-            const uint64_t h = mixer64(key);
-            table_count(table, p.table_mask, h >> p.table_shift, key + 1, p.sample, ctr);
+        const int n_iter = __reduce_max_sync(kFull, (unsigned)__popcll(vm));
+        for (int it = 0; it < n_iter; ++it) {
+            if (vm) {
+                const int j = __clzll(vm);
+                vm &= ~(0x8000000000000000ull >> j);
+                const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
+                const uint64_t h = mixer64(key);
+                table_count(table, p.table_mask, h >> p.table_shift, key + 1, p.sample, ctr);
+            }
+            __syncwarp();
         }
     }
 }
@@ -172,7 +183,7 @@ __global__ void k_compact(const Slot* __restrict__ table, uint64_t n_slots, int 
             const uint64_t key = v.x - 1;
             keys[pos] = key;
             vals[pos] = v.y;
-            atomicAdd(hist + (key >> prefix_shift), 1u);
+            if (hist) atomicAdd(hist + (key >> prefix_shift), 1u);
         }
     }
 }
@@ -215,14 +226,23 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ hist
 }
 
 __global__ void k_scatter(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals,
-                          const DevCounters* __restrict__ ctr, int prefix_shift,
+                          DevCounters* __restrict__ ctr, uint64_t cap, int prefix_shift, uint64_t n_buckets,
                           unsigned long long* __restrict__ cursor, uint64_t* __restrict__ out_keys,
                           uint64_t* __restrict__ out_vals) {
-    const uint64_t n = ctr->survivors;
+    const uint64_t n = ctr->survivors < cap ? ctr->survivors : cap;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint64_t key = keys[i];
-        const uint64_t pos = atomicAdd(cursor + (key >> prefix_shift), 1ull);
+        const uint64_t b = key >> prefix_shift;
+        if (b >= n_buckets) {
+            atomicOr(&ctr->err, DERR_INTERNAL);
+            continue;
+        }
+        const uint64_t pos = atomicAdd(cursor + b, 1ull);
+        if (pos >= cap) {
+            atomicOr(&ctr->err, DERR_INTERNAL);
+            continue;
+        }
         out_keys[pos] = key;
         out_vals[pos] = vals[i];
     }
@@ -363,9 +383,10 @@ void launch_scan(const uint32_t* hist, uint64_t n, uint64_t* starts, uint64_t* c
     k_scan<<<1, 1024, 0, st>>>(hist, n, starts, cursor);
 }
 
-void launch_scatter(const uint64_t* keys, const uint64_t* vals, const DevCounters* ctr, int prefix_shift,
-                    uint64_t* cursor, uint64_t* out_keys, uint64_t* out_vals, const Grid& g, cudaStream_t st) {
-    k_scatter<<<g.sm_count * 8, 256, 0, st>>>(keys, vals, ctr, prefix_shift,
+void launch_scatter(const uint64_t* keys, const uint64_t* vals, DevCounters* ctr, uint64_t cap, int prefix_shift,
+                    uint64_t n_buckets, uint64_t* cursor, uint64_t* out_keys, uint64_t* out_vals, const Grid& g,
+                    cudaStream_t st) {
+    k_scatter<<<g.sm_count * 8, 256, 0, st>>>(keys, vals, ctr, cap, prefix_shift, n_buckets,
                                                reinterpret_cast<unsigned long long*>(cursor), out_keys, out_vals);
 }
 

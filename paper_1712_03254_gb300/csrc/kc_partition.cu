@@ -1,0 +1,381 @@
+// Partitioned counting path (sm_103a): hash-prefix buckets in HBM, one
+// partition's filter slice and table in shared memory.
+//
+// The paper splits the k-mers of each chunk by the consumer thread that owns
+// them with a counting-sort shuffle (histogram, prefix sum, broker copy;
+// Section III-B) so that every consumer updates only its own structures
+// (two-level partitioning, Section II-B).  Here the consumer is a CTA and its
+// structures live in shared memory:
+//
+//   ingest (per kc_add_reads call)
+//     k_bucket_pass<false>  per window: canonical key, h = mixer64(key),
+//                           bucket = top a bits of h; per-CTA histogram in
+//                           shared memory, written out CTA-major (no global
+//                           atomics)
+//     k_bucket_offsets      per bucket: exclusive prefix over CTAs
+//     (scan)                bucket starts
+//     k_bucket_base         absolute start of every (CTA, bucket) run
+//     k_bucket_pass<true>   the same windows again; each h is stored at its
+//                           CTA's run of its bucket (shared-memory cursors)
+//   finalize
+//     k_part_consume        one CTA per bucket ("partition"): the filter words
+//                           of the partition (a contiguous slice, since the
+//                           filter word is also a prefix of h) and an open-
+//                           addressing table in shared memory; filter update,
+//                           candidate claims, exact recount, compaction of
+//                           survivors (key recovered by unmixer64), slice
+//                           written back to the global filter.  A partition
+//                           whose table overflows is left to the fallback.
+//     k_fb_*                fallback for such partitions: the same steps with
+//                           the partition's filter slice and a table in global
+//                           memory.
+
+#include "kc_internal.h"
+
+namespace kc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kProbeLimit = 64;  // shared-memory table probes before a partition falls back
+
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+template <bool kScatter>
+__global__ void __launch_bounds__(512) k_bucket_pass(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw,
+                                                     uint64_t n_units, uint64_t units_per_cta, PassParams p, int a,
+                                                     uint32_t* __restrict__ counts,
+                                                     const uint64_t* __restrict__ base,
+                                                     uint64_t* __restrict__ out) {
+    extern __shared__ uint32_t s_cnt[];
+    const uint32_t P = 1u << a;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    const uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
+    const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint64_t* my_base = kScatter ? base + (uint64_t)blockIdx.x * P : nullptr;
+    for (uint64_t g = lo + (uint64_t)wid * 32; g < hi; g += (uint64_t)nwarps * 32) {
+        const UnitWords uw = load_unit(pw, vw, g + lane, hi, lane);
+        uint64_t vm = uw.v;
+        const int n_iter = __reduce_max_sync(kFull, (unsigned)__popcll(vm));
+        for (int it = 0; it < n_iter; ++it) {
+            if (vm) {
+                const int j = __clzll(vm);
+                vm &= ~(0x8000000000000000ull >> j);
+                const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
+                const uint64_t h = mixer64(key);
+                const uint32_t b = (uint32_t)(h >> (64 - a));
+                const uint32_t r = atomicAdd(&s_cnt[b], 1u);
+                if (kScatter) out[__ldg(my_base + b) + r] = h;
+            }
+            __syncwarp();
+        }
+    }
+    if (!kScatter) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[(uint64_t)blockIdx.x * P + i] = s_cnt[i];
+    }
+}
+
+// rel[c][b] = sum of counts[c'][b] over c' < c; total[b] = sum over all CTAs.
+// One thread per bucket; the column is read 16 CTAs at a time so that the
+// loads are independent and in flight together.
+__global__ void k_bucket_offsets(const uint32_t* __restrict__ counts, int n_ctas, uint32_t P,
+                                 uint64_t* __restrict__ rel, uint32_t* __restrict__ total) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= P) return;
+    uint64_t run = 0;
+    for (int c0 = 0; c0 < n_ctas; c0 += 16) {
+        uint32_t x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = c0 + j < n_ctas ? __ldg(counts + (uint64_t)(c0 + j) * P + b) : 0u;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (c0 + j < n_ctas) rel[(uint64_t)(c0 + j) * P + b] = run;
+            run += x[j];
+        }
+    }
+    total[b] = (uint32_t)run;
+}
+
+__global__ void k_bucket_base(uint64_t* __restrict__ rel, const uint64_t* __restrict__ starts, int n_ctas,
+                              uint32_t P) {
+    const uint64_t n = (uint64_t)n_ctas * P;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) rel[i] += starts[i % P];
+}
+
+// Shared-memory table: keys[T] hold (h & low_mask) + 1 (0 = empty), counts
+// follow as n_samples uint32 per slot.  Returns 1 = claimed, 0 = present,
+// -1 = no free slot within kProbeLimit probes.
+__device__ __forceinline__ int smem_claim(unsigned long long* keys, uint32_t tmask, uint32_t s,
+                                          unsigned long long stored) {
+    for (int i = 0; i < kProbeLimit; ++i) {
+        const unsigned long long cur = keys[s];
+        if (cur == stored) return 0;
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(&keys[s], 0ull, stored);
+            if (prev == 0ull) return 1;
+            if (prev == stored) return 0;
+        }
+        s = (s + 1) & tmask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int smem_find(const unsigned long long* keys, uint32_t tmask, uint32_t s,
+                                         unsigned long long stored) {
+    for (uint32_t i = 0; i <= tmask; ++i) {
+        const unsigned long long cur = keys[s];
+        if (cur == stored) return (int)s;
+        if (cur == 0ull) return -1;
+        s = (s + 1) & tmask;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(512) k_part_consume(ConsumeArgs A) {
+    extern __shared__ unsigned long long s_mem[];
+    const uint32_t n_sw = 1u << A.slice_log2;  // filter words of one partition
+    const uint32_t T = 1u << A.table_log2;
+    const uint32_t tmask = T - 1;
+    unsigned long long* sb = s_mem;
+    unsigned long long* sk = s_mem + n_sw;
+    uint32_t* sc = reinterpret_cast<uint32_t*>(s_mem + n_sw + T);
+    __shared__ int s_fail;
+    const int S = A.n_samples;
+    const int a = A.part_bits;
+    const uint64_t low_mask = (1ull << (64 - a)) - 1ull;
+    const int home_shift = 64 - a - A.table_log2;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t cand = 0, claimed = 0;
+
+    for (uint32_t part = blockIdx.x; part < (1u << a); part += gridDim.x) {
+        for (uint32_t i = threadIdx.x; i < n_sw; i += blockDim.x) sb[i] = 0ull;
+        for (uint32_t i = threadIdx.x; i < T; i += blockDim.x) sk[i] = 0ull;
+        for (uint32_t i = threadIdx.x; i < T * S; i += blockDim.x) sc[i] = 0u;
+        if (threadIdx.x == 0) s_fail = 0;
+        __syncthreads();
+        // filter update and candidate claims
+        for (int bt = 0; bt < A.n_batches; ++bt) {
+            const uint64_t* __restrict__ d = A.data[bt];
+            const uint64_t lo = A.starts[bt][part], hi = A.starts[bt][part + 1];
+            for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const uint64_t h = __ldcs(d + i);
+                const uint32_t w = (uint32_t)(h >> A.bloom_shift) & (n_sw - 1);
+                const uint64_t pat = bloom_pattern(mixer64(h), A.n_hashes);
+                const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
+                if (A.all_candidates || (old & pat) == pat) {
+                    ++cand;
+                    const int r = smem_claim(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
+                    if (r < 0) s_fail = 1;
+                    else claimed += (uint64_t)r;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            if (threadIdx.x == 0) A.failed[atomicAdd(A.n_failed, 1u)] = part;
+            __syncthreads();
+            continue;
+        }
+        // exact recount
+        for (int bt = 0; bt < A.n_batches; ++bt) {
+            const uint64_t* __restrict__ d = A.data[bt];
+            const int smp = A.samples[bt];
+            const uint64_t lo = A.starts[bt][part], hi = A.starts[bt][part + 1];
+            for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const uint64_t h = __ldcs(d + i);
+                const int s = smem_find(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
+                if (s >= 0) atomicAdd(sc + (uint32_t)s * S + smp, 1u);
+            }
+        }
+        __syncthreads();
+        // survivors: key = unmixer64(h), counts packed little-endian
+        const uint64_t hpre = (uint64_t)part << (64 - a);
+        for (uint32_t i0 = threadIdx.x & ~31u; i0 < T; i0 += blockDim.x) {
+            const uint32_t i = i0 + lane;
+            const unsigned long long k1 = sk[i];
+            uint64_t v = 0;
+            bool keep = false;
+            if (k1 != 0ull) {
+                const uint32_t c0 = sc[i * S];
+                const uint32_t c1 = S == 2 ? sc[i * S + 1] : 0u;
+                keep = (uint64_t)c0 + c1 >= A.min_count;
+                v = (uint64_t)c0 | ((uint64_t)c1 << 32);
+            }
+            const unsigned ballot = __ballot_sync(kFull, keep);
+            if (ballot) {
+                const int leader = __ffs(ballot) - 1;
+                unsigned long long pos0 = 0;
+                if (lane == leader) pos0 = atomicAdd(A.n_out, (unsigned long long)__popc(ballot));
+                pos0 = __shfl_sync(kFull, pos0, leader);
+                if (keep) {
+                    const uint64_t pos = pos0 + __popc(ballot & lt);
+                    if (pos < A.out_cap) {
+                        A.out_keys[pos] = unmixer64(hpre | (k1 - 1ull));
+                        A.out_vals[pos] = v;
+                    }
+                }
+            }
+        }
+        // the partition's filter words
+        unsigned long long* gb = A.bloom + (uint64_t)part * n_sw;
+        for (uint32_t i = threadIdx.x; i < n_sw; i += blockDim.x) gb[i] = sb[i];
+        __syncthreads();
+    }
+    cand = warp_sum64(cand);
+    claimed = warp_sum64(claimed);
+    if (lane == 0) {
+        if (cand) atomicAdd(&A.ctr->candidates, (unsigned long long)cand);
+        if (claimed) atomicAdd(&A.ctr->claimed, (unsigned long long)claimed);
+    }
+}
+
+// ---- fallback for partitions whose shared-memory table overflowed ----------
+
+__global__ void k_fb_claim(FallbackArgs F, int bt) {
+    const uint64_t* __restrict__ d = F.data[bt];
+    const uint64_t lo = F.starts[bt][F.part], hi = F.starts[bt][F.part + 1];
+    const uint64_t low_mask = (1ull << (64 - F.part_bits)) - 1ull;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t cand = 0, claimed = 0;
+    for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride) {
+        const uint64_t h = d[i];
+        const uint64_t pat = bloom_pattern(mixer64(h), F.n_hashes);
+        const unsigned long long old = atomicOr(F.bloom + (h >> F.bloom_shift), (unsigned long long)pat);
+        if (F.all_candidates || (old & pat) == pat) {
+            ++cand;
+            claimed += table_claim(F.table, F.table_mask, (h & low_mask) & F.table_mask, (h & low_mask) + 1ull,
+                                   F.ctr);
+        }
+    }
+    cand = warp_sum64(cand);
+    claimed = warp_sum64(claimed);
+    if ((threadIdx.x & 31) == 0) {
+        if (cand) atomicAdd(&F.ctr->candidates, (unsigned long long)cand);
+        if (claimed) atomicAdd(&F.ctr->claimed, (unsigned long long)claimed);
+    }
+}
+
+__global__ void k_fb_recount(FallbackArgs F, int bt) {
+    const uint64_t* __restrict__ d = F.data[bt];
+    const uint64_t lo = F.starts[bt][F.part], hi = F.starts[bt][F.part + 1];
+    const uint64_t low_mask = (1ull << (64 - F.part_bits)) - 1ull;
+    const int smp = F.samples[bt];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride) {
+        const uint64_t h = d[i];
+        table_count(F.table, F.table_mask, (h & low_mask) & F.table_mask, (h & low_mask) + 1ull, smp, F.ctr);
+    }
+}
+
+__global__ void k_fb_compact(FallbackArgs F) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint64_t n = F.table_mask + 1;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t hpre = (uint64_t)F.part << (64 - F.part_bits);
+    for (uint64_t b0 = warp * 32; b0 < n; b0 += n_warps * 32) {
+        const uint64_t i = b0 + lane;
+        bool keep = false;
+        ulonglong2 v = make_ulonglong2(0, 0);
+        if (i < n) {
+            v = *reinterpret_cast<const ulonglong2*>(F.table + i);
+            if (v.x != 0ull) {
+                uint64_t sum = (uint32_t)v.y;
+                if (F.n_samples == 2) sum += (uint32_t)(v.y >> 32);
+                keep = sum >= F.min_count;
+            }
+        }
+        const unsigned ballot = __ballot_sync(kFull, keep);
+        if (!ballot) continue;
+        const int leader = __ffs(ballot) - 1;
+        unsigned long long pos0 = 0;
+        if (lane == leader) pos0 = atomicAdd(F.n_out, (unsigned long long)__popc(ballot));
+        pos0 = __shfl_sync(kFull, pos0, leader);
+        if (keep) {
+            const uint64_t pos = pos0 + __popc(ballot & lt);
+            if (pos < F.out_cap) {
+                F.out_keys[pos] = unmixer64(hpre | (v.x - 1ull));
+                F.out_vals[pos] = v.y;
+            }
+        }
+    }
+}
+
+__global__ void k_prefix_hist(const uint64_t* __restrict__ keys, DevCounters* __restrict__ ctr, uint64_t cap,
+                              int shift, uint64_t n_buckets, uint32_t* __restrict__ hist) {
+    const uint64_t n = ctr->survivors < cap ? ctr->survivors : cap;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t b = keys[i] >> shift;
+        if (b < n_buckets) atomicAdd(hist + b, 1u);
+        else atomicOr(&ctr->err, DERR_INTERNAL);
+    }
+}
+
+}  // namespace
+
+size_t bucket_pass_smem(int a) { return sizeof(uint32_t) << a; }
+
+void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
+                         int n_ctas, const PassParams& p, int a, uint32_t* counts, cudaStream_t st) {
+    const size_t smem = bucket_pass_smem(a);
+    cudaFuncSetAttribute(k_bucket_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bucket_pass<false><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts, nullptr, nullptr);
+}
+
+void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, uint64_t* rel, uint32_t* total,
+                           cudaStream_t st) {
+    const uint32_t P = 1u << a;
+    k_bucket_offsets<<<(P + 63) / 64, 64, 0, st>>>(counts, n_ctas, P, rel, total);
+}
+
+void launch_bucket_base(uint64_t* rel, const uint64_t* starts, int n_ctas, int a, cudaStream_t st) {
+    const uint64_t n = (uint64_t)n_ctas << a;
+    unsigned grid = (unsigned)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    k_bucket_base<<<grid, 256, 0, st>>>(rel, starts, n_ctas, 1u << a);
+}
+
+void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
+                           int n_ctas, const PassParams& p, int a, const uint64_t* base, uint64_t* out,
+                           cudaStream_t st) {
+    const size_t smem = bucket_pass_smem(a);
+    cudaFuncSetAttribute(k_bucket_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bucket_pass<true><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, nullptr, base, out);
+}
+
+size_t consume_smem(int slice_log2, int table_log2, int n_samples) {
+    return (sizeof(uint64_t) << slice_log2) + (sizeof(uint64_t) << table_log2) +
+           ((sizeof(uint32_t) * (size_t)n_samples) << table_log2);
+}
+
+int launch_part_consume(const ConsumeArgs& A, int n_ctas, cudaStream_t st) {
+    const size_t smem = consume_smem(A.slice_log2, A.table_log2, A.n_samples);
+    cudaError_t e = cudaFuncSetAttribute(k_part_consume, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k_part_consume<<<n_ctas, 512, smem, st>>>(A);
+    return 0;
+}
+
+void launch_fb_claim(const FallbackArgs& F, int bt, cudaStream_t st) { k_fb_claim<<<1024, 256, 0, st>>>(F, bt); }
+void launch_fb_recount(const FallbackArgs& F, int bt, cudaStream_t st) {
+    k_fb_recount<<<1024, 256, 0, st>>>(F, bt);
+}
+void launch_fb_compact(const FallbackArgs& F, cudaStream_t st) { k_fb_compact<<<1024, 256, 0, st>>>(F); }
+
+void launch_prefix_hist(const uint64_t* keys, DevCounters* ctr, uint64_t cap, int shift, uint64_t n_buckets,
+                        uint32_t* hist, const Grid& g, cudaStream_t st) {
+    k_prefix_hist<<<g.sm_count * 4, 256, 0, st>>>(keys, ctr, cap, shift, n_buckets, hist);
+}
+
+}  // namespace kc

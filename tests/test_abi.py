@@ -96,3 +96,15 @@ def test_pack_ascii_matches_format(n):
     ref_p, ref_m = _pack_reference(ascii.tobytes())
     assert np.array_equal(packed, ref_p)
     assert np.array_equal(mask, ref_m)
+
+
+@pytest.mark.parametrize("bloom_log2,part_bits,ok", [(24, 1, False), (24, 4, False), (24, 5, True), (24, 15, False),
+                                                     (20, 1, True), (36, 14, False)])
+def test_partitioned_slice_limit(bloom_log2, part_bits, ok):
+    """The partitioned strategy keeps one partition's filter words (at most
+    8192) in shared memory; larger slices are rejected before any CUDA call."""
+    if ok:
+        pytest.skip("valid configurations need a GPU to create")
+    with pytest.raises(kc.KcError) as e:
+        kc.KmerCounter(31, 1, 1 << bloom_log2, 4, 2, strategy="partitioned", part_bits=part_bits)
+    assert e.value.name == "KC_ERR_ARG"

@@ -23,9 +23,17 @@ def _cuda():
     kc.lib()
 
 
+STRATEGIES = ["direct", "partitioned"]
+
+
+@pytest.fixture(params=STRATEGIES)
+def strategy(request):
+    return request.param
+
+
 def gpu_count(w, batches=1, **kw):
-    c = kc.KmerCounter(w.k, len(w.samples), w.bloom_bits, w.n_hashes, w.min_count,
-                       table_slots=w.table_slots, **kw)
+    kw.setdefault("table_slots", w.table_slots)
+    c = kc.KmerCounter(w.k, len(w.samples), w.bloom_bits, w.n_hashes, w.min_count, **kw)
     for s, rs in enumerate(w.samples):
         if batches == 1:
             c.add_readset(s, rs)
@@ -49,11 +57,11 @@ def assert_same_bloom(c, o):
     assert np.array_equal(c.export_bloom(), o.bloom())
 
 
-def test_tiny_full_parity(oracle_mod):
+def test_tiny_full_parity(oracle_mod, strategy):
     """20,000 x 100 bp reads, k=31, 2^24-bit filter, 4 hashes, min_count 2."""
     w = synth.tiny()
     o = oracle_mod.count(w)
-    c = gpu_count(w)
+    c = gpu_count(w, strategy=strategy)
     assert_same_result(c, o)
     assert_same_bloom(c, o)
     st = c.stats()
@@ -63,7 +71,7 @@ def test_tiny_full_parity(oracle_mod):
 
 @pytest.mark.parametrize("k", [1, 2, 5, 8, 16, 25, 31])
 @pytest.mark.parametrize("min_count", [1, 2, 3])
-def test_ragged_random_reads(oracle_mod, k, min_count):
+def test_ragged_random_reads(oracle_mod, k, min_count, strategy):
     """Read lengths 0..300 (shorter than k, exactly k, across word boundaries), 2 % N."""
     rng = random.Random(31 * k + min_count)
     g = "".join(rng.choice("ACGT") for _ in range(3000))
@@ -79,38 +87,38 @@ def test_ragged_random_reads(oracle_mod, k, min_count):
         reads.append("".join(r))
     w = synth.Workload("ragged", [synth.ReadSet.from_strings(reads)], k, 1 << 16, 3, min_count)
     o = oracle_mod.count(w)
-    c = gpu_count(w, table_slots=1 << 16)
+    c = gpu_count(w, table_slots=1 << 16, strategy=strategy)
     assert_same_result(c, o)
     assert_same_bloom(c, o)
     assert c.stats()["windows"] == o.windows
 
 
-def test_n_at_every_position(oracle_mod):
+def test_n_at_every_position(oracle_mod, strategy):
     k = 7
     base = "ACGTTGCAACGTAGGCTAAC"
     reads = [base[:i] + "N" + base[i + 1 :] for i in range(len(base))] + [base, "N" * 40, "NACGTACGN"]
     w = synth.Workload("nmask", [synth.ReadSet.from_strings(reads)], k, 1 << 12, 2, 1)
     o = oracle_mod.count(w)
-    c = gpu_count(w, table_slots=1 << 12)
+    c = gpu_count(w, table_slots=1 << 12, strategy=strategy)
     assert_same_result(c, o)
     assert_same_bloom(c, o)
 
 
-def test_empty_and_degenerate_inputs(oracle_mod):
+def test_empty_and_degenerate_inputs(oracle_mod, strategy):
     for reads in ([], [""], ["", "", ""], ["ACG"], ["NNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNNN"]):
         w = synth.Workload("empty", [synth.ReadSet.from_strings(reads)], 5, 1 << 12, 4, 1)
         o = oracle_mod.count(w)
-        c = gpu_count(w, table_slots=1 << 12)
+        c = gpu_count(w, table_slots=1 << 12, strategy=strategy)
         assert_same_result(c, o)
         assert c.result_size() == 0
         assert_same_bloom(c, o)
 
 
-def test_several_batches_and_offset_base(oracle_mod):
+def test_several_batches_and_offset_base(oracle_mod, strategy):
     """Reads added in uneven batches, with offsets not starting at 0 (unaligned base)."""
     w = synth.tiny(scale=0.2)
     o = oracle_mod.count(w)
-    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count)
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, strategy=strategy)
     rs = w.samples[0]
     packed, mask = kc.pack_ascii(rs.ascii)
     cuts = [0, 1, 7, 500, 1333, 2000, rs.n_reads]
@@ -122,17 +130,17 @@ def test_several_batches_and_offset_base(oracle_mod):
     assert_same_bloom(c, o)
 
 
-def test_two_samples_joint_table(oracle_mod):
+def test_two_samples_joint_table(oracle_mod, strategy):
     w = synth.paired(scale=0.002)
     o = oracle_mod.count(w)
-    c = gpu_count(w)
+    c = gpu_count(w, strategy=strategy)
     assert_same_result(c, o)
     assert_same_bloom(c, o)
     gk, gc = c.dump()
     assert gc.shape[1] == 2 and gc[:, 0].sum() > 0 and gc[:, 1].sum() > 0
 
 
-def test_device_resident_inputs(oracle_mod):
+def test_device_resident_inputs(oracle_mod, strategy):
     torch = pytest.importorskip("torch")
     w = synth.tiny(scale=0.3)
     o = oracle_mod.count(w)
@@ -142,7 +150,7 @@ def test_device_resident_inputs(oracle_mod):
     dm = torch.from_numpy(mask.view(np.int64)).cuda()
     do = torch.from_numpy(rs.offsets.view(np.int64)).cuda()
     torch.cuda.synchronize()
-    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count)
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, strategy=strategy)
     c.add_reads(0, dp, do, dm)
     c.finalize()
     n = c.result_size()
@@ -157,10 +165,10 @@ def test_device_resident_inputs(oracle_mod):
     assert np.array_equal(bloom.cpu().numpy().view(np.uint64), o.bloom())
 
 
-def test_reset_reuses_handle(oracle_mod):
+def test_reset_reuses_handle(oracle_mod, strategy):
     w = synth.tiny(scale=0.25)
     o = oracle_mod.count(w)
-    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count)
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, strategy=strategy)
     for _ in range(3):
         c.add_readset(0, w.samples[0])
         c.finalize()
@@ -172,7 +180,7 @@ def test_reset_reuses_handle(oracle_mod):
 def test_errors_are_reported_not_faulted(oracle_mod):
     w = synth.tiny(scale=0.2)
     # table far too small: probes are bounded, the job reports KC_ERR_CAPACITY
-    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=1024)
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=1024, strategy="direct")
     c.add_readset(0, w.samples[0])
     with pytest.raises(kc.KcError) as e:
         c.finalize()
@@ -181,6 +189,8 @@ def test_errors_are_reported_not_faulted(oracle_mod):
         c.finalize()
     assert e.value.name == "KC_ERR_STATE"
     c.reset()
+    c.close()
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count)
     # decreasing offsets are rejected on the host
     packed, mask = kc.pack_ascii(np.frombuffer(b"ACGT" * 40, dtype=np.uint8))
     with pytest.raises(kc.KcError) as e:
@@ -198,14 +208,42 @@ def test_errors_are_reported_not_faulted(oracle_mod):
     assert e.value.name == "KC_ERR_CAPACITY"
 
 
-def test_mid_full_size_sampled_partitions(oracle_mod):
+def test_partition_fallback_matches(oracle_mod):
+    """Two partitions with 1024-slot shared-memory tables cannot hold tiny's
+    candidates: every partition takes the global-memory fallback."""
+    w = synth.tiny(scale=0.5)
+    w.bloom_bits = 1 << 20  # 2 partitions of 8192 filter words
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", part_bits=1, smem_table_log2=10)
+    st = c.stats()
+    assert st["fallback_partitions"] == 2
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    # sixteen partitions of about 6,100 candidates each, 4096-slot tables
+    c = gpu_count(w, strategy="partitioned", part_bits=4, smem_table_log2=12)
+    assert c.stats()["fallback_partitions"] == 16
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+@pytest.mark.parametrize("part_bits", [5, 8, 10, 14])
+def test_partition_counts(oracle_mod, part_bits):
+    w = synth.tiny(scale=0.3)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", part_bits=part_bits)
+    assert c.stats()["partitions"] == 1 << part_bits
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+def test_mid_full_size_sampled_partitions(oracle_mod, strategy):
     """1,000,000 x 150 bp, 2^30-bit filter, 2^24 slots: the configuration the
     benchmark times.  The oracle counts four of 64 hash partitions in full;
     the GPU result restricted to them, and their filter words, must match."""
     w = synth.mid()
     q, parts = 6, [0, 17, 42, 63]
     o = oracle_mod.count(w, restrict=(q, parts))
-    c = gpu_count(w)
+    c = gpu_count(w, strategy=strategy)
     gk, gc = c.dump()
     sel = np.isin(oracle_mod.partitions(gk, q), parts)
     ok, oc = o.result()

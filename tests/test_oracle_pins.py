@@ -96,6 +96,13 @@ def test_edge_reads(oracle_mod):
     assert o.windows == _brute.n_valid_windows(reads, k)
 
 
+def test_empty_read_sets(oracle_mod):
+    for reads in ([], [""], ["", "", ""], ["ACG"], ["N" * 40]):
+        o, got = _oracle_result(oracle_mod, [reads], 5, 1)
+        assert got == [] and o.windows == 0
+        assert not o.bloom().any()
+
+
 def test_even_k_palindrome(oracle_mod):
     # ACGT is its own reverse complement: fwd == rc, counted once per window.
     _, got = _oracle_result(oracle_mod, [["ACGT", "ACGT", "TTTT"]], 4, 1)
