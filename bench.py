@@ -180,7 +180,7 @@ def measured_hbm_peak():
 def _kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1712_03254_gb300", "csrc")
-    for f in ("kc_device.cuh", "kc_kernels.cu"):
+    for f in ("kc_device.cuh", "kc_kernels.cu", "kc_partition.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -208,9 +208,10 @@ def roofline_of(st, phases, rs, w):
       direct     pass1: reads + filter read and written once + 32 B per claimed
                  key; pass2: reads + 32 B per claimed key (slot read, counts
                  written)
-      partitioned bucketing (count + scatter): reads twice + 8 B hash written
-                 per window; consumer: 8 B hash read per window + filter
-                 written once + 16 B per result key
+      partitioned bucketing (extraction + staged scatter): reads once + 8 B
+                 hash written per window into its partition (the linear array
+                 in between is implementation traffic); consumer: 8 B hash read
+                 per window + filter written once + 16 B per result key
     """
     import statistics as _st
 
@@ -222,7 +223,7 @@ def roofline_of(st, phases, rs, w):
         table = {"pass1": ("k_pass1", read_bytes + 2 * bloom_bytes + 32 * st["table_keys"]),
                  "pass2": ("k_pass2", read_bytes + 32 * st["table_keys"])}
     else:
-        table = {"pass1": ("k_bucket_pass (count + scatter)", 2 * read_bytes + 8 * W),
+        table = {"pass1": ("k_extract_count + k_scatter_staged_lin (bucketing)", read_bytes + 8 * W),
                  "pass2": ("k_part_consume", 8 * W + bloom_bytes + 16 * st["result_keys"])}
     phase = max(table, key=lambda k: mean[k])
     kernel, algo = table[phase]
@@ -294,7 +295,8 @@ def run_kc(args):
     torch.cuda.synchronize()
 
     c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots, timing=True,
-                       strategy=args.strategy, stream=stream)
+                       strategy=args.strategy, scatter_mode=args.scatter_mode, ctas_per_sm=args.ctas_per_sm,
+                       stream=stream)
 
     # size result buffers with one untimed job
     c.add_reads(0, d_packed, d_off, d_mask)
@@ -444,6 +446,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--strategy", choices=["auto", "direct", "partitioned"], default="auto")
+    ap.add_argument("--scatter-mode", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -91,7 +91,14 @@ typedef struct kc_config {
     uint32_t strategy;            /* KC_STRATEGY_*                                  */
     uint32_t smem_table_log2;     /* partitioned: log2 shared-memory table slots of
                                      one partition (10..13)                         */
-    uint64_t reserved[5];
+    uint32_t scatter_mode;        /* partitioned ingest: 1 = one global cursor per
+                                     partition, 2 = one exact run per (CTA,
+                                     partition), 3 = runs padded to whole 32-byte
+                                     sectors, staged in shared memory, 4 = as 3,
+                                     from hashes first written per CTA to a linear
+                                     array (default)                                */
+    uint32_t reserved1;
+    uint64_t reserved[4];
 } kc_config;
 
 /*

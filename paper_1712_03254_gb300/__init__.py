@@ -38,7 +38,7 @@ class Config(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("part_bits", ctypes.c_uint32),
                 ("table_slots", ctypes.c_uint64), ("spill", ctypes.c_uint32), ("timing", ctypes.c_uint32),
                 ("strategy", ctypes.c_uint32), ("smem_table_log2", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint64 * 5)]
+                ("scatter_mode", ctypes.c_uint32), ("reserved1", ctypes.c_uint32), ("reserved", ctypes.c_uint64 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -132,7 +132,8 @@ class KmerCounter:
 
     def __init__(self, k: int, n_samples: int, bloom_bits: int, n_hashes: int = 4, min_count: int = 2,
                  table_slots: int = 0, part_bits: int = 0, spill: bool = False, ctas_per_sm: int = 0,
-                 timing: bool = False, strategy: str = "auto", smem_table_log2: int = 0, stream=None):
+                 timing: bool = False, strategy: str = "auto", smem_table_log2: int = 0, scatter_mode: int = 0,
+                 stream=None):
         L = lib()
         cfg = Config()
         L.kc_default_config(ctypes.byref(cfg))
@@ -143,6 +144,7 @@ class KmerCounter:
         cfg.timing = 1 if timing else 0
         cfg.strategy = {"auto": 0, "direct": 1, "partitioned": 2}[strategy]
         cfg.smem_table_log2 = smem_table_log2
+        cfg.scatter_mode = scatter_mode
         h = ctypes.c_void_p()
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream

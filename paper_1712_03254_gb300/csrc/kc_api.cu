@@ -225,51 +225,73 @@ kc_status device_errors(kc_handle h) {
 kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st) {
     const int a = h->part_bits;
     const uint64_t P = 1ull << a;
-    const int max_ctas = h->grid.sm_count * 2;
+    int mode = h->cfg.scatter_mode ? (int)h->cfg.scatter_mode : 4;
+    int max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (mode >= 3 && kc::staged_scatter_smem(a) > (size_t)max_optin) mode = 2;
+    const int max_ctas = h->grid.sm_count * (h->cfg.ctas_per_sm ? (int)h->cfg.ctas_per_sm : 1);
     const uint64_t upc = std::max<uint64_t>(1, (b.n_units + max_ctas - 1) / max_ctas);
     const int n_ctas = (int)((b.n_units + upc - 1) / upc);
-    uint32_t* counts = nullptr;
-    uint32_t* total = nullptr;
-    uint64_t *rel = nullptr, *cursor = nullptr;
-    b.hcap = n_local;  // at most one window per base
-    cudaError_t e;
+    uint32_t *counts = nullptr, *total = nullptr;
+    uint64_t *rel = nullptr, *cursor = nullptr, *lin = nullptr, *seg = nullptr;
+    // at most one window per base, plus run padding of up to 3 per (CTA, partition)
+    b.hcap = n_local + (mode >= 3 ? 3ull * (uint64_t)n_ctas * P : 0ull);
+    cudaError_t e = cudaSuccess;
+    auto bail = [&](cudaError_t err) {
+        if (counts) cudaFreeAsync(counts, st);
+        if (rel) cudaFreeAsync(rel, st);
+        if (total) cudaFreeAsync(total, st);
+        if (cursor) cudaFreeAsync(cursor, st);
+        if (lin) cudaFreeAsync(lin, st);
+        if (seg) cudaFreeAsync(seg, st);
+        if (b.hstarts) cudaFreeAsync(b.hstarts, st);
+        if (b.hdata) cudaFreeAsync(b.hdata, st);
+        b.hstarts = b.hdata = nullptr;
+        return cuda_fail(err, "cudaMallocAsync(partition buckets)");
+    };
     if ((e = cudaMallocAsync(&counts, (size_t)n_ctas * P * 4, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&rel, (size_t)n_ctas * P * 8, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&total, P * 4, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&cursor, P * 8, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&b.hstarts, (P + 1) * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, b.hcap) * 8, st)) != cudaSuccess) {
-        cudaFreeAsync(counts, st);
-        cudaFreeAsync(rel, st);
-        cudaFreeAsync(total, st);
-        cudaFreeAsync(cursor, st);
-        if (b.hstarts) cudaFreeAsync(b.hstarts, st);
-        if (b.hdata) cudaFreeAsync(b.hdata, st);
-        b.hstarts = b.hdata = nullptr;
-        return cuda_fail(e, "cudaMallocAsync(partition buckets)");
-    }
+        (e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, b.hcap) * 8, st)) != cudaSuccess)
+        return bail(e);
+    if (mode == 4 && ((e = cudaMallocAsync(&lin, std::max<uint64_t>(1, n_local) * 8, st)) != cudaSuccess ||
+                      (e = cudaMallocAsync(&seg, (size_t)n_ctas * 16 + 8, st)) != cudaSuccess))
+        return bail(e);
     const kc::PassParams p = h->params(b.sample);
-    kc::launch_bucket_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, st);
-    kc::launch_bucket_offsets(counts, n_ctas, a, rel, total, st);
-    kc::launch_scan(total, P, b.hstarts, cursor, st);
-    kc::launch_bucket_base(rel, b.hstarts, n_ctas, a, st);
-    kc::launch_bucket_scatter(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, rel, b.hdata, st);
+    if (mode == 4) {
+        uint64_t* g_cursor = seg + 2 * (size_t)n_ctas;
+        KC_CUDA(cudaMemsetAsync(g_cursor, 0, 8, st));
+        kc::launch_extract_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, g_cursor, seg, lin, st);
+    } else {
+        kc::launch_bucket_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, st);
+    }
+    kc::launch_bucket_offsets(counts, n_ctas, a, mode >= 3 ? 1 : 0, rel, total, st);
+    if ((e = kc::launch_scan(total, P, b.hstarts, cursor, st)) != cudaSuccess) return bail(e);
+    if (mode != 1) kc::launch_bucket_base(rel, b.hstarts, n_ctas, a, st);
+    if (mode == 4) kc::launch_scatter_staged_lin(lin, seg, n_ctas, a, rel, b.hdata, st);
+    else kc::launch_bucket_scatter(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, mode, rel, cursor, b.hdata, st);
+    h->launches += mode != 1 ? 5 : 4;
     cudaFreeAsync(counts, st);
     cudaFreeAsync(rel, st);
     cudaFreeAsync(total, st);
     cudaFreeAsync(cursor, st);
+    if (lin) cudaFreeAsync(lin, st);
+    if (seg) cudaFreeAsync(seg, st);
     return KC_OK;
 }
 
 // Sort the survivors held in tk/tv (count in host_ctr.survivors, already
 // read back) into res_keys/res_vals: bucket by the top bits of the 2k-bit
-// key (about 512 keys a bucket), then sort every bucket in shared memory.
+// key (about 64 keys a bucket), then sort every bucket: one warp per bucket
+// in registers, larger buckets in shared memory or, rarely, global memory.
 kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
     cudaStream_t st = h->stream;
     const uint64_t n = h->host_ctr.survivors;
     const uint64_t cap = std::max<uint64_t>(1, n);
     int bits = 0;
-    while (bits < 22 && bits < 2 * h->k && (cap >> bits) > 512) ++bits;
+    while (bits < 22 && bits < 2 * h->k && (cap >> bits) > 64) ++bits;
     const uint64_t n_buckets = 1ull << bits;
     const int prefix_shift = 2 * h->k - bits;
     uint64_t *starts = nullptr, *cursor = nullptr;
@@ -289,9 +311,9 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
     cudaEvent_t t0 = phase_begin(h);
     KC_CUDA(cudaMemsetAsync(hist, 0, n_buckets * 4, st));
     kc::launch_prefix_hist(tk, h->ctr, n, prefix_shift, n_buckets, hist, h->grid, st);
-    kc::launch_scan(hist, n_buckets, starts, cursor, st);
+    KC_CUDA(kc::launch_scan(hist, n_buckets, starts, cursor, st));
     kc::launch_scatter(tk, tv, h->ctr, n, prefix_shift, n_buckets, cursor, h->res_keys, h->res_vals, h->grid, st);
-    kc::launch_bucket_sort(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, st);
+    kc::launch_bucket_sort_warp(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, h->grid, st);
     phase_end(h, kSort, t0);
     h->launches += 4;
     KC_CUDA(cudaGetLastError());
@@ -300,6 +322,12 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
     if (h->host_ctr.err & kc::DERR_INTERNAL) {
         h->state = State::Poisoned;
         return fail(KC_ERR_INTERNAL, "sort: key outside its bucket range");
+    }
+    if (h->host_ctr.err & kc::DERR_SORT_MEDIUM) {
+        kc::launch_bucket_sort(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, st);
+        h->launches += 1;
+        KC_CUDA(cudaGetLastError());
+        if ((s = read_counters(h)) != KC_OK) return s;
     }
     if (h->host_ctr.err & kc::DERR_SORT_BUCKET) {
         // Rare: a bucket larger than the shared-memory tile; sort it in global memory.
@@ -316,9 +344,11 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
                 kc::launch_bitonic_global(h->res_keys + hs[i], h->res_vals + hs[i], m, st);
                 h->launches += steps;
             }
+        KC_CUDA(cudaGetLastError());
+    }
+    if (h->host_ctr.err & (kc::DERR_SORT_MEDIUM | kc::DERR_SORT_BUCKET)) {
         unsigned zero = 0;
         KC_CUDA(cudaMemcpyAsync(&h->ctr->err, &zero, 4, cudaMemcpyHostToDevice, st));
-        KC_CUDA(cudaGetLastError());
     }
     cudaFreeAsync(hist, st);
     cudaFreeAsync(starts, st);
@@ -598,6 +628,7 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     if (c.block_threads && c.block_threads != 256) return fail(KC_ERR_ARG, "block_threads must be 256");
     if (c.strategy > KC_STRATEGY_PARTITIONED) return fail(KC_ERR_ARG, "unknown strategy");
     if (c.part_bits > 14) return fail(KC_ERR_ARG, "part_bits must be <= 14");
+    if (c.scatter_mode > 4) return fail(KC_ERR_ARG, "scatter_mode must be in 0..4");
     if (c.smem_table_log2 && (c.smem_table_log2 < 10 || c.smem_table_log2 > 13))
         return fail(KC_ERR_ARG, "smem_table_log2 must be in 10..13");
     // Partitions: filter slices of 4096 words (32 KiB) unless set; the
@@ -794,7 +825,7 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
             cudaFreeAsync(doff, st);
             return s;
         }
-        h->launches += 7;
+        h->launches += 2;
     }
     phase_end(h, kPass1, t0);
     KC_CUDA(cudaGetLastError());

@@ -34,6 +34,7 @@ enum : unsigned int {
     DERR_OFFSETS = 4u,         // decreasing read offsets
     DERR_SORT_BUCKET = 8u,     // a sort bucket exceeded the shared-memory tile
     DERR_INTERNAL = 16u,       // a self-check failed (index out of range)
+    DERR_SORT_MEDIUM = 32u,    // a sort bucket exceeded one warp's registers
 };
 
 // Parameters shared by the extraction passes.
@@ -96,7 +97,21 @@ __device__ __forceinline__ uint64_t canonical_key(uint64_t fwd, const PassParams
     return fwd < rc ? fwd : rc;
 }
 
-// Bits of one key in its filter word: bit (g >> 6i) & 63 for i < n_hashes.
+// Bits of one key in its filter word: bit (g >> 6i) & 63 for i < n_hashes,
+// assembled in two 32-bit halves.
+template <int NH>
+__device__ __forceinline__ uint64_t bloom_pattern_n(uint64_t g) {
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < NH; ++i) {
+        const uint32_t bit = (uint32_t)(g >> (6 * i)) & 63u;
+        const uint32_t m = 1u << (bit & 31u);
+        if (bit & 32u) hi |= m;
+        else lo |= m;
+    }
+    return ((uint64_t)hi << 32) | lo;
+}
+
 __device__ __forceinline__ uint64_t bloom_pattern(uint64_t g, int n_hashes) {
     uint64_t pat = 0;
 #pragma unroll

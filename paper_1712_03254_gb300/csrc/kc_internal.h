@@ -35,14 +35,22 @@ void launch_compact(const Slot* table, uint64_t n_slots, int n_samples, uint32_t
                     uint64_t* vals, DevCounters* ctr, uint32_t* hist, int prefix_shift, const Grid& g,
                     cudaStream_t st);
 // starts[0..n] = exclusive scan of hist[0..n); cursor[0..n) = starts[0..n).
-void launch_scan(const uint32_t* hist, uint64_t n, uint64_t* starts, uint64_t* cursor, cudaStream_t st);
+// Above 4096 counters a three-kernel multi-CTA scan with a small stream-
+// ordered temporary (n <= 2^25).
+cudaError_t launch_scan(const uint32_t* hist, uint64_t n, uint64_t* starts, uint64_t* cursor, cudaStream_t st);
 // Scatter survivors (at most cap of them) into their buckets; keys whose
 // bucket or position would fall outside the arrays set DERR_INTERNAL.
 void launch_scatter(const uint64_t* keys, const uint64_t* vals, DevCounters* ctr, uint64_t cap, int prefix_shift,
                     uint64_t n_buckets, uint64_t* cursor, uint64_t* out_keys, uint64_t* out_vals, const Grid& g,
                     cudaStream_t st);
-// Sort every bucket in place; buckets larger than the shared-memory tile set
-// DERR_SORT_BUCKET and are left for launch_bitonic_global.
+// Sort every bucket of at most warp_sort_capacity() keys in place, one warp
+// per bucket; larger buckets set DERR_SORT_MEDIUM and are left alone.
+void launch_bucket_sort_warp(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets,
+                             DevCounters* ctr, const Grid& g, cudaStream_t st);
+int warp_sort_capacity();
+// Sort buckets of warp_sort_capacity()+1 .. bucket_sort_capacity() keys in
+// shared memory, one CTA per bucket; larger buckets set DERR_SORT_BUCKET and
+// are left for launch_bitonic_global.
 void launch_bucket_sort(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets,
                         DevCounters* ctr, cudaStream_t st);
 int bucket_sort_capacity();
@@ -99,12 +107,22 @@ struct FallbackArgs {
 size_t bucket_pass_smem(int a);
 void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                          int n_ctas, const PassParams& p, int a, uint32_t* counts, cudaStream_t st);
-void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, uint64_t* rel, uint32_t* total,
+void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, int pad4, uint64_t* rel, uint32_t* total,
                            cudaStream_t st);
+size_t staged_scatter_smem(int a);
+// mode 4: the extraction pass writes every CTA's hashes to its own segment of
+// a linear array (plus counts); the staged scatter then moves the segments
+void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
+                          int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, uint64_t* seg,
+                          uint64_t* lin, cudaStream_t st);
+void launch_scatter_staged_lin(const uint64_t* lin, const uint64_t* seg, int n_ctas, int a, const uint64_t* base,
+                               uint64_t* out, cudaStream_t st);
 void launch_bucket_base(uint64_t* rel, const uint64_t* starts, int n_ctas, int a, cudaStream_t st);
+// mode 1: global per-bucket cursors; mode 2: per-CTA runs at base[cta][bucket];
+// mode 3: per-CTA runs padded to whole sectors, staged in shared memory
 void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
-                           int n_ctas, const PassParams& p, int a, const uint64_t* base, uint64_t* out,
-                           cudaStream_t st);
+                           int n_ctas, const PassParams& p, int a, int mode, const uint64_t* base, uint64_t* cursor,
+                           uint64_t* out, cudaStream_t st);
 size_t consume_smem(int slice_log2, int table_log2, int n_samples);
 int launch_part_consume(const ConsumeArgs& A, int n_ctas, cudaStream_t st);
 void launch_fb_claim(const FallbackArgs& F, int bt, cudaStream_t st);

@@ -225,6 +225,95 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ hist
     if (t == (int)blockDim.x - 1) starts[n] = warp_tot[(blockDim.x >> 5) - 1];
 }
 
+// Multi-CTA exclusive scan for long counter arrays: per-tile sums, a scan of
+// the tile sums, then every tile rescanned with its offset.
+constexpr int kScanTile = 4096;
+
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long x, unsigned long long* total) {
+    __shared__ unsigned long long s_w[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_w[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = lane < nw ? s_w[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    *total = s_w[nw - 1];
+    return v - x + (wid ? s_w[wid - 1] : 0ull);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* __restrict__ hist, uint64_t n,
+                                                     unsigned long long* __restrict__ tile_sums) {
+    const uint64_t t0 = (uint64_t)blockIdx.x * kScanTile;
+    unsigned long long x = 0;
+    for (int j = 0; j < kScanTile / 1024; ++j) {
+        const uint64_t i = t0 + (uint64_t)j * 1024 + threadIdx.x;
+        if (i < n) x += hist[i];
+    }
+    unsigned long long tot;
+    block_exclusive_scan(x, &tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* __restrict__ tile_sums, int n_tiles) {
+    // one CTA; n_tiles <= 1024 * 8
+    unsigned long long x[8];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int i = threadIdx.x * 8 + j;
+        x[j] = i < n_tiles ? tile_sums[i] : 0ull;
+        sum += x[j];
+    }
+    unsigned long long tot;
+    unsigned long long run = block_exclusive_scan(sum, &tot);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int i = threadIdx.x * 8 + j;
+        if (i < n_tiles) tile_sums[i] = run;
+        run += x[j];
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t* __restrict__ hist, uint64_t n,
+                                                     const unsigned long long* __restrict__ tile_off,
+                                                     uint64_t* __restrict__ starts, uint64_t* __restrict__ cursor) {
+    // each thread takes 4 consecutive counters of the tile
+    const uint64_t t0 = (uint64_t)blockIdx.x * kScanTile;
+    const uint64_t i0 = t0 + (uint64_t)threadIdx.x * 4;
+    uint32_t c[4];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j] = i0 + j < n ? hist[i0 + j] : 0u;
+        sum += c[j];
+    }
+    unsigned long long tot;
+    unsigned long long run = block_exclusive_scan(sum, &tot) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (i0 + j < n) {
+            starts[i0 + j] = run;
+            cursor[i0 + j] = run;
+        }
+        run += c[j];
+    }
+    if (i0 < n && i0 + 4 >= n) starts[n] = run;  // the thread holding the last counter
+}
+
 __global__ void k_scatter(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals,
                           DevCounters* __restrict__ ctr, uint64_t cap, int prefix_shift, uint64_t n_buckets,
                           unsigned long long* __restrict__ cursor, uint64_t* __restrict__ out_keys,
@@ -248,7 +337,8 @@ __global__ void k_scatter(const uint64_t* __restrict__ keys, const uint64_t* __r
     }
 }
 
-constexpr int kSortCap = 4096;    // keys per shared-memory tile
+constexpr int kSortCap = 2048;    // keys per shared-memory tile
+constexpr int kWarpSortMax = 256; // keys one warp sorts in registers
 constexpr int kSortThreads = 256;
 
 // Ascending bitonic network in the "mirror" form: every comparator puts the
@@ -263,7 +353,7 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(uint64_t* __restri
     uint64_t* sv = smem + kSortCap;
     const uint64_t lo = starts[blockIdx.x];
     const uint64_t n64 = starts[blockIdx.x + 1] - lo;
-    if (n64 <= 1) return;
+    if (n64 <= (uint64_t)kWarpSortMax) return;  // sorted by k_bucket_sort_warp
     if (n64 > (uint64_t)kSortCap) {
         if (threadIdx.x == 0) atomicOr(&ctr->err, DERR_SORT_BUCKET);
         return;
@@ -307,6 +397,93 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(uint64_t* __restri
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         keys[lo + i] = sk[i];
         vals[lo + i] = sv[i];
+    }
+}
+
+// Warp-per-bucket sort: the bucket's keys sit in registers, R per lane
+// (element r*32 + lane), padded with ~0 keys; a bitonic network runs with
+// register compare-exchanges for strides >= 32 and shuffles below.
+template <int R>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&k)[R], uint64_t (&v)[R], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * R; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int rs = stride >> 5;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if ((r & rs) == 0) {
+                        const int q = r | rs;
+                        const bool asc = (((r << 5) | lane) & size) == 0;
+                        if ((k[r] > k[q]) == asc) {
+                            const uint64_t tk = k[r], tv = v[r];
+                            k[r] = k[q];
+                            v[r] = v[q];
+                            k[q] = tk;
+                            v[q] = tv;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = (r << 5) | lane;
+                    const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[r], stride);
+                    const uint64_t ov = __shfl_xor_sync(0xffffffffu, v[r], stride);
+                    const bool asc = (i & size) == 0;
+                    const bool lower = (i & stride) == 0;
+                    const bool take_other = lower ? (asc ? ok < k[r] : ok > k[r]) : (asc ? ok > k[r] : ok < k[r]);
+                    if (take_other) {
+                        k[r] = ok;
+                        v[r] = ov;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void warp_sort_bucket(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
+                                                 uint64_t lo, int n, int lane) {
+    uint64_t k[R], v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = (r << 5) | lane;
+        k[r] = i < n ? keys[lo + i] : ~0ull;
+        v[r] = i < n ? vals[lo + i] : 0ull;
+    }
+    warp_bitonic<R>(k, v, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = (r << 5) | lane;
+        if (i < n) {
+            keys[lo + i] = k[r];
+            vals[lo + i] = v[r];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_bucket_sort_warp(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
+                                                          const uint64_t* __restrict__ starts, uint64_t n_buckets,
+                                                          DevCounters* __restrict__ ctr) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t b = warp; b < n_buckets; b += n_warps) {
+        const uint64_t lo = starts[b];
+        const uint64_t n64 = starts[b + 1] - lo;
+        if (n64 <= 1) continue;
+        if (n64 > (uint64_t)kWarpSortMax) {
+            if (lane == 0) atomicOr(&ctr->err, DERR_SORT_MEDIUM);
+            continue;
+        }
+        const int n = (int)n64;
+        if (n <= 32) warp_sort_bucket<1>(keys, vals, lo, n, lane);
+        else if (n <= 64) warp_sort_bucket<2>(keys, vals, lo, n, lane);
+        else if (n <= 128) warp_sort_bucket<4>(keys, vals, lo, n, lane);
+        else warp_sort_bucket<8>(keys, vals, lo, n, lane);
     }
 }
 
@@ -379,8 +556,20 @@ void launch_compact(const Slot* table, uint64_t n_slots, int n_samples, uint32_t
                                                                        vals, ctr, hist, prefix_shift);
 }
 
-void launch_scan(const uint32_t* hist, uint64_t n, uint64_t* starts, uint64_t* cursor, cudaStream_t st) {
-    k_scan<<<1, 1024, 0, st>>>(hist, n, starts, cursor);
+cudaError_t launch_scan(const uint32_t* hist, uint64_t n, uint64_t* starts, uint64_t* cursor, cudaStream_t st) {
+    if (n <= (uint64_t)kScanTile) {
+        k_scan<<<1, 1024, 0, st>>>(hist, n, starts, cursor);
+        return cudaSuccess;
+    }
+    const uint64_t n_tiles = (n + kScanTile - 1) / kScanTile;
+    if (n_tiles > 8192) return cudaErrorInvalidValue;
+    unsigned long long* tile = nullptr;
+    cudaError_t e = cudaMallocAsync(&tile, n_tiles * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_scan_tiles<<<(unsigned)n_tiles, 1024, 0, st>>>(hist, n, tile);
+    k_scan_top<<<1, 1024, 0, st>>>(tile, (int)n_tiles);
+    k_scan_apply<<<(unsigned)n_tiles, 1024, 0, st>>>(hist, n, tile, starts, cursor);
+    return cudaFreeAsync(tile, st);
 }
 
 void launch_scatter(const uint64_t* keys, const uint64_t* vals, DevCounters* ctr, uint64_t cap, int prefix_shift,
@@ -391,6 +580,18 @@ void launch_scatter(const uint64_t* keys, const uint64_t* vals, DevCounters* ctr
 }
 
 int bucket_sort_capacity() { return kSortCap; }
+
+void launch_bucket_sort_warp(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets,
+                             DevCounters* ctr, const Grid& g, cudaStream_t st) {
+    const uint64_t warps = n_buckets;
+    unsigned grid = (unsigned)((warps + 7) / 8);
+    const unsigned cap = (unsigned)g.sm_count * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_bucket_sort_warp<<<grid, 256, 0, st>>>(keys, vals, starts, n_buckets, ctr);
+}
+
+int warp_sort_capacity() { return kWarpSortMax; }
 
 void launch_bucket_sort(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets,
                         DevCounters* ctr, cudaStream_t st) {

@@ -8,15 +8,15 @@
 // structures live in shared memory:
 //
 //   ingest (per kc_add_reads call)
-//     k_bucket_pass<false>  per window: canonical key, h = mixer64(key),
+//     k_bucket_pass<count>  per window: canonical key, h = mixer64(key),
 //                           bucket = top a bits of h; per-CTA histogram in
-//                           shared memory, written out CTA-major (no global
-//                           atomics)
-//     k_bucket_offsets      per bucket: exclusive prefix over CTAs
+//                           shared memory, written out CTA-major
+//     k_bucket_offsets      per bucket: exclusive prefix over CTAs, totals
 //     (scan)                bucket starts
 //     k_bucket_base         absolute start of every (CTA, bucket) run
-//     k_bucket_pass<true>   the same windows again; each h is stored at its
-//                           CTA's run of its bucket (shared-memory cursors)
+//     k_bucket_pass<scatter> the same windows again; each h is stored at the
+//                           next position of its CTA's run of its bucket (or
+//                           at a position from a global per-bucket cursor)
 //   finalize
 //     k_part_consume        one CTA per bucket ("partition"): the filter words
 //                           of the partition (a contiguous slice, since the
@@ -45,20 +45,49 @@ __device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
     return v;
 }
 
-template <bool kScatter>
+// L2 cache policy "evict last" for stores whose sectors are completed over
+// time by later stores of the same CTA (sm_80+ createpolicy / cache_hint).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void st_u64_l2_hint(uint64_t* p, uint64_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+
+enum BucketMode { kCountPerCta = 0, kScatterCursor = 1, kScatterRegion = 2, kScatterStaged = 3 };
+
+// Filler for the unused tail of a padded run: a hash whose partition prefix
+// is that of the neighbouring partition, so that every reader of partition b
+// (which checks the prefix) skips it.
+__device__ __forceinline__ uint64_t pad_hash(uint32_t b, int a) { return (uint64_t)(b ^ 1u) << (64 - a); }
+
+// kCountPerCta: per-CTA histogram of the windows' buckets in shared memory,
+// written out CTA-major.  kScatterRegion: the same windows again; each CTA
+// owns one run per bucket (exact offsets from the counts) and stores each h
+// at the next position of its run, with an evict-last L2 policy so that the
+// partly written sectors stay in L2 until later stores complete them.
+// kScatterCursor: positions come from one global cursor per bucket instead.
+template <int kMode>
 __global__ void __launch_bounds__(512) k_bucket_pass(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw,
                                                      uint64_t n_units, uint64_t units_per_cta, PassParams p, int a,
                                                      uint32_t* __restrict__ counts,
                                                      const uint64_t* __restrict__ base,
+                                                     unsigned long long* __restrict__ cursor,
                                                      uint64_t* __restrict__ out) {
     extern __shared__ uint32_t s_cnt[];
     const uint32_t P = 1u << a;
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_cnt[i] = 0;
-    __syncthreads();
+    if (kMode != kScatterCursor) {
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+    }
+    const uint64_t pol = kMode == kScatterRegion ? l2_evict_last_policy() : 0ull;
     const uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
     const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint64_t* my_base = kScatter ? base + (uint64_t)blockIdx.x * P : nullptr;
+    const uint64_t* my_base = kMode == kScatterRegion ? base + (uint64_t)blockIdx.x * P : nullptr;
     for (uint64_t g = lo + (uint64_t)wid * 32; g < hi; g += (uint64_t)nwarps * 32) {
         const UnitWords uw = load_unit(pw, vw, g + lane, hi, lane);
         uint64_t vm = uw.v;
@@ -70,22 +99,246 @@ __global__ void __launch_bounds__(512) k_bucket_pass(const uint64_t* __restrict_
                 const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
                 const uint64_t h = mixer64(key);
                 const uint32_t b = (uint32_t)(h >> (64 - a));
-                const uint32_t r = atomicAdd(&s_cnt[b], 1u);
-                if (kScatter) out[__ldg(my_base + b) + r] = h;
+                if (kMode == kScatterCursor) {
+                    const unsigned long long pos = atomicAdd(cursor + b, 1ull);
+                    out[pos] = h;
+                } else {
+                    const uint32_t r = atomicAdd(&s_cnt[b], 1u);
+                    if (kMode == kScatterRegion) st_u64_l2_hint(out + __ldg(my_base + b) + r, h, pol);
+                }
             }
             __syncwarp();
         }
     }
-    if (!kScatter) {
+    if (kMode == kCountPerCta) {
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[(uint64_t)blockIdx.x * P + i] = s_cnt[i];
+    }
+}
+
+// Staged scatter: every CTA owns one run per partition whose start and length
+// are multiples of 4 (padded counts), and stages up to 4 hashes per partition
+// in shared memory; a full stage leaves as one aligned 32-byte sector, so
+// DRAM only ever sees whole-sector writes.  Rounds are CTA-synchronous: each
+// lane places at most one window per round, full stages are flushed after a
+// barrier, and a window that found its stage full retries next round.
+constexpr int kStagedThreads = 1024;
+
+__global__ void __launch_bounds__(kStagedThreads) k_bucket_scatter_staged(
+    const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw, uint64_t n_units, uint64_t units_per_cta,
+    PassParams p, int a, const uint64_t* __restrict__ base, uint64_t* __restrict__ out) {
+    extern __shared__ unsigned long long s_stage[];
+    const uint32_t P = 1u << a;
+    uint32_t* fill = reinterpret_cast<uint32_t*>(s_stage + 4 * (size_t)P);
+    uint32_t* wpos = fill + P;
+    __shared__ unsigned s_next;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        fill[i] = 0;
+        wpos[i] = 0;
+    }
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    const uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
+    const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
+    const uint64_t n_groups = (hi - lo + 31) / 32;
+    const uint64_t* my_base = base + (uint64_t)blockIdx.x * P;
+    const int lane = threadIdx.x & 31;
+    UnitWords uw{0, 0, 0, 0};
+    uint64_t vm = 0, ph = 0;
+    uint32_t pb = 0;
+    bool pend = false, warp_done = false;
+    for (;;) {
+        // a warp whose lanes have nothing left takes the next group of 32 units
+        const bool need = __all_sync(kFull, vm == 0 && !pend);
+        if (need && !warp_done) {
+            unsigned g = 0;
+            if (lane == 0) g = atomicAdd(&s_next, 1u);
+            g = __shfl_sync(kFull, g, 0);
+            if (g < n_groups) {
+                uw = load_unit(pw, vw, lo + (uint64_t)g * 32 + lane, hi, lane);
+                vm = uw.v;
+            } else {
+                warp_done = true;
+            }
+        }
+        if (!pend && vm) {
+            const int j = __clzll(vm);
+            vm &= ~(0x8000000000000000ull >> j);
+            const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
+            ph = mixer64(key);
+            pb = (uint32_t)(ph >> (64 - a));
+            pend = true;
+        }
+        if (pend) {
+            const uint32_t pos = atomicAdd(&fill[pb], 1u);
+            if (pos < 4) {
+                s_stage[(size_t)pb * 4 + pos] = ph;
+                pend = false;
+            }
+        }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
+            if (fill[b] >= 4) {
+                const ulonglong2* src = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
+                ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + __ldg(my_base + b) + wpos[b]);
+                dst[0] = src[0];
+                dst[1] = src[1];
+                wpos[b] += 4;
+                fill[b] = 0;  // windows beyond the 4 staged ones retry next round
+            }
+        }
+        if (!__syncthreads_or(!warp_done || vm != 0 || pend)) break;
+    }
+    // partly filled stages: pad to a whole sector
+    for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
+        const uint32_t f = fill[b];
+        if (f) {
+            uint64_t* dst = out + __ldg(my_base + b) + wpos[b];
+            for (uint32_t i = 0; i < 4; ++i) dst[i] = i < f ? (uint64_t)s_stage[(size_t)b * 4 + i] : pad_hash(b, a);
+        }
+    }
+}
+
+// Extraction pass: every window's h is written once, CTA by CTA, into one
+// contiguous segment per CTA of a linear array (warp-aggregated positions, so
+// the stores are coalesced), and the CTA's histogram over partitions goes to
+// counts[cta][*].  seg[2*cta] = segment start, seg[2*cta+1] = its length.
+__global__ void __launch_bounds__(512) k_extract_count(const uint64_t* __restrict__ pw,
+                                                       const uint64_t* __restrict__ vw, uint64_t n_units,
+                                                       uint64_t units_per_cta, PassParams p, int a,
+                                                       uint32_t* __restrict__ counts,
+                                                       unsigned long long* __restrict__ g_cursor,
+                                                       uint64_t* __restrict__ seg, uint64_t* __restrict__ lin) {
+    extern __shared__ uint32_t s_cnt[];
+    __shared__ unsigned long long s_base;
+    __shared__ unsigned s_pos;
+    __shared__ unsigned long long s_warp_tot[16];
+    const uint32_t P = 1u << a;
+    const uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
+    const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_cnt[i] = 0;
+    // the CTA's window count, from the valid-window bits
+    unsigned long long mine = 0;
+    for (uint64_t u = lo + threadIdx.x; u < hi; u += blockDim.x) mine += __popcll(__ldg(vw + u));
+    mine = warp_sum64(mine);
+    if (lane == 0) s_warp_tot[wid] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tot = 0;
+        for (int w = 0; w < nwarps; ++w) tot += s_warp_tot[w];
+        s_base = atomicAdd(g_cursor, tot);
+        s_pos = 0;
+        seg[2 * blockIdx.x] = s_base;
+        seg[2 * blockIdx.x + 1] = tot;
+    }
+    __syncthreads();
+    const uint64_t base = s_base;
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint64_t g = lo + (uint64_t)wid * 32; g < hi; g += (uint64_t)nwarps * 32) {
+        const UnitWords uw = load_unit(pw, vw, g + lane, hi, lane);
+        uint64_t vm = uw.v;
+        const int n_iter = __reduce_max_sync(kFull, (unsigned)__popcll(vm));
+        for (int it = 0; it < n_iter; ++it) {
+            const bool has = vm != 0;
+            uint64_t h = 0;
+            if (has) {
+                const int j = __clzll(vm);
+                vm &= ~(0x8000000000000000ull >> j);
+                const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
+                h = mixer64(key);
+                atomicAdd(&s_cnt[(uint32_t)(h >> (64 - a))], 1u);
+            }
+            // consecutive positions for the warp's windows of this round: the
+            // stores of a round are coalesced
+            const unsigned ballot = __ballot_sync(kFull, has);
+            unsigned wb = 0;
+            if (lane == 0) wb = atomicAdd(&s_pos, (unsigned)__popc(ballot));
+            wb = __shfl_sync(kFull, wb, 0);
+            if (has) lin[base + wb + __popc(ballot & lt)] = h;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[(uint64_t)blockIdx.x * P + i] = s_cnt[i];
+}
+
+// Staged scatter from the linear array: CTA c moves its own segment (whose
+// histogram is counts[c][*]) into its padded runs, 4 hashes per thread per
+// round; full 4-entry stages leave as aligned 32-byte sectors.
+constexpr int kLinThreads = 1024;
+constexpr int kLinPerThread = 4;
+
+__global__ void __launch_bounds__(kLinThreads) k_scatter_staged_lin(const uint64_t* __restrict__ lin,
+                                                                    const uint64_t* __restrict__ seg, int a,
+                                                                    const uint64_t* __restrict__ base,
+                                                                    uint64_t* __restrict__ out) {
+    extern __shared__ unsigned long long s_stage[];
+    const uint32_t P = 1u << a;
+    uint32_t* fill = reinterpret_cast<uint32_t*>(s_stage + 4 * (size_t)P);
+    uint32_t* wpos = fill + P;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        fill[i] = 0;
+        wpos[i] = 0;
+    }
+    __syncthreads();
+    const uint64_t s0 = seg[2 * blockIdx.x], len = seg[2 * blockIdx.x + 1];
+    const uint64_t* my_base = base + (uint64_t)blockIdx.x * P;
+    // thread t owns elements t, t + nt, t + 2 nt, ... of the segment, in order
+    uint64_t next = threadIdx.x;
+    uint64_t ph[kLinPerThread];
+    uint32_t pend = 0;  // bit e: ph[e] still to be staged
+    for (;;) {
+        // Warp-uniform: a warp loads its next rows only when none of its lanes
+        // still holds a pending hash, so every load stays coalesced.
+        if (__all_sync(kFull, pend == 0)) {
+#pragma unroll
+            for (int e = 0; e < kLinPerThread; ++e) {
+                if (next < len) {
+                    ph[e] = __ldcg(lin + s0 + next);
+                    pend |= 1u << e;
+                }
+                next += blockDim.x;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < kLinPerThread; ++e) {
+            if (pend & (1u << e)) {
+                const uint64_t h = ph[e];
+                const uint32_t b = (uint32_t)(h >> (64 - a));
+                const uint32_t pos = atomicAdd(&fill[b], 1u);
+                if (pos < 4) {
+                    s_stage[(size_t)b * 4 + pos] = h;
+                    pend &= ~(1u << e);
+                }  // else the stage is full: retry next round
+            }
+        }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
+            if (fill[b] >= 4) {
+                const ulonglong2* src = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
+                ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + __ldg(my_base + b) + wpos[b]);
+                dst[0] = src[0];
+                dst[1] = src[1];
+                wpos[b] += 4;
+                fill[b] = 0;
+            }
+        }
+        if (!__syncthreads_or(pend != 0 || next < len)) break;
+    }
+    for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
+        const uint32_t f = fill[b];
+        if (f) {
+            uint64_t* dst = out + __ldg(my_base + b) + wpos[b];
+            for (uint32_t i = 0; i < 4; ++i) dst[i] = i < f ? (uint64_t)s_stage[(size_t)b * 4 + i] : pad_hash(b, a);
+        }
     }
 }
 
 // rel[c][b] = sum of counts[c'][b] over c' < c; total[b] = sum over all CTAs.
 // One thread per bucket; the column is read 16 CTAs at a time so that the
 // loads are independent and in flight together.
-__global__ void k_bucket_offsets(const uint32_t* __restrict__ counts, int n_ctas, uint32_t P,
+// With pad4, every count is rounded up to a multiple of 4 first.
+__global__ void k_bucket_offsets(const uint32_t* __restrict__ counts, int n_ctas, uint32_t P, int pad4,
                                  uint64_t* __restrict__ rel, uint32_t* __restrict__ total) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= P) return;
@@ -93,7 +346,10 @@ __global__ void k_bucket_offsets(const uint32_t* __restrict__ counts, int n_ctas
     for (int c0 = 0; c0 < n_ctas; c0 += 16) {
         uint32_t x[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) x[j] = c0 + j < n_ctas ? __ldg(counts + (uint64_t)(c0 + j) * P + b) : 0u;
+        for (int j = 0; j < 16; ++j) {
+            x[j] = c0 + j < n_ctas ? __ldg(counts + (uint64_t)(c0 + j) * P + b) : 0u;
+            if (pad4) x[j] = (x[j] + 3u) & ~3u;
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             if (c0 + j < n_ctas) rel[(uint64_t)(c0 + j) * P + b] = run;
@@ -139,6 +395,7 @@ __device__ __forceinline__ int smem_find(const unsigned long long* keys, uint32_
     return -1;
 }
 
+template <int NH>
 __global__ void __launch_bounds__(512) k_part_consume(ConsumeArgs A) {
     extern __shared__ unsigned long long s_mem[];
     const uint32_t n_sw = 1u << A.slice_log2;  // filter words of one partition
@@ -167,9 +424,10 @@ __global__ void __launch_bounds__(512) k_part_consume(ConsumeArgs A) {
             const uint64_t* __restrict__ d = A.data[bt];
             const uint64_t lo = A.starts[bt][part], hi = A.starts[bt][part + 1];
             for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const uint64_t h = __ldcs(d + i);
+                const uint64_t h = __ldcg(d + i);  // read again by the recount: keep in L2
+                if ((uint32_t)(h >> (64 - a)) != part) continue;  // run padding
                 const uint32_t w = (uint32_t)(h >> A.bloom_shift) & (n_sw - 1);
-                const uint64_t pat = bloom_pattern(mixer64(h), A.n_hashes);
+                const uint64_t pat = bloom_pattern_n<NH>(mixer64(h));
                 const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
                 if (A.all_candidates || (old & pat) == pat) {
                     ++cand;
@@ -191,7 +449,8 @@ __global__ void __launch_bounds__(512) k_part_consume(ConsumeArgs A) {
             const int smp = A.samples[bt];
             const uint64_t lo = A.starts[bt][part], hi = A.starts[bt][part + 1];
             for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const uint64_t h = __ldcs(d + i);
+                const uint64_t h = __ldcs(d + i);  // last use
+                if ((uint32_t)(h >> (64 - a)) != part) continue;
                 const int s = smem_find(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
                 if (s >= 0) atomicAdd(sc + (uint32_t)s * S + smp, 1u);
             }
@@ -248,6 +507,7 @@ __global__ void k_fb_claim(FallbackArgs F, int bt) {
     uint64_t cand = 0, claimed = 0;
     for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride) {
         const uint64_t h = d[i];
+        if ((uint32_t)(h >> (64 - F.part_bits)) != F.part) continue;  // run padding
         const uint64_t pat = bloom_pattern(mixer64(h), F.n_hashes);
         const unsigned long long old = atomicOr(F.bloom + (h >> F.bloom_shift), (unsigned long long)pat);
         if (F.all_candidates || (old & pat) == pat) {
@@ -272,6 +532,7 @@ __global__ void k_fb_recount(FallbackArgs F, int bt) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride) {
         const uint64_t h = d[i];
+        if ((uint32_t)(h >> (64 - F.part_bits)) != F.part) continue;
         table_count(F.table, F.table_mask, (h & low_mask) & F.table_mask, (h & low_mask) + 1ull, smp, F.ctr);
     }
 }
@@ -325,18 +586,36 @@ __global__ void k_prefix_hist(const uint64_t* __restrict__ keys, DevCounters* __
 }  // namespace
 
 size_t bucket_pass_smem(int a) { return sizeof(uint32_t) << a; }
+size_t staged_scatter_smem(int a) { return (4 * sizeof(uint64_t) + 2 * sizeof(uint32_t)) << a; }
 
 void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                          int n_ctas, const PassParams& p, int a, uint32_t* counts, cudaStream_t st) {
     const size_t smem = bucket_pass_smem(a);
-    cudaFuncSetAttribute(k_bucket_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_bucket_pass<false><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts, nullptr, nullptr);
+    cudaFuncSetAttribute(k_bucket_pass<kCountPerCta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bucket_pass<kCountPerCta><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts, nullptr,
+                                                           nullptr, nullptr);
 }
 
-void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, uint64_t* rel, uint32_t* total,
+void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
+                          int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, uint64_t* seg,
+                          uint64_t* lin, cudaStream_t st) {
+    const size_t smem = bucket_pass_smem(a);
+    cudaFuncSetAttribute(k_extract_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_extract_count<<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
+                                               reinterpret_cast<unsigned long long*>(g_cursor), seg, lin);
+}
+
+void launch_scatter_staged_lin(const uint64_t* lin, const uint64_t* seg, int n_ctas, int a, const uint64_t* base,
+                               uint64_t* out, cudaStream_t st) {
+    const size_t smem = staged_scatter_smem(a);
+    cudaFuncSetAttribute(k_scatter_staged_lin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_scatter_staged_lin<<<n_ctas, kLinThreads, smem, st>>>(lin, seg, a, base, out);
+}
+
+void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, int pad4, uint64_t* rel, uint32_t* total,
                            cudaStream_t st) {
     const uint32_t P = 1u << a;
-    k_bucket_offsets<<<(P + 63) / 64, 64, 0, st>>>(counts, n_ctas, P, rel, total);
+    k_bucket_offsets<<<(P + 63) / 64, 64, 0, st>>>(counts, n_ctas, P, pad4, rel, total);
 }
 
 void launch_bucket_base(uint64_t* rel, const uint64_t* starts, int n_ctas, int a, cudaStream_t st) {
@@ -347,11 +626,21 @@ void launch_bucket_base(uint64_t* rel, const uint64_t* starts, int n_ctas, int a
 }
 
 void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
-                           int n_ctas, const PassParams& p, int a, const uint64_t* base, uint64_t* out,
-                           cudaStream_t st) {
-    const size_t smem = bucket_pass_smem(a);
-    cudaFuncSetAttribute(k_bucket_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_bucket_pass<true><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, nullptr, base, out);
+                           int n_ctas, const PassParams& p, int a, int mode, const uint64_t* base, uint64_t* cursor,
+                           uint64_t* out, cudaStream_t st) {
+    if (mode == kScatterStaged) {
+        const size_t smem = staged_scatter_smem(a);
+        cudaFuncSetAttribute(k_bucket_scatter_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_bucket_scatter_staged<<<n_ctas, kStagedThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, base, out);
+    } else if (mode == kScatterCursor) {
+        k_bucket_pass<kScatterCursor><<<n_ctas, 512, 0, st>>>(pw, vw, n_units, units_per_cta, p, a, nullptr, nullptr,
+                                                             reinterpret_cast<unsigned long long*>(cursor), out);
+    } else {
+        const size_t smem = bucket_pass_smem(a);
+        cudaFuncSetAttribute(k_bucket_pass<kScatterRegion>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_bucket_pass<kScatterRegion><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, nullptr, base,
+                                                                 nullptr, out);
+    }
 }
 
 size_t consume_smem(int slice_log2, int table_log2, int n_samples) {
@@ -359,12 +648,28 @@ size_t consume_smem(int slice_log2, int table_log2, int n_samples) {
            ((sizeof(uint32_t) * (size_t)n_samples) << table_log2);
 }
 
+template <int NH>
+int launch_consume_nh(const ConsumeArgs& A, int n_ctas, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_part_consume<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k_part_consume<NH><<<n_ctas, 512, smem, st>>>(A);
+    return 0;
+}
+
 int launch_part_consume(const ConsumeArgs& A, int n_ctas, cudaStream_t st) {
     const size_t smem = consume_smem(A.slice_log2, A.table_log2, A.n_samples);
-    cudaError_t e = cudaFuncSetAttribute(k_part_consume, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    k_part_consume<<<n_ctas, 512, smem, st>>>(A);
-    return 0;
+    switch (A.n_hashes) {
+        case 1: return launch_consume_nh<1>(A, n_ctas, smem, st);
+        case 2: return launch_consume_nh<2>(A, n_ctas, smem, st);
+        case 3: return launch_consume_nh<3>(A, n_ctas, smem, st);
+        case 4: return launch_consume_nh<4>(A, n_ctas, smem, st);
+        case 5: return launch_consume_nh<5>(A, n_ctas, smem, st);
+        case 6: return launch_consume_nh<6>(A, n_ctas, smem, st);
+        case 7: return launch_consume_nh<7>(A, n_ctas, smem, st);
+        case 8: return launch_consume_nh<8>(A, n_ctas, smem, st);
+        case 9: return launch_consume_nh<9>(A, n_ctas, smem, st);
+        default: return launch_consume_nh<10>(A, n_ctas, smem, st);
+    }
 }
 
 void launch_fb_claim(const FallbackArgs& F, int bt, cudaStream_t st) { k_fb_claim<<<1024, 256, 0, st>>>(F, bt); }

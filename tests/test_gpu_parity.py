@@ -256,3 +256,26 @@ def test_mid_full_size_sampled_partitions(oracle_mod, strategy):
         assert np.array_equal(c.export_bloom(p * per, per), o.bloom(p * per, per))
     st = c.stats()
     assert st["windows"] == o.windows
+
+
+@pytest.mark.parametrize("scatter_mode", [1, 2, 3, 4])
+@pytest.mark.parametrize("ctas_per_sm", [1, 2])
+def test_scatter_modes(oracle_mod, scatter_mode, ctas_per_sm):
+    w = synth.tiny(scale=0.5)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", scatter_mode=scatter_mode, ctas_per_sm=ctas_per_sm)
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+@pytest.mark.parametrize("n_reads", [200, 1500, 6000])
+def test_skewed_key_prefixes_sort_paths(oracle_mod, n_reads, strategy):
+    """Keys sharing a 20-base prefix land in one sort bucket: up to 256 keys
+    are sorted by a warp, up to 2048 by a CTA, more in global memory."""
+    rng = random.Random(n_reads)
+    reads = ["A" * 20 + "".join(rng.choice("ACGT") for _ in range(11)) for _ in range(n_reads)]
+    w = synth.Workload("skew", [synth.ReadSet.from_strings(reads)], 31, 1 << 16, 4, 1)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, table_slots=1 << 16, strategy=strategy)
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
