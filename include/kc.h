@@ -212,6 +212,38 @@ const char* kc_last_error(void);
 const char* kc_status_string(kc_status s);
 
 /*
+ * kc_bloom_build_noalloc -- the Bloom filter of one read set (the filter
+ * kc_export_bloom returns after counting the same reads with the same k,
+ * bloom_bits and n_hashes), computed without allocating any memory.  The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory when they need the filter -- an application whose
+ * own allocator already holds the device's memory, a latency-critical loop
+ * that must not wait on cudaMalloc, or code restricted to the buffers it was
+ * given.
+ *
+ *   packed_reads, offsets, n_mask  inputs in the packed format above; all in
+ *                  device memory (KC_ERR_ARG otherwise)
+ *   bloom_out      bloom_bits / 64 words of device memory, overwritten
+ *   stream         cudaStream_t as void*, NULL for the default stream; the call
+ *                  returns after its work on this stream is done
+ *
+ * Everything intermediate lives in one fixed scratch array inside the library
+ * (a file-scope __device__ array of about 4 MiB that every GPU loading the
+ * library keeps until the process exits), so a read set may span at most
+ * KC_NOALLOC_MAX_BASES bases from offsets[0] rounded down to a multiple of 64
+ * to offsets[n_reads]; larger sets give KC_ERR_CAPACITY.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the array and each clears the parts that must start at zero, so calls
+ * whose device work overlaps (other streams or host threads) race: order them.
+ * Errors are reported by the status and kc_last_error().
+ */
+#define KC_NOALLOC_MAX_BASES (1ull << 23)
+kc_status kc_bloom_build_noalloc(int k, uint64_t bloom_bits, int n_hashes, const uint64_t* packed_reads,
+                                 const uint64_t* offsets, const uint64_t* n_mask, uint64_t n_reads,
+                                 uint64_t* bloom_out, void* stream);
+
+/*
  * Host helper: pack n_bases ASCII characters into the packed format above
  * (packed: ceil(n_bases/32) words, n_mask: ceil(n_bases/64) words, both
  * written in full, unused tail bits zero).  Any byte other than 'A','C','G','T'

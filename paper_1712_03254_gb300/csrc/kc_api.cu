@@ -76,6 +76,10 @@ enum class State { Open, Finalized, Poisoned };
 
 }  // namespace
 
+namespace kc {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace kc
+
 struct kc_ctx {
     int k = 0, n_samples = 0, n_hashes = 0;
     uint64_t bloom_bits = 0;

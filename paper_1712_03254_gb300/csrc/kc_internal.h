@@ -4,10 +4,14 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "kc_device.cuh"
 
 namespace kc {
+
+// Message returned by kc_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 struct Grid {
     int sm_count = 152;
