@@ -144,6 +144,26 @@ typedef struct kc_stats {
     uint32_t fallback_partitions;   /* partitions whose table left shared memory    */
 } kc_stats;
 
+/*
+ * Batched finalize (partitioned strategy): many handles finalized together.
+ * Their partitions form one work queue served by one persistent launch (each
+ * CTA takes the next (job, partition) item); their survivors are sorted by a
+ * CUDA graph captured once per batch object and replayed for every batch.
+ * Results are the same as finalizing each handle alone.
+ */
+typedef struct kc_batch_ctx* kc_batch;
+
+/* Create a batch object whose work is ordered on stream (a cudaStream_t as
+ * void*; NULL = its own stream). */
+kc_status kc_batch_create(void* stream, kc_batch* out);
+
+/* Finalize n open handles (all partitioned, distinct) together.  Work queued
+ * on each handle's stream is finished first; afterwards each handle is
+ * finalized as by kc_finalize and its stream is ordered after the batch. */
+kc_status kc_batch_finalize(kc_batch b, kc_handle* handles, int n);
+
+void kc_batch_destroy(kc_batch b);
+
 /* Fill *cfg with the defaults (struct_size set). */
 void kc_default_config(kc_config* cfg);
 

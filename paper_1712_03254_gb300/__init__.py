@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["KmerCounter", "KcError", "pack_ascii", "lib", "build", "Config", "Stats"]
+__all__ = ["KmerCounter", "KcBatch", "KcError", "pack_ascii", "lib", "build", "Config", "Stats"]
 
 _lock = threading.Lock()
 _lib = None
@@ -92,6 +92,12 @@ def lib():
             L.kc_status_string.restype = ctypes.c_char_p
             L.kc_pack_ascii.argtypes = [p, u64, p, p]
             L.kc_pack_ascii.restype = st
+            L.kc_batch_create.argtypes = [p, ctypes.POINTER(p)]
+            L.kc_batch_create.restype = st
+            L.kc_batch_finalize.argtypes = [p, ctypes.POINTER(p), i]
+            L.kc_batch_finalize.restype = st
+            L.kc_batch_destroy.argtypes = [p]
+            L.kc_batch_destroy.restype = None
             _lib = L
     return _lib
 
@@ -213,3 +219,28 @@ class KmerCounter:
 
     def reset(self):
         _check(self._L.kc_reset(self._h), "kc_reset")
+
+
+class KcBatch:
+    """Finalizes several partitioned KmerCounter jobs together (kc_batch_*)."""
+
+    def __init__(self, stream=None):
+        L = lib()
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        b = ctypes.c_void_p()
+        _check(L.kc_batch_create(stream, ctypes.byref(b)), "kc_batch_create")
+        self._b = b
+        self._L = L
+
+    def finalize(self, counters):
+        arr = (ctypes.c_void_p * len(counters))(*[c._h for c in counters])
+        _check(self._L.kc_batch_finalize(self._b, arr, len(counters)), "kc_batch_finalize")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.kc_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        self.close()

@@ -19,10 +19,9 @@
 #include <string>
 #include <vector>
 
-#include "../../include/kc.h"
-#include "kc_internal.h"
+#include "kc_ctx.h"
 
-namespace {
+namespace kcapi {
 
 thread_local std::string g_last_error;
 
@@ -36,11 +35,6 @@ kc_status cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? KC_ERR_OOM_DEVICE : KC_ERR_CUDA;
 }
 
-#define KC_CUDA(call)                                          \
-    do {                                                       \
-        cudaError_t e_ = (call);                               \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
-    } while (0)
 
 int log2_exact(uint64_t x) {
     int r = 0;
@@ -60,87 +54,16 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-struct Batch {
-    int sample = 0;
-    // direct strategy: the resident reads, rescanned by the recount
-    uint64_t* pw = nullptr;  // packed words, 2 * n_units + 2
-    uint64_t* vw = nullptr;  // valid-window-start words, n_units
-    uint64_t n_units = 0;
-    // partitioned strategy: window hashes grouped by partition
-    uint64_t* hdata = nullptr;    // capacity: one per base of the batch
-    uint64_t* hstarts = nullptr;  // partition starts, 2^part_bits + 1
-    uint64_t hcap = 0;
-};
 
-enum class State { Open, Finalized, Poisoned };
 
-}  // namespace
+}  // namespace kcapi
 
 namespace kc {
-void set_last_error(const std::string& msg) { g_last_error = msg; }
+void set_last_error(const std::string& msg) { kcapi::g_last_error = msg; }
 }  // namespace kc
 
-struct kc_ctx {
-    int k = 0, n_samples = 0, n_hashes = 0;
-    uint64_t bloom_bits = 0;
-    uint32_t min_count = 0;
-    kc_config cfg{};
-    int device = 0;
-    cudaStream_t stream = nullptr, copy_stream = nullptr;
-    bool own_stream = false;
-    cudaEvent_t ev_copy = nullptr, ev_main = nullptr;
-    kc::Grid grid;
-    int log2_words = 0, log2_slots = 0;
-    uint64_t n_slots = 0;
-    int strategy = KC_STRATEGY_DIRECT;
-    int part_bits = 0;   // partitioned: 2^part_bits partitions
-    int slice_log2 = 0;  // partitioned: filter words per partition
 
-    uint64_t* bloom = nullptr;
-    kc::Slot* table = nullptr;
-    kc::DevCounters* ctr = nullptr;
-    std::vector<Batch> batches;
-    uint64_t bases = 0;
-
-    uint64_t* res_keys = nullptr;
-    uint64_t* res_vals = nullptr;
-    uint64_t n_result = 0;
-    uint64_t res_cap = 0;
-
-    kc::DevCounters host_ctr{};
-    State state = State::Open;
-    size_t fixed_bytes = 0;
-
-    // Phase timing (kc_config.timing): event pairs recorded on the stream,
-    // turned into milliseconds after the next synchronisation.
-    struct Mark {
-        int phase;
-        cudaEvent_t a, b;
-    };
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<Mark> marks;
-    double ms[5] = {0, 0, 0, 0, 0};
-    uint64_t launches = 0;
-    uint32_t fallback_partitions = 0;
-
-    kc::PassParams params(int sample) const {
-        kc::PassParams p{};
-        p.k = k;
-        p.rc_shift = 64 - 2 * k;
-        p.kmask = (1ull << (2 * k)) - 1ull;
-        p.bloom_shift = 64 - log2_words;
-        p.n_hashes = n_hashes;
-        p.table_shift = 64 - log2_slots;
-        p.table_mask = n_slots - 1;
-        p.all_candidates = min_count <= 1 ? 1 : 0;
-        p.sample = sample;
-        return p;
-    }
-};
-
-namespace {
-
-enum Phase { kIngest = 0, kPass1 = 1, kPass2 = 2, kCompact = 3, kSort = 4 };
+namespace kcapi {
 
 cudaEvent_t phase_begin(kc_handle h) {
     if (!h->cfg.timing) return nullptr;
@@ -394,192 +317,17 @@ kc_status finalize_direct(kc_handle h) {
     return s;
 }
 
-// Fallback for partitions whose shared-memory table overflowed: the
-// partition's filter slice is rebuilt from zero and its keys are counted in a
-// global table sized for every window of the partition.
-kc_status fallback_partitions(kc_handle h, const std::vector<uint32_t>& failed, const std::vector<uint64_t>& hs,
-                              const kc::ConsumeArgs& A, uint64_t*& tk, uint64_t*& tv, uint64_t& out_cap) {
-    cudaStream_t st = h->stream;
-    const uint64_t P = 1ull << h->part_bits;
-    const size_t nb = h->batches.size();
-    auto windows_of = [&](uint32_t p) {
-        uint64_t w = 0;
-        for (size_t b = 0; b < nb; ++b) w += hs[b * (P + 1) + p + 1] - hs[b * (P + 1) + p];
-        return w;
-    };
-    uint64_t extra = 0;
-    for (uint32_t p : failed) extra += windows_of(p);
-    kc_status s = read_counters(h);
-    if (s != KC_OK) return s;
-    const uint64_t need = h->host_ctr.survivors + extra;
-    if (need > out_cap) {  // grow the survivor arrays, keeping what is there
-        uint64_t *nk = nullptr, *nv = nullptr;
-        cudaError_t e;
-        if ((e = cudaMallocAsync(&nk, need * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&nv, need * 8, st)) != cudaSuccess) {
-            if (nk) cudaFreeAsync(nk, st);
-            return cuda_fail(e, "cudaMallocAsync(fallback survivors)");
-        }
-        const uint64_t have = std::min<uint64_t>(h->host_ctr.survivors, out_cap);
-        KC_CUDA(cudaMemcpyAsync(nk, tk, have * 8, cudaMemcpyDeviceToDevice, st));
-        KC_CUDA(cudaMemcpyAsync(nv, tv, have * 8, cudaMemcpyDeviceToDevice, st));
-        cudaFreeAsync(tk, st);
-        cudaFreeAsync(tv, st);
-        tk = nk;
-        tv = nv;
-        out_cap = need;
-    }
-    const uint64_t n_sw = 1ull << h->slice_log2;
-    for (uint32_t p : failed) {
-        const uint64_t w = windows_of(p);
-        uint64_t slots = 1024;
-        while (slots < 2 * w) slots <<= 1;
-        kc::Slot* table = nullptr;
-        cudaError_t e = cudaMallocAsync(&table, slots * sizeof(kc::Slot), st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(fallback table)");
-        KC_CUDA(cudaMemsetAsync(table, 0, slots * sizeof(kc::Slot), st));
-        KC_CUDA(cudaMemsetAsync(h->bloom + p * n_sw, 0, n_sw * 8, st));
-        kc::FallbackArgs F{};
-        F.data = A.data;
-        F.starts = A.starts;
-        F.samples = A.samples;
-        F.part = p;
-        F.part_bits = h->part_bits;
-        F.bloom_shift = A.bloom_shift;
-        F.n_hashes = h->n_hashes;
-        F.n_samples = h->n_samples;
-        F.all_candidates = A.all_candidates;
-        F.min_count = h->min_count;
-        F.bloom = reinterpret_cast<unsigned long long*>(h->bloom);
-        F.table = table;
-        F.table_mask = slots - 1;
-        F.out_keys = tk;
-        F.out_vals = tv;
-        F.out_cap = out_cap;
-        F.n_out = &h->ctr->survivors;
-        F.ctr = h->ctr;
-        for (size_t b = 0; b < nb; ++b) kc::launch_fb_claim(F, (int)b, st);
-        for (size_t b = 0; b < nb; ++b) kc::launch_fb_recount(F, (int)b, st);
-        kc::launch_fb_compact(F, st);
-        h->launches += 2 * nb + 1;
-        KC_CUDA(cudaGetLastError());
-        cudaFreeAsync(table, st);
-    }
-    return KC_OK;
-}
-
 kc_status finalize_partitioned(kc_handle h) {
-    cudaStream_t st = h->stream;
-    const int a = h->part_bits;
-    const uint64_t P = 1ull << a;
-    const size_t nb = h->batches.size();
-    // partition sizes over all batches
-    std::vector<uint64_t> hs(nb * (P + 1));
-    for (size_t b = 0; b < nb; ++b)
-        KC_CUDA(cudaMemcpyAsync(hs.data() + b * (P + 1), h->batches[b].hstarts, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
-    kc_status s = read_counters(h);
-    if (s != KC_OK) return s;
-    if ((s = device_errors(h)) != KC_OK) return s;
-    uint64_t max_w = 0, total_w = 0;
-    for (uint64_t p = 0; p < P; ++p) {
-        uint64_t w = 0;
-        for (size_t b = 0; b < nb; ++b) w += hs[b * (P + 1) + p + 1] - hs[b * (P + 1) + p];
-        max_w = std::max(max_w, w);
-        total_w += w;
+    if (!h->engine) {
+        kc_status s = kc_batch_create_internal(h->stream, &h->engine);
+        if (s != KC_OK) return s;
     }
-    // Shared-memory table: about one slot per 8 windows of the largest
-    // partition (keys seen at least twice, at half load), 1024..8192 slots.
-    int tl = (int)h->cfg.smem_table_log2;
-    if (!tl) {
-        tl = 10;
-        while (tl < 13 && (1ull << tl) < max_w / 8) ++tl;
-    }
-    int max_optin = 0, max_sm = 0;
-    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
-    while (tl > 10 && kc::consume_smem(h->slice_log2, tl, h->n_samples) + 1024 > (size_t)max_optin) --tl;
-    const size_t smem = kc::consume_smem(h->slice_log2, tl, h->n_samples);
-    if (smem + 1024 > (size_t)max_optin) return fail(KC_ERR_INTERNAL, "partition does not fit shared memory");
-    const int per_sm = std::max(1, std::min(4, max_sm / (int)(smem + 2048)));
-    const int n_ctas = (int)std::min<uint64_t>(P, (uint64_t)h->grid.sm_count * per_sm);
-
-    uint64_t out_cap = std::max<uint64_t>(1, std::min<uint64_t>(P << tl, total_w));
-    uint64_t *tk = nullptr, *tv = nullptr;
-    uint32_t* failed = nullptr;
-    void* meta = nullptr;
-    const size_t meta_bytes = std::max<size_t>(16, nb * 16 + nb * 4);
-    cudaError_t e;
-    if ((e = cudaMallocAsync(&tk, out_cap * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&tv, out_cap * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&failed, (P + 1) * 4, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&meta, meta_bytes, st)) != cudaSuccess) {
-        if (tk) cudaFreeAsync(tk, st);
-        if (tv) cudaFreeAsync(tv, st);
-        if (failed) cudaFreeAsync(failed, st);
-        return cuda_fail(e, "cudaMallocAsync(partition consumer)");
-    }
-    std::vector<unsigned char> hmeta(meta_bytes, 0);
-    for (size_t b = 0; b < nb; ++b) {
-        const uint64_t dp = (uint64_t)(uintptr_t)h->batches[b].hdata, sp = (uint64_t)(uintptr_t)h->batches[b].hstarts;
-        const int smp = h->batches[b].sample;
-        std::memcpy(hmeta.data() + b * 8, &dp, 8);
-        std::memcpy(hmeta.data() + nb * 8 + b * 8, &sp, 8);
-        std::memcpy(hmeta.data() + nb * 16 + b * 4, &smp, 4);
-    }
-    KC_CUDA(cudaMemcpyAsync(meta, hmeta.data(), meta_bytes, cudaMemcpyHostToDevice, st));
-    KC_CUDA(cudaMemsetAsync(failed + P, 0, 4, st));
-    KC_CUDA(cudaMemsetAsync(&h->ctr->survivors, 0, 8, st));
-
-    kc::ConsumeArgs A{};
-    A.data = reinterpret_cast<const uint64_t* const*>(meta);
-    A.starts = reinterpret_cast<const uint64_t* const*>(static_cast<char*>(meta) + nb * 8);
-    A.samples = reinterpret_cast<const int*>(static_cast<char*>(meta) + nb * 16);
-    A.n_batches = (int)nb;
-    A.part_bits = a;
-    A.slice_log2 = h->slice_log2;
-    A.table_log2 = tl;
-    A.bloom_shift = 64 - h->log2_words;
-    A.n_hashes = h->n_hashes;
-    A.n_samples = h->n_samples;
-    A.all_candidates = h->min_count <= 1 ? 1 : 0;
-    A.min_count = h->min_count;
-    A.bloom = reinterpret_cast<unsigned long long*>(h->bloom);
-    A.out_keys = tk;
-    A.out_vals = tv;
-    A.out_cap = out_cap;
-    A.n_out = &h->ctr->survivors;
-    A.failed = failed;
-    A.n_failed = failed + P;
-    A.ctr = h->ctr;
-    cudaEvent_t t0 = phase_begin(h);
-    if (kc::launch_part_consume(A, n_ctas, st) != 0) {
-        cudaGetLastError();
-        return fail(KC_ERR_CUDA, "partition consumer launch configuration");
-    }
-    phase_end(h, kPass2, t0);
-    h->launches += 1;
-    KC_CUDA(cudaGetLastError());
-    uint32_t n_failed = 0;
-    KC_CUDA(cudaMemcpyAsync(&n_failed, failed + P, 4, cudaMemcpyDeviceToHost, st));
-    if ((s = read_counters(h)) != KC_OK) return s;
-    if (n_failed) {
-        std::vector<uint32_t> fl(n_failed);
-        KC_CUDA(cudaMemcpyAsync(fl.data(), failed, n_failed * 4, cudaMemcpyDeviceToHost, st));
-        KC_CUDA(cudaStreamSynchronize(st));
-        t0 = phase_begin(h);
-        s = fallback_partitions(h, fl, hs, A, tk, tv, out_cap);
-        phase_end(h, kCompact, t0);
-        if (s == KC_OK) s = read_counters(h);
-        if (s == KC_OK) s = device_errors(h);
-    }
-    h->fallback_partitions = n_failed;
-    if (s == KC_OK) s = sort_result(h, tk, tv);
-    cudaFreeAsync(tk, st);
-    cudaFreeAsync(tv, st);
-    cudaFreeAsync(failed, st);
-    cudaFreeAsync(meta, st);
-    return s;
+    return kc_batch_finalize_internal(h->engine, &h, 1);
 }
 
-}  // namespace
+}  // namespace kcapi
+
+using namespace kcapi;
 
 extern "C" {
 
@@ -730,6 +478,7 @@ void kc_destroy(kc_handle h) {
         free_result(h);
         cudaStreamSynchronize(h->stream);
     }
+    if (h->engine) kc_batch_destroy_internal(h->engine);
     if (h->bloom) cudaFree(h->bloom);
     if (h->table) cudaFree(h->table);
     if (h->ctr) cudaFree(h->ctr);
@@ -852,7 +601,8 @@ kc_status kc_finalize(kc_handle h) {
     kc_status s = check_open(h);
     if (s != KC_OK) return s;
     if (h->state == State::Finalized) return KC_OK;
-    s = h->strategy == KC_STRATEGY_DIRECT ? finalize_direct(h) : finalize_partitioned(h);
+    if (h->strategy != KC_STRATEGY_DIRECT) return finalize_partitioned(h);  // sets the state
+    s = finalize_direct(h);
     if (s != KC_OK) return s;
     h->state = State::Finalized;
     return KC_OK;

@@ -1,0 +1,968 @@
+// Batched finalize: many partitioned counting jobs in one set of launches.
+//
+// Consume: one persistent launch over a device work queue of (job, partition)
+// items from every job of the batch.  Each CTA takes the next item, keeps the
+// partition's filter slice and table in shared memory (filter update, candidate
+// claims, exact recount, survivor compaction; the same steps as the single-job
+// consumer) and moves on, so uneven jobs share the GPU without a launch each.
+// Sort: every job's survivors are bucketed by the top bits of their key into
+// one flat bucket array covering all jobs, scanned once, scattered into each
+// job's own result arrays, and each bucket sorted by one warp.  These launches
+// read every size and pointer from a device-side batch descriptor, so the
+// sequence is captured once in a CUDA graph and replayed for every batch.
+// A single kc_finalize is a batch of one.
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "kc_ctx.h"
+
+namespace kc {
+
+struct JobDesc {
+    // consumer
+    int part_bits, slice_log2, table_log2, bloom_shift;
+    int n_hashes, n_samples, all_candidates, key_bits;
+    uint32_t min_count;
+    int n_batches;
+    uint32_t item_base;  // first queue item of this job
+    uint32_t pad0;
+    const uint64_t* const* data;
+    const uint64_t* const* starts;
+    const int* samples;
+    unsigned long long* bloom;
+    uint64_t* sv_keys;
+    uint64_t* sv_vals;
+    uint64_t sv_cap;
+    uint32_t* failed;
+    DevCounters* ctr;
+    // sort
+    int sort_bits;
+    int pad1;
+    uint64_t bucket_base;  // first bucket of this job in the flat arrays
+    uint64_t n_buckets;
+    uint64_t* res_keys;
+    uint64_t* res_vals;
+    uint64_t res_cap;
+};
+
+struct BatchDesc {
+    const JobDesc* jobs;
+    const uint32_t* item_job;
+    unsigned long long* counters;  // per job: [2j] survivors, [2j+1] failed partitions
+    unsigned int* head;            // work-queue head
+    unsigned int* err;             // DERR_* bits of the sort
+    uint32_t n_jobs;
+    uint32_t n_items;
+    uint64_t n_buckets;  // total over jobs
+    uint32_t* hist;
+    uint64_t* starts;
+    uint64_t* cursor;
+    unsigned long long* tiles;
+    uint64_t n_tiles;
+};
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kConsumeThreads = 512;
+constexpr int kTile = 4096;
+
+// NH > 0: every job of the batch sets NH bits per key; NH = 0: per job.
+template <int NH>
+__global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDesc* __restrict__ D) {
+    extern __shared__ unsigned long long s_mem[];
+    __shared__ int s_fail;
+    __shared__ unsigned s_item;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t n_items = D->n_items;
+    uint64_t cand = 0, claimed = 0;
+    DevCounters* last_ctr = nullptr;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(D->head, 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        if (item >= n_items) break;
+        const uint32_t j = D->item_job[item];
+        const JobDesc& J = D->jobs[j];
+        const uint32_t part = item - J.item_base;
+        const uint32_t n_sw = 1u << J.slice_log2;
+        const uint32_t T = 1u << J.table_log2;
+        const uint32_t tmask = T - 1;
+        const int S = J.n_samples;
+        const int a = J.part_bits;
+        const uint64_t low_mask = (1ull << (64 - a)) - 1ull;
+        const int home_shift = 64 - a - J.table_log2;
+        unsigned long long* sb = s_mem;
+        unsigned long long* sk = s_mem + n_sw;
+        uint32_t* sc = reinterpret_cast<uint32_t*>(s_mem + n_sw + T);
+        if (J.ctr != last_ctr) {  // per-job candidate counters
+            cand = warp_sum(cand);
+            claimed = warp_sum(claimed);
+            if (lane == 0 && last_ctr) {
+                if (cand) atomicAdd(&last_ctr->candidates, (unsigned long long)cand);
+                if (claimed) atomicAdd(&last_ctr->claimed, (unsigned long long)claimed);
+            }
+            cand = claimed = 0;
+            last_ctr = J.ctr;
+        }
+        for (uint32_t i = threadIdx.x; i < n_sw; i += blockDim.x) sb[i] = 0ull;
+        for (uint32_t i = threadIdx.x; i < T; i += blockDim.x) sk[i] = 0ull;
+        for (uint32_t i = threadIdx.x; i < T * S; i += blockDim.x) sc[i] = 0u;
+        if (threadIdx.x == 0) s_fail = 0;
+        __syncthreads();
+        for (int bt = 0; bt < J.n_batches; ++bt) {
+            const uint64_t* __restrict__ d = J.data[bt];
+            const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
+            for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const uint64_t h = __ldcg(d + i);  // read again by the recount: keep in L2
+                if ((uint32_t)(h >> (64 - a)) != part) continue;  // run padding
+                const uint32_t w = (uint32_t)(h >> J.bloom_shift) & (n_sw - 1);
+                const uint64_t g = mixer64(h);
+                const uint64_t pat = NH > 0 ? bloom_pattern_n<(NH > 0 ? NH : 1)>(g) : bloom_pattern_rt(g, J.n_hashes);
+                const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
+                if (J.all_candidates || (old & pat) == pat) {
+                    ++cand;
+                    const int r = smem_claim(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
+                    if (r < 0) s_fail = 1;
+                    else claimed += (uint64_t)r;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            if (threadIdx.x == 0) J.failed[atomicAdd(&D->counters[2 * j + 1], 1ull)] = part;
+            __syncthreads();
+            continue;
+        }
+        for (int bt = 0; bt < J.n_batches; ++bt) {
+            const uint64_t* __restrict__ d = J.data[bt];
+            const int smp = J.samples[bt];
+            const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
+            for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const uint64_t h = __ldcs(d + i);  // last use
+                if ((uint32_t)(h >> (64 - a)) != part) continue;
+                const int s = smem_find(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
+                if (s >= 0) atomicAdd(sc + (uint32_t)s * S + smp, 1u);
+            }
+        }
+        __syncthreads();
+        const uint64_t hpre = (uint64_t)part << (64 - a);
+        for (uint32_t i0 = threadIdx.x & ~31u; i0 < T; i0 += blockDim.x) {
+            const uint32_t i = i0 + lane;
+            const unsigned long long k1 = sk[i];
+            uint64_t v = 0;
+            bool keep = false;
+            if (k1 != 0ull) {
+                const uint32_t c0 = sc[i * S];
+                const uint32_t c1 = S == 2 ? sc[i * S + 1] : 0u;
+                keep = (uint64_t)c0 + c1 >= J.min_count;
+                v = (uint64_t)c0 | ((uint64_t)c1 << 32);
+            }
+            const unsigned ballot = __ballot_sync(kFull, keep);
+            if (ballot) {
+                const int leader = __ffs(ballot) - 1;
+                unsigned long long pos0 = 0;
+                if (lane == leader) pos0 = atomicAdd(&D->counters[2 * j], (unsigned long long)__popc(ballot));
+                pos0 = __shfl_sync(kFull, pos0, leader);
+                if (keep) {
+                    const uint64_t pos = pos0 + __popc(ballot & lt);
+                    if (pos < J.sv_cap) {
+                        J.sv_keys[pos] = unmixer64(hpre | (k1 - 1ull));
+                        J.sv_vals[pos] = v;
+                    }
+                }
+            }
+        }
+        unsigned long long* gb = J.bloom + (uint64_t)part * n_sw;
+        for (uint32_t i = threadIdx.x; i < n_sw; i += blockDim.x) gb[i] = sb[i];
+        __syncthreads();
+    }
+    cand = warp_sum(cand);
+    claimed = warp_sum(claimed);
+    if (lane == 0 && last_ctr) {
+        if (cand) atomicAdd(&last_ctr->candidates, (unsigned long long)cand);
+        if (claimed) atomicAdd(&last_ctr->claimed, (unsigned long long)claimed);
+    }
+}
+
+__global__ void k_prefix_hist_q(const BatchDesc* __restrict__ D) {
+    for (uint32_t j = blockIdx.y; j < D->n_jobs; j += gridDim.y) {
+        const JobDesc& J = D->jobs[j];
+        const uint64_t n = min((uint64_t)D->counters[2 * j], J.sv_cap);
+        const int shift = J.key_bits - J.sort_bits;
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            const uint64_t b = J.sv_keys[i] >> shift;
+            if (b < J.n_buckets) atomicAdd(D->hist + J.bucket_base + b, 1u);
+            else atomicOr(D->err, DERR_INTERNAL);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long block_scan_ex(unsigned long long x, unsigned long long* total) {
+    __shared__ unsigned long long s_w[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_w[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = lane < nw ? s_w[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        s_w[lane] = w;
+    }
+    __syncthreads();
+    *total = s_w[nw - 1];
+    return v - x + (wid ? s_w[wid - 1] : 0ull);
+}
+
+// Flat exclusive scan of D->hist over D->n_buckets counters (fixed grid of
+// D's tile capacity; tiles past the end exit).
+__global__ void __launch_bounds__(1024) k_scan_tiles_q(const BatchDesc* __restrict__ D) {
+    const uint64_t n = D->n_buckets;
+    const uint64_t t0 = (uint64_t)blockIdx.x * kTile;
+    if (t0 >= n) return;
+    unsigned long long x = 0;
+    for (int j = 0; j < kTile / 1024; ++j) {
+        const uint64_t i = t0 + (uint64_t)j * 1024 + threadIdx.x;
+        if (i < n) x += D->hist[i];
+    }
+    unsigned long long tot;
+    block_scan_ex(x, &tot);
+    if (threadIdx.x == 0) D->tiles[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top_q(const BatchDesc* __restrict__ D) {
+    const uint64_t n_tiles = (D->n_buckets + kTile - 1) / kTile;
+    unsigned long long run_base = 0;
+    for (uint64_t c0 = 0; c0 < n_tiles; c0 += 1024) {
+        const uint64_t i = c0 + threadIdx.x;
+        const unsigned long long x = i < n_tiles ? D->tiles[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = block_scan_ex(x, &tot);
+        if (i < n_tiles) D->tiles[i] = run_base + ex;
+        run_base += tot;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply_q(const BatchDesc* __restrict__ D) {
+    const uint64_t n = D->n_buckets;
+    const uint64_t t0 = (uint64_t)blockIdx.x * kTile;
+    if (t0 >= n) return;
+    const uint64_t i0 = t0 + (uint64_t)threadIdx.x * 4;
+    uint32_t c[4];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j] = i0 + j < n ? D->hist[i0 + j] : 0u;
+        sum += c[j];
+    }
+    unsigned long long tot;
+    unsigned long long run = block_scan_ex(sum, &tot) + D->tiles[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (i0 + j < n) {
+            D->starts[i0 + j] = run;
+            D->cursor[i0 + j] = run;
+        }
+        run += c[j];
+    }
+    if (i0 < n && i0 + 4 >= n) D->starts[n] = run;
+}
+
+__global__ void k_scatter_q(const BatchDesc* __restrict__ D) {
+    for (uint32_t j = blockIdx.y; j < D->n_jobs; j += gridDim.y) {
+        const JobDesc& J = D->jobs[j];
+        const uint64_t n = min((uint64_t)D->counters[2 * j], J.sv_cap);
+        const int shift = J.key_bits - J.sort_bits;
+        const uint64_t job0 = D->starts[J.bucket_base];
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            const uint64_t key = J.sv_keys[i];
+            const uint64_t b = key >> shift;
+            if (b >= J.n_buckets) {
+                atomicOr(D->err, DERR_INTERNAL);
+                continue;
+            }
+            const uint64_t pos = atomicAdd(reinterpret_cast<unsigned long long*>(D->cursor) + J.bucket_base + b, 1ull) - job0;
+            if (pos >= J.res_cap) {
+                atomicOr(D->err, DERR_INTERNAL);
+                continue;
+            }
+            J.res_keys[pos] = key;
+            J.res_vals[pos] = J.sv_vals[i];
+        }
+    }
+}
+
+// Job owning flat bucket fb (jobs are in bucket order).
+__device__ __forceinline__ uint32_t job_of_bucket(const BatchDesc* D, uint64_t fb) {
+    uint32_t lo = 0, hi = D->n_jobs;  // invariant: jobs[lo].bucket_base <= fb
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (D->jobs[mid].bucket_base <= fb) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256, 2) k_warp_sort_q(const BatchDesc* __restrict__ D) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t nb = D->n_buckets;
+    for (uint64_t fb = warp; fb < nb; fb += n_warps) {
+        const uint64_t n64 = D->starts[fb + 1] - D->starts[fb];
+        if (n64 <= 1) continue;
+        if (n64 > 256) {
+            if (lane == 0) atomicOr(D->err, DERR_SORT_MEDIUM);
+            continue;
+        }
+        const JobDesc& J = D->jobs[job_of_bucket(D, fb)];
+        const uint64_t lo = D->starts[fb] - D->starts[J.bucket_base];
+        const int n = (int)n64;
+        if (n <= 32) warp_sort_bucket<1>(J.res_keys, J.res_vals, lo, n, lane);
+        else if (n <= 64) warp_sort_bucket<2>(J.res_keys, J.res_vals, lo, n, lane);
+        else if (n <= 128) warp_sort_bucket<4>(J.res_keys, J.res_vals, lo, n, lane);
+        else warp_sort_bucket<8>(J.res_keys, J.res_vals, lo, n, lane);
+    }
+}
+
+// Buckets of 257..2048 keys: one CTA each, bitonic network in shared memory
+// (mirror form, indices >= n act as +infinity).  Larger ones are flagged.
+constexpr int kMedCap = 2048;
+
+__global__ void __launch_bounds__(256) k_medium_sort_q(const BatchDesc* __restrict__ D) {
+    __shared__ uint64_t sk[kMedCap];
+    __shared__ uint64_t sv[kMedCap];
+    for (uint64_t fb = blockIdx.x; fb < D->n_buckets; fb += gridDim.x) {
+        const uint64_t n64 = D->starts[fb + 1] - D->starts[fb];
+        if (n64 <= 256) continue;
+        if (n64 > (uint64_t)kMedCap) {
+            if (threadIdx.x == 0) atomicOr(D->err, DERR_SORT_BUCKET);
+            continue;
+        }
+        const JobDesc& J = D->jobs[job_of_bucket(D, fb)];
+        const uint64_t lo = D->starts[fb] - D->starts[J.bucket_base];
+        const int n = (int)n64;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            sk[i] = J.res_keys[lo + i];
+            sv[i] = J.res_vals[lo + i];
+        }
+        int n2 = 1;
+        while (n2 < n) n2 <<= 1;
+        __syncthreads();
+        for (int size = 2; size <= n2; size <<= 1) {
+            const int half = size >> 1;
+            for (int i = threadIdx.x; i < (n2 >> 1); i += blockDim.x) {
+                const int blk = i / half, off = i % half;
+                const int x = blk * size + off, y = blk * size + size - 1 - off;
+                if (y < n && sk[x] > sk[y]) {
+                    const uint64_t tk = sk[x], tv = sv[x];
+                    sk[x] = sk[y];
+                    sv[x] = sv[y];
+                    sk[y] = tk;
+                    sv[y] = tv;
+                }
+            }
+            __syncthreads();
+            for (int stride = size >> 2; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < (n2 >> 1); i += blockDim.x) {
+                    const int x = 2 * i - (i & (stride - 1)), y = x + stride;
+                    if (y < n && sk[x] > sk[y]) {
+                        const uint64_t tk = sk[x], tv = sv[x];
+                        sk[x] = sk[y];
+                        sv[x] = sv[y];
+                        sk[y] = tk;
+                        sv[y] = tv;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            J.res_keys[lo + i] = sk[i];
+            J.res_vals[lo + i] = sv[i];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+}  // namespace kc
+
+using namespace kcapi;
+
+struct kc_batch_ctx {
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int device = 0, sm_count = 152, max_optin = 0, max_sm = 0;
+    kc::BatchDesc* d_desc = nullptr;
+    kc::JobDesc* d_jobs = nullptr;
+    uint32_t* d_item_job = nullptr;
+    unsigned long long* d_counters = nullptr;
+    unsigned int* d_flags = nullptr;  // [0] queue head, [1] sort error bits
+    size_t jobs_cap = 0, items_cap = 0;
+    uint32_t* d_hist = nullptr;
+    uint64_t* d_starts = nullptr;
+    uint64_t* d_cursor = nullptr;
+    unsigned long long* d_tiles = nullptr;
+    uint64_t buckets_cap = 0, tiles_cap = 0;
+    cudaGraphExec_t sort_graph = nullptr;
+    std::vector<kc::JobDesc> jobs;
+    std::vector<uint32_t> item_job;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+template <class T>
+kc_status grow(T*& p, size_t& cap, size_t need) {
+    if (need <= cap) return KC_OK;
+    size_t n = std::max<size_t>(need, cap * 2);
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    KC_CUDA(cudaMalloc(&p, n * sizeof(T)));
+    cap = n;
+    return KC_OK;
+}
+
+kc_status ensure_jobs(kc_batch_ctx* b, size_t n_jobs, size_t n_items) {
+    if (n_jobs > b->jobs_cap) {
+        size_t n = std::max<size_t>(n_jobs, b->jobs_cap * 2);
+        if (b->d_jobs) cudaFree(b->d_jobs);
+        if (b->d_counters) cudaFree(b->d_counters);
+        b->d_jobs = nullptr;
+        b->d_counters = nullptr;
+        b->jobs_cap = 0;
+        KC_CUDA(cudaMalloc(&b->d_jobs, n * sizeof(kc::JobDesc)));
+        KC_CUDA(cudaMalloc(&b->d_counters, 2 * n * sizeof(unsigned long long)));
+        b->jobs_cap = n;
+    }
+    size_t cap = b->items_cap;
+    kc_status s = grow(b->d_item_job, cap, n_items);
+    b->items_cap = cap;
+    return s;
+}
+
+kc_status ensure_buckets(kc_batch_ctx* b, uint64_t n_buckets) {
+    if (n_buckets <= b->buckets_cap) return KC_OK;
+    const uint64_t n = std::max<uint64_t>(n_buckets, 1ull << 16);
+    if (b->d_hist) cudaFree(b->d_hist);
+    if (b->d_starts) cudaFree(b->d_starts);
+    if (b->d_cursor) cudaFree(b->d_cursor);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    b->d_hist = nullptr;
+    b->d_starts = b->d_cursor = nullptr;
+    b->d_tiles = nullptr;
+    b->buckets_cap = 0;
+    const uint64_t tiles = (n + kc::kTile - 1) / kc::kTile;
+    KC_CUDA(cudaMalloc(&b->d_hist, n * 4));
+    KC_CUDA(cudaMalloc(&b->d_starts, (n + 1) * 8));
+    KC_CUDA(cudaMalloc(&b->d_cursor, n * 8));
+    KC_CUDA(cudaMalloc(&b->d_tiles, tiles * 8));
+    b->buckets_cap = n;
+    b->tiles_cap = tiles;
+    if (b->sort_graph) {  // the graph holds the old capacities
+        cudaGraphExecDestroy(b->sort_graph);
+        b->sort_graph = nullptr;
+    }
+    return KC_OK;
+}
+
+// Capture the sort sequence once; it reads everything else from d_desc.
+kc_status capture_sort_graph(kc_batch_ctx* b) {
+    cudaGraph_t g = nullptr;
+    KC_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    const dim3 grid2((unsigned)b->sm_count * 4, 32);
+    cudaMemsetAsync(b->d_hist, 0, b->buckets_cap * 4, b->st);
+    kc::k_prefix_hist_q<<<grid2, 256, 0, b->st>>>(b->d_desc);
+    kc::k_scan_tiles_q<<<(unsigned)b->tiles_cap, 1024, 0, b->st>>>(b->d_desc);
+    kc::k_scan_top_q<<<1, 1024, 0, b->st>>>(b->d_desc);
+    kc::k_scan_apply_q<<<(unsigned)b->tiles_cap, 1024, 0, b->st>>>(b->d_desc);
+    kc::k_scatter_q<<<grid2, 256, 0, b->st>>>(b->d_desc);
+    kc::k_warp_sort_q<<<(unsigned)b->sm_count * 8, 256, 0, b->st>>>(b->d_desc);
+    cudaError_t e = cudaStreamEndCapture(b->st, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(sort)");
+    e = cudaGraphInstantiate(&b->sort_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(sort)");
+    return KC_OK;
+}
+
+kc_status upload_desc(kc_batch_ctx* b, uint32_t n_jobs, uint32_t n_items, uint64_t n_buckets) {
+    kc::BatchDesc d{};
+    d.jobs = b->d_jobs;
+    d.item_job = b->d_item_job;
+    d.counters = b->d_counters;
+    d.head = b->d_flags;
+    d.err = b->d_flags + 1;
+    d.n_jobs = n_jobs;
+    d.n_items = n_items;
+    d.n_buckets = n_buckets;
+    d.hist = b->d_hist;
+    d.starts = b->d_starts;
+    d.cursor = b->d_cursor;
+    d.tiles = b->d_tiles;
+    d.n_tiles = b->tiles_cap;
+    KC_CUDA(cudaMemcpyAsync(b->d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, b->st));
+    KC_CUDA(cudaMemcpyAsync(b->d_jobs, b->jobs.data(), n_jobs * sizeof(kc::JobDesc), cudaMemcpyHostToDevice, b->st));
+    return KC_OK;
+}
+
+struct JobWork {
+    kc_handle h;
+    std::vector<uint64_t> hs;  // partition starts of every batch
+    uint64_t total_w = 0, max_w = 0;
+    uint64_t* sv_keys = nullptr;
+    uint64_t* sv_vals = nullptr;
+    uint64_t sv_cap = 0;
+    uint32_t* failed = nullptr;
+    void* meta = nullptr;
+};
+
+void release_work(kc_batch_ctx* b, std::vector<JobWork>& w) {
+    for (auto& x : w) {
+        if (x.sv_keys) cudaFreeAsync(x.sv_keys, b->st);
+        if (x.sv_vals) cudaFreeAsync(x.sv_vals, b->st);
+        if (x.failed) cudaFreeAsync(x.failed, b->st);
+        if (x.meta) cudaFreeAsync(x.meta, b->st);
+        x.sv_keys = x.sv_vals = nullptr;
+        x.failed = nullptr;
+        x.meta = nullptr;
+    }
+}
+
+template <int NH>
+cudaError_t launch_consume_nh(int n_ctas, size_t smem, const kc::BatchDesc* d, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(kc::k_consume_q<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kc::k_consume_q<NH><<<n_ctas, kc::kConsumeThreads, smem, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_consume(int nh, int n_ctas, size_t smem, const kc::BatchDesc* d, cudaStream_t st) {
+    switch (nh) {
+        case 1: return launch_consume_nh<1>(n_ctas, smem, d, st);
+        case 2: return launch_consume_nh<2>(n_ctas, smem, d, st);
+        case 3: return launch_consume_nh<3>(n_ctas, smem, d, st);
+        case 4: return launch_consume_nh<4>(n_ctas, smem, d, st);
+        case 5: return launch_consume_nh<5>(n_ctas, smem, d, st);
+        case 6: return launch_consume_nh<6>(n_ctas, smem, d, st);
+        case 7: return launch_consume_nh<7>(n_ctas, smem, d, st);
+        case 8: return launch_consume_nh<8>(n_ctas, smem, d, st);
+        case 9: return launch_consume_nh<9>(n_ctas, smem, d, st);
+        case 10: return launch_consume_nh<10>(n_ctas, smem, d, st);
+        default: return launch_consume_nh<0>(n_ctas, smem, d, st);
+    }
+}
+
+// Partitions whose shared-memory table overflowed: rebuild their filter
+// slice from zero and count them in a global table (kc_partition.cu kernels).
+kc_status run_fallbacks(kc_batch_ctx* b, JobWork& x, uint32_t j, uint32_t n_failed) {
+    kc_handle h = x.h;
+    const kc::JobDesc& J = b->jobs[j];
+    const uint64_t P = 1ull << h->part_bits;
+    const size_t nb = h->batches.size();
+    std::vector<uint32_t> fl(n_failed);
+    KC_CUDA(cudaMemcpyAsync(fl.data(), x.failed, n_failed * 4, cudaMemcpyDeviceToHost, b->st));
+    unsigned long long n_sv = 0;
+    KC_CUDA(cudaMemcpyAsync(&n_sv, b->d_counters + 2 * j, 8, cudaMemcpyDeviceToHost, b->st));
+    KC_CUDA(cudaStreamSynchronize(b->st));
+    auto windows_of = [&](uint32_t p) {
+        uint64_t w = 0;
+        for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
+        return w;
+    };
+    uint64_t extra = 0;
+    for (uint32_t p : fl) extra += windows_of(p);
+    const uint64_t need = n_sv + extra;
+    if (need > x.sv_cap) {
+        uint64_t *nk = nullptr, *nv = nullptr;
+        cudaError_t e;
+        if ((e = cudaMallocAsync(&nk, need * 8, b->st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&nv, need * 8, b->st)) != cudaSuccess) {
+            if (nk) cudaFreeAsync(nk, b->st);
+            return cuda_fail(e, "cudaMallocAsync(fallback survivors)");
+        }
+        const uint64_t have = std::min<uint64_t>(n_sv, x.sv_cap);
+        KC_CUDA(cudaMemcpyAsync(nk, x.sv_keys, have * 8, cudaMemcpyDeviceToDevice, b->st));
+        KC_CUDA(cudaMemcpyAsync(nv, x.sv_vals, have * 8, cudaMemcpyDeviceToDevice, b->st));
+        cudaFreeAsync(x.sv_keys, b->st);
+        cudaFreeAsync(x.sv_vals, b->st);
+        x.sv_keys = nk;
+        x.sv_vals = nv;
+        x.sv_cap = need;
+    }
+    const uint64_t n_sw = 1ull << h->slice_log2;
+    for (uint32_t p : fl) {
+        uint64_t slots = 1024;
+        while (slots < 2 * windows_of(p)) slots <<= 1;
+        kc::Slot* table = nullptr;
+        cudaError_t e = cudaMallocAsync(&table, slots * sizeof(kc::Slot), b->st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(fallback table)");
+        KC_CUDA(cudaMemsetAsync(table, 0, slots * sizeof(kc::Slot), b->st));
+        KC_CUDA(cudaMemsetAsync(h->bloom + p * n_sw, 0, n_sw * 8, b->st));
+        kc::FallbackArgs F{};
+        F.data = J.data;
+        F.starts = J.starts;
+        F.samples = J.samples;
+        F.part = p;
+        F.part_bits = h->part_bits;
+        F.bloom_shift = J.bloom_shift;
+        F.n_hashes = h->n_hashes;
+        F.n_samples = h->n_samples;
+        F.all_candidates = J.all_candidates;
+        F.min_count = h->min_count;
+        F.bloom = reinterpret_cast<unsigned long long*>(h->bloom);
+        F.table = table;
+        F.table_mask = slots - 1;
+        F.out_keys = x.sv_keys;
+        F.out_vals = x.sv_vals;
+        F.out_cap = x.sv_cap;
+        F.n_out = b->d_counters + 2 * j;
+        F.ctr = h->ctr;
+        for (size_t t = 0; t < nb; ++t) kc::launch_fb_claim(F, (int)t, b->st);
+        for (size_t t = 0; t < nb; ++t) kc::launch_fb_recount(F, (int)t, b->st);
+        kc::launch_fb_compact(F, b->st);
+        h->launches += 2 * nb + 1;
+        KC_CUDA(cudaGetLastError());
+        cudaFreeAsync(table, b->st);
+    }
+    h->fallback_partitions += n_failed;
+    return KC_OK;
+}
+
+}  // namespace
+
+kc_status kc_batch_create_internal(cudaStream_t st, kc_batch_ctx** out) {
+    *out = nullptr;
+    kc_batch_ctx* b = new (std::nothrow) kc_batch_ctx();
+    if (!b) return fail(KC_ERR_OOM_HOST, "host allocation");
+    auto bail = [&](kc_status s) {
+        kc_batch_destroy_internal(b);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+    cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+    cudaDeviceGetAttribute(&b->max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    cudaDeviceGetAttribute(&b->max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device);
+    if (st) {
+        b->st = st;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaStreamCreate"));
+        b->own_stream = true;
+    }
+    if ((e = cudaMalloc(&b->d_desc, sizeof(kc::BatchDesc))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_flags, 2 * sizeof(unsigned int))) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMalloc(batch descriptor)"));
+    *out = b;
+    return KC_OK;
+}
+
+void kc_batch_destroy_internal(kc_batch_ctx* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->sort_graph) cudaGraphExecDestroy(b->sort_graph);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_flags);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_item_job);
+    cudaFree(b->d_hist);
+    cudaFree(b->d_starts);
+    cudaFree(b->d_cursor);
+    cudaFree(b->d_tiles);
+    if (b->own_stream && b->st) cudaStreamDestroy(b->st);
+    delete b;
+}
+
+kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
+    if (!b || !hs || n < 0) return fail(KC_ERR_ARG, "null argument");
+    if (n == 0) return KC_OK;
+    cudaStream_t st = b->st;
+    std::vector<JobWork> work((size_t)n);
+    const bool one = n == 1 && hs[0]->stream == st;
+    // order the batch after every handle's queued work
+    for (int j = 0; j < n; ++j) {
+        kc_handle h = hs[j];
+        if (!h) return fail(KC_ERR_ARG, "null handle in batch");
+        if (h->state == State::Poisoned) return fail(KC_ERR_STATE, "handle poisoned by an earlier error; call kc_reset");
+        if (h->state != State::Open) return fail(KC_ERR_STATE, "handle already finalized");
+        if (h->strategy != KC_STRATEGY_PARTITIONED) return fail(KC_ERR_ARG, "batched finalize needs the partitioned strategy");
+        for (int i = 0; i < j; ++i)
+            if (hs[i] == h) return fail(KC_ERR_ARG, "handle listed twice");
+        if (!one) {
+            KC_CUDA(cudaEventRecord(h->ev_main, h->stream));
+            KC_CUDA(cudaStreamWaitEvent(st, h->ev_main, 0));
+        }
+        work[j].h = h;
+    }
+    // partition sizes of every job, and each job's counters (ingest errors)
+    std::vector<kc::DevCounters> hc((size_t)n);
+    for (int j = 0; j < n; ++j) {
+        kc_handle h = hs[j];
+        const uint64_t P = 1ull << h->part_bits;
+        work[j].hs.resize(h->batches.size() * (P + 1));
+        for (size_t t = 0; t < h->batches.size(); ++t)
+            KC_CUDA(cudaMemcpyAsync(work[j].hs.data() + t * (P + 1), h->batches[t].hstarts, (P + 1) * 8,
+                                    cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaMemcpyAsync(&hc[j], h->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
+    }
+    KC_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < n; ++j) {
+        hs[j]->host_ctr = hc[j];
+        kc_status s = device_errors(hs[j]);
+        if (s != KC_OK) return s;
+    }
+
+    // per-job consumer setup
+    b->jobs.assign((size_t)n, kc::JobDesc{});
+    b->item_job.clear();
+    size_t smem_max = 0;
+    for (int j = 0; j < n; ++j) {
+        JobWork& x = work[j];
+        kc_handle h = x.h;
+        const uint64_t P = 1ull << h->part_bits;
+        const size_t nb = h->batches.size();
+        for (uint64_t p = 0; p < P; ++p) {
+            uint64_t w = 0;
+            for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
+            x.max_w = std::max(x.max_w, w);
+            x.total_w += w;
+        }
+        int tl = (int)h->cfg.smem_table_log2;
+        if (!tl) {
+            tl = 10;
+            while (tl < 13 && (1ull << tl) < x.max_w / 8) ++tl;
+        }
+        while (tl > 10 && kc::consume_smem(h->slice_log2, tl, h->n_samples) + 1024 > (size_t)b->max_optin) --tl;
+        const size_t smem = kc::consume_smem(h->slice_log2, tl, h->n_samples);
+        if (smem + 1024 > (size_t)b->max_optin) {
+            release_work(b, work);
+            return fail(KC_ERR_INTERNAL, "partition does not fit shared memory");
+        }
+        smem_max = std::max(smem_max, smem);
+        x.sv_cap = std::max<uint64_t>(1, std::min<uint64_t>(P << tl, x.total_w));
+        const size_t meta_bytes = std::max<size_t>(16, nb * 20);
+        cudaError_t e;
+        if ((e = cudaMallocAsync(&x.sv_keys, x.sv_cap * 8, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&x.sv_vals, x.sv_cap * 8, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&x.failed, P * 4, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&x.meta, meta_bytes, st)) != cudaSuccess) {
+            release_work(b, work);
+            return cuda_fail(e, "cudaMallocAsync(batch consumer)");
+        }
+        std::vector<unsigned char> hm(meta_bytes, 0);
+        for (size_t t = 0; t < nb; ++t) {
+            const uint64_t dp = (uint64_t)(uintptr_t)h->batches[t].hdata;
+            const uint64_t sp = (uint64_t)(uintptr_t)h->batches[t].hstarts;
+            const int smp = h->batches[t].sample;
+            std::memcpy(hm.data() + t * 8, &dp, 8);
+            std::memcpy(hm.data() + nb * 8 + t * 8, &sp, 8);
+            std::memcpy(hm.data() + nb * 16 + t * 4, &smp, 4);
+        }
+        KC_CUDA(cudaMemcpyAsync(x.meta, hm.data(), meta_bytes, cudaMemcpyHostToDevice, st));
+        kc::JobDesc& J = b->jobs[j];
+        J.part_bits = h->part_bits;
+        J.slice_log2 = h->slice_log2;
+        J.table_log2 = tl;
+        J.bloom_shift = 64 - h->log2_words;
+        J.n_hashes = h->n_hashes;
+        J.n_samples = h->n_samples;
+        J.all_candidates = h->min_count <= 1 ? 1 : 0;
+        J.key_bits = 2 * h->k;
+        J.min_count = h->min_count;
+        J.n_batches = (int)nb;
+        J.item_base = (uint32_t)b->item_job.size();
+        J.data = reinterpret_cast<const uint64_t* const*>(x.meta);
+        J.starts = reinterpret_cast<const uint64_t* const*>(static_cast<char*>(x.meta) + nb * 8);
+        J.samples = reinterpret_cast<const int*>(static_cast<char*>(x.meta) + nb * 16);
+        J.bloom = reinterpret_cast<unsigned long long*>(h->bloom);
+        J.sv_keys = x.sv_keys;
+        J.sv_vals = x.sv_vals;
+        J.sv_cap = x.sv_cap;
+        J.failed = x.failed;
+        J.ctr = h->ctr;
+        for (uint64_t p = 0; p < P; ++p) b->item_job.push_back((uint32_t)j);
+    }
+    const uint32_t n_items = (uint32_t)b->item_job.size();
+    kc_status s = ensure_jobs(b, (size_t)n, n_items);
+    if (s != KC_OK) {
+        release_work(b, work);
+        return s;
+    }
+    KC_CUDA(cudaMemcpyAsync(b->d_item_job, b->item_job.data(), n_items * 4, cudaMemcpyHostToDevice, st));
+    KC_CUDA(cudaMemsetAsync(b->d_counters, 0, 2 * (size_t)n * 8, st));
+    KC_CUDA(cudaMemsetAsync(b->d_flags, 0, 2 * sizeof(unsigned int), st));
+    if ((s = upload_desc(b, (uint32_t)n, n_items, 0)) != KC_OK) {
+        release_work(b, work);
+        return s;
+    }
+
+    // consume: one persistent launch over the (job, partition) queue
+    cudaEvent_t t0 = one ? phase_begin(hs[0]) : nullptr;
+    int nh = hs[0]->n_hashes;
+    for (int j = 1; j < n; ++j)
+        if (hs[j]->n_hashes != nh) nh = 0;
+    const int per_sm = std::max(1, std::min(4, b->max_sm / (int)(smem_max + 2048)));
+    const int n_ctas = std::max(1, (int)std::min<uint64_t>(n_items, (uint64_t)b->sm_count * per_sm));
+    if (launch_consume(nh, n_ctas, smem_max, b->d_desc, st) != cudaSuccess) {
+        cudaGetLastError();
+        release_work(b, work);
+        return fail(KC_ERR_CUDA, "consumer launch");
+    }
+    if (one) phase_end(hs[0], kPass2, t0);
+    KC_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> cnt(2 * (size_t)n);
+    KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    KC_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < n; ++j) {
+        work[j].h->launches += 1;
+        if (cnt[2 * j + 1]) {
+            t0 = one ? phase_begin(hs[0]) : nullptr;
+            s = run_fallbacks(b, work[j], (uint32_t)j, (uint32_t)cnt[2 * j + 1]);
+            if (one) phase_end(hs[0], kCompact, t0);
+            if (s != KC_OK) {
+                release_work(b, work);
+                return s;
+            }
+            b->jobs[j].sv_keys = work[j].sv_keys;
+            b->jobs[j].sv_vals = work[j].sv_vals;
+            b->jobs[j].sv_cap = work[j].sv_cap;
+        }
+    }
+    if (n > 0) {
+        bool any_fb = false;
+        for (int j = 0; j < n; ++j) any_fb |= cnt[2 * j + 1] != 0;
+        if (any_fb) {
+            KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+            for (int j = 0; j < n; ++j) KC_CUDA(cudaMemcpyAsync(&hc[j], hs[j]->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
+            KC_CUDA(cudaStreamSynchronize(st));
+            for (int j = 0; j < n; ++j) {
+                hs[j]->host_ctr = hc[j];
+                if ((s = device_errors(hs[j])) != KC_OK) {
+                    release_work(b, work);
+                    return s;
+                }
+            }
+        }
+    }
+
+    // sort: per job, bucket bits for about 64 survivors a bucket
+    uint64_t n_buckets = 0;
+    for (int j = 0; j < n; ++j) {
+        kc_handle h = hs[j];
+        kc::JobDesc& J = b->jobs[j];
+        const uint64_t nsv = std::min<uint64_t>(cnt[2 * j], work[j].sv_cap);
+        int bits = 0;
+        while (bits < 22 && bits < 2 * h->k && (std::max<uint64_t>(1, nsv) >> bits) > 64) ++bits;
+        J.sort_bits = bits;
+        J.bucket_base = n_buckets;
+        J.n_buckets = 1ull << bits;
+        n_buckets += J.n_buckets;
+        free_result(h);
+        const uint64_t cap = std::max<uint64_t>(1, nsv);
+        cudaError_t e;
+        if ((e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess) {
+            free_result(h);
+            release_work(b, work);
+            return cuda_fail(e, "cudaMallocAsync(result)");
+        }
+        h->res_cap = cap;
+        h->n_result = nsv;
+        J.res_keys = h->res_keys;
+        J.res_vals = h->res_vals;
+        J.res_cap = cap;
+    }
+    if ((s = ensure_buckets(b, n_buckets)) != KC_OK || (s = upload_desc(b, (uint32_t)n, n_items, n_buckets)) != KC_OK) {
+        release_work(b, work);
+        return s;
+    }
+    if (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK) {
+        release_work(b, work);
+        return s;
+    }
+    t0 = one ? phase_begin(hs[0]) : nullptr;
+    KC_CUDA(cudaGraphLaunch(b->sort_graph, st));
+    unsigned err = 0;
+    KC_CUDA(cudaMemcpyAsync(&err, b->d_flags + 1, 4, cudaMemcpyDeviceToHost, st));
+    KC_CUDA(cudaStreamSynchronize(st));
+    if (err & kc::DERR_INTERNAL) {
+        release_work(b, work);
+        for (int j = 0; j < n; ++j) hs[j]->state = State::Poisoned;
+        return fail(KC_ERR_INTERNAL, "sort: key outside its bucket range");
+    }
+    if (err & kc::DERR_SORT_MEDIUM) {
+        kc::k_medium_sort_q<<<(unsigned)b->sm_count * 4, 256, 0, st>>>(b->d_desc);
+        KC_CUDA(cudaGetLastError());
+        KC_CUDA(cudaMemcpyAsync(&err, b->d_flags + 1, 4, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        for (int j = 0; j < n; ++j) hs[j]->launches += 1;
+    }
+    if (err & kc::DERR_SORT_BUCKET) {  // rare: buckets above 2048 keys, sorted in global memory
+        std::vector<uint64_t> starts(n_buckets + 1);
+        KC_CUDA(cudaMemcpyAsync(starts.data(), b->d_starts, (n_buckets + 1) * 8, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        for (int j = 0; j < n; ++j) {
+            const kc::JobDesc& J = b->jobs[j];
+            const uint64_t job0 = starts[J.bucket_base];
+            for (uint64_t q = 0; q < J.n_buckets; ++q) {
+                const uint64_t lo = starts[J.bucket_base + q], m = starts[J.bucket_base + q + 1] - lo;
+                if (m > 2048) {
+                    kc::launch_bitonic_global(J.res_keys + (lo - job0), J.res_vals + (lo - job0), m, st);
+                    hs[j]->launches += 1;
+                }
+            }
+        }
+        KC_CUDA(cudaGetLastError());
+    }
+    if (one) phase_end(hs[0], kSort, t0);
+    release_work(b, work);
+    KC_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < n; ++j) {
+        kc_handle h = hs[j];
+        h->launches += 6;
+        h->host_ctr.survivors = h->n_result;
+        if (!one) {  // the handle's later work is ordered after the batch
+            KC_CUDA(cudaEventRecord(h->ev_copy, st));
+            KC_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copy, 0));
+        }
+        phase_collect(h);
+        h->state = State::Finalized;
+    }
+    b->launches += 7;
+    return KC_OK;
+}
+
+extern "C" {
+
+kc_status kc_batch_create(void* stream, kc_batch* out) {
+    if (!out) return fail(KC_ERR_ARG, "out is null");
+    kc_batch_ctx* b = nullptr;
+    kc_status s = kc_batch_create_internal((cudaStream_t)stream, &b);
+    *out = b;
+    return s;
+}
+
+kc_status kc_batch_finalize(kc_batch b, kc_handle* handles, int n) { return kc_batch_finalize_internal(b, handles, n); }
+
+void kc_batch_destroy(kc_batch b) { kc_batch_destroy_internal(b); }
+
+}  // extern "C"

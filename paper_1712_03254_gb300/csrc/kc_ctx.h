@@ -1,0 +1,119 @@
+// Handle state shared by the C-ABI layer (kc_api.cu) and the batched
+// finalize engine (kc_batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kc.h"
+#include "kc_internal.h"
+
+struct kc_batch_ctx;
+
+namespace kcapi {
+
+struct Batch {
+    int sample = 0;
+    // direct strategy: the resident reads, rescanned by the recount
+    uint64_t* pw = nullptr;  // packed words, 2 * n_units + 2
+    uint64_t* vw = nullptr;  // valid-window-start words, n_units
+    uint64_t n_units = 0;
+    // partitioned strategy: window hashes grouped by partition
+    uint64_t* hdata = nullptr;    // capacity: one per base of the batch
+    uint64_t* hstarts = nullptr;  // partition starts, 2^part_bits + 1
+    uint64_t hcap = 0;
+};
+
+enum class State { Open, Finalized, Poisoned };
+
+kc_status fail(kc_status s, const std::string& msg);
+kc_status cuda_fail(cudaError_t e, const char* what);
+
+#define KC_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return kcapi::cuda_fail(e_, #call); \
+    } while (0)
+
+}  // namespace kcapi
+
+struct kc_ctx {
+    int k = 0, n_samples = 0, n_hashes = 0;
+    uint64_t bloom_bits = 0;
+    uint32_t min_count = 0;
+    kc_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev_copy = nullptr, ev_main = nullptr;
+    kc::Grid grid;
+    int log2_words = 0, log2_slots = 0;
+    uint64_t n_slots = 0;
+    int strategy = KC_STRATEGY_DIRECT;
+    int part_bits = 0;   // partitioned: 2^part_bits partitions
+    int slice_log2 = 0;  // partitioned: filter words per partition
+
+    uint64_t* bloom = nullptr;
+    kc::Slot* table = nullptr;
+    kc::DevCounters* ctr = nullptr;
+    std::vector<kcapi::Batch> batches;
+    uint64_t bases = 0;
+
+    uint64_t* res_keys = nullptr;
+    uint64_t* res_vals = nullptr;
+    uint64_t n_result = 0;
+    uint64_t res_cap = 0;
+
+    kc::DevCounters host_ctr{};
+    kcapi::State state = kcapi::State::Open;
+    size_t fixed_bytes = 0;
+
+    // Phase timing (kc_config.timing): event pairs recorded on the stream,
+    // turned into milliseconds after the next synchronisation.
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<Mark> marks;
+    double ms[5] = {0, 0, 0, 0, 0};
+    uint64_t launches = 0;
+    uint32_t fallback_partitions = 0;
+
+    // partitioned strategy: this handle's own finalize engine (batch of one)
+    kc_batch_ctx* engine = nullptr;
+
+    kc::PassParams params(int sample) const {
+        kc::PassParams p{};
+        p.k = k;
+        p.rc_shift = 64 - 2 * k;
+        p.kmask = (1ull << (2 * k)) - 1ull;
+        p.bloom_shift = 64 - log2_words;
+        p.n_hashes = n_hashes;
+        p.table_shift = 64 - log2_slots;
+        p.table_mask = n_slots - 1;
+        p.all_candidates = min_count <= 1 ? 1 : 0;
+        p.sample = sample;
+        return p;
+    }
+};
+
+namespace kcapi {
+
+enum Phase { kIngest = 0, kPass1 = 1, kPass2 = 2, kCompact = 3, kSort = 4 };
+
+cudaEvent_t phase_begin(kc_handle h);
+void phase_end(kc_handle h, int phase, cudaEvent_t a);
+void phase_collect(kc_handle h);
+kc_status read_counters(kc_handle h);
+kc_status device_errors(kc_handle h);
+void free_result(kc_handle h);
+
+}  // namespace kcapi
+
+// Batched finalize of partitioned handles (kc_batch.cu).
+kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n);
+kc_status kc_batch_create_internal(cudaStream_t st, kc_batch_ctx** out);
+void kc_batch_destroy_internal(kc_batch_ctx* b);

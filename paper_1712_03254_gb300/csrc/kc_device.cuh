@@ -180,6 +180,115 @@ __device__ __forceinline__ void table_count(Slot* __restrict__ table, uint64_t m
     }
 }
 
+// Warp-per-bucket sort: the bucket's keys sit in registers, R per lane
+// (element r*32 + lane), padded with ~0 keys; a bitonic network runs with
+// register compare-exchanges for strides >= 32 and shuffles below.
+template <int R>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&k)[R], uint64_t (&v)[R], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * R; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int rs = stride >> 5;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if ((r & rs) == 0) {
+                        const int q = r | rs;
+                        const bool asc = (((r << 5) | lane) & size) == 0;
+                        if ((k[r] > k[q]) == asc) {
+                            const uint64_t tk = k[r], tv = v[r];
+                            k[r] = k[q];
+                            v[r] = v[q];
+                            k[q] = tk;
+                            v[q] = tv;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = (r << 5) | lane;
+                    const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[r], stride);
+                    const uint64_t ov = __shfl_xor_sync(0xffffffffu, v[r], stride);
+                    const bool asc = (i & size) == 0;
+                    const bool lower = (i & stride) == 0;
+                    const bool take_other = lower ? (asc ? ok < k[r] : ok > k[r]) : (asc ? ok > k[r] : ok < k[r]);
+                    if (take_other) {
+                        k[r] = ok;
+                        v[r] = ov;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void warp_sort_bucket(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
+                                                 uint64_t lo, int n, int lane) {
+    uint64_t k[R], v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = (r << 5) | lane;
+        k[r] = i < n ? keys[lo + i] : ~0ull;
+        v[r] = i < n ? vals[lo + i] : 0ull;
+    }
+    warp_bitonic<R>(k, v, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = (r << 5) | lane;
+        if (i < n) {
+            keys[lo + i] = k[r];
+            vals[lo + i] = v[r];
+        }
+    }
+}
+
+constexpr int kProbeLimit = 64;  // shared-memory table probes before a partition falls back
+
+// Shared-memory table: keys[T] hold (h & low_mask) + 1 (0 = empty), counts
+// follow as n_samples uint32 per slot.  Returns 1 = claimed, 0 = present,
+// -1 = no free slot within kProbeLimit probes.
+__device__ __forceinline__ int smem_claim(unsigned long long* keys, uint32_t tmask, uint32_t s,
+                                          unsigned long long stored) {
+    for (int i = 0; i < kProbeLimit; ++i) {
+        const unsigned long long cur = keys[s];
+        if (cur == stored) return 0;
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(&keys[s], 0ull, stored);
+            if (prev == 0ull) return 1;
+            if (prev == stored) return 0;
+        }
+        s = (s + 1) & tmask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int smem_find(const unsigned long long* keys, uint32_t tmask, uint32_t s,
+                                         unsigned long long stored) {
+    for (uint32_t i = 0; i <= tmask; ++i) {
+        const unsigned long long cur = keys[s];
+        if (cur == stored) return (int)s;
+        if (cur == 0ull) return -1;
+        s = (s + 1) & tmask;
+    }
+    return -1;
+}
+
+// Filter pattern with the number of bits chosen at run time.
+__device__ __forceinline__ uint64_t bloom_pattern_rt(uint64_t g, int n_hashes) {
+    uint32_t lo = 0, hi = 0;
+    for (int i = 0; i < n_hashes; ++i) {
+        const uint32_t bit = (uint32_t)g & 63u;
+        g >>= 6;
+        const uint32_t m = 1u << (bit & 31u);
+        if (bit & 32u) hi |= m;
+        else lo |= m;
+    }
+    return ((uint64_t)hi << 32) | lo;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

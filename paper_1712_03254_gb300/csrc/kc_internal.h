@@ -64,29 +64,6 @@ void launch_counts_narrow(const uint64_t* vals, uint64_t n, uint32_t* out, cudaS
 
 // ---- partitioned strategy (kc_partition.cu) --------------------------------
 
-struct ConsumeArgs {
-    const uint64_t* const* data;    // per batch: window hashes grouped by bucket
-    const uint64_t* const* starts;  // per batch: bucket starts, 2^part_bits + 1
-    const int* samples;             // per batch: sample index
-    int n_batches;
-    int part_bits;                  // partitions = 2^part_bits (top bits of h)
-    int slice_log2;                 // filter words per partition
-    int table_log2;                 // shared-memory table slots per partition
-    int bloom_shift;                // 64 - log2(filter words)
-    int n_hashes;
-    int n_samples;
-    int all_candidates;
-    uint32_t min_count;
-    unsigned long long* bloom;
-    uint64_t* out_keys;
-    uint64_t* out_vals;
-    uint64_t out_cap;
-    unsigned long long* n_out;
-    uint32_t* failed;               // partitions left to the fallback
-    uint32_t* n_failed;
-    DevCounters* ctr;
-};
-
 struct FallbackArgs {
     const uint64_t* const* data;
     const uint64_t* const* starts;
@@ -128,7 +105,6 @@ void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_un
                            int n_ctas, const PassParams& p, int a, int mode, const uint64_t* base, uint64_t* cursor,
                            uint64_t* out, cudaStream_t st);
 size_t consume_smem(int slice_log2, int table_log2, int n_samples);
-int launch_part_consume(const ConsumeArgs& A, int n_ctas, cudaStream_t st);
 void launch_fb_claim(const FallbackArgs& F, int bt, cudaStream_t st);
 void launch_fb_recount(const FallbackArgs& F, int bt, cudaStream_t st);
 void launch_fb_compact(const FallbackArgs& F, cudaStream_t st);

@@ -400,71 +400,6 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(uint64_t* __restri
     }
 }
 
-// Warp-per-bucket sort: the bucket's keys sit in registers, R per lane
-// (element r*32 + lane), padded with ~0 keys; a bitonic network runs with
-// register compare-exchanges for strides >= 32 and shuffles below.
-template <int R>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&k)[R], uint64_t (&v)[R], int lane) {
-#pragma unroll
-    for (int size = 2; size <= 32 * R; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= 32) {
-                const int rs = stride >> 5;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if ((r & rs) == 0) {
-                        const int q = r | rs;
-                        const bool asc = (((r << 5) | lane) & size) == 0;
-                        if ((k[r] > k[q]) == asc) {
-                            const uint64_t tk = k[r], tv = v[r];
-                            k[r] = k[q];
-                            v[r] = v[q];
-                            k[q] = tk;
-                            v[q] = tv;
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int i = (r << 5) | lane;
-                    const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[r], stride);
-                    const uint64_t ov = __shfl_xor_sync(0xffffffffu, v[r], stride);
-                    const bool asc = (i & size) == 0;
-                    const bool lower = (i & stride) == 0;
-                    const bool take_other = lower ? (asc ? ok < k[r] : ok > k[r]) : (asc ? ok > k[r] : ok < k[r]);
-                    if (take_other) {
-                        k[r] = ok;
-                        v[r] = ov;
-                    }
-                }
-            }
-        }
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void warp_sort_bucket(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
-                                                 uint64_t lo, int n, int lane) {
-    uint64_t k[R], v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = (r << 5) | lane;
-        k[r] = i < n ? keys[lo + i] : ~0ull;
-        v[r] = i < n ? vals[lo + i] : 0ull;
-    }
-    warp_bitonic<R>(k, v, lane);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = (r << 5) | lane;
-        if (i < n) {
-            keys[lo + i] = k[r];
-            vals[lo + i] = v[r];
-        }
-    }
-}
-
 __global__ void __launch_bounds__(256, 2) k_bucket_sort_warp(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
                                                           const uint64_t* __restrict__ starts, uint64_t n_buckets,
                                                           DevCounters* __restrict__ ctr) {

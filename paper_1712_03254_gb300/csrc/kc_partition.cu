@@ -17,18 +17,13 @@
 //     k_bucket_pass<scatter> the same windows again; each h is stored at the
 //                           next position of its CTA's run of its bucket (or
 //                           at a position from a global per-bucket cursor)
-//   finalize
-//     k_part_consume        one CTA per bucket ("partition"): the filter words
-//                           of the partition (a contiguous slice, since the
-//                           filter word is also a prefix of h) and an open-
-//                           addressing table in shared memory; filter update,
-//                           candidate claims, exact recount, compaction of
-//                           survivors (key recovered by unmixer64), slice
-//                           written back to the global filter.  A partition
-//                           whose table overflows is left to the fallback.
-//     k_fb_*                fallback for such partitions: the same steps with
-//                           the partition's filter slice and a table in global
-//                           memory.
+//   finalize (the consumer itself is k_consume_q in kc_batch.cu: one CTA per
+//   partition holds the partition's filter words -- a contiguous slice, since
+//   the filter word is also a prefix of h -- and an open-addressing table in
+//   shared memory)
+//     k_fb_*                fallback for partitions whose shared-memory table
+//                           overflowed: the same steps with the partition's
+//                           filter slice and a table in global memory.
 
 #include "kc_internal.h"
 
@@ -37,7 +32,6 @@ namespace kc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kProbeLimit = 64;  // shared-memory table probes before a partition falls back
 
 __device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
 #pragma unroll
@@ -366,137 +360,6 @@ __global__ void k_bucket_base(uint64_t* __restrict__ rel, const uint64_t* __rest
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) rel[i] += starts[i % P];
 }
 
-// Shared-memory table: keys[T] hold (h & low_mask) + 1 (0 = empty), counts
-// follow as n_samples uint32 per slot.  Returns 1 = claimed, 0 = present,
-// -1 = no free slot within kProbeLimit probes.
-__device__ __forceinline__ int smem_claim(unsigned long long* keys, uint32_t tmask, uint32_t s,
-                                          unsigned long long stored) {
-    for (int i = 0; i < kProbeLimit; ++i) {
-        const unsigned long long cur = keys[s];
-        if (cur == stored) return 0;
-        if (cur == 0ull) {
-            const unsigned long long prev = atomicCAS(&keys[s], 0ull, stored);
-            if (prev == 0ull) return 1;
-            if (prev == stored) return 0;
-        }
-        s = (s + 1) & tmask;
-    }
-    return -1;
-}
-
-__device__ __forceinline__ int smem_find(const unsigned long long* keys, uint32_t tmask, uint32_t s,
-                                         unsigned long long stored) {
-    for (uint32_t i = 0; i <= tmask; ++i) {
-        const unsigned long long cur = keys[s];
-        if (cur == stored) return (int)s;
-        if (cur == 0ull) return -1;
-        s = (s + 1) & tmask;
-    }
-    return -1;
-}
-
-template <int NH>
-__global__ void __launch_bounds__(512) k_part_consume(ConsumeArgs A) {
-    extern __shared__ unsigned long long s_mem[];
-    const uint32_t n_sw = 1u << A.slice_log2;  // filter words of one partition
-    const uint32_t T = 1u << A.table_log2;
-    const uint32_t tmask = T - 1;
-    unsigned long long* sb = s_mem;
-    unsigned long long* sk = s_mem + n_sw;
-    uint32_t* sc = reinterpret_cast<uint32_t*>(s_mem + n_sw + T);
-    __shared__ int s_fail;
-    const int S = A.n_samples;
-    const int a = A.part_bits;
-    const uint64_t low_mask = (1ull << (64 - a)) - 1ull;
-    const int home_shift = 64 - a - A.table_log2;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    uint64_t cand = 0, claimed = 0;
-
-    for (uint32_t part = blockIdx.x; part < (1u << a); part += gridDim.x) {
-        for (uint32_t i = threadIdx.x; i < n_sw; i += blockDim.x) sb[i] = 0ull;
-        for (uint32_t i = threadIdx.x; i < T; i += blockDim.x) sk[i] = 0ull;
-        for (uint32_t i = threadIdx.x; i < T * S; i += blockDim.x) sc[i] = 0u;
-        if (threadIdx.x == 0) s_fail = 0;
-        __syncthreads();
-        // filter update and candidate claims
-        for (int bt = 0; bt < A.n_batches; ++bt) {
-            const uint64_t* __restrict__ d = A.data[bt];
-            const uint64_t lo = A.starts[bt][part], hi = A.starts[bt][part + 1];
-            for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const uint64_t h = __ldcg(d + i);  // read again by the recount: keep in L2
-                if ((uint32_t)(h >> (64 - a)) != part) continue;  // run padding
-                const uint32_t w = (uint32_t)(h >> A.bloom_shift) & (n_sw - 1);
-                const uint64_t pat = bloom_pattern_n<NH>(mixer64(h));
-                const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
-                if (A.all_candidates || (old & pat) == pat) {
-                    ++cand;
-                    const int r = smem_claim(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
-                    if (r < 0) s_fail = 1;
-                    else claimed += (uint64_t)r;
-                }
-            }
-        }
-        __syncthreads();
-        if (s_fail) {
-            if (threadIdx.x == 0) A.failed[atomicAdd(A.n_failed, 1u)] = part;
-            __syncthreads();
-            continue;
-        }
-        // exact recount
-        for (int bt = 0; bt < A.n_batches; ++bt) {
-            const uint64_t* __restrict__ d = A.data[bt];
-            const int smp = A.samples[bt];
-            const uint64_t lo = A.starts[bt][part], hi = A.starts[bt][part + 1];
-            for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const uint64_t h = __ldcs(d + i);  // last use
-                if ((uint32_t)(h >> (64 - a)) != part) continue;
-                const int s = smem_find(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
-                if (s >= 0) atomicAdd(sc + (uint32_t)s * S + smp, 1u);
-            }
-        }
-        __syncthreads();
-        // survivors: key = unmixer64(h), counts packed little-endian
-        const uint64_t hpre = (uint64_t)part << (64 - a);
-        for (uint32_t i0 = threadIdx.x & ~31u; i0 < T; i0 += blockDim.x) {
-            const uint32_t i = i0 + lane;
-            const unsigned long long k1 = sk[i];
-            uint64_t v = 0;
-            bool keep = false;
-            if (k1 != 0ull) {
-                const uint32_t c0 = sc[i * S];
-                const uint32_t c1 = S == 2 ? sc[i * S + 1] : 0u;
-                keep = (uint64_t)c0 + c1 >= A.min_count;
-                v = (uint64_t)c0 | ((uint64_t)c1 << 32);
-            }
-            const unsigned ballot = __ballot_sync(kFull, keep);
-            if (ballot) {
-                const int leader = __ffs(ballot) - 1;
-                unsigned long long pos0 = 0;
-                if (lane == leader) pos0 = atomicAdd(A.n_out, (unsigned long long)__popc(ballot));
-                pos0 = __shfl_sync(kFull, pos0, leader);
-                if (keep) {
-                    const uint64_t pos = pos0 + __popc(ballot & lt);
-                    if (pos < A.out_cap) {
-                        A.out_keys[pos] = unmixer64(hpre | (k1 - 1ull));
-                        A.out_vals[pos] = v;
-                    }
-                }
-            }
-        }
-        // the partition's filter words
-        unsigned long long* gb = A.bloom + (uint64_t)part * n_sw;
-        for (uint32_t i = threadIdx.x; i < n_sw; i += blockDim.x) gb[i] = sb[i];
-        __syncthreads();
-    }
-    cand = warp_sum64(cand);
-    claimed = warp_sum64(claimed);
-    if (lane == 0) {
-        if (cand) atomicAdd(&A.ctr->candidates, (unsigned long long)cand);
-        if (claimed) atomicAdd(&A.ctr->claimed, (unsigned long long)claimed);
-    }
-}
-
 // ---- fallback for partitions whose shared-memory table overflowed ----------
 
 __global__ void k_fb_claim(FallbackArgs F, int bt) {
@@ -646,30 +509,6 @@ void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_un
 size_t consume_smem(int slice_log2, int table_log2, int n_samples) {
     return (sizeof(uint64_t) << slice_log2) + (sizeof(uint64_t) << table_log2) +
            ((sizeof(uint32_t) * (size_t)n_samples) << table_log2);
-}
-
-template <int NH>
-int launch_consume_nh(const ConsumeArgs& A, int n_ctas, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_part_consume<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    k_part_consume<NH><<<n_ctas, 512, smem, st>>>(A);
-    return 0;
-}
-
-int launch_part_consume(const ConsumeArgs& A, int n_ctas, cudaStream_t st) {
-    const size_t smem = consume_smem(A.slice_log2, A.table_log2, A.n_samples);
-    switch (A.n_hashes) {
-        case 1: return launch_consume_nh<1>(A, n_ctas, smem, st);
-        case 2: return launch_consume_nh<2>(A, n_ctas, smem, st);
-        case 3: return launch_consume_nh<3>(A, n_ctas, smem, st);
-        case 4: return launch_consume_nh<4>(A, n_ctas, smem, st);
-        case 5: return launch_consume_nh<5>(A, n_ctas, smem, st);
-        case 6: return launch_consume_nh<6>(A, n_ctas, smem, st);
-        case 7: return launch_consume_nh<7>(A, n_ctas, smem, st);
-        case 8: return launch_consume_nh<8>(A, n_ctas, smem, st);
-        case 9: return launch_consume_nh<9>(A, n_ctas, smem, st);
-        default: return launch_consume_nh<10>(A, n_ctas, smem, st);
-    }
 }
 
 void launch_fb_claim(const FallbackArgs& F, int bt, cudaStream_t st) { k_fb_claim<<<1024, 256, 0, st>>>(F, bt); }
