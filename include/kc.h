@@ -164,6 +164,55 @@ kc_status kc_batch_finalize(kc_batch b, kc_handle* handles, int n);
 
 void kc_batch_destroy(kc_batch b);
 
+/*
+ * Job server with continuous batching (host-submitted jobs).  An ingest
+ * thread admits queued jobs in arrival order as soon as their estimated
+ * device footprint fits device_budget_bytes and adds their reads on their own
+ * streams; a finalize thread repeatedly finalizes every job ingested so far
+ * (at most max_batch) as one batch (kc_batch_finalize), copies the results to
+ * host memory and releases the jobs' device memory.  Jobs that arrive while a
+ * batch runs are ingested at once and join the next batch.  Each job's result
+ * is the one kc_finalize would give it alone.  All kc_server_* calls are
+ * thread-safe.
+ */
+typedef struct kc_server_ctx* kc_server;
+
+typedef struct kc_job_spec {
+    int k, n_samples, n_hashes;
+    uint32_t min_count;
+    uint64_t bloom_bits;
+    /* per sample, in the packed format above, HOST memory that must stay
+     * valid until kc_server_wait has returned for the job */
+    const uint64_t* packed[2];
+    const uint64_t* offsets[2];
+    const uint64_t* n_mask[2];
+    uint64_t n_reads[2];
+} kc_job_spec;
+
+typedef struct kc_server_stats {
+    uint64_t submitted, completed, failed, batches;
+    double mean_batch;        /* jobs per finalized batch                      */
+    double p50_ms, p99_ms, mean_ms;  /* submit -> result in host memory        */
+    double jobs_per_s;        /* completed jobs / (last completion - first submit) */
+    uint64_t peak_bytes;      /* largest admitted footprint sum                */
+    uint64_t budget_bytes;
+} kc_server_stats;
+
+/* Create a server on the current device (max_batch >= 1). */
+kc_status kc_server_create(uint64_t device_budget_bytes, int max_batch, kc_server* out);
+/* Queue a job; *job_id identifies it.  KC_ERR_ARG for device pointers. */
+kc_status kc_server_submit(kc_server s, const kc_job_spec* spec, uint64_t* job_id);
+/* Wait for a job (timeout_s < 0: no limit; KC_ERR_TIMEOUT when it runs out);
+ * returns the job's status, its result size and its latency. */
+kc_status kc_server_wait(kc_server s, uint64_t job_id, double timeout_s, uint64_t* n_keys, double* latency_ms);
+/* Copy a finished job's result (as kc_dump) and forget the job; keys == NULL
+ * only reports the size and keeps the job. */
+kc_status kc_server_result(kc_server s, uint64_t job_id, uint64_t* keys, uint32_t* counts, uint64_t capacity,
+                           uint64_t* n_out);
+kc_status kc_server_stats_get(kc_server s, kc_server_stats* out);
+/* Stop the threads; jobs not finished are dropped. */
+void kc_server_destroy(kc_server s);
+
 /* Fill *cfg with the defaults (struct_size set). */
 void kc_default_config(kc_config* cfg);
 

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["KmerCounter", "KcBatch", "KcError", "pack_ascii", "lib", "build", "Config", "Stats"]
+__all__ = ["KmerCounter", "KcBatch", "KcServer", "KcError", "pack_ascii", "lib", "build", "Config", "Stats"]
 
 _lock = threading.Lock()
 _lib = None
@@ -49,6 +49,23 @@ class Stats(ctypes.Structure):
                 ("ms_ingest", ctypes.c_double), ("ms_pass1", ctypes.c_double), ("ms_pass2", ctypes.c_double),
                 ("ms_compact", ctypes.c_double), ("ms_sort", ctypes.c_double), ("strategy", ctypes.c_uint32),
                 ("fallback_partitions", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class JobSpec(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n_samples", ctypes.c_int), ("n_hashes", ctypes.c_int),
+                ("min_count", ctypes.c_uint32), ("bloom_bits", ctypes.c_uint64),
+                ("packed", ctypes.c_void_p * 2), ("offsets", ctypes.c_void_p * 2), ("n_mask", ctypes.c_void_p * 2),
+                ("n_reads", ctypes.c_uint64 * 2)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("jobs_per_s", ctypes.c_double),
+                ("peak_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -98,6 +115,18 @@ def lib():
             L.kc_batch_finalize.restype = st
             L.kc_batch_destroy.argtypes = [p]
             L.kc_batch_destroy.restype = None
+            L.kc_server_create.argtypes = [u64, i, ctypes.POINTER(p)]
+            L.kc_server_create.restype = st
+            L.kc_server_submit.argtypes = [p, ctypes.POINTER(JobSpec), ctypes.POINTER(u64)]
+            L.kc_server_submit.restype = st
+            L.kc_server_wait.argtypes = [p, u64, ctypes.c_double, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double)]
+            L.kc_server_wait.restype = st
+            L.kc_server_result.argtypes = [p, u64, p, p, u64, ctypes.POINTER(u64)]
+            L.kc_server_result.restype = st
+            L.kc_server_stats_get.argtypes = [p, ctypes.POINTER(ServerStats)]
+            L.kc_server_stats_get.restype = st
+            L.kc_server_destroy.argtypes = [p]
+            L.kc_server_destroy.restype = None
             _lib = L
     return _lib
 
@@ -241,6 +270,76 @@ class KcBatch:
         if getattr(self, "_b", None):
             self._L.kc_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        self.close()
+
+
+class KcServer:
+    """Continuous-batching job server (kc_server_*); inputs are packed host arrays."""
+
+    def __init__(self, device_budget_bytes: int, max_batch: int = 64):
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.kc_server_create(device_budget_bytes, max_batch, ctypes.byref(h)), "kc_server_create")
+        self._s = h
+        self._L = L
+        self._keep = {}  # job id -> host arrays that must outlive the job
+        self._samples = {}
+
+    def submit(self, k, bloom_bits, n_hashes, min_count, samples) -> int:
+        """samples: list of (packed, offsets, n_mask) numpy arrays, one per sample."""
+        spec = JobSpec()
+        spec.k, spec.n_samples, spec.n_hashes, spec.min_count, spec.bloom_bits = (
+            k, len(samples), n_hashes, min_count, bloom_bits)
+        keep = []
+        for i, (packed, offsets, mask) in enumerate(samples):
+            offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+            keep += [packed, offsets, mask]
+            spec.packed[i] = _ptr(packed)
+            spec.offsets[i] = _ptr(offsets)
+            spec.n_mask[i] = _ptr(mask)
+            spec.n_reads[i] = len(offsets) - 1
+        jid = ctypes.c_uint64()
+        _check(self._L.kc_server_submit(self._s, ctypes.byref(spec), ctypes.byref(jid)), "kc_server_submit")
+        self._keep[jid.value] = keep
+        self._samples[jid.value] = len(samples)
+        return jid.value
+
+    def submit_workload(self, w) -> int:
+        samples = []
+        for rs in w.samples:
+            packed, mask = pack_ascii(rs.ascii)
+            samples.append((packed, rs.offsets, mask))
+        return self.submit(w.k, w.bloom_bits, w.n_hashes, w.min_count, samples)
+
+    def wait(self, job_id: int, timeout_s: float = -1.0):
+        n = ctypes.c_uint64()
+        lat = ctypes.c_double()
+        _check(self._L.kc_server_wait(self._s, job_id, timeout_s, ctypes.byref(n), ctypes.byref(lat)),
+               "kc_server_wait")
+        self._keep.pop(job_id, None)
+        return n.value, lat.value
+
+    def result(self, job_id: int):
+        n = ctypes.c_uint64()
+        _check(self._L.kc_server_result(self._s, job_id, None, None, 0, ctypes.byref(n)), "kc_server_result")
+        keys = np.empty(n.value, dtype=np.uint64)
+        counts = np.empty((n.value, self._samples.get(job_id, 1)), dtype=np.uint32)
+        _check(self._L.kc_server_result(self._s, job_id, keys.ctypes.data, counts.ctypes.data, n.value,
+                                        ctypes.byref(n)), "kc_server_result")
+        self._samples.pop(job_id, None)
+        return keys, counts
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._L.kc_server_stats_get(self._s, ctypes.byref(st)), "kc_server_stats_get")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._L.kc_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         self.close()

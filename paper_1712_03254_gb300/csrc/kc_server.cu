@@ -1,0 +1,323 @@
+// Continuous-batching job server over the C ABI (kc_server_* in include/kc.h).
+//
+// Two host threads drive the GPU:
+//   ingest    takes queued jobs in arrival order, admits the next one as soon as
+//             its estimated device footprint fits the budget (memory frees up
+//             as jobs finish), creates its handle on its own stream and adds
+//             its reads;
+//   finalize  takes every job ingested so far (at most max_batch), finalizes
+//             them together with one kc_batch_finalize (one persistent
+//             consumer launch over all their partitions and one replay of the
+//             sort graph), copies each result to host memory, frees the job's
+//             device memory and wakes its waiters.
+// Jobs that arrive while a batch runs are ingested at once on their own
+// streams, so their work overlaps the batch on the device, and they join the
+// next batch: a batch never waits for stragglers and a job never waits for a
+// whole batch to drain before it starts.
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/kc.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    uint64_t id = 0;
+    kc_job_spec spec{};
+    uint64_t footprint = 0;
+    kc_handle h = nullptr;
+    Clock::time_point t_submit, t_done;
+    kc_status status = KC_OK;
+    std::string error;
+    bool done = false;
+    std::vector<uint64_t> keys;
+    std::vector<uint32_t> counts;
+};
+
+}  // namespace
+
+struct kc_server_ctx {
+    uint64_t budget = 0;
+    int max_batch = 64;
+    std::mutex mu;
+    std::condition_variable cv_ingest, cv_final, cv_done;
+    std::deque<std::shared_ptr<Job>> pending;   // submitted, not admitted
+    std::deque<std::shared_ptr<Job>> ingested;  // admitted and ingested
+    std::map<uint64_t, std::shared_ptr<Job>> jobs;
+    uint64_t next_id = 1, in_use = 0, peak = 0;
+    bool stop = false;
+    std::thread t_ingest, t_final;
+    kc_batch batch = nullptr;
+    int device = 0;
+    // statistics
+    std::vector<double> latencies_ms;
+    uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_jobs = 0;
+    Clock::time_point t_first, t_last;
+    bool any = false;
+};
+
+namespace {
+
+// Device bytes a job may hold at its peak (upper bounds): filter; per base the
+// packed reads, N mask, read-start and valid bits, the linear and the
+// partitioned hash of a window, survivors and result (16 bytes each) and the
+// offsets.
+uint64_t footprint(const kc_job_spec& s) {
+    uint64_t bases = 0, reads = 0;
+    for (int i = 0; i < s.n_samples; ++i) {
+        if (s.n_reads[i]) bases += s.offsets[i][s.n_reads[i]] - s.offsets[i][0];
+        reads += s.n_reads[i];
+    }
+    return s.bloom_bits / 8 + bases * 50 + reads * 8 + (8ull << 20);
+}
+
+void fail_job(kc_server_ctx* S, const std::shared_ptr<Job>& j, kc_status st) {
+    j->status = st;
+    j->error = kc_last_error();
+    if (j->h) kc_destroy(j->h);
+    j->h = nullptr;
+    j->t_done = Clock::now();
+    j->done = true;
+    S->in_use -= j->footprint;
+    S->failed += 1;
+}
+
+void ingest_loop(kc_server_ctx* S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::shared_ptr<Job> j;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_ingest.wait(lk, [&] {
+                return S->stop || (!S->pending.empty() &&
+                                   (S->in_use + S->pending.front()->footprint <= S->budget || S->in_use == 0));
+            });
+            if (S->stop) return;
+            j = S->pending.front();
+            S->pending.pop_front();
+            S->in_use += j->footprint;  // admitted
+            S->peak = std::max(S->peak, S->in_use);
+        }
+        const kc_job_spec& s = j->spec;
+        kc_config cfg;
+        kc_default_config(&cfg);
+        cfg.strategy = KC_STRATEGY_PARTITIONED;
+        kc_status st = kc_create_ex(s.k, s.n_samples, s.bloom_bits, s.n_hashes, s.min_count, &cfg, nullptr, &j->h);
+        for (int i = 0; st == KC_OK && i < s.n_samples; ++i)
+            st = kc_add_reads(j->h, i, s.packed[i], s.offsets[i], s.n_mask[i], s.n_reads[i]);
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (st != KC_OK) {
+            fail_job(S, j, st);
+            S->cv_done.notify_all();
+            S->cv_ingest.notify_all();
+            continue;
+        }
+        S->ingested.push_back(j);
+        S->cv_final.notify_all();
+    }
+}
+
+void finalize_loop(kc_server_ctx* S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<std::shared_ptr<Job>> run;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_final.wait(lk, [&] { return S->stop || !S->ingested.empty(); });
+            if (S->stop) return;
+            while (!S->ingested.empty() && (int)run.size() < S->max_batch) {
+                run.push_back(S->ingested.front());
+                S->ingested.pop_front();
+            }
+        }
+        std::vector<kc_handle> hs;
+        for (auto& j : run) hs.push_back(j->h);
+        kc_status st = kc_batch_finalize(S->batch, hs.data(), (int)hs.size());
+        for (auto& j : run) {
+            kc_status js = st;
+            uint64_t n = 0;
+            if (js == KC_OK) js = kc_dump(j->h, nullptr, nullptr, 0, &n);
+            if (js == KC_OK) {
+                j->keys.resize(n);
+                j->counts.resize(n * (size_t)j->spec.n_samples);
+                if (n) js = kc_dump(j->h, j->keys.data(), j->counts.data(), n, &n);
+            }
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (js != KC_OK) {
+                fail_job(S, j, js);
+                continue;
+            }
+            kc_destroy(j->h);
+            j->h = nullptr;
+            j->t_done = Clock::now();
+            j->done = true;
+            S->in_use -= j->footprint;
+            S->completed += 1;
+            S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count());
+            S->t_last = j->t_done;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->batches += 1;
+            S->batched_jobs += run.size();
+        }
+        S->cv_done.notify_all();
+        S->cv_ingest.notify_all();
+    }
+}
+
+double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q * (double)(v.size() - 1);
+    const size_t i = (size_t)pos;
+    const double f = pos - (double)i;
+    return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+kc_status kc_server_create(uint64_t device_budget_bytes, int max_batch, kc_server* out) {
+    if (!out || device_budget_bytes == 0 || max_batch < 1) return KC_ERR_ARG;
+    *out = nullptr;
+    kc_server_ctx* S = new (std::nothrow) kc_server_ctx();
+    if (!S) return KC_ERR_OOM_HOST;
+    S->budget = device_budget_bytes;
+    S->max_batch = max_batch;
+    cudaGetDevice(&S->device);
+    kc_status st = kc_batch_create(nullptr, &S->batch);
+    if (st != KC_OK) {
+        delete S;
+        return st;
+    }
+    S->t_ingest = std::thread(ingest_loop, S);
+    S->t_final = std::thread(finalize_loop, S);
+    *out = S;
+    return KC_OK;
+}
+
+static bool host_memory(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type != cudaMemoryTypeDevice;
+}
+
+kc_status kc_server_submit(kc_server S, const kc_job_spec* spec, uint64_t* job_id) {
+    if (!S || !spec || !job_id) return KC_ERR_ARG;
+    if (spec->n_samples < 1 || spec->n_samples > 2) return KC_ERR_ARG;
+    for (int i = 0; i < spec->n_samples; ++i) {
+        if (spec->n_reads[i] && !spec->offsets[i]) return KC_ERR_ARG;
+        if (!host_memory(spec->offsets[i]) || !host_memory(spec->packed[i]) || !host_memory(spec->n_mask[i]))
+            return KC_ERR_ARG;
+    }
+    auto j = std::make_shared<Job>();
+    j->spec = *spec;
+    j->footprint = footprint(*spec);
+    j->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->any) {
+        S->t_first = j->t_submit;
+        S->any = true;
+    }
+    j->id = S->next_id++;
+    S->jobs[j->id] = j;
+    S->pending.push_back(j);
+    S->submitted += 1;
+    *job_id = j->id;
+    S->cv_ingest.notify_all();
+    return KC_OK;
+}
+
+kc_status kc_server_wait(kc_server S, uint64_t job_id, double timeout_s, uint64_t* n_keys, double* latency_ms) {
+    if (!S) return KC_ERR_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->jobs.find(job_id);
+    if (it == S->jobs.end()) return KC_ERR_ARG;
+    std::shared_ptr<Job> j = it->second;
+    const auto pred = [&] { return j->done; };
+    if (timeout_s < 0) {
+        S->cv_done.wait(lk, pred);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
+        return KC_ERR_TIMEOUT;
+    }
+    if (n_keys) *n_keys = j->keys.size();
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
+    return j->status;
+}
+
+kc_status kc_server_result(kc_server S, uint64_t job_id, uint64_t* keys, uint32_t* counts, uint64_t capacity,
+                           uint64_t* n_out) {
+    if (!S) return KC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->jobs.find(job_id);
+    if (it == S->jobs.end()) return KC_ERR_ARG;
+    std::shared_ptr<Job> j = it->second;
+    if (!j->done) return KC_ERR_STATE;
+    if (j->status != KC_OK) return j->status;
+    if (n_out) *n_out = j->keys.size();
+    if (!keys) return KC_OK;
+    if (capacity < j->keys.size()) return KC_ERR_CAPACITY;
+    std::memcpy(keys, j->keys.data(), j->keys.size() * 8);
+    if (counts) std::memcpy(counts, j->counts.data(), j->counts.size() * 4);
+    S->jobs.erase(it);  // the result has been handed over
+    return KC_OK;
+}
+
+kc_status kc_server_stats_get(kc_server S, kc_server_stats* out) {
+    if (!S || !out) return KC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->failed = S->failed;
+    out->batches = S->batches;
+    out->mean_batch = S->batches ? (double)S->batched_jobs / (double)S->batches : 0.0;
+    out->p50_ms = percentile(S->latencies_ms, 0.50);
+    out->p99_ms = percentile(S->latencies_ms, 0.99);
+    double sum = 0;
+    for (double x : S->latencies_ms) sum += x;
+    out->mean_ms = S->latencies_ms.empty() ? 0.0 : sum / (double)S->latencies_ms.size();
+    const double span = S->any ? std::chrono::duration<double>(S->t_last - S->t_first).count() : 0.0;
+    out->jobs_per_s = span > 0 ? (double)S->completed / span : 0.0;
+    out->peak_bytes = S->peak;
+    out->budget_bytes = S->budget;
+    return KC_OK;
+}
+
+void kc_server_destroy(kc_server S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_ingest.notify_all();
+    S->cv_final.notify_all();
+    if (S->t_ingest.joinable()) S->t_ingest.join();
+    if (S->t_final.joinable()) S->t_final.join();
+    for (auto& d : S->ingested)
+        if (d->h) kc_destroy(d->h);
+    kc_batch_destroy(S->batch);
+    delete S;
+}
+
+}  // extern "C"
