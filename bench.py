@@ -25,6 +25,8 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+
+import numpy as np
 import json
 import os
 import statistics
@@ -381,6 +383,10 @@ def run_kc(args):
                "sample": f"first {n_s:,} of {rs.n_reads:,} reads of the mid workload ({win:,} windows, "
                          f"{dt:.1f} s, single-threaded C++ oracle, {os.cpu_count()} host cores present)"}
 
+    served = None
+    if rank == 0 and world == 1 and not args.no_served:
+        served = run_served_trace(args.served_jobs, args.served_max_reads)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -397,11 +403,127 @@ def run_kc(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3 / args.steps, 4)},
             "clocks": clk,
             "gpu_launches": int(launches),
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     c.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- served stream
+
+
+def _served_jobs(n_jobs: int, max_reads: int):
+    """Job shapes of the served stream with their packed reads (host memory)."""
+    import paper_1712_03254_gb300 as kc
+    import synth
+
+    jobs = []
+    for spec in synth.served_specs(n_jobs, 1.0, max_reads):
+        w = synth.served_job(spec)
+        rs = w.samples[0]
+        packed, mask = kc.pack_ascii(rs.ascii)
+        jobs.append({"w": w, "packed": packed, "mask": mask, "offsets": np.ascontiguousarray(rs.offsets),
+                     "windows": None})
+    return jobs
+
+
+def _plain_job(kc, j):
+    w = j["w"]
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, strategy="partitioned")
+    c.add_reads(0, j["packed"], j["offsets"], j["mask"])
+    c.finalize()
+    keys, counts = c.dump()
+    win = c.stats()["windows"]
+    c.close()
+    return keys, counts, win
+
+
+def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes=64 << 30):
+    """The same Poisson trace through one-at-a-time plain launches and the
+    continuous-batching server, at offered loads relative to plain capacity."""
+    import threading
+
+    import paper_1712_03254_gb300 as kc
+
+    jobs = _served_jobs(n_jobs, max_reads)
+    # plain capacity: the jobs back to back, one at a time
+    for j in jobs[:2]:
+        _plain_job(kc, j)
+    t0 = time.perf_counter()
+    ref = []
+    for j in jobs:
+        keys, counts, win = _plain_job(kc, j)
+        j["windows"] = win
+        ref.append(keys)
+    plain_cap = len(jobs) / (time.perf_counter() - t0)
+    windows = sum(j["windows"] for j in jobs)
+    rng = np.random.default_rng(99)
+    gaps = rng.exponential(1.0, size=len(jobs))
+    out = {"jobs": len(jobs), "max_reads": max_reads, "windows": int(windows),
+           "plain_capacity_jobs_per_s": round(plain_cap, 2), "loads": []}
+    for load in loads:
+        arr = np.concatenate([[0.0], np.cumsum(gaps[1:])]) / (load * plain_cap)
+        # plain: one worker, FIFO, one job at a time
+        lat_plain = []
+        start = time.perf_counter()
+        for i, j in enumerate(jobs):
+            now = time.perf_counter() - start
+            if now < arr[i]:
+                time.sleep(arr[i] - now)
+            _plain_job(kc, j)
+            lat_plain.append((time.perf_counter() - start - arr[i]) * 1e3)
+        span_plain = time.perf_counter() - start
+        # served: the same arrivals submitted to the server
+        srv = kc.KcServer(budget_bytes, max_batch=64)
+        ids = [None] * len(jobs)
+        start = time.perf_counter()
+
+        def feeder():
+            for i, j in enumerate(jobs):
+                now = time.perf_counter() - start
+                if now < arr[i]:
+                    time.sleep(arr[i] - now)
+                ids[i] = srv.submit(j["w"].k, j["w"].bloom_bits, j["w"].n_hashes, j["w"].min_count,
+                                    [(j["packed"], j["offsets"], j["mask"])])
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        same = True
+        for i in range(len(jobs)):
+            srv.wait(ids[i], timeout_s=600)
+            keys, _ = srv.result(ids[i])
+            same &= bool(np.array_equal(keys, ref[i]))
+        span_served = time.perf_counter() - start
+        st = srv.stats()
+        srv.close()
+        out["loads"].append({
+            "offered_load": load, "arrival_rate_jobs_per_s": round(load * plain_cap, 2),
+            "plain": {"jobs_per_s": round(len(jobs) / span_plain, 2),
+                      "p50_ms": round(float(np.percentile(lat_plain, 50)), 3),
+                      "p99_ms": round(float(np.percentile(lat_plain, 99)), 3)},
+            "served": {"jobs_per_s": round(len(jobs) / span_served, 2), "p50_ms": round(st["p50_ms"], 3),
+                       "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 2),
+                       "k_mers_per_s": round(windows / span_served, 1)},
+            "results_equal_alone": same,
+        })
+    # saturation: every job submitted at once
+    srv = kc.KcServer(budget_bytes, max_batch=64)
+    start = time.perf_counter()
+    ids = [srv.submit(j["w"].k, j["w"].bloom_bits, j["w"].n_hashes, j["w"].min_count,
+                      [(j["packed"], j["offsets"], j["mask"])]) for j in jobs]
+    for i in ids:
+        srv.wait(i, timeout_s=600)
+    span = time.perf_counter() - start
+    st = srv.stats()
+    srv.close()
+    out["saturated"] = {"served_jobs_per_s": round(len(jobs) / span, 2), "plain_jobs_per_s": round(plain_cap, 2),
+                        "served_k_mers_per_s": round(windows / span, 1),
+                        "plain_k_mers_per_s": round(windows * plain_cap / len(jobs), 1),
+                        "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 2)}
+    return out
 
 
 # ---------------------------------------------------------------- reference arm
@@ -446,6 +568,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--strategy", choices=["auto", "direct", "partitioned"], default="auto")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-stream comparison")
+    ap.add_argument("--served-jobs", type=int, default=64)
+    ap.add_argument("--served-max-reads", type=int, default=200_000)
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     args = ap.parse_args(argv)

@@ -79,7 +79,8 @@ def test_mix_equals_alone_with_staggered_arrivals(oracle_mod):
 def test_budget_admission_still_exact(oracle_mod):
     jobs = _jobs(4, 8)
     # a budget of about two average jobs: admission has to wait for memory
-    est = [w.bloom_bits // 8 + 50 * w.n_bases + (8 << 20) for w in jobs]
+    # the server's footprint bound: filter + 50 B per base + 8 B per read + 8 MiB
+    est = [w.bloom_bits // 8 + 50 * w.n_bases + 8 * sum(rs.n_reads for rs in w.samples) + (8 << 20) for w in jobs]
     budget = int(2 * np.mean(est))
     srv = kc.KcServer(device_budget_bytes=budget, max_batch=4)
     ids = [srv.submit_workload(w) for w in jobs]
