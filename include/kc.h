@@ -81,7 +81,8 @@ typedef struct kc_config {
     uint32_t block_threads;       /* threads per CTA of the streaming kernels       */
     uint32_t ctas_per_sm;         /* resident CTAs per SM for grid sizing           */
     uint32_t part_bits;           /* partitioned: log2 of the number of hash-prefix
-                                     partitions (1..14)                             */
+                                     partitions (1..20; above 12 the hashes are
+                                     grouped in two levels)                         */
     uint64_t table_slots;         /* direct: open-addressing slots (power of two)
                                      of the global table                            */
     uint32_t spill;               /* 1: each finished partition's result is copied

@@ -15,6 +15,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <thread>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -65,7 +67,7 @@ void set_last_error(const std::string& msg) { kcapi::g_last_error = msg; }
 
 namespace kcapi {
 
-cudaEvent_t phase_begin(kc_handle h) {
+cudaEvent_t phase_begin(kc_handle h, cudaStream_t st) {
     if (!h->cfg.timing) return nullptr;
     cudaEvent_t e = nullptr;
     if (!h->ev_pool.empty()) {
@@ -75,13 +77,13 @@ cudaEvent_t phase_begin(kc_handle h) {
         cudaGetLastError();
         return nullptr;
     }
-    cudaEventRecord(e, h->stream);
+    cudaEventRecord(e, st ? st : h->stream);
     return e;
 }
 
-void phase_end(kc_handle h, int phase, cudaEvent_t a) {
+void phase_end(kc_handle h, int phase, cudaEvent_t a, cudaStream_t st) {
     if (!a) return;
-    cudaEvent_t b = phase_begin(h);
+    cudaEvent_t b = phase_begin(h, st);
     if (!b) {
         h->ev_pool.push_back(a);
         return;
@@ -117,6 +119,70 @@ void free_batches(kc_handle h) {
     h->batches.clear();
 }
 
+void release_spill(kc_handle h) {
+    for (auto& r : h->spill_dir)
+        if (r.host) cudaFreeHost(r.host);
+    h->spill_dir.clear();
+    h->spilled = false;
+    h->spilled_bytes = 0;
+}
+
+// Merge the spilled sorted runs into keys[] / vals[] (host), in key ranges
+// split among threads: each range is cut out of every run by binary search
+// and merged with a small heap.
+void merge_runs(const std::vector<SpillRun>& runs, uint64_t* keys, uint64_t* vals) {
+    std::vector<uint64_t> sample;
+    for (const auto& r : runs)
+        for (uint64_t i = 0; i < r.n_items; i += std::max<uint64_t>(1, r.n_items / 256)) sample.push_back(r.host[i]);
+    std::sort(sample.begin(), sample.end());
+    unsigned T = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<uint64_t> split;  // T-1 splitters
+    for (unsigned t = 1; t < T && !sample.empty(); ++t) split.push_back(sample[sample.size() * t / T]);
+    T = (unsigned)split.size() + 1;
+    // per thread and run: [lo, hi) of the run inside the thread's key range
+    std::vector<std::vector<std::pair<uint64_t, uint64_t>>> cut(T, std::vector<std::pair<uint64_t, uint64_t>>(runs.size()));
+    std::vector<uint64_t> out_off(T + 1, 0);
+    for (size_t r = 0; r < runs.size(); ++r) {
+        const uint64_t* k = runs[r].host;
+        uint64_t prev = 0;
+        for (unsigned t = 0; t < T; ++t) {
+            uint64_t hi = t + 1 < T ? (uint64_t)(std::lower_bound(k, k + runs[r].n_items, split[t]) - k) : runs[r].n_items;
+            hi = std::max(hi, prev);
+            cut[t][r] = {prev, hi};
+            out_off[t + 1] += hi - prev;
+            prev = hi;
+        }
+    }
+    for (unsigned t = 0; t < T; ++t) out_off[t + 1] += out_off[t];
+    auto work = [&](unsigned t) {
+        using Item = std::pair<uint64_t, size_t>;  // key, run
+        std::vector<Item> heap;
+        std::vector<uint64_t> pos(runs.size());
+        for (size_t r = 0; r < runs.size(); ++r) {
+            pos[r] = cut[t][r].first;
+            if (pos[r] < cut[t][r].second) heap.push_back({runs[r].host[pos[r]], r});
+        }
+        auto greater = [](const Item& a, const Item& b) { return a.first > b.first; };
+        std::make_heap(heap.begin(), heap.end(), greater);
+        uint64_t o = out_off[t];
+        while (!heap.empty()) {
+            std::pop_heap(heap.begin(), heap.end(), greater);
+            const size_t r = heap.back().second;
+            heap.pop_back();
+            keys[o] = runs[r].host[pos[r]];
+            vals[o] = runs[r].host[runs[r].n_items + pos[r]];
+            ++o;
+            if (++pos[r] < cut[t][r].second) {
+                heap.push_back({runs[r].host[pos[r]], r});
+                std::push_heap(heap.begin(), heap.end(), greater);
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < T; ++t) pool.emplace_back(work, t);
+    for (auto& th : pool) th.join();
+}
+
 void free_result(kc_handle h) {
     if (h->res_keys) cudaFreeAsync(h->res_keys, h->stream);
     if (h->res_vals) cudaFreeAsync(h->res_vals, h->stream);
@@ -147,12 +213,76 @@ kc_status device_errors(kc_handle h) {
     return KC_OK;
 }
 
+// Second partitioning level: every level-1 group of the batch is split into
+// segments (several CTAs per group), each segment re-bucketed by the next a2
+// bits of h with the same staged whole-sector scatter.  The batch then holds
+// 2^(l1_bits + a2) partitions, exactly as a single level would give them.
+kc_status regroup_batch(kc_handle h, Batch& b, cudaStream_t st) {
+    const int a1 = h->l1_bits, a2 = h->part_bits - h->l1_bits;
+    const uint64_t P1 = 1ull << a1, P2 = 1ull << a2, P = P1 * P2;
+    std::vector<uint64_t> st1(P1 + 1);
+    KC_CUDA(cudaMemcpyAsync(st1.data(), b.hstarts, (P1 + 1) * 8, cudaMemcpyDeviceToHost, st));
+    KC_CUDA(cudaStreamSynchronize(st));
+    const uint64_t total_in = st1[P1];
+    const uint64_t chunk = std::max<uint64_t>(1ull << 16, total_in / ((uint64_t)h->grid.sm_count * 4) + 1);
+    std::vector<kc::SegDesc> segs;
+    std::vector<uint32_t> vlo(P1 + 1);
+    for (uint64_t g = 0; g < P1; ++g) {
+        vlo[g] = (uint32_t)segs.size();
+        for (uint64_t o = st1[g]; o < st1[g + 1]; o += chunk)
+            segs.push_back(kc::SegDesc{o, std::min(chunk, st1[g + 1] - o), g, 0});
+    }
+    vlo[P1] = (uint32_t)segs.size();
+    const uint64_t nv = std::max<size_t>(1, segs.size());
+    if (segs.empty()) segs.push_back(kc::SegDesc{0, 0, 0, 0});
+    uint32_t *counts = nullptr, *total = nullptr, *dvlo = nullptr;
+    uint64_t *rel = nullptr, *starts = nullptr, *cursor = nullptr, *out = nullptr;
+    kc::SegDesc* dsegs = nullptr;
+    const uint64_t cap = total_in + 3 * nv * P2;
+    cudaError_t e;
+    auto bail = [&](cudaError_t err) {
+        for (void* q : {(void*)counts, (void*)total, (void*)dvlo, (void*)rel, (void*)starts, (void*)cursor,
+                        (void*)out, (void*)dsegs})
+            if (q) cudaFreeAsync(q, st);
+        return cuda_fail(err, "cudaMallocAsync(second partitioning level)");
+    };
+    if ((e = cudaMallocAsync(&counts, nv * P2 * 4, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&rel, nv * P2 * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&total, P * 4, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&starts, (P + 1) * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&cursor, P * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&out, std::max<uint64_t>(1, cap) * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&dsegs, nv * sizeof(kc::SegDesc), st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&dvlo, (P1 + 1) * 4, st)) != cudaSuccess)
+        return bail(e);
+    KC_CUDA(cudaMemcpyAsync(dsegs, segs.data(), nv * sizeof(kc::SegDesc), cudaMemcpyHostToDevice, st));
+    KC_CUDA(cudaMemcpyAsync(dvlo, vlo.data(), (P1 + 1) * 4, cudaMemcpyHostToDevice, st));
+    kc::launch_count_seg(b.hdata, dsegs, (int)nv, a1, a2, counts, st);
+    kc::launch_regroup_offsets(counts, dvlo, a1, a2, rel, total, st);
+    if ((e = kc::launch_scan(total, P, starts, cursor, st)) != cudaSuccess) return bail(e);
+    kc::launch_regroup_base(rel, starts, dsegs, nv, a2, st);
+    kc::launch_scatter_staged_seg(b.hdata, dsegs, (int)nv, a1, a2, rel, out, st);
+    h->launches += 5;
+    KC_CUDA(cudaGetLastError());
+    for (void* q : {(void*)counts, (void*)total, (void*)dvlo, (void*)rel, (void*)cursor, (void*)dsegs})
+        cudaFreeAsync(q, st);
+    cudaFreeAsync(b.hdata, st);
+    cudaFreeAsync(b.hstarts, st);
+    b.hdata = out;
+    b.hstarts = starts;
+    b.hcap = cap;
+    return KC_OK;
+}
+
 // Partitioned strategy, ingest: group the batch's window hashes by partition
-// (count pass, per-partition prefix over CTAs, scan, scatter pass).
+// (count pass, per-partition prefix over CTAs, scan, scatter pass).  With more
+// than 12 partition bits the hashes are first grouped by the top l1_bits, then
+// every group is re-bucketed by the next 12 bits (regroup_batch).
 kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st) {
-    const int a = h->part_bits;
+    const int a = h->l1_bits;
     const uint64_t P = 1ull << a;
     int mode = h->cfg.scatter_mode ? (int)h->cfg.scatter_mode : 4;
+    if (h->l1_bits != h->part_bits) mode = 4;  // two levels: staged scatter only
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     if (mode >= 3 && kc::staged_scatter_smem(a) > (size_t)max_optin) mode = 2;
@@ -160,7 +290,8 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
     const uint64_t upc = std::max<uint64_t>(1, (b.n_units + max_ctas - 1) / max_ctas);
     const int n_ctas = (int)((b.n_units + upc - 1) / upc);
     uint32_t *counts = nullptr, *total = nullptr;
-    uint64_t *rel = nullptr, *cursor = nullptr, *lin = nullptr, *seg = nullptr;
+    uint64_t *rel = nullptr, *cursor = nullptr, *lin = nullptr, *g_cursor = nullptr;
+    kc::SegDesc* seg = nullptr;
     // at most one window per base, plus run padding of up to 3 per (CTA, partition)
     b.hcap = n_local + (mode >= 3 ? 3ull * (uint64_t)n_ctas * P : 0ull);
     cudaError_t e = cudaSuccess;
@@ -171,6 +302,7 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
         if (cursor) cudaFreeAsync(cursor, st);
         if (lin) cudaFreeAsync(lin, st);
         if (seg) cudaFreeAsync(seg, st);
+        if (g_cursor) cudaFreeAsync(g_cursor, st);
         if (b.hstarts) cudaFreeAsync(b.hstarts, st);
         if (b.hdata) cudaFreeAsync(b.hdata, st);
         b.hstarts = b.hdata = nullptr;
@@ -184,11 +316,11 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
         (e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, b.hcap) * 8, st)) != cudaSuccess)
         return bail(e);
     if (mode == 4 && ((e = cudaMallocAsync(&lin, std::max<uint64_t>(1, n_local) * 8, st)) != cudaSuccess ||
-                      (e = cudaMallocAsync(&seg, (size_t)n_ctas * 16 + 8, st)) != cudaSuccess))
+                      (e = cudaMallocAsync(&seg, (size_t)n_ctas * sizeof(kc::SegDesc), st)) != cudaSuccess ||
+                      (e = cudaMallocAsync(&g_cursor, 8, st)) != cudaSuccess))
         return bail(e);
     const kc::PassParams p = h->params(b.sample);
     if (mode == 4) {
-        uint64_t* g_cursor = seg + 2 * (size_t)n_ctas;
         KC_CUDA(cudaMemsetAsync(g_cursor, 0, 8, st));
         kc::launch_extract_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, g_cursor, seg, lin, st);
     } else {
@@ -197,7 +329,7 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
     kc::launch_bucket_offsets(counts, n_ctas, a, mode >= 3 ? 1 : 0, rel, total, st);
     if ((e = kc::launch_scan(total, P, b.hstarts, cursor, st)) != cudaSuccess) return bail(e);
     if (mode != 1) kc::launch_bucket_base(rel, b.hstarts, n_ctas, a, st);
-    if (mode == 4) kc::launch_scatter_staged_lin(lin, seg, n_ctas, a, rel, b.hdata, st);
+    if (mode == 4) kc::launch_scatter_staged_seg(lin, seg, n_ctas, 0, a, rel, b.hdata, st);
     else kc::launch_bucket_scatter(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, mode, rel, cursor, b.hdata, st);
     h->launches += mode != 1 ? 5 : 4;
     cudaFreeAsync(counts, st);
@@ -206,6 +338,8 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
     cudaFreeAsync(cursor, st);
     if (lin) cudaFreeAsync(lin, st);
     if (seg) cudaFreeAsync(seg, st);
+    if (g_cursor) cudaFreeAsync(g_cursor, st);
+    if (h->l1_bits != h->part_bits) return regroup_batch(h, b, st);
     return KC_OK;
 }
 
@@ -317,12 +451,19 @@ kc_status finalize_direct(kc_handle h) {
     return s;
 }
 
+// One finalize engine per device, shared by every handle (its buffers and
+// captured sort graph are reused); calls on it are serialised.
+std::mutex g_engine_mutex;
+kc_batch_ctx* g_engines[64] = {};
+
 kc_status finalize_partitioned(kc_handle h) {
-    if (!h->engine) {
-        kc_status s = kc_batch_create_internal(h->stream, &h->engine);
+    if (h->device < 0 || h->device >= 64) return fail(KC_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_engine_mutex);
+    if (!g_engines[h->device]) {
+        kc_status s = kc_batch_create_internal(nullptr, &g_engines[h->device]);
         if (s != KC_OK) return s;
     }
-    return kc_batch_finalize_internal(h->engine, &h, 1);
+    return kc_batch_finalize_internal(g_engines[h->device], &h, 1);
 }
 
 }  // namespace kcapi
@@ -379,14 +520,14 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     if (!is_pow2(slots) || slots < 1024) return fail(KC_ERR_ARG, "table_slots must be a power of two >= 1024");
     if (c.block_threads && c.block_threads != 256) return fail(KC_ERR_ARG, "block_threads must be 256");
     if (c.strategy > KC_STRATEGY_PARTITIONED) return fail(KC_ERR_ARG, "unknown strategy");
-    if (c.part_bits > 14) return fail(KC_ERR_ARG, "part_bits must be <= 14");
+    if (c.part_bits > 20) return fail(KC_ERR_ARG, "part_bits must be <= 20");
     if (c.scatter_mode > 4) return fail(KC_ERR_ARG, "scatter_mode must be in 0..4");
     if (c.smem_table_log2 && (c.smem_table_log2 < 10 || c.smem_table_log2 > 13))
         return fail(KC_ERR_ARG, "smem_table_log2 must be in 10..13");
     // Partitions: filter slices of 4096 words (32 KiB) unless set; the
     // partitioned strategy needs a slice of at most 8192 words in shared memory.
     const int lw = log2_exact(bloom_bits / 64);
-    int pb = c.part_bits ? (int)c.part_bits : std::min(14, std::max(1, lw - 12));
+    int pb = c.part_bits ? (int)c.part_bits : std::min(20, std::max(1, lw - 12));
     pb = std::min(pb, lw);
     const bool part_ok = lw - pb <= 13 && pb >= 1;
     int strategy = (int)c.strategy;
@@ -405,6 +546,7 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     h->log2_words = log2_exact(bloom_bits / 64);
     h->strategy = strategy;
     h->part_bits = pb;
+    h->l1_bits = pb <= 12 ? pb : pb - 12;
     h->slice_log2 = lw - pb;
     if (strategy == KC_STRATEGY_PARTITIONED) slots = 0;
     h->n_slots = slots;
@@ -438,11 +580,13 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     const size_t bloom_bytes = bloom_bits / 8, table_bytes = slots * sizeof(kc::Slot);
-    if ((e = cudaMalloc(&h->bloom, bloom_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(filter)"));
-    if (table_bytes && (e = cudaMalloc(&h->table, table_bytes)) != cudaSuccess)
-        return bail(cuda_fail(e, "cudaMalloc(table)"));
-    if ((e = cudaMalloc(&h->ctr, sizeof(kc::DevCounters))) != cudaSuccess)
-        return bail(cuda_fail(e, "cudaMalloc(counters)"));
+    // stream-ordered pool allocations: no device-wide synchronisation
+    if ((e = cudaMallocAsync(&h->bloom, bloom_bytes, h->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMallocAsync(filter)"));
+    if (table_bytes && (e = cudaMallocAsync(&h->table, table_bytes, h->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMallocAsync(table)"));
+    if ((e = cudaMallocAsync(&h->ctr, sizeof(kc::DevCounters), h->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMallocAsync(counters)"));
     h->fixed_bytes = bloom_bytes + table_bytes + sizeof(kc::DevCounters);
     kc_status s = kc_reset(h);
     if (s != KC_OK) return bail(s);
@@ -454,6 +598,10 @@ kc_status kc_reset(kc_handle h) {
     if (!h) return fail(KC_ERR_ARG, "null handle");
     free_batches(h);
     free_result(h);
+    if (!h->spill_dir.empty()) {
+        cudaStreamSynchronize(h->copy_stream);
+        release_spill(h);
+    }
     KC_CUDA(cudaMemsetAsync(h->bloom, 0, h->bloom_bits / 8, h->stream));
     if (h->table) KC_CUDA(cudaMemsetAsync(h->table, 0, h->n_slots * sizeof(kc::Slot), h->stream));
     KC_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(kc::DevCounters), h->stream));
@@ -476,12 +624,14 @@ void kc_destroy(kc_handle h) {
     if (h->stream) {
         free_batches(h);
         free_result(h);
-        cudaStreamSynchronize(h->stream);
+        if (!h->spill_dir.empty()) {
+            cudaStreamSynchronize(h->copy_stream);
+            release_spill(h);
+        }
+        if (h->bloom) cudaFreeAsync(h->bloom, h->stream);
+        if (h->table) cudaFreeAsync(h->table, h->stream);
+        if (h->ctr) cudaFreeAsync(h->ctr, h->stream);
     }
-    if (h->engine) kc_batch_destroy_internal(h->engine);
-    if (h->bloom) cudaFree(h->bloom);
-    if (h->table) cudaFree(h->table);
-    if (h->ctr) cudaFree(h->ctr);
     for (const auto& m : h->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -617,6 +767,30 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
     if (capacity < h->n_result) return fail(KC_ERR_CAPACITY, "dump capacity smaller than the result");
     if (h->n_result == 0) return KC_OK;
     cudaStream_t st = h->stream;
+    if (h->spilled) {  // merge the host runs
+        const bool dev_k = is_device_ptr(keys), dev_c = counts && is_device_ptr(counts);
+        std::vector<uint64_t> mk, mv(h->n_result);
+        uint64_t* kout = keys;
+        if (dev_k) {
+            mk.resize(h->n_result);
+            kout = mk.data();
+        }
+        merge_runs(h->spill_dir, kout, mv.data());
+        if (dev_k) KC_CUDA(cudaMemcpy(keys, kout, h->n_result * 8, cudaMemcpyHostToDevice));
+        if (counts) {
+            std::vector<uint32_t> c32;
+            uint32_t* cout = counts;
+            if (dev_c) {
+                c32.resize(h->n_result * (size_t)h->n_samples);
+                cout = c32.data();
+            }
+            if (h->n_samples == 2) std::memcpy(cout, mv.data(), h->n_result * 8);
+            else
+                for (uint64_t i = 0; i < h->n_result; ++i) cout[i] = (uint32_t)mv[i];
+            if (dev_c) KC_CUDA(cudaMemcpy(counts, cout, h->n_result * 4 * (size_t)h->n_samples, cudaMemcpyHostToDevice));
+        }
+        return KC_OK;
+    }
     KC_CUDA(cudaMemcpyAsync(keys, h->res_keys, h->n_result * 8, cudaMemcpyDefault, st));
     if (counts) {
         if (h->n_samples == 2) {
@@ -657,6 +831,7 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->partitions = h->strategy == KC_STRATEGY_DIRECT ? 1u : (1u << h->part_bits);
     out->table_log2 = (uint32_t)h->log2_slots;
     out->fallback_partitions = h->fallback_partitions;
+    out->spilled_bytes = h->spilled_bytes;
     out->strategy = (uint32_t)h->strategy;
     size_t bytes = h->fixed_bytes + h->res_cap * 16;
     for (const auto& b : h->batches) {

@@ -27,7 +27,7 @@ struct JobDesc {
     uint32_t min_count;
     int n_batches;
     uint32_t item_base;  // first queue item of this job
-    uint32_t pad0;
+    uint32_t part_base;  // partition of the job's first item
     const uint64_t* const* data;
     const uint64_t* const* starts;
     const int* samples;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
         if (item >= n_items) break;
         const uint32_t j = D->item_job[item];
         const JobDesc& J = D->jobs[j];
-        const uint32_t part = item - J.item_base;
+        const uint32_t part = J.part_base + (item - J.item_base);
         const uint32_t n_sw = 1u << J.slice_log2;
         const uint32_t T = 1u << J.table_log2;
         const uint32_t tmask = T - 1;
@@ -692,12 +692,15 @@ void kc_batch_destroy_internal(kc_batch_ctx* b) {
     delete b;
 }
 
-kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
+// Finalize partitions [part_lo, part_hi) of every job (clamped to the job's
+// partition count); the handles become finalized only when `last`.
+kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo, uint32_t part_hi, bool last) {
     if (!b || !hs || n < 0) return fail(KC_ERR_ARG, "null argument");
     if (n == 0) return KC_OK;
     cudaStream_t st = b->st;
     std::vector<JobWork> work((size_t)n);
-    const bool one = n == 1 && hs[0]->stream == st;
+    const bool one = n == 1 && hs[0]->stream == st;  // no cross-stream ordering needed
+    const bool timed = n == 1;                         // phase times go to the only handle
     // order the batch after every handle's queued work
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
@@ -739,8 +742,9 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
         JobWork& x = work[j];
         kc_handle h = x.h;
         const uint64_t P = 1ull << h->part_bits;
+        const uint64_t p_lo = std::min<uint64_t>(part_lo, P), p_hi = std::min<uint64_t>(part_hi, P);
         const size_t nb = h->batches.size();
-        for (uint64_t p = 0; p < P; ++p) {
+        for (uint64_t p = p_lo; p < p_hi; ++p) {
             uint64_t w = 0;
             for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
             x.max_w = std::max(x.max_w, w);
@@ -758,7 +762,7 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
             return fail(KC_ERR_INTERNAL, "partition does not fit shared memory");
         }
         smem_max = std::max(smem_max, smem);
-        x.sv_cap = std::max<uint64_t>(1, std::min<uint64_t>(P << tl, x.total_w));
+        x.sv_cap = std::max<uint64_t>(1, std::min<uint64_t>((p_hi - p_lo) << tl, x.total_w));
         const size_t meta_bytes = std::max<size_t>(16, nb * 20);
         cudaError_t e;
         if ((e = cudaMallocAsync(&x.sv_keys, x.sv_cap * 8, st)) != cudaSuccess ||
@@ -790,6 +794,7 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
         J.min_count = h->min_count;
         J.n_batches = (int)nb;
         J.item_base = (uint32_t)b->item_job.size();
+        J.part_base = (uint32_t)p_lo;
         J.data = reinterpret_cast<const uint64_t* const*>(x.meta);
         J.starts = reinterpret_cast<const uint64_t* const*>(static_cast<char*>(x.meta) + nb * 8);
         J.samples = reinterpret_cast<const int*>(static_cast<char*>(x.meta) + nb * 16);
@@ -799,7 +804,7 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
         J.sv_cap = x.sv_cap;
         J.failed = x.failed;
         J.ctr = h->ctr;
-        for (uint64_t p = 0; p < P; ++p) b->item_job.push_back((uint32_t)j);
+        for (uint64_t p = p_lo; p < p_hi; ++p) b->item_job.push_back((uint32_t)j);
     }
     const uint32_t n_items = (uint32_t)b->item_job.size();
     kc_status s = ensure_jobs(b, (size_t)n, n_items);
@@ -816,7 +821,7 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
     }
 
     // consume: one persistent launch over the (job, partition) queue
-    cudaEvent_t t0 = one ? phase_begin(hs[0]) : nullptr;
+    cudaEvent_t t0 = timed ? phase_begin(hs[0], st) : nullptr;
     int nh = hs[0]->n_hashes;
     for (int j = 1; j < n; ++j)
         if (hs[j]->n_hashes != nh) nh = 0;
@@ -827,7 +832,7 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
         release_work(b, work);
         return fail(KC_ERR_CUDA, "consumer launch");
     }
-    if (one) phase_end(hs[0], kPass2, t0);
+    if (timed) phase_end(hs[0], kPass2, t0, st);
     KC_CUDA(cudaGetLastError());
     std::vector<unsigned long long> cnt(2 * (size_t)n);
     KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
@@ -835,9 +840,9 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
     for (int j = 0; j < n; ++j) {
         work[j].h->launches += 1;
         if (cnt[2 * j + 1]) {
-            t0 = one ? phase_begin(hs[0]) : nullptr;
+            t0 = timed ? phase_begin(hs[0], st) : nullptr;
             s = run_fallbacks(b, work[j], (uint32_t)j, (uint32_t)cnt[2 * j + 1]);
-            if (one) phase_end(hs[0], kCompact, t0);
+            if (timed) phase_end(hs[0], kCompact, t0, st);
             if (s != KC_OK) {
                 release_work(b, work);
                 return s;
@@ -899,7 +904,7 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
         release_work(b, work);
         return s;
     }
-    t0 = one ? phase_begin(hs[0]) : nullptr;
+    t0 = timed ? phase_begin(hs[0], st) : nullptr;
     KC_CUDA(cudaGraphLaunch(b->sort_graph, st));
     unsigned err = 0;
     KC_CUDA(cudaMemcpyAsync(&err, b->d_flags + 1, 4, cudaMemcpyDeviceToHost, st));
@@ -933,7 +938,7 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
         }
         KC_CUDA(cudaGetLastError());
     }
-    if (one) phase_end(hs[0], kSort, t0);
+    if (timed) phase_end(hs[0], kSort, t0, st);
     release_work(b, work);
     KC_CUDA(cudaStreamSynchronize(st));
     for (int j = 0; j < n; ++j) {
@@ -945,10 +950,61 @@ kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
             KC_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copy, 0));
         }
         phase_collect(h);
-        h->state = State::Finalized;
+        if (last) h->state = State::Finalized;
     }
     b->launches += 7;
     return KC_OK;
+}
+
+// Out-of-core finalize of one handle: the partitions are processed in
+// kSpillGroups hash-prefix groups in turn; each group's sorted survivors are
+// copied to pinned host memory on the handle's side stream while the next
+// group runs, and recorded in the spill directory (first partition, number
+// of partitions, host location, items).  kc_dump merges the sorted runs.
+constexpr uint32_t kSpillGroups = 64;
+
+kc_status finalize_spilled(kc_batch_ctx* b, kc_handle h) {
+    const uint32_t P = 1u << h->part_bits;
+    const uint32_t G = std::min(P, kSpillGroups), per = P / G;
+    release_spill(h);
+    for (uint32_t g = 0; g < G; ++g) {
+        kc_status s = finalize_core(b, &h, 1, g * per, (g + 1) * per, g + 1 == G);
+        if (s != KC_OK) return s;
+        SpillRun run;
+        run.first_part = g * per;
+        run.n_parts = per;
+        run.n_items = h->n_result;
+        if (run.n_items) {
+            cudaError_t e = cudaMallocHost(&run.host, run.n_items * 16);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost(spill)");
+            // the copy waits for the group's sort; the next group runs meanwhile
+            KC_CUDA(cudaEventRecord(h->ev_main, b->st));
+            KC_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_main, 0));
+            KC_CUDA(cudaMemcpyAsync(run.host, h->res_keys, run.n_items * 8, cudaMemcpyDeviceToHost, h->copy_stream));
+            KC_CUDA(cudaMemcpyAsync(run.host + run.n_items, h->res_vals, run.n_items * 8, cudaMemcpyDeviceToHost,
+                                    h->copy_stream));
+        }
+        if (h->res_keys) cudaFreeAsync(h->res_keys, h->copy_stream);
+        if (h->res_vals) cudaFreeAsync(h->res_vals, h->copy_stream);
+        h->res_keys = h->res_vals = nullptr;
+        h->res_cap = 0;
+        h->spill_dir.push_back(run);
+        h->spilled_bytes += run.n_items * 16;
+    }
+    KC_CUDA(cudaStreamSynchronize(h->copy_stream));
+    uint64_t total = 0;
+    for (const auto& r : h->spill_dir) total += r.n_items;
+    h->n_result = total;
+    h->host_ctr.survivors = total;
+    h->spilled = true;
+    return KC_OK;
+}
+
+kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
+    if (n == 1 && hs && hs[0] && hs[0]->cfg.spill && hs[0]->strategy == KC_STRATEGY_PARTITIONED &&
+        hs[0]->state == State::Open)
+        return finalize_spilled(b, hs[0]);
+    return finalize_core(b, hs, n, 0, 0xffffffffu, true);
 }
 
 extern "C" {

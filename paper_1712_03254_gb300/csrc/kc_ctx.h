@@ -28,6 +28,15 @@ struct Batch {
 
 enum class State { Open, Finalized, Poisoned };
 
+// One spilled group of partitions: its sorted survivors in pinned host
+// memory (keys, then packed counts), the swap metadata of the paper's Count
+// unit (partition range, location, number of items).
+struct SpillRun {
+    uint32_t first_part = 0, n_parts = 0;
+    uint64_t* host = nullptr;  // n_items keys followed by n_items packed counts
+    uint64_t n_items = 0;
+};
+
 kc_status fail(kc_status s, const std::string& msg);
 kc_status cuda_fail(cudaError_t e, const char* what);
 
@@ -53,6 +62,7 @@ struct kc_ctx {
     uint64_t n_slots = 0;
     int strategy = KC_STRATEGY_DIRECT;
     int part_bits = 0;   // partitioned: 2^part_bits partitions
+    int l1_bits = 0;     // partitioned: bits of the first grouping at ingest (= part_bits up to 12)
     int slice_log2 = 0;  // partitioned: filter words per partition
 
     uint64_t* bloom = nullptr;
@@ -82,8 +92,11 @@ struct kc_ctx {
     uint64_t launches = 0;
     uint32_t fallback_partitions = 0;
 
-    // partitioned strategy: this handle's own finalize engine (batch of one)
-    kc_batch_ctx* engine = nullptr;
+    // out-of-core results (kc_config.spill)
+    bool spilled = false;
+    std::vector<kcapi::SpillRun> spill_dir;
+    uint64_t spilled_bytes = 0;
+
 
     kc::PassParams params(int sample) const {
         kc::PassParams p{};
@@ -104,12 +117,14 @@ namespace kcapi {
 
 enum Phase { kIngest = 0, kPass1 = 1, kPass2 = 2, kCompact = 3, kSort = 4 };
 
-cudaEvent_t phase_begin(kc_handle h);
-void phase_end(kc_handle h, int phase, cudaEvent_t a);
+// Phase timing events, recorded on stream st (the handle's stream if null).
+cudaEvent_t phase_begin(kc_handle h, cudaStream_t st = nullptr);
+void phase_end(kc_handle h, int phase, cudaEvent_t a, cudaStream_t st = nullptr);
 void phase_collect(kc_handle h);
 kc_status read_counters(kc_handle h);
 kc_status device_errors(kc_handle h);
 void free_result(kc_handle h);
+void release_spill(kc_handle h);
 
 }  // namespace kcapi
 

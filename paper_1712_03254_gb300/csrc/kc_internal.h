@@ -90,17 +90,30 @@ void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_unit
                          int n_ctas, const PassParams& p, int a, uint32_t* counts, cudaStream_t st);
 void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, int pad4, uint64_t* rel, uint32_t* total,
                            cudaStream_t st);
+void launch_bucket_base(uint64_t* rel, const uint64_t* starts, int n_ctas, int a, cudaStream_t st);
 size_t staged_scatter_smem(int a);
+// A run of hashes handled by one CTA: src + off .. src + off + len; group =
+// the level-1 group the run belongs to (0 with a single level).
+struct SegDesc {
+    uint64_t off, len, group, pad;
+};
 // mode 4: the extraction pass writes every CTA's hashes to its own segment of
 // a linear array (plus counts); the staged scatter then moves the segments
 void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
-                          int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, uint64_t* seg,
+                          int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, SegDesc* seg,
                           uint64_t* lin, cudaStream_t st);
-void launch_scatter_staged_lin(const uint64_t* lin, const uint64_t* seg, int n_ctas, int a, const uint64_t* base,
-                               uint64_t* out, cudaStream_t st);
-void launch_bucket_base(uint64_t* rel, const uint64_t* starts, int n_ctas, int a, cudaStream_t st);
-// mode 1: global per-bucket cursors; mode 2: per-CTA runs at base[cta][bucket];
-// mode 3: per-CTA runs padded to whole sectors, staged in shared memory
+// Staged scatter of segs[c] into its runs: bucket (h >> (64 - a1 - a2)) mod
+// 2^a2; with a1 > 0 only hashes of the segment's level-1 group.
+void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,
+                               const uint64_t* base, uint64_t* out, cudaStream_t st);
+// Level-2 re-bucketing of level-1 groups: per-segment counts, per-(group,
+// partition) offsets and totals (padded to 4), absolute run starts.
+void launch_count_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2, uint32_t* counts,
+                      cudaStream_t st);
+void launch_regroup_offsets(const uint32_t* counts, const uint32_t* vlo, int a1, int a2, uint64_t* rel,
+                            uint32_t* total, cudaStream_t st);
+void launch_regroup_base(uint64_t* rel, const uint64_t* starts, const SegDesc* segs, uint64_t n_segs, int a2,
+                         cudaStream_t st);
 void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                            int n_ctas, const PassParams& p, int a, int mode, const uint64_t* base, uint64_t* cursor,
                            uint64_t* out, cudaStream_t st);

@@ -196,13 +196,13 @@ __global__ void __launch_bounds__(kStagedThreads) k_bucket_scatter_staged(
 // Extraction pass: every window's h is written once, CTA by CTA, into one
 // contiguous segment per CTA of a linear array (warp-aggregated positions, so
 // the stores are coalesced), and the CTA's histogram over partitions goes to
-// counts[cta][*].  seg[2*cta] = segment start, seg[2*cta+1] = its length.
+// counts[cta][*].  seg[cta] = {segment start, its length}.
 __global__ void __launch_bounds__(512) k_extract_count(const uint64_t* __restrict__ pw,
                                                        const uint64_t* __restrict__ vw, uint64_t n_units,
                                                        uint64_t units_per_cta, PassParams p, int a,
                                                        uint32_t* __restrict__ counts,
                                                        unsigned long long* __restrict__ g_cursor,
-                                                       uint64_t* __restrict__ seg, uint64_t* __restrict__ lin) {
+                                                       SegDesc* __restrict__ seg, uint64_t* __restrict__ lin) {
     extern __shared__ uint32_t s_cnt[];
     __shared__ unsigned long long s_base;
     __shared__ unsigned s_pos;
@@ -223,8 +223,7 @@ __global__ void __launch_bounds__(512) k_extract_count(const uint64_t* __restric
         for (int w = 0; w < nwarps; ++w) tot += s_warp_tot[w];
         s_base = atomicAdd(g_cursor, tot);
         s_pos = 0;
-        seg[2 * blockIdx.x] = s_base;
-        seg[2 * blockIdx.x + 1] = tot;
+        seg[blockIdx.x] = SegDesc{s_base, tot, 0ull, 0ull};
     }
     __syncthreads();
     const uint64_t base = s_base;
@@ -256,18 +255,22 @@ __global__ void __launch_bounds__(512) k_extract_count(const uint64_t* __restric
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[(uint64_t)blockIdx.x * P + i] = s_cnt[i];
 }
 
-// Staged scatter from the linear array: CTA c moves its own segment (whose
-// histogram is counts[c][*]) into its padded runs, 4 hashes per thread per
-// round; full 4-entry stages leave as aligned 32-byte sectors.
+// Staged scatter of hashes already in memory.  CTA c moves segment c
+// (seg[c] = {offset into src, length, group}) into its padded runs, 4 hashes
+// per thread per round; full 4-entry stages leave as aligned 32-byte sectors.
+// A hash goes to bucket (h >> (64 - a1 - a2)) & (2^a2 - 1); with a1 > 0 the
+// segment belongs to level-1 group `group`, hashes of another group (the
+// level-1 run padding) are skipped, and the run padding written here carries
+// the prefix of another level-2 partition.
 constexpr int kLinThreads = 1024;
 constexpr int kLinPerThread = 4;
 
-__global__ void __launch_bounds__(kLinThreads) k_scatter_staged_lin(const uint64_t* __restrict__ lin,
-                                                                    const uint64_t* __restrict__ seg, int a,
+__global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64_t* __restrict__ src,
+                                                                    const SegDesc* __restrict__ segs, int a1, int a2,
                                                                     const uint64_t* __restrict__ base,
                                                                     uint64_t* __restrict__ out) {
     extern __shared__ unsigned long long s_stage[];
-    const uint32_t P = 1u << a;
+    const uint32_t P = 1u << a2;
     uint32_t* fill = reinterpret_cast<uint32_t*>(s_stage + 4 * (size_t)P);
     uint32_t* wpos = fill + P;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
@@ -275,7 +278,10 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_lin(const uint64
         wpos[i] = 0;
     }
     __syncthreads();
-    const uint64_t s0 = seg[2 * blockIdx.x], len = seg[2 * blockIdx.x + 1];
+    const SegDesc sd = segs[blockIdx.x];
+    const uint64_t s0 = sd.off, len = sd.len;
+    const uint32_t group = (uint32_t)sd.group;
+    const int shift = 64 - a1 - a2;
     const uint64_t* my_base = base + (uint64_t)blockIdx.x * P;
     // thread t owns elements t, t + nt, t + 2 nt, ... of the segment, in order
     uint64_t next = threadIdx.x;
@@ -288,8 +294,8 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_lin(const uint64
 #pragma unroll
             for (int e = 0; e < kLinPerThread; ++e) {
                 if (next < len) {
-                    ph[e] = __ldcg(lin + s0 + next);
-                    pend |= 1u << e;
+                    ph[e] = __ldcg(src + s0 + next);
+                    if (a1 == 0 || (uint32_t)(ph[e] >> (64 - a1)) == group) pend |= 1u << e;
                 }
                 next += blockDim.x;
             }
@@ -298,7 +304,7 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_lin(const uint64
         for (int e = 0; e < kLinPerThread; ++e) {
             if (pend & (1u << e)) {
                 const uint64_t h = ph[e];
-                const uint32_t b = (uint32_t)(h >> (64 - a));
+                const uint32_t b = (uint32_t)(h >> shift) & (P - 1);
                 const uint32_t pos = atomicAdd(&fill[b], 1u);
                 if (pos < 4) {
                     s_stage[(size_t)b * 4 + pos] = h;
@@ -309,10 +315,10 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_lin(const uint64
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
             if (fill[b] >= 4) {
-                const ulonglong2* src = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
+                const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
                 ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + __ldg(my_base + b) + wpos[b]);
-                dst[0] = src[0];
-                dst[1] = src[1];
+                dst[0] = sp[0];
+                dst[1] = sp[1];
                 wpos[b] += 4;
                 fill[b] = 0;
             }
@@ -323,8 +329,59 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_lin(const uint64
         const uint32_t f = fill[b];
         if (f) {
             uint64_t* dst = out + __ldg(my_base + b) + wpos[b];
-            for (uint32_t i = 0; i < 4; ++i) dst[i] = i < f ? (uint64_t)s_stage[(size_t)b * 4 + i] : pad_hash(b, a);
+            const uint64_t pad = pad_hash((group << a2) | b, a1 + a2);
+            for (uint32_t i = 0; i < 4; ++i) dst[i] = i < f ? (uint64_t)s_stage[(size_t)b * 4 + i] : pad;
         }
+    }
+}
+
+// Per-segment histogram over the level-2 buckets of a level-1 group's
+// hashes (hashes of another group -- padding -- are skipped).
+__global__ void __launch_bounds__(1024) k_count_seg(const uint64_t* __restrict__ src, const SegDesc* __restrict__ segs,
+                                                    int a1, int a2, uint32_t* __restrict__ counts) {
+    extern __shared__ uint32_t s_cnt[];
+    const uint32_t P = 1u << a2;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    const SegDesc sd = segs[blockIdx.x];
+    const uint32_t group = (uint32_t)sd.group;
+    const int shift = 64 - a1 - a2;
+    for (uint64_t i = threadIdx.x; i < sd.len; i += blockDim.x) {
+        const uint64_t h = __ldcg(src + sd.off + i);
+        if ((uint32_t)(h >> (64 - a1)) == group) atomicAdd(&s_cnt[(uint32_t)(h >> shift) & (P - 1)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[(uint64_t)blockIdx.x * P + i] = s_cnt[i];
+}
+
+// Level-2 offsets: for partition (g, s), the prefix over the segments of
+// group g (segments vlo[g] .. vlo[g+1]-1) of their padded counts; totals into
+// the flat (g, s) order.  One thread per (g, s).
+__global__ void k_regroup_offsets(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ vlo, int a1, int a2,
+                                  uint64_t* __restrict__ rel, uint32_t* __restrict__ total) {
+    const uint32_t P2 = 1u << a2;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ((uint64_t)1 << (a1 + a2))) return;
+    const uint32_t g = (uint32_t)(t >> a2), sb = (uint32_t)(t & (P2 - 1));
+    uint64_t run = 0;
+    for (uint32_t v = vlo[g]; v < vlo[g + 1]; ++v) {
+        uint32_t x = counts[(uint64_t)v * P2 + sb];
+        x = (x + 3u) & ~3u;
+        rel[(uint64_t)v * P2 + sb] = run;
+        run += x;
+    }
+    total[t] = (uint32_t)run;
+}
+
+// rel[v][s] += starts[(group of v, s)]
+__global__ void k_regroup_base(uint64_t* __restrict__ rel, const uint64_t* __restrict__ starts,
+                               const SegDesc* __restrict__ segs, uint64_t n_segs, int a2) {
+    const uint32_t P2 = 1u << a2;
+    const uint64_t n = n_segs * P2;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t v = i >> a2;
+        rel[i] += starts[((uint64_t)segs[v].group << a2) + (i & (P2 - 1))];
     }
 }
 
@@ -460,7 +517,7 @@ void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_unit
 }
 
 void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
-                          int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, uint64_t* seg,
+                          int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, SegDesc* seg,
                           uint64_t* lin, cudaStream_t st) {
     const size_t smem = bucket_pass_smem(a);
     cudaFuncSetAttribute(k_extract_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -468,11 +525,32 @@ void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_uni
                                                reinterpret_cast<unsigned long long*>(g_cursor), seg, lin);
 }
 
-void launch_scatter_staged_lin(const uint64_t* lin, const uint64_t* seg, int n_ctas, int a, const uint64_t* base,
-                               uint64_t* out, cudaStream_t st) {
-    const size_t smem = staged_scatter_smem(a);
-    cudaFuncSetAttribute(k_scatter_staged_lin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_scatter_staged_lin<<<n_ctas, kLinThreads, smem, st>>>(lin, seg, a, base, out);
+void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,
+                               const uint64_t* base, uint64_t* out, cudaStream_t st) {
+    const size_t smem = staged_scatter_smem(a2);
+    cudaFuncSetAttribute(k_scatter_staged_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_scatter_staged_seg<<<n_segs, kLinThreads, smem, st>>>(src, segs, a1, a2, base, out);
+}
+
+void launch_count_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2, uint32_t* counts,
+                      cudaStream_t st) {
+    const size_t smem = bucket_pass_smem(a2);
+    cudaFuncSetAttribute(k_count_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_count_seg<<<n_segs, 1024, smem, st>>>(src, segs, a1, a2, counts);
+}
+
+void launch_regroup_offsets(const uint32_t* counts, const uint32_t* vlo, int a1, int a2, uint64_t* rel,
+                            uint32_t* total, cudaStream_t st) {
+    const uint64_t n = 1ull << (a1 + a2);
+    k_regroup_offsets<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(counts, vlo, a1, a2, rel, total);
+}
+
+void launch_regroup_base(uint64_t* rel, const uint64_t* starts, const SegDesc* segs, uint64_t n_segs, int a2,
+                         cudaStream_t st) {
+    const uint64_t n = n_segs << a2;
+    unsigned grid = (unsigned)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    k_regroup_base<<<grid, 256, 0, st>>>(rel, starts, segs, n_segs, a2);
 }
 
 void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, int pad4, uint64_t* rel, uint32_t* total,

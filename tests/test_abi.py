@@ -98,7 +98,7 @@ def test_pack_ascii_matches_format(n):
     assert np.array_equal(mask, ref_m)
 
 
-@pytest.mark.parametrize("bloom_log2,part_bits,ok", [(24, 1, False), (24, 4, False), (24, 5, True), (24, 15, False),
+@pytest.mark.parametrize("bloom_log2,part_bits,ok", [(24, 1, False), (24, 4, False), (24, 5, True), (24, 21, False),
                                                      (20, 1, True), (36, 14, False)])
 def test_partitioned_slice_limit(bloom_log2, part_bits, ok):
     """The partitioned strategy keeps one partition's filter words (at most

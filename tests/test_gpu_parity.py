@@ -279,3 +279,39 @@ def test_skewed_key_prefixes_sort_paths(oracle_mod, n_reads, strategy):
     c = gpu_count(w, table_slots=1 << 16, strategy=strategy)
     assert_same_result(c, o)
     assert_same_bloom(c, o)
+
+
+@pytest.mark.parametrize("part_bits", [13, 16, 18])
+def test_two_level_partitions(oracle_mod, part_bits):
+    """More than 12 partition bits: hashes are grouped by the top bits at
+    ingest and each group re-bucketed by the next 12 bits."""
+    w = synth.tiny(scale=0.5)
+    w.bloom_bits = 1 << 30  # 2^24 words: slices of at most 2^11 words at 13+ bits
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", part_bits=part_bits, batches=3)
+    assert c.stats()["partitions"] == 1 << part_bits
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+@pytest.mark.parametrize("part_bits", [10, 16])  # 2^22 filter words: slices of 2^12 and 2^6 words
+def test_spill_to_host_merges_runs(oracle_mod, part_bits):
+    """Out-of-core finalize: 64 groups of partitions in turn, each group's
+    sorted survivors copied to pinned host memory; kc_dump merges the runs."""
+    w = synth.paired(scale=0.002)
+    w.bloom_bits = 1 << 28
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", part_bits=part_bits, spill=True)
+    st = c.stats()
+    assert st["spilled_bytes"] == 16 * st["result_keys"] > 0
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    # dump into device buffers as well
+    torch = pytest.importorskip("torch")
+    n = c.result_size()
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    counts = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+    c.dump(keys, counts)
+    ok, oc = o.result()
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), ok)
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32), oc)
