@@ -298,6 +298,7 @@ def run_kc(args):
 
     c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots, timing=True,
                        strategy=args.strategy, scatter_mode=args.scatter_mode, ctas_per_sm=args.ctas_per_sm,
+                       part_bits=args.part_bits,
                        stream=stream)
 
     # size result buffers with one untimed job
@@ -480,22 +481,36 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
         ids = [None] * len(jobs)
         start = time.perf_counter()
 
+        late = [0.0] * len(jobs)  # submit time after the scheduled arrival
+        submitted = [threading.Event() for _ in jobs]
+
         def feeder():
             for i, j in enumerate(jobs):
                 now = time.perf_counter() - start
                 if now < arr[i]:
                     time.sleep(arr[i] - now)
+                late[i] = time.perf_counter() - start - arr[i]
                 ids[i] = srv.submit(j["w"].k, j["w"].bloom_bits, j["w"].n_hashes, j["w"].min_count,
                                     [(j["packed"], j["offsets"], j["mask"])])
+                submitted[i].set()
 
-        th = threading.Thread(target=feeder)
-        th.start()
-        th.join()
-        same = True
-        for i in range(len(jobs)):
-            srv.wait(ids[i], timeout_s=600)
-            keys, _ = srv.result(ids[i])
-            same &= bool(np.array_equal(keys, ref[i]))
+        same = [True]
+        lat_served = [0.0] * len(jobs)
+
+        def collector():  # takes each result as it completes, as a client would
+            for i in range(len(jobs)):
+                submitted[i].wait()
+                _, lat = srv.wait(ids[i], timeout_s=600)
+                lat_served[i] = lat + late[i] * 1e3  # from the scheduled arrival, as for plain
+                keys, _ = srv.result(ids[i])
+                same[0] &= bool(np.array_equal(keys, ref[i]))
+
+        threads = [threading.Thread(target=feeder), threading.Thread(target=collector)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        same = same[0]
         span_served = time.perf_counter() - start
         st = srv.stats()
         srv.close()
@@ -504,9 +519,13 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
             "plain": {"jobs_per_s": round(len(jobs) / span_plain, 2),
                       "p50_ms": round(float(np.percentile(lat_plain, 50)), 3),
                       "p99_ms": round(float(np.percentile(lat_plain, 99)), 3)},
-            "served": {"jobs_per_s": round(len(jobs) / span_served, 2), "p50_ms": round(st["p50_ms"], 3),
-                       "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 2),
-                       "k_mers_per_s": round(windows / span_served, 1)},
+            "served": {"jobs_per_s": round(len(jobs) / span_served, 2),
+                       "p50_ms": round(float(np.percentile(lat_served, 50)), 3),
+                       "p99_ms": round(float(np.percentile(lat_served, 99)), 3),
+                       "mean_batch": round(st["mean_batch"], 2),
+                       "k_mers_per_s": round(windows / span_served, 1),
+                       "stage_ms": {x: round(st["mean_" + x + "_ms"], 3)
+                                    for x in ("queue", "ingest", "batch_wait", "finalize")}},
             "results_equal_alone": same,
         })
     # saturation: every job submitted at once
@@ -522,7 +541,9 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
     out["saturated"] = {"served_jobs_per_s": round(len(jobs) / span, 2), "plain_jobs_per_s": round(plain_cap, 2),
                         "served_k_mers_per_s": round(windows / span, 1),
                         "plain_k_mers_per_s": round(windows * plain_cap / len(jobs), 1),
-                        "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 2)}
+                        "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 2),
+                        "stage_ms": {x: round(st["mean_" + x + "_ms"], 3)
+                                     for x in ("queue", "ingest", "batch_wait", "finalize")}}
     return out
 
 
@@ -573,6 +594,7 @@ def main(argv=None):
     ap.add_argument("--served-max-reads", type=int, default=200_000)
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--part-bits", type=int, default=0)
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

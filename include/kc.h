@@ -98,9 +98,16 @@ typedef struct kc_config {
                                      sectors, staged in shared memory, 4 = as 3,
                                      from hashes first written per CTA to a linear
                                      array (default)                                */
-    uint32_t reserved1;
+    uint32_t split_max;           /* partitioned: a partition whose candidates
+                                     overflow its shared-memory table is counted
+                                     again as 2, 4, ... 2^split_max sub-ranges of
+                                     its filter slice before it falls back to a
+                                     global table (0 = 6; at most the slice's
+                                     log2 words; KC_SPLIT_NONE = never split)       */
     uint64_t reserved[4];
 } kc_config;
+
+#define KC_SPLIT_NONE 0xffffffffu
 
 /*
  * Strategies.  Both compute the same result and filter bit for bit.
@@ -143,6 +150,8 @@ typedef struct kc_stats {
     double ms_ingest, ms_pass1, ms_pass2, ms_compact, ms_sort;
     uint32_t strategy;              /* KC_STRATEGY_DIRECT or KC_STRATEGY_PARTITIONED */
     uint32_t fallback_partitions;   /* partitions whose table left shared memory    */
+    uint32_t split_partitions;      /* partitions counted as sub-ranges (split_max) */
+    uint32_t split_level;           /* finest split level any partition needed      */
 } kc_stats;
 
 /*
@@ -197,6 +206,10 @@ typedef struct kc_server_stats {
     double jobs_per_s;        /* completed jobs / (last completion - first submit) */
     uint64_t peak_bytes;      /* largest admitted footprint sum                */
     uint64_t budget_bytes;
+    /* mean stage times of completed jobs: submit -> admitted, admitted ->
+     * reads on the device, -> its batch starts, batch start -> result in host
+     * memory */
+    double mean_queue_ms, mean_ingest_ms, mean_batch_wait_ms, mean_finalize_ms;
 } kc_server_stats;
 
 /* Create a server on the current device (max_batch >= 1). */

@@ -38,7 +38,7 @@ class Config(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("part_bits", ctypes.c_uint32),
                 ("table_slots", ctypes.c_uint64), ("spill", ctypes.c_uint32), ("timing", ctypes.c_uint32),
                 ("strategy", ctypes.c_uint32), ("smem_table_log2", ctypes.c_uint32),
-                ("scatter_mode", ctypes.c_uint32), ("reserved1", ctypes.c_uint32), ("reserved", ctypes.c_uint64 * 4)]
+                ("scatter_mode", ctypes.c_uint32), ("split_max", ctypes.c_uint32), ("reserved", ctypes.c_uint64 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -48,7 +48,8 @@ class Stats(ctypes.Structure):
                 ("table_log2", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("ms_ingest", ctypes.c_double), ("ms_pass1", ctypes.c_double), ("ms_pass2", ctypes.c_double),
                 ("ms_compact", ctypes.c_double), ("ms_sort", ctypes.c_double), ("strategy", ctypes.c_uint32),
-                ("fallback_partitions", ctypes.c_uint32)]
+                ("fallback_partitions", ctypes.c_uint32), ("split_partitions", ctypes.c_uint32),
+                ("split_level", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -65,7 +66,9 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
                 ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("jobs_per_s", ctypes.c_double),
-                ("peak_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
+                ("peak_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
+                ("mean_queue_ms", ctypes.c_double), ("mean_ingest_ms", ctypes.c_double),
+                ("mean_batch_wait_ms", ctypes.c_double), ("mean_finalize_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -162,13 +165,16 @@ def pack_ascii(ascii: np.ndarray):
     return packed, mask
 
 
+SPLIT_NONE = 0xFFFFFFFF  # kc_config.split_max: overflowing partitions go straight to the global table
+
+
 class KmerCounter:
     """One counting job: add reads per sample, finalize, dump sorted counts."""
 
     def __init__(self, k: int, n_samples: int, bloom_bits: int, n_hashes: int = 4, min_count: int = 2,
                  table_slots: int = 0, part_bits: int = 0, spill: bool = False, ctas_per_sm: int = 0,
                  timing: bool = False, strategy: str = "auto", smem_table_log2: int = 0, scatter_mode: int = 0,
-                 stream=None):
+                 split_max: int = 0, stream=None):
         L = lib()
         cfg = Config()
         L.kc_default_config(ctypes.byref(cfg))
@@ -180,6 +186,7 @@ class KmerCounter:
         cfg.strategy = {"auto": 0, "direct": 1, "partitioned": 2}[strategy]
         cfg.smem_table_log2 = smem_table_log2
         cfg.scatter_mode = scatter_mode
+        cfg.split_max = SPLIT_NONE if split_max < 0 else split_max  # -1: never split an overflowing partition
         h = ctypes.c_void_p()
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream

@@ -524,6 +524,7 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     if (c.scatter_mode > 4) return fail(KC_ERR_ARG, "scatter_mode must be in 0..4");
     if (c.smem_table_log2 && (c.smem_table_log2 < 10 || c.smem_table_log2 > 13))
         return fail(KC_ERR_ARG, "smem_table_log2 must be in 10..13");
+    if (c.split_max != KC_SPLIT_NONE && c.split_max > 13) return fail(KC_ERR_ARG, "split_max must be in 0..13");
     // Partitions: filter slices of 4096 words (32 KiB) unless set; the
     // partitioned strategy needs a slice of at most 8192 words in shared memory.
     const int lw = log2_exact(bloom_bits / 64);
@@ -831,6 +832,8 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->partitions = h->strategy == KC_STRATEGY_DIRECT ? 1u : (1u << h->part_bits);
     out->table_log2 = (uint32_t)h->log2_slots;
     out->fallback_partitions = h->fallback_partitions;
+    out->split_partitions = h->host_ctr.split_parts;
+    out->split_level = h->host_ctr.split_hint;
     out->spilled_bytes = h->spilled_bytes;
     out->strategy = (uint32_t)h->strategy;
     size_t bytes = h->fixed_bytes + h->res_cap * 16;

@@ -35,11 +35,11 @@ struct JobDesc {
     uint64_t* sv_keys;
     uint64_t* sv_vals;
     uint64_t sv_cap;
-    uint32_t* failed;
+    uint64_t* failed;  // per overflowing partition: its first hash not yet counted
     DevCounters* ctr;
     // sort
     int sort_bits;
-    int pad1;
+    int split_max;  // consumer: finest split level 2^split_max before the fallback
     uint64_t bucket_base;  // first bucket of this job in the flat arrays
     uint64_t n_buckets;
     uint64_t* res_keys;
@@ -70,10 +70,20 @@ constexpr int kConsumeThreads = 512;
 constexpr int kTile = 4096;
 
 // NH > 0: every job of the batch sets NH bits per key; NH = 0: per job.
+//
+// A partition whose candidates overflow the shared-memory table is counted
+// again in 2, 4, ... 2^split_max sub-ranges of its filter slice: the top bits
+// of a window's in-slice word index pick its sub-range, so two sub-ranges
+// never share a filter word and each one's filter, claims and recount are
+// exactly those of the whole partition restricted to its keys.  Sub-ranges
+// already finished stay finished when a later one has to split further.
+// Only a partition that overflows at the finest level is left to the global
+// fallback.  The finest level a job has needed is kept in its counters, and
+// its later partitions start there instead of overflowing again.
 template <int NH>
 __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDesc* __restrict__ D) {
     extern __shared__ unsigned long long s_mem[];
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_hint;
     __shared__ unsigned s_item;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -81,9 +91,15 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
     uint64_t cand = 0, claimed = 0;
     DevCounters* last_ctr = nullptr;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(D->head, 1u);
+        if (threadIdx.x == 0) {
+            const unsigned it = atomicAdd(D->head, 1u);
+            s_item = it;
+            // the finest level this job's partitions have needed so far
+            s_hint = it < n_items ? (int)*(volatile unsigned*)&D->jobs[D->item_job[it]].ctr->split_hint : 0;
+        }
         __syncthreads();
         const unsigned item = s_item;
+        const int hint = s_hint;
         if (item >= n_items) break;
         const uint32_t j = D->item_job[item];
         const JobDesc& J = D->jobs[j];
@@ -94,7 +110,6 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
         const int S = J.n_samples;
         const int a = J.part_bits;
         const uint64_t low_mask = (1ull << (64 - a)) - 1ull;
-        const int home_shift = 64 - a - J.table_log2;
         unsigned long long* sb = s_mem;
         unsigned long long* sk = s_mem + n_sw;
         uint32_t* sc = reinterpret_cast<uint32_t*>(s_mem + n_sw + T);
@@ -108,77 +123,117 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
             cand = claimed = 0;
             last_ctr = J.ctr;
         }
-        for (uint32_t i = threadIdx.x; i < n_sw; i += blockDim.x) sb[i] = 0ull;
-        for (uint32_t i = threadIdx.x; i < T; i += blockDim.x) sk[i] = 0ull;
-        for (uint32_t i = threadIdx.x; i < T * S; i += blockDim.x) sc[i] = 0u;
-        if (threadIdx.x == 0) s_fail = 0;
-        __syncthreads();
-        for (int bt = 0; bt < J.n_batches; ++bt) {
-            const uint64_t* __restrict__ d = J.data[bt];
-            const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
-            for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const uint64_t h = __ldcg(d + i);  // read again by the recount: keep in L2
-                if ((uint32_t)(h >> (64 - a)) != part) continue;  // run padding
-                const uint32_t w = (uint32_t)(h >> J.bloom_shift) & (n_sw - 1);
-                const uint64_t g = mixer64(h);
-                const uint64_t pat = NH > 0 ? bloom_pattern_n<(NH > 0 ? NH : 1)>(g) : bloom_pattern_rt(g, J.n_hashes);
-                const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
-                if (J.all_candidates || (old & pat) == pat) {
-                    ++cand;
-                    const int r = smem_claim(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
-                    if (r < 0) s_fail = 1;
-                    else claimed += (uint64_t)r;
-                }
-            }
-        }
-        __syncthreads();
-        if (s_fail) {
-            if (threadIdx.x == 0) J.failed[atomicAdd(&D->counters[2 * j + 1], 1ull)] = part;
-            __syncthreads();
-            continue;
-        }
-        for (int bt = 0; bt < J.n_batches; ++bt) {
-            const uint64_t* __restrict__ d = J.data[bt];
-            const int smp = J.samples[bt];
-            const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
-            for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const uint64_t h = __ldcs(d + i);  // last use
-                if ((uint32_t)(h >> (64 - a)) != part) continue;
-                const int s = smem_find(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
-                if (s >= 0) atomicAdd(sc + (uint32_t)s * S + smp, 1u);
-            }
-        }
-        __syncthreads();
         const uint64_t hpre = (uint64_t)part << (64 - a);
-        for (uint32_t i0 = threadIdx.x & ~31u; i0 < T; i0 += blockDim.x) {
-            const uint32_t i = i0 + lane;
-            const unsigned long long k1 = sk[i];
-            uint64_t v = 0;
-            bool keep = false;
-            if (k1 != 0ull) {
-                const uint32_t c0 = sc[i * S];
-                const uint32_t c1 = S == 2 ? sc[i * S + 1] : 0u;
-                keep = (uint64_t)c0 + c1 >= J.min_count;
-                v = (uint64_t)c0 | ((uint64_t)c1 << 32);
-            }
-            const unsigned ballot = __ballot_sync(kFull, keep);
-            if (ballot) {
-                const int leader = __ffs(ballot) - 1;
-                unsigned long long pos0 = 0;
-                if (lane == leader) pos0 = atomicAdd(&D->counters[2 * j], (unsigned long long)__popc(ballot));
-                pos0 = __shfl_sync(kFull, pos0, leader);
-                if (keep) {
-                    const uint64_t pos = pos0 + __popc(ballot & lt);
-                    if (pos < J.sv_cap) {
-                        J.sv_keys[pos] = unmixer64(hpre | (k1 - 1ull));
-                        J.sv_vals[pos] = v;
+        int sl = min(hint, J.split_max);  // split level: the partition is taken as 2^sl sub-ranges
+        uint32_t sub = 0;  // the sub-range being counted
+        bool overflow = false;
+        uint64_t h_left = 0;  // first hash left to the fallback
+        for (;;) {
+            const uint32_t w_n = n_sw >> sl;
+            const uint32_t w_lo = sub * w_n;
+            const uint32_t smask = (1u << sl) - 1u;
+            const int sub_shift = 64 - a - sl;  // sub-range = h bits [sub_shift, 64 - a)
+            const int home_shift = sub_shift - J.table_log2;
+            uint64_t c_try = 0, k_try = 0;
+            for (uint32_t i = threadIdx.x; i < w_n; i += blockDim.x) sb[w_lo + i] = 0ull;
+            for (uint32_t i = threadIdx.x; i < T; i += blockDim.x) sk[i] = 0ull;
+            for (uint32_t i = threadIdx.x; i < T * S; i += blockDim.x) sc[i] = 0u;
+            if (threadIdx.x == 0) s_fail = 0;
+            __syncthreads();
+            bool stop = false;
+            for (int bt = 0; bt < J.n_batches && !stop; ++bt) {
+                const uint64_t* __restrict__ d = J.data[bt];
+                const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
+                for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                    const uint64_t h = __ldcg(d + i);  // read again by the recount: keep in L2
+                    if ((uint32_t)(h >> (64 - a)) != part) continue;  // run padding
+                    if (sl && ((uint32_t)(h >> sub_shift) & smask) != sub) continue;
+                    const uint32_t w = (uint32_t)(h >> J.bloom_shift) & (n_sw - 1);
+                    const uint64_t g = mixer64(h);
+                    const uint64_t pat = NH > 0 ? bloom_pattern_n<(NH > 0 ? NH : 1)>(g) : bloom_pattern_rt(g, J.n_hashes);
+                    const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
+                    if (J.all_candidates || (old & pat) == pat) {
+                        ++c_try;
+                        const int r = smem_claim(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
+                        if (r < 0) {
+                            s_fail = 1;
+                            stop = true;
+                            break;
+                        }
+                        if (r > 0) {
+                            ++k_try;
+                            if (*(volatile int*)&s_fail) {  // another thread overflowed: give up early
+                                stop = true;
+                                break;
+                            }
+                        }
                     }
                 }
             }
+            __syncthreads();
+            const int failed = s_fail;
+            __syncthreads();
+            if (failed) {
+                if (sl < J.split_max) {
+                    ++sl;
+                    sub <<= 1;
+                    continue;
+                }
+                overflow = true;
+                h_left = hpre | ((uint64_t)sub << sub_shift);
+                break;
+            }
+            cand += c_try;
+            claimed += k_try;
+            for (int bt = 0; bt < J.n_batches; ++bt) {
+                const uint64_t* __restrict__ d = J.data[bt];
+                const int smp = J.samples[bt];
+                const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
+                for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                    const uint64_t h = sl ? __ldcg(d + i) : __ldcs(d + i);  // last use unless split
+                    if ((uint32_t)(h >> (64 - a)) != part) continue;
+                    if (sl && ((uint32_t)(h >> sub_shift) & smask) != sub) continue;
+                    const int s = smem_find(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
+                    if (s >= 0) atomicAdd(sc + (uint32_t)s * S + smp, 1u);
+                }
+            }
+            __syncthreads();
+            for (uint32_t i0 = threadIdx.x & ~31u; i0 < T; i0 += blockDim.x) {
+                const uint32_t i = i0 + lane;
+                const unsigned long long k1 = sk[i];
+                uint64_t v = 0;
+                bool keep = false;
+                if (k1 != 0ull) {
+                    const uint32_t c0 = sc[i * S];
+                    const uint32_t c1 = S == 2 ? sc[i * S + 1] : 0u;
+                    keep = (uint64_t)c0 + c1 >= J.min_count;
+                    v = (uint64_t)c0 | ((uint64_t)c1 << 32);
+                }
+                const unsigned ballot = __ballot_sync(kFull, keep);
+                if (ballot) {
+                    const int leader = __ffs(ballot) - 1;
+                    unsigned long long pos0 = 0;
+                    if (lane == leader) pos0 = atomicAdd(&D->counters[2 * j], (unsigned long long)__popc(ballot));
+                    pos0 = __shfl_sync(kFull, pos0, leader);
+                    if (keep) {
+                        const uint64_t pos = pos0 + __popc(ballot & lt);
+                        if (pos < J.sv_cap) {
+                            J.sv_keys[pos] = unmixer64(hpre | (k1 - 1ull));
+                            J.sv_vals[pos] = v;
+                        }
+                    }
+                }
+            }
+            unsigned long long* gb = J.bloom + (uint64_t)part * n_sw + w_lo;
+            for (uint32_t i = threadIdx.x; i < w_n; i += blockDim.x) gb[i] = sb[w_lo + i];
+            __syncthreads();
+            if (++sub > smask) break;
         }
-        unsigned long long* gb = J.bloom + (uint64_t)part * n_sw;
-        for (uint32_t i = threadIdx.x; i < n_sw; i += blockDim.x) gb[i] = sb[i];
-        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (overflow) J.failed[atomicAdd(&D->counters[2 * j + 1], 1ull)] = h_left;
+            else if (sl) atomicAdd(&J.ctr->split_parts, 1u);
+            if (sl > hint) atomicMax(&J.ctr->split_hint, (unsigned)sl);
+        }
     }
     cand = warp_sum(cand);
     claimed = warp_sum(claimed);
@@ -530,7 +585,7 @@ struct JobWork {
     uint64_t* sv_keys = nullptr;
     uint64_t* sv_vals = nullptr;
     uint64_t sv_cap = 0;
-    uint32_t* failed = nullptr;
+    uint64_t* failed = nullptr;
     void* meta = nullptr;
 };
 
@@ -577,8 +632,8 @@ kc_status run_fallbacks(kc_batch_ctx* b, JobWork& x, uint32_t j, uint32_t n_fail
     const kc::JobDesc& J = b->jobs[j];
     const uint64_t P = 1ull << h->part_bits;
     const size_t nb = h->batches.size();
-    std::vector<uint32_t> fl(n_failed);
-    KC_CUDA(cudaMemcpyAsync(fl.data(), x.failed, n_failed * 4, cudaMemcpyDeviceToHost, b->st));
+    std::vector<uint64_t> fl(n_failed);  // first hash of each partition not yet counted
+    KC_CUDA(cudaMemcpyAsync(fl.data(), x.failed, n_failed * 8, cudaMemcpyDeviceToHost, b->st));
     unsigned long long n_sv = 0;
     KC_CUDA(cudaMemcpyAsync(&n_sv, b->d_counters + 2 * j, 8, cudaMemcpyDeviceToHost, b->st));
     KC_CUDA(cudaStreamSynchronize(b->st));
@@ -587,8 +642,9 @@ kc_status run_fallbacks(kc_batch_ctx* b, JobWork& x, uint32_t j, uint32_t n_fail
         for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
         return w;
     };
+    const int a = h->part_bits;
     uint64_t extra = 0;
-    for (uint32_t p : fl) extra += windows_of(p);
+    for (uint64_t hl : fl) extra += windows_of((uint32_t)(hl >> (64 - a)));
     const uint64_t need = n_sv + extra;
     if (need > x.sv_cap) {
         uint64_t *nk = nullptr, *nv = nullptr;
@@ -608,19 +664,22 @@ kc_status run_fallbacks(kc_batch_ctx* b, JobWork& x, uint32_t j, uint32_t n_fail
         x.sv_cap = need;
     }
     const uint64_t n_sw = 1ull << h->slice_log2;
-    for (uint32_t p : fl) {
+    for (uint64_t hl : fl) {
+        const uint32_t p = (uint32_t)(hl >> (64 - a));
+        const uint64_t w_lo = (hl >> J.bloom_shift) & (n_sw - 1);  // sub-ranges below are finished
         uint64_t slots = 1024;
         while (slots < 2 * windows_of(p)) slots <<= 1;
         kc::Slot* table = nullptr;
         cudaError_t e = cudaMallocAsync(&table, slots * sizeof(kc::Slot), b->st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(fallback table)");
         KC_CUDA(cudaMemsetAsync(table, 0, slots * sizeof(kc::Slot), b->st));
-        KC_CUDA(cudaMemsetAsync(h->bloom + p * n_sw, 0, n_sw * 8, b->st));
+        KC_CUDA(cudaMemsetAsync(h->bloom + p * n_sw + w_lo, 0, (n_sw - w_lo) * 8, b->st));
         kc::FallbackArgs F{};
         F.data = J.data;
         F.starts = J.starts;
         F.samples = J.samples;
         F.part = p;
+        F.h_lo = hl;
         F.part_bits = h->part_bits;
         F.bloom_shift = J.bloom_shift;
         F.n_hashes = h->n_hashes;
@@ -750,6 +809,8 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
             x.max_w = std::max(x.max_w, w);
             x.total_w += w;
         }
+        // Shared-memory table: one slot per 8 windows of the largest partition
+        // (2^10..2^13 slots); partitions with more candidates split.
         int tl = (int)h->cfg.smem_table_log2;
         if (!tl) {
             tl = 10;
@@ -762,12 +823,22 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
             return fail(KC_ERR_INTERNAL, "partition does not fit shared memory");
         }
         smem_max = std::max(smem_max, smem);
-        x.sv_cap = std::max<uint64_t>(1, std::min<uint64_t>((p_hi - p_lo) << tl, x.total_w));
+        // survivors: a partition holds at most 2^split_max tables of keys and
+        // one key per min_count of its windows
+        const int split_max = h->cfg.split_max == KC_SPLIT_NONE ? 0
+                              : std::min<int>(h->slice_log2, h->cfg.split_max ? (int)h->cfg.split_max : 6);
+        x.sv_cap = 0;
+        for (uint64_t p = p_lo; p < p_hi; ++p) {
+            uint64_t w = 0;
+            for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
+            x.sv_cap += std::min<uint64_t>(1ull << (tl + split_max), w / std::max<uint32_t>(1, h->min_count));
+        }
+        x.sv_cap = std::max<uint64_t>(1, x.sv_cap);
         const size_t meta_bytes = std::max<size_t>(16, nb * 20);
         cudaError_t e;
         if ((e = cudaMallocAsync(&x.sv_keys, x.sv_cap * 8, st)) != cudaSuccess ||
             (e = cudaMallocAsync(&x.sv_vals, x.sv_cap * 8, st)) != cudaSuccess ||
-            (e = cudaMallocAsync(&x.failed, P * 4, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&x.failed, P * 8, st)) != cudaSuccess ||
             (e = cudaMallocAsync(&x.meta, meta_bytes, st)) != cudaSuccess) {
             release_work(b, work);
             return cuda_fail(e, "cudaMallocAsync(batch consumer)");
@@ -792,6 +863,7 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         J.all_candidates = h->min_count <= 1 ? 1 : 0;
         J.key_bits = 2 * h->k;
         J.min_count = h->min_count;
+        J.split_max = split_max;
         J.n_batches = (int)nb;
         J.item_base = (uint32_t)b->item_job.size();
         J.part_base = (uint32_t)p_lo;

@@ -25,7 +25,9 @@ struct DevCounters {
     unsigned long long claimed;     // keys inserted into the table
     unsigned long long survivors;   // keys written by the compaction
     unsigned int err;               // DERR_* bits
-    unsigned int pad[7];
+    unsigned int split_parts;       // partitions counted in sub-ranges
+    unsigned int split_hint;        // split level the job's partitions start at
+    unsigned int pad[5];
 };
 
 enum : unsigned int {

@@ -69,6 +69,7 @@ struct FallbackArgs {
     const uint64_t* const* starts;
     const int* samples;
     uint32_t part;
+    uint64_t h_lo;  // hashes of the partition below h_lo are already counted
     int part_bits;
     int bloom_shift;
     int n_hashes;

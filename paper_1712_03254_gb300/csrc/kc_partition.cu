@@ -58,6 +58,13 @@ enum BucketMode { kCountPerCta = 0, kScatterCursor = 1, kScatterRegion = 2, kSca
 // (which checks the prefix) skips it.
 __device__ __forceinline__ uint64_t pad_hash(uint32_t b, int a) { return (uint64_t)(b ^ 1u) << (64 - a); }
 
+// Entries staged per bucket by the segment scatter: about 16K entries in all
+// (128 KiB), never fewer than one sector's 4 per bucket.
+__host__ __device__ __forceinline__ uint32_t stage_depth(int a) {
+    const uint32_t d = (16384u >> a) & ~3u;
+    return d < 4u ? 4u : d;
+}
+
 // kCountPerCta: per-CTA histogram of the windows' buckets in shared memory,
 // written out CTA-major.  kScatterRegion: the same windows again; each CTA
 // owns one run per bucket (exact offsets from the counts) and stores each h
@@ -271,7 +278,8 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
                                                                     uint64_t* __restrict__ out) {
     extern __shared__ unsigned long long s_stage[];
     const uint32_t P = 1u << a2;
-    uint32_t* fill = reinterpret_cast<uint32_t*>(s_stage + 4 * (size_t)P);
+    const uint32_t D = stage_depth(a2);  // entries staged per bucket, a multiple of 4
+    uint32_t* fill = reinterpret_cast<uint32_t*>(s_stage + (size_t)D * P);
     uint32_t* wpos = fill + P;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
         fill[i] = 0;
@@ -283,6 +291,7 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
     const uint32_t group = (uint32_t)sd.group;
     const int shift = 64 - a1 - a2;
     const uint64_t* my_base = base + (uint64_t)blockIdx.x * P;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     // thread t owns elements t, t + nt, t + 2 nt, ... of the segment, in order
     uint64_t next = threadIdx.x;
     uint64_t ph[kLinPerThread];
@@ -306,31 +315,54 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
                 const uint64_t h = ph[e];
                 const uint32_t b = (uint32_t)(h >> shift) & (P - 1);
                 const uint32_t pos = atomicAdd(&fill[b], 1u);
-                if (pos < 4) {
-                    s_stage[(size_t)b * 4 + pos] = h;
+                if (pos < D) {
+                    s_stage[(size_t)b * D + pos] = h;
                     pend &= ~(1u << e);
                 }  // else the stage is full: retry next round
             }
         }
         __syncthreads();
-        for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
-            if (fill[b] >= 4) {
-                const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
-                ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + __ldg(my_base + b) + wpos[b]);
-                dst[0] = sp[0];
-                dst[1] = sp[1];
-                wpos[b] += 4;
-                fill[b] = 0;
+        if (D == 4) {
+            // shallow stages (many buckets): a thread per bucket, one sector
+            for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
+                if (fill[b] >= 4) {
+                    const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
+                    ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + __ldg(my_base + b) + wpos[b]);
+                    dst[0] = sp[0];
+                    dst[1] = sp[1];
+                    wpos[b] += 4;
+                    fill[b] = 0;
+                }
+            }
+        } else {
+            // deep stages (few buckets): a warp per bucket writes its whole
+            // sectors, then keeps the 0..3 entries left over at the front
+            for (uint32_t b = wid; b < P; b += nwarps) {
+                const uint32_t f = min(fill[b], D);
+                const uint32_t whole = f & ~3u;
+                unsigned long long* st = s_stage + (size_t)b * D;
+                uint64_t* dst = out + __ldg(my_base + b) + wpos[b];
+                for (uint32_t i = lane * 2; i < whole; i += 64)
+                    *reinterpret_cast<ulonglong2*>(dst + i) = *reinterpret_cast<const ulonglong2*>(st + i);
+                __syncwarp();
+                if (lane == 0) {
+                    for (uint32_t i = whole; i < f; ++i) st[i - whole] = st[i];
+                    wpos[b] += whole;
+                    fill[b] = f - whole;  // windows beyond D retry next round
+                }
+                __syncwarp();
             }
         }
         if (!__syncthreads_or(pend != 0 || next < len)) break;
     }
     for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
-        const uint32_t f = fill[b];
-        if (f) {
-            uint64_t* dst = out + __ldg(my_base + b) + wpos[b];
+        const uint32_t f = min(fill[b], D);
+        const uint32_t whole = f & ~3u;
+        uint64_t* dst = out + __ldg(my_base + b) + wpos[b];
+        for (uint32_t i = 0; i < whole; ++i) dst[i] = s_stage[(size_t)b * D + i];
+        if (f > whole) {
             const uint64_t pad = pad_hash((group << a2) | b, a1 + a2);
-            for (uint32_t i = 0; i < 4; ++i) dst[i] = i < f ? (uint64_t)s_stage[(size_t)b * 4 + i] : pad;
+            for (uint32_t i = whole; i < whole + 4; ++i) dst[i] = i < f ? (uint64_t)s_stage[(size_t)b * D + i] : pad;
         }
     }
 }
@@ -427,7 +459,7 @@ __global__ void k_fb_claim(FallbackArgs F, int bt) {
     uint64_t cand = 0, claimed = 0;
     for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride) {
         const uint64_t h = d[i];
-        if ((uint32_t)(h >> (64 - F.part_bits)) != F.part) continue;  // run padding
+        if ((uint32_t)(h >> (64 - F.part_bits)) != F.part || h < F.h_lo) continue;  // padding, done
         const uint64_t pat = bloom_pattern(mixer64(h), F.n_hashes);
         const unsigned long long old = atomicOr(F.bloom + (h >> F.bloom_shift), (unsigned long long)pat);
         if (F.all_candidates || (old & pat) == pat) {
@@ -452,7 +484,7 @@ __global__ void k_fb_recount(FallbackArgs F, int bt) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride) {
         const uint64_t h = d[i];
-        if ((uint32_t)(h >> (64 - F.part_bits)) != F.part) continue;
+        if ((uint32_t)(h >> (64 - F.part_bits)) != F.part || h < F.h_lo) continue;
         table_count(F.table, F.table_mask, (h & low_mask) & F.table_mask, (h & low_mask) + 1ull, smp, F.ctr);
     }
 }
@@ -506,7 +538,9 @@ __global__ void k_prefix_hist(const uint64_t* __restrict__ keys, DevCounters* __
 }  // namespace
 
 size_t bucket_pass_smem(int a) { return sizeof(uint32_t) << a; }
-size_t staged_scatter_smem(int a) { return (4 * sizeof(uint64_t) + 2 * sizeof(uint32_t)) << a; }
+size_t staged_scatter_smem(int a) {
+    return ((size_t)stage_depth(a) * sizeof(uint64_t) + 2 * sizeof(uint32_t)) << a;
+}
 
 void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                          int n_ctas, const PassParams& p, int a, uint32_t* counts, cudaStream_t st) {

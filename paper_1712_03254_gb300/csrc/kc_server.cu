@@ -40,7 +40,7 @@ struct Job {
     kc_job_spec spec{};
     uint64_t footprint = 0;
     kc_handle h = nullptr;
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_admit, t_ingested, t_fstart, t_done;
     kc_status status = KC_OK;
     std::string error;
     bool done = false;
@@ -66,6 +66,7 @@ struct kc_server_ctx {
     // statistics
     std::vector<double> latencies_ms;
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_jobs = 0;
+    double sum_stage_ms[4] = {};  // queue, ingest, batch wait, finalize + copy-out of completed jobs
     Clock::time_point t_first, t_last;
     bool any = false;
 };
@@ -83,6 +84,10 @@ uint64_t footprint(const kc_job_spec& s) {
         reads += s.n_reads[i];
     }
     return s.bloom_bits / 8 + bases * 50 + reads * 8 + (8ull << 20);
+}
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
 void fail_job(kc_server_ctx* S, const std::shared_ptr<Job>& j, kc_status st) {
@@ -112,6 +117,7 @@ void ingest_loop(kc_server_ctx* S) {
             S->in_use += j->footprint;  // admitted
             S->peak = std::max(S->peak, S->in_use);
         }
+        j->t_admit = Clock::now();
         const kc_job_spec& s = j->spec;
         kc_config cfg;
         kc_default_config(&cfg);
@@ -126,6 +132,7 @@ void ingest_loop(kc_server_ctx* S) {
             S->cv_ingest.notify_all();
             continue;
         }
+        j->t_ingested = Clock::now();
         S->ingested.push_back(j);
         S->cv_final.notify_all();
     }
@@ -145,7 +152,11 @@ void finalize_loop(kc_server_ctx* S) {
             }
         }
         std::vector<kc_handle> hs;
-        for (auto& j : run) hs.push_back(j->h);
+        const Clock::time_point t_start = Clock::now();
+        for (auto& j : run) {
+            hs.push_back(j->h);
+            j->t_fstart = t_start;
+        }
         kc_status st = kc_batch_finalize(S->batch, hs.data(), (int)hs.size());
         for (auto& j : run) {
             kc_status js = st;
@@ -167,7 +178,11 @@ void finalize_loop(kc_server_ctx* S) {
             j->done = true;
             S->in_use -= j->footprint;
             S->completed += 1;
-            S->latencies_ms.push_back(std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count());
+            S->latencies_ms.push_back(ms_between(j->t_submit, j->t_done));
+            S->sum_stage_ms[0] += ms_between(j->t_submit, j->t_admit);
+            S->sum_stage_ms[1] += ms_between(j->t_admit, j->t_ingested);
+            S->sum_stage_ms[2] += ms_between(j->t_ingested, j->t_fstart);
+            S->sum_stage_ms[3] += ms_between(j->t_fstart, j->t_done);
             S->t_last = j->t_done;
         }
         {
@@ -301,6 +316,11 @@ kc_status kc_server_stats_get(kc_server S, kc_server_stats* out) {
     out->jobs_per_s = span > 0 ? (double)S->completed / span : 0.0;
     out->peak_bytes = S->peak;
     out->budget_bytes = S->budget;
+    const double nc = S->completed ? (double)S->completed : 1.0;
+    out->mean_queue_ms = S->sum_stage_ms[0] / nc;
+    out->mean_ingest_ms = S->sum_stage_ms[1] / nc;
+    out->mean_batch_wait_ms = S->sum_stage_ms[2] / nc;
+    out->mean_finalize_ms = S->sum_stage_ms[3] / nc;
     return KC_OK;
 }
 

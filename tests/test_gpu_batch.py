@@ -40,8 +40,8 @@ def _jobs(seed, n):
     return jobs
 
 
-def _counter(w):
-    c = kc.KmerCounter(w.k, len(w.samples), w.bloom_bits, w.n_hashes, w.min_count, strategy="partitioned")
+def _counter(w, **kw):
+    c = kc.KmerCounter(w.k, len(w.samples), w.bloom_bits, w.n_hashes, w.min_count, strategy="partitioned", **kw)
     for s, rs in enumerate(w.samples):
         c.add_readset(s, rs)
     return c
@@ -95,6 +95,24 @@ def test_uniform_bits_per_key_batch(oracle_mod):
     kc.KcBatch().finalize(counters)
     for c, w in zip(counters, jobs):
         _check(c, oracle_mod.count(w))
+
+
+def test_batch_mixes_split_fallback_and_plain_jobs(oracle_mod):
+    """1024-slot tables and few partitions: some jobs' partitions are counted
+    as sub-ranges (each job learning its own split level), one job falls back
+    to global tables, small jobs need neither; one launch serves them all."""
+    jobs = _jobs(31, 6)
+    # filters of 2^18, 2^18, 2^22, 2^18, 2^22, 2^22 bits (slices of at most 2^13 words)
+    kws = [dict(part_bits=1, smem_table_log2=10), dict(part_bits=2, smem_table_log2=10),
+           dict(part_bits=3, smem_table_log2=10, split_max=-1), dict(part_bits=3, smem_table_log2=11),
+           dict(), dict(part_bits=3, smem_table_log2=10, split_max=2)]
+    counters = [_counter(w, **kw) for w, kw in zip(jobs, kws)]
+    kc.KcBatch().finalize(counters)
+    for c, w in zip(counters, jobs):
+        _check(c, oracle_mod.count(w))
+    st = [c.stats() for c in counters]
+    assert sum(x["split_partitions"] for x in st) > 0
+    assert st[2]["split_partitions"] == 0
 
 
 def test_batch_rejects_bad_lists():

@@ -209,19 +209,95 @@ def test_errors_are_reported_not_faulted(oracle_mod):
 
 
 def test_partition_fallback_matches(oracle_mod):
-    """Two partitions with 1024-slot shared-memory tables cannot hold tiny's
-    candidates: every partition takes the global-memory fallback."""
+    """With splitting switched off, two partitions with 1024-slot shared-memory
+    tables cannot hold tiny's candidates: every partition takes the
+    global-memory fallback."""
     w = synth.tiny(scale=0.5)
     w.bloom_bits = 1 << 20  # 2 partitions of 8192 filter words
     o = oracle_mod.count(w)
-    c = gpu_count(w, strategy="partitioned", part_bits=1, smem_table_log2=10)
+    c = gpu_count(w, strategy="partitioned", part_bits=1, smem_table_log2=10, split_max=-1)
     st = c.stats()
-    assert st["fallback_partitions"] == 2
+    assert st["fallback_partitions"] == 2 and st["split_partitions"] == 0
     assert_same_result(c, o)
     assert_same_bloom(c, o)
     # sixteen partitions of about 6,100 candidates each, 4096-slot tables
-    c = gpu_count(w, strategy="partitioned", part_bits=4, smem_table_log2=12)
+    c = gpu_count(w, strategy="partitioned", part_bits=4, smem_table_log2=12, split_max=-1)
     assert c.stats()["fallback_partitions"] == 16
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+def test_overflowing_partitions_split(oracle_mod):
+    """Sixteen partitions of about 6,100 candidates, 4096-slot tables: each is
+    counted as sub-ranges of its filter slice in shared memory, none falls
+    back, and the result and filter are the oracle's."""
+    w = synth.tiny(scale=0.5)
+    w.bloom_bits = 1 << 20
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", part_bits=4, smem_table_log2=12)
+    st = c.stats()
+    assert st["fallback_partitions"] == 0
+    assert st["split_partitions"] == 16 and st["split_level"] >= 1
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    # two partitions of about 49,000 candidates, 1024-slot tables: down to 64 sub-ranges
+    c = gpu_count(w, strategy="partitioned", part_bits=1, smem_table_log2=10)
+    st = c.stats()
+    assert st["split_partitions"] + st["fallback_partitions"] == 2 and st["split_level"] >= 5
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+@pytest.mark.parametrize("split_max", [1, 2, 3])
+def test_split_then_fallback_for_the_rest(oracle_mod, split_max):
+    """Splitting capped below what the candidates need: the sub-ranges that
+    fit are finished in shared memory, the rest of the partition (from its
+    first unfinished sub-range on) goes to the global table; nothing is
+    counted twice."""
+    w = synth.tiny(scale=0.5)
+    w.bloom_bits = 1 << 20
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", part_bits=1, smem_table_log2=13, split_max=split_max)
+    st = c.stats()
+    assert st["fallback_partitions"] + st["split_partitions"] == 2
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+def test_finished_sub_range_then_fallback(oracle_mod):
+    """Keys chosen by hash: partition 0 holds 200 keys in its first half-slice
+    and 10,000 in its second, more than an 8192-slot table takes.  With one
+    split level the first half is finished in shared memory and only the
+    second half goes to the global table."""
+    rng = random.Random(77)
+    lo, hi = [], []
+    while len(lo) < 200 or len(hi) < 10_000:
+        s = "".join(rng.choice("ACGT") for _ in range(31))
+        h = oracle_mod.mixer64(oracle_mod.canonical(s))
+        if h >> 63:  # partition 1 stays empty
+            continue
+        side, cap = (hi, 10_000) if (h >> 62) & 1 else (lo, 200)
+        if len(side) < cap:
+            side.append(s)
+    reads = lo + hi + lo + hi  # every key twice
+    w = synth.Workload("split_half", [synth.ReadSet.from_strings(reads)], k=31, bloom_bits=1 << 20, n_hashes=4,
+                       min_count=2)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, table_slots=0, strategy="partitioned", part_bits=1, smem_table_log2=13, split_max=1)
+    st = c.stats()
+    assert st["fallback_partitions"] == 1
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    assert c.result_size() == 10_200
+
+
+def test_split_two_samples(oracle_mod):
+    """Per-sample counts of split partitions (tumour/normal pair)."""
+    w = synth.paired(scale=0.002)
+    w.bloom_bits = 1 << 22
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", part_bits=3, smem_table_log2=10, batches=2)  # slices of 2^13 words
+    assert c.stats()["split_partitions"] > 0
     assert_same_result(c, o)
     assert_same_bloom(c, o)
 
