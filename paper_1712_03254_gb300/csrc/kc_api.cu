@@ -285,7 +285,7 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
     if (h->l1_bits != h->part_bits) mode = 4;  // two levels: staged scatter only
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    if (mode >= 3 && kc::staged_scatter_smem(a) > (size_t)max_optin) mode = 2;
+    if (mode >= 3 && std::max(kc::staged_scatter_smem(a), kc::staged_seg_smem(a)) > (size_t)max_optin) mode = 2;
     const int max_ctas = h->grid.sm_count * (h->cfg.ctas_per_sm ? (int)h->cfg.ctas_per_sm : 1);
     const uint64_t upc = std::max<uint64_t>(1, (b.n_units + max_ctas - 1) / max_ctas);
     const int n_ctas = (int)((b.n_units + upc - 1) / upc);

@@ -110,6 +110,9 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
         const int S = J.n_samples;
         const int a = J.part_bits;
         const uint64_t low_mask = (1ull << (64 - a)) - 1ull;
+        // the job's fields the inner loops use, in registers
+        const int bloom_shift = J.bloom_shift;
+        const bool all_cand = J.all_candidates != 0;
         unsigned long long* sb = s_mem;
         unsigned long long* sk = s_mem + n_sw;
         uint32_t* sc = reinterpret_cast<uint32_t*>(s_mem + n_sw + T);
@@ -148,11 +151,11 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
                     const uint64_t h = __ldcg(d + i);  // read again by the recount: keep in L2
                     if ((uint32_t)(h >> (64 - a)) != part) continue;  // run padding
                     if (sl && ((uint32_t)(h >> sub_shift) & smask) != sub) continue;
-                    const uint32_t w = (uint32_t)(h >> J.bloom_shift) & (n_sw - 1);
+                    const uint32_t w = (uint32_t)(h >> bloom_shift) & (n_sw - 1);
                     const uint64_t g = mixer64(h);
                     const uint64_t pat = NH > 0 ? bloom_pattern_n<(NH > 0 ? NH : 1)>(g) : bloom_pattern_rt(g, J.n_hashes);
                     const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
-                    if (J.all_candidates || (old & pat) == pat) {
+                    if (all_cand || (old & pat) == pat) {
                         ++c_try;
                         const int r = smem_claim(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
                         if (r < 0) {

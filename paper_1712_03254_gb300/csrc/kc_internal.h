@@ -93,6 +93,7 @@ void launch_bucket_offsets(const uint32_t* counts, int n_ctas, int a, int pad4, 
                            cudaStream_t st);
 void launch_bucket_base(uint64_t* rel, const uint64_t* starts, int n_ctas, int a, cudaStream_t st);
 size_t staged_scatter_smem(int a);
+size_t staged_seg_smem(int a);
 // A run of hashes handled by one CTA: src + off .. src + off + len; group =
 // the level-1 group the run belongs to (0 with a single level).
 struct SegDesc {

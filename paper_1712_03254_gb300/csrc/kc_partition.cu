@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(kStagedThreads) k_bucket_scatter_staged(
 // contiguous segment per CTA of a linear array (warp-aggregated positions, so
 // the stores are coalesced), and the CTA's histogram over partitions goes to
 // counts[cta][*].  seg[cta] = {segment start, its length}.
-__global__ void __launch_bounds__(512) k_extract_count(const uint64_t* __restrict__ pw,
+constexpr int kExtractThreads = 1024;
+
+__global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_t* __restrict__ pw,
                                                        const uint64_t* __restrict__ vw, uint64_t n_units,
                                                        uint64_t units_per_cta, PassParams p, int a,
                                                        uint32_t* __restrict__ counts,
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(512) k_extract_count(const uint64_t* __restric
     extern __shared__ uint32_t s_cnt[];
     __shared__ unsigned long long s_base;
     __shared__ unsigned s_pos;
-    __shared__ unsigned long long s_warp_tot[16];
+    __shared__ unsigned long long s_warp_tot[kExtractThreads / 32];
     const uint32_t P = 1u << a;
     const uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
     const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
@@ -238,7 +240,14 @@ __global__ void __launch_bounds__(512) k_extract_count(const uint64_t* __restric
     for (uint64_t g = lo + (uint64_t)wid * 32; g < hi; g += (uint64_t)nwarps * 32) {
         const UnitWords uw = load_unit(pw, vw, g + lane, hi, lane);
         uint64_t vm = uw.v;
-        const int n_iter = __reduce_max_sync(kFull, (unsigned)__popcll(vm));
+        const unsigned nv = (unsigned)__popcll(vm);
+        const int n_iter = __reduce_max_sync(kFull, nv);
+        // the warp's windows of these 32 units get consecutive positions,
+        // claimed once; each round's stores are coalesced
+        const unsigned tot = __reduce_add_sync(kFull, nv);
+        unsigned wb = 0;
+        if (lane == 0) wb = atomicAdd(&s_pos, tot);
+        wb = __shfl_sync(kFull, wb, 0);
         for (int it = 0; it < n_iter; ++it) {
             const bool has = vm != 0;
             uint64_t h = 0;
@@ -249,13 +258,9 @@ __global__ void __launch_bounds__(512) k_extract_count(const uint64_t* __restric
                 h = mixer64(key);
                 atomicAdd(&s_cnt[(uint32_t)(h >> (64 - a))], 1u);
             }
-            // consecutive positions for the warp's windows of this round: the
-            // stores of a round are coalesced
             const unsigned ballot = __ballot_sync(kFull, has);
-            unsigned wb = 0;
-            if (lane == 0) wb = atomicAdd(&s_pos, (unsigned)__popc(ballot));
-            wb = __shfl_sync(kFull, wb, 0);
             if (has) lin[base + wb + __popc(ballot & lt)] = h;
+            wb += __popc(ballot);
         }
     }
     __syncthreads();
@@ -280,31 +285,47 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
     const uint32_t P = 1u << a2;
     const uint32_t D = stage_depth(a2);  // entries staged per bucket, a multiple of 4
     uint32_t* fill = reinterpret_cast<uint32_t*>(s_stage + (size_t)D * P);
-    uint32_t* wpos = fill + P;
+    uint64_t* cursor = reinterpret_cast<uint64_t*>(fill + P);  // next output position of each run
+    const uint64_t* my_base = base + (uint64_t)blockIdx.x * P;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
         fill[i] = 0;
-        wpos[i] = 0;
+        cursor[i] = __ldg(my_base + i);
     }
     __syncthreads();
     const SegDesc sd = segs[blockIdx.x];
     const uint64_t s0 = sd.off, len = sd.len;
     const uint32_t group = (uint32_t)sd.group;
     const int shift = 64 - a1 - a2;
-    const uint64_t* my_base = base + (uint64_t)blockIdx.x * P;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    // thread t owns elements t, t + nt, t + 2 nt, ... of the segment, in order
+    // thread t owns elements t, t + nt, t + 2 nt, ... of the segment, in order;
+    // the next rows are always in flight while the current ones are staged
     uint64_t next = threadIdx.x;
-    uint64_t ph[kLinPerThread];
+    uint64_t ph[kLinPerThread], nx[kLinPerThread];
     uint32_t pend = 0;  // bit e: ph[e] still to be staged
+    uint32_t nval = 0;  // bit e: nx[e] loaded, not yet taken
+#pragma unroll
+    for (int e = 0; e < kLinPerThread; ++e) {
+        if (next < len) {
+            nx[e] = __ldcg(src + s0 + next);
+            nval |= 1u << e;
+        }
+        next += blockDim.x;
+    }
     for (;;) {
-        // Warp-uniform: a warp loads its next rows only when none of its lanes
+        // Warp-uniform: a warp takes its next rows only when none of its lanes
         // still holds a pending hash, so every load stays coalesced.
         if (__all_sync(kFull, pend == 0)) {
 #pragma unroll
             for (int e = 0; e < kLinPerThread; ++e) {
+                ph[e] = nx[e];
+                if (((nval >> e) & 1u) && (a1 == 0 || (uint32_t)(ph[e] >> (64 - a1)) == group)) pend |= 1u << e;
+            }
+            nval = 0;
+#pragma unroll
+            for (int e = 0; e < kLinPerThread; ++e) {
                 if (next < len) {
-                    ph[e] = __ldcg(src + s0 + next);
-                    if (a1 == 0 || (uint32_t)(ph[e] >> (64 - a1)) == group) pend |= 1u << e;
+                    nx[e] = __ldcg(src + s0 + next);
+                    nval |= 1u << e;
                 }
                 next += blockDim.x;
             }
@@ -327,10 +348,10 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
             for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
                 if (fill[b] >= 4) {
                     const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
-                    ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + __ldg(my_base + b) + wpos[b]);
+                    ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + cursor[b]);
                     dst[0] = sp[0];
                     dst[1] = sp[1];
-                    wpos[b] += 4;
+                    cursor[b] += 4;
                     fill[b] = 0;
                 }
             }
@@ -341,24 +362,24 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
                 const uint32_t f = min(fill[b], D);
                 const uint32_t whole = f & ~3u;
                 unsigned long long* st = s_stage + (size_t)b * D;
-                uint64_t* dst = out + __ldg(my_base + b) + wpos[b];
+                uint64_t* dst = out + cursor[b];
                 for (uint32_t i = lane * 2; i < whole; i += 64)
                     *reinterpret_cast<ulonglong2*>(dst + i) = *reinterpret_cast<const ulonglong2*>(st + i);
                 __syncwarp();
                 if (lane == 0) {
                     for (uint32_t i = whole; i < f; ++i) st[i - whole] = st[i];
-                    wpos[b] += whole;
+                    cursor[b] += whole;
                     fill[b] = f - whole;  // windows beyond D retry next round
                 }
                 __syncwarp();
             }
         }
-        if (!__syncthreads_or(pend != 0 || next < len)) break;
+        if (!__syncthreads_or(pend != 0 || nval != 0)) break;
     }
     for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
         const uint32_t f = min(fill[b], D);
         const uint32_t whole = f & ~3u;
-        uint64_t* dst = out + __ldg(my_base + b) + wpos[b];
+        uint64_t* dst = out + cursor[b];
         for (uint32_t i = 0; i < whole; ++i) dst[i] = s_stage[(size_t)b * D + i];
         if (f > whole) {
             const uint64_t pad = pad_hash((group << a2) | b, a1 + a2);
@@ -555,13 +576,18 @@ void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_uni
                           uint64_t* lin, cudaStream_t st) {
     const size_t smem = bucket_pass_smem(a);
     cudaFuncSetAttribute(k_extract_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_extract_count<<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
+    k_extract_count<<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
                                                reinterpret_cast<unsigned long long*>(g_cursor), seg, lin);
+}
+
+// stage, fill count and 64-bit output cursor per bucket
+size_t staged_seg_smem(int a) {
+    return ((size_t)stage_depth(a) * sizeof(uint64_t) + sizeof(uint32_t) + sizeof(uint64_t)) << a;
 }
 
 void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,
                                const uint64_t* base, uint64_t* out, cudaStream_t st) {
-    const size_t smem = staged_scatter_smem(a2);
+    const size_t smem = staged_seg_smem(a2);
     cudaFuncSetAttribute(k_scatter_staged_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_scatter_staged_seg<<<n_segs, kLinThreads, smem, st>>>(src, segs, a1, a2, base, out);
 }
