@@ -147,8 +147,11 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
             for (int bt = 0; bt < J.n_batches && !stop; ++bt) {
                 const uint64_t* __restrict__ d = J.data[bt];
                 const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
+                // each thread's next hash is in flight while it handles the current one
+                uint64_t hn = lo + threadIdx.x < hi ? __ldcg(d + lo + threadIdx.x) : 0ull;
                 for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                    const uint64_t h = __ldcg(d + i);  // read again by the recount: keep in L2
+                    const uint64_t h = hn;
+                    if (i + blockDim.x < hi) hn = __ldcg(d + i + blockDim.x);  // read again by the recount: keep in L2
                     if ((uint32_t)(h >> (64 - a)) != part) continue;  // run padding
                     if (sl && ((uint32_t)(h >> sub_shift) & smask) != sub) continue;
                     const uint32_t w = (uint32_t)(h >> bloom_shift) & (n_sw - 1);
@@ -192,8 +195,10 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
                 const uint64_t* __restrict__ d = J.data[bt];
                 const int smp = J.samples[bt];
                 const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
+                uint64_t hn = lo + threadIdx.x < hi ? __ldcg(d + lo + threadIdx.x) : 0ull;
                 for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                    const uint64_t h = sl ? __ldcg(d + i) : __ldcs(d + i);  // last use unless split
+                    const uint64_t h = hn;
+                    if (i + blockDim.x < hi) hn = sl ? __ldcg(d + i + blockDim.x) : __ldcs(d + i + blockDim.x);  // last use unless split
                     if ((uint32_t)(h >> (64 - a)) != part) continue;
                     if (sl && ((uint32_t)(h >> sub_shift) & smask) != sub) continue;
                     const int s = smem_find(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
