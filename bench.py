@@ -7,7 +7,10 @@ with 0.5 % substitutions and 0.05 % N; k = 31, a 2^30-bit filter with 4 bits
 per key, a 2^24-slot table, min_count 2.  The step is reset (filter and table
 zeroed), ingest, pass 1 (filter + candidate claims), finalize (exact recount,
 compaction, sort) and dump.  The unit of work is one valid window (an N-free
-k-window inside one read).
+k-window inside one read).  Before the warm-up, kc_autotune picks the
+strategy and its knobs on the same device-resident reads (untimed; the
+choice and every trial are in the "tuning" field); --no-tune keeps the
+library defaults.
 
   value  device-resident inputs, CUDA events on the library's stream
   e2e    the same step through the C ABI from pinned host buffers, the host to
@@ -17,6 +20,12 @@ k-window inside one read).
 With N ranks (torchrun) every rank counts its own job (independent read set),
 no collective is on the data path, and value = all ranks' windows / the
 slowest rank's time ("weak" scaling).
+
+The "served" field replays a Poisson stream of 64 jobs of mixed size (1-20
+Mbp genomes, 10^4-2x10^5 reads, k 25 or 31, filters of 8 bits per expected
+distinct k-mer) through one-at-a-time plain jobs and through the
+continuous-batching server, at 0.7 and 0.9 of the plain capacity and all at
+once; latencies count from each job's scheduled arrival.
 
 --impl reference times the CPU oracle (single thread, as it stands) on a
 bounded sample of the same workload.
@@ -205,7 +214,7 @@ def ncu_traffic(kernel: str):
 def roofline_of(st, phases, rs, w):
     """Roofline entry for the phase that takes the most device time.
 
-    Algorithmic bytes are compulsory traffic only (measurement):
+    Algorithmic bytes are compulsory traffic only:
       reads      2 bits (packed base) + 1 bit (valid-window bit) per base
       direct     pass1: reads + filter read and written once + 32 B per claimed
                  key; pass2: reads + 32 B per claimed key (slot read, counts
@@ -296,10 +305,23 @@ def run_kc(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
 
+    # autotune on this job's own device-resident reads (outside the timed
+    # region) unless knobs were given on the command line
+    tuning = None
+    knobs = dict(strategy=args.strategy, scatter_mode=args.scatter_mode, ctas_per_sm=args.ctas_per_sm,
+                 part_bits=args.part_bits, smem_table_log2=0)
+    if not args.no_tune and args.strategy == "auto" and not (args.scatter_mode or args.ctas_per_sm or args.part_bits):
+        t0 = time.perf_counter()
+        best, trials = kc.autotune(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, [(0, d_packed, d_off, d_mask)],
+                                   reps=3)
+        knobs = dict(strategy=best["strategy"], scatter_mode=best["scatter_mode"], ctas_per_sm=best["ctas_per_sm"],
+                     part_bits=best["part_bits"], smem_table_log2=best["smem_table_log2"])
+        short = lambda cfg: {k: v for k, v in cfg.items() if k in ("strategy", "part_bits", "smem_table_log2",
+                                                                    "ctas_per_sm")}
+        tuning = {"best": short(best), "seconds": round(time.perf_counter() - t0, 2),
+                  "trials": [[short(cfg), round(ms, 3)] for cfg, ms in trials]}
     c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots, timing=True,
-                       strategy=args.strategy, scatter_mode=args.scatter_mode, ctas_per_sm=args.ctas_per_sm,
-                       part_bits=args.part_bits,
-                       stream=stream)
+                       stream=stream, **knobs)
 
     # size result buffers with one untimed job
     c.add_reads(0, d_packed, d_off, d_mask)
@@ -397,6 +419,7 @@ def run_kc(args):
                        "l2": "256 MiB written between timed steps (outside the step events)",
                        "parallelism": f"{world} independent jobs, one per GPU" if world > 1 else "1 GPU"},
             "strategy": strategy,
+            "tuning": tuning,
             "phase_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -595,6 +618,7 @@ def main(argv=None):
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--part-bits", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="library defaults instead of kc_autotune's choice")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -214,6 +214,11 @@ typedef struct kc_server_stats {
 
 /* Create a server on the current device (max_batch >= 1). */
 kc_status kc_server_create(uint64_t device_budget_bytes, int max_batch, kc_server* out);
+/* As kc_server_create; flags KC_SERVER_TUNED: every job takes the partitioned
+ * knobs of its class from the tuning cache (kc_tune_lookup) when there is an
+ * entry, the defaults otherwise. */
+#define KC_SERVER_TUNED 1u
+kc_status kc_server_create_ex(uint64_t device_budget_bytes, int max_batch, uint32_t flags, kc_server* out);
 /* Queue a job; *job_id identifies it.  KC_ERR_ARG for device pointers. */
 kc_status kc_server_submit(kc_server s, const kc_job_spec* spec, uint64_t* job_id);
 /* Wait for a job (timeout_s < 0: no limit; KC_ERR_TIMEOUT when it runs out);
@@ -229,6 +234,64 @@ void kc_server_destroy(kc_server s);
 
 /* Fill *cfg with the defaults (struct_size set). */
 void kc_default_config(kc_config* cfg);
+
+/*
+ * Autotuning.  The paper sizes its work units by hand and notes that the
+ * chunk sizes have to be chosen with care (Section III-B, the Orchestrator's
+ * cycles); here the library measures instead.  kc_autotune runs the caller's
+ * own job (the same reads, k, filter, hashes, min_count) once per candidate
+ * configuration and keeps the fastest:
+ *   PARTITIONED  partition bits (filter slices of 2^13 down to 2^8 words),
+ *                then the shared-memory table size (2^10..2^13 slots), then
+ *                extraction CTAs per SM (the reads each CTA takes: 1, 2, 3)
+ *   DIRECT       grid CTAs per SM (4, 8, 16)
+ * Each candidate is timed as the median, over `reps` runs after one warm-up
+ * run, of the CUDA-event time from before kc_add_reads to after kc_finalize
+ * on the tuner's stream (allocation in kc_create_ex is outside the timing).
+ * Block sizes are fixed per kernel and are not searched.
+ *
+ *   inputs    n_inputs read batches, each added with kc_add_reads (host or
+ *             device pointers, as there; device inputs time the counting alone)
+ *   best      the fastest configuration
+ *   trials    if not NULL, up to max_trials timed candidates in the order
+ *             tried (ms < 0: the candidate was rejected or failed); *n_trials
+ *             receives the number written
+ *
+ * The best configuration is also stored in a process-wide cache under the
+ * job's class (k, n_samples, bloom_bits, n_hashes, min_count > 1, the bases
+ * rounded up to a power of two, the device's SM count), where kc_tune_lookup
+ * finds it; kc_tune_cache_save / kc_tune_cache_load keep the cache in a text
+ * file, one class per line.
+ */
+typedef struct kc_tune_input {
+    int sample;
+    const uint64_t* packed_reads;
+    const uint64_t* offsets;
+    const uint64_t* n_mask;
+    uint64_t n_reads;
+} kc_tune_input;
+
+typedef struct kc_tune_trial {
+    kc_config config;
+    double ms;
+} kc_tune_trial;
+
+kc_status kc_autotune(int k, int n_samples, uint64_t bloom_bits, int n_hashes, uint32_t min_count,
+                      const kc_tune_input* inputs, int n_inputs, int reps, kc_config* best,
+                      kc_tune_trial* trials, int max_trials, int* n_trials);
+
+/* The cached configuration of the job class of (k, n_samples, bloom_bits,
+ * n_hashes, min_count, n_bases) on the current device: *found = 1 and *out
+ * filled, or *found = 0 and *out left alone. */
+kc_status kc_tune_lookup(int k, int n_samples, uint64_t bloom_bits, int n_hashes, uint32_t min_count,
+                         uint64_t n_bases, kc_config* out, int* found);
+
+/* Write the cache to path (replacing the file) / merge the entries of path
+ * into the cache (KC_ERR_ARG for a malformed file, which changes nothing). */
+kc_status kc_tune_cache_save(const char* path);
+kc_status kc_tune_cache_load(const char* path);
+/* Drop every cached entry. */
+void kc_tune_cache_clear(void);
 
 /*
  * Create a counting job on the current CUDA device.

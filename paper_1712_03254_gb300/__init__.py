@@ -17,7 +17,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["KmerCounter", "KcBatch", "KcServer", "KcError", "pack_ascii", "lib", "build", "Config", "Stats"]
+__all__ = ["KmerCounter", "KcBatch", "KcServer", "KcError", "pack_ascii", "lib", "build", "Config", "Stats",
+           "autotune", "tune_lookup", "tune_cache_save", "tune_cache_load", "tune_cache_clear"]
 
 _lock = threading.Lock()
 _lib = None
@@ -53,6 +54,15 @@ class Stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class TuneInput(ctypes.Structure):
+    _fields_ = [("sample", ctypes.c_int), ("packed_reads", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("n_mask", ctypes.c_void_p), ("n_reads", ctypes.c_uint64)]
+
+
+class TuneTrial(ctypes.Structure):
+    _fields_ = [("config", Config), ("ms", ctypes.c_double)]
 
 
 class JobSpec(ctypes.Structure):
@@ -130,6 +140,19 @@ def lib():
             L.kc_server_stats_get.restype = st
             L.kc_server_destroy.argtypes = [p]
             L.kc_server_destroy.restype = None
+            L.kc_server_create_ex.argtypes = [u64, i, u32, ctypes.POINTER(p)]
+            L.kc_server_create_ex.restype = st
+            L.kc_autotune.argtypes = [i, i, u64, i, u32, ctypes.POINTER(TuneInput), i, i, ctypes.POINTER(Config),
+                                      ctypes.POINTER(TuneTrial), i, ctypes.POINTER(i)]
+            L.kc_autotune.restype = st
+            L.kc_tune_lookup.argtypes = [i, i, u64, i, u32, u64, ctypes.POINTER(Config), ctypes.POINTER(i)]
+            L.kc_tune_lookup.restype = st
+            L.kc_tune_cache_save.argtypes = [ctypes.c_char_p]
+            L.kc_tune_cache_save.restype = st
+            L.kc_tune_cache_load.argtypes = [ctypes.c_char_p]
+            L.kc_tune_cache_load.restype = st
+            L.kc_tune_cache_clear.argtypes = []
+            L.kc_tune_cache_clear.restype = None
             _lib = L
     return _lib
 
@@ -166,6 +189,8 @@ def pack_ascii(ascii: np.ndarray):
 
 
 SPLIT_NONE = 0xFFFFFFFF  # kc_config.split_max: overflowing partitions go straight to the global table
+STRATEGY_NAMES = {0: "auto", 1: "direct", 2: "partitioned"}
+SERVER_TUNED = 1  # kc_server_create_ex flag
 
 
 class KmerCounter:
@@ -174,10 +199,22 @@ class KmerCounter:
     def __init__(self, k: int, n_samples: int, bloom_bits: int, n_hashes: int = 4, min_count: int = 2,
                  table_slots: int = 0, part_bits: int = 0, spill: bool = False, ctas_per_sm: int = 0,
                  timing: bool = False, strategy: str = "auto", smem_table_log2: int = 0, scatter_mode: int = 0,
-                 split_max: int = 0, stream=None):
+                 split_max: int = 0, tune_bases: int = 0, stream=None):
         L = lib()
         cfg = Config()
         L.kc_default_config(ctypes.byref(cfg))
+        if tune_bases:  # the tuning cache's knobs for this job class, when it has an entry
+            found = ctypes.c_int()
+            _check(L.kc_tune_lookup(k, n_samples, bloom_bits, n_hashes, min_count, tune_bases, ctypes.byref(cfg),
+                                    ctypes.byref(found)), "kc_tune_lookup")
+            if found.value:
+                table_slots = table_slots or cfg.table_slots
+                part_bits = part_bits or cfg.part_bits
+                ctas_per_sm = ctas_per_sm or cfg.ctas_per_sm
+                strategy = strategy if strategy != "auto" else STRATEGY_NAMES[cfg.strategy]
+                smem_table_log2 = smem_table_log2 or cfg.smem_table_log2
+                scatter_mode = scatter_mode or cfg.scatter_mode
+                split_max = split_max or (-1 if cfg.split_max == SPLIT_NONE else cfg.split_max)
         cfg.table_slots = table_slots
         cfg.part_bits = part_bits
         cfg.spill = 1 if spill else 0
@@ -282,13 +319,64 @@ class KcBatch:
         self.close()
 
 
+def config_dict(cfg: Config) -> dict:
+    return {"strategy": STRATEGY_NAMES[cfg.strategy], "part_bits": cfg.part_bits,
+            "smem_table_log2": cfg.smem_table_log2, "ctas_per_sm": cfg.ctas_per_sm,
+            "scatter_mode": cfg.scatter_mode, "split_max": cfg.split_max}
+
+
+def autotune(k: int, n_samples: int, bloom_bits: int, n_hashes: int, min_count: int, inputs, reps: int = 3,
+             max_trials: int = 64):
+    """kc_autotune: inputs = [(sample, packed, offsets, n_mask), ...] (numpy or torch, host or device).
+
+    Returns (best config dict, [(config dict, ms), ...] in the order tried); the best
+    configuration also goes into the process-wide tuning cache."""
+    L = lib()
+    arr = (TuneInput * max(1, len(inputs)))()
+    keep = []
+    for t, (sample, packed, offsets, mask) in enumerate(inputs):
+        if isinstance(offsets, np.ndarray):
+            offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        keep.append(offsets)
+        n = (offsets.numel() if hasattr(offsets, "numel") else len(offsets)) - 1
+        arr[t] = TuneInput(sample, _ptr(packed), _ptr(offsets), _ptr(mask), max(0, n))
+    best = Config()
+    trials = (TuneTrial * max_trials)()
+    n = ctypes.c_int()
+    _check(L.kc_autotune(k, n_samples, bloom_bits, n_hashes, min_count, arr, len(inputs), reps, ctypes.byref(best),
+                         trials, max_trials, ctypes.byref(n)), "kc_autotune")
+    return config_dict(best), [(config_dict(trials[i].config), trials[i].ms) for i in range(n.value)]
+
+
+def tune_lookup(k: int, n_samples: int, bloom_bits: int, n_hashes: int, min_count: int, n_bases: int):
+    """The tuning cache's configuration for this job class (dict), or None."""
+    cfg = Config()
+    found = ctypes.c_int()
+    _check(lib().kc_tune_lookup(k, n_samples, bloom_bits, n_hashes, min_count, n_bases, ctypes.byref(cfg),
+                                ctypes.byref(found)), "kc_tune_lookup")
+    return config_dict(cfg) if found.value else None
+
+
+def tune_cache_save(path: str):
+    _check(lib().kc_tune_cache_save(os.fsencode(path)), "kc_tune_cache_save")
+
+
+def tune_cache_load(path: str):
+    _check(lib().kc_tune_cache_load(os.fsencode(path)), "kc_tune_cache_load")
+
+
+def tune_cache_clear():
+    lib().kc_tune_cache_clear()
+
+
 class KcServer:
     """Continuous-batching job server (kc_server_*); inputs are packed host arrays."""
 
-    def __init__(self, device_budget_bytes: int, max_batch: int = 64):
+    def __init__(self, device_budget_bytes: int, max_batch: int = 64, tuned: bool = False):
         L = lib()
         h = ctypes.c_void_p()
-        _check(L.kc_server_create(device_budget_bytes, max_batch, ctypes.byref(h)), "kc_server_create")
+        _check(L.kc_server_create_ex(device_budget_bytes, max_batch, SERVER_TUNED if tuned else 0, ctypes.byref(h)),
+               "kc_server_create_ex")
         self._s = h
         self._L = L
         self._keep = {}  # job id -> host arrays that must outlive the job

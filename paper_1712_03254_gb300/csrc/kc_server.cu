@@ -53,6 +53,7 @@ struct Job {
 struct kc_server_ctx {
     uint64_t budget = 0;
     int max_batch = 64;
+    uint32_t flags = 0;
     std::mutex mu;
     std::condition_variable cv_ingest, cv_final, cv_done;
     std::deque<std::shared_ptr<Job>> pending;   // submitted, not admitted
@@ -121,6 +122,16 @@ void ingest_loop(kc_server_ctx* S) {
         const kc_job_spec& s = j->spec;
         kc_config cfg;
         kc_default_config(&cfg);
+        if (S->flags & KC_SERVER_TUNED) {
+            uint64_t bases = 0;
+            for (int i = 0; i < s.n_samples; ++i)
+                if (s.n_reads[i]) bases += s.offsets[i][s.n_reads[i]] - s.offsets[i][0];
+            kc_config tuned;
+            int found = 0;
+            if (kc_tune_lookup(s.k, s.n_samples, s.bloom_bits, s.n_hashes, s.min_count, bases, &tuned, &found) == KC_OK &&
+                found && tuned.strategy == KC_STRATEGY_PARTITIONED)
+                cfg = tuned;  // batched finalize needs the partitioned strategy
+        }
         cfg.strategy = KC_STRATEGY_PARTITIONED;
         kc_status st = kc_create_ex(s.k, s.n_samples, s.bloom_bits, s.n_hashes, s.min_count, &cfg, nullptr, &j->h);
         for (int i = 0; st == KC_OK && i < s.n_samples; ++i)
@@ -209,12 +220,17 @@ double percentile(std::vector<double> v, double q) {
 extern "C" {
 
 kc_status kc_server_create(uint64_t device_budget_bytes, int max_batch, kc_server* out) {
-    if (!out || device_budget_bytes == 0 || max_batch < 1) return KC_ERR_ARG;
+    return kc_server_create_ex(device_budget_bytes, max_batch, 0, out);
+}
+
+kc_status kc_server_create_ex(uint64_t device_budget_bytes, int max_batch, uint32_t flags, kc_server* out) {
+    if (!out || device_budget_bytes == 0 || max_batch < 1 || (flags & ~KC_SERVER_TUNED)) return KC_ERR_ARG;
     *out = nullptr;
     kc_server_ctx* S = new (std::nothrow) kc_server_ctx();
     if (!S) return KC_ERR_OOM_HOST;
     S->budget = device_budget_bytes;
     S->max_batch = max_batch;
+    S->flags = flags;
     cudaGetDevice(&S->device);
     kc_status st = kc_batch_create(nullptr, &S->batch);
     if (st != KC_OK) {
