@@ -189,40 +189,59 @@ def measured_hbm_peak():
 
 
 def _kernel_source_hash():
+    """Hash of every source of libkc: counters taken on other sources are not used."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1712_03254_gb300", "csrc")
-    for f in ("kc_device.cuh", "kc_kernels.cu", "kc_partition.cu"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+def ncu_kernel(kernel: str):
+    """Per-launch ncu counters of a kernel from the committed profile, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_kernels.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    e = d.get(kernel)
-    if not e or e.get("source_hash") != _kernel_source_hash():
+    if d.get("source_hash") != _kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return d.get("kernels", {}).get(kernel)
 
 
-def roofline_of(st, phases, rs, w):
-    """Roofline entry for the phase that takes the most device time.
+ISSUE_PER_SM_CYCLE = 4  # four warp schedulers per SM, one warp instruction each per cycle
 
-    Algorithmic bytes are compulsory traffic only:
+
+def issue_peak(sm_count: int):
+    """Warp instructions per second the SMs can issue at the maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        mhz = 2070.0
+    return sm_count * ISSUE_PER_SM_CYCLE * mhz * 1e6, mhz
+
+
+def roofline_of(st, phases, rs, w, sm_count):
+    """Roofline entry of the kernel that takes the most device time.
+
+    Partitioned strategy: the consumer k_consume_q (the largest single kernel;
+    the "pass2" phase events bracket exactly its one launch).  Direct strategy:
+    the larger of k_pass1 / k_pass2.  Algorithmic bytes are compulsory traffic:
       reads      2 bits (packed base) + 1 bit (valid-window bit) per base
       direct     pass1: reads + filter read and written once + 32 B per claimed
-                 key; pass2: reads + 32 B per claimed key (slot read, counts
-                 written)
-      partitioned bucketing (extraction + staged scatter): reads once + 8 B
-                 hash written per window into its partition (the linear array
-                 in between is implementation traffic); consumer: 8 B hash read
-                 per window + filter written once + 16 B per result key
+                 key; pass2: reads + 32 B per claimed key
+      consumer   8 B hash read per window + filter written once + 16 B per
+                 result key
+    When the committed ncu counters match the current sources, the kernel's
+    DRAM traffic and instruction count come from them; the kernel then reports
+    against the SM issue limit ("alu": warp instructions issued per second
+    over 152 SMs x 4 schedulers x the maximum SM clock), with the HBM figures
+    beside it.  Otherwise it reports against HBM bandwidth alone.
     """
     import statistics as _st
 
@@ -233,17 +252,27 @@ def roofline_of(st, phases, rs, w):
     if st["strategy"] == 1:
         table = {"pass1": ("k_pass1", read_bytes + 2 * bloom_bytes + 32 * st["table_keys"]),
                  "pass2": ("k_pass2", read_bytes + 32 * st["table_keys"])}
+        phase = max(table, key=lambda k: mean[k])
     else:
-        table = {"pass1": ("k_extract_count + k_scatter_staged_lin (bucketing)", read_bytes + 8 * W),
-                 "pass2": ("k_part_consume", 8 * W + bloom_bytes + 16 * st["result_keys"])}
-    phase = max(table, key=lambda k: mean[k])
+        table = {"pass2": ("k_consume_q", 8 * W + bloom_bytes + 16 * st["result_keys"])}
+        phase = "pass2"
     kernel, algo = table[phase]
     ms = mean[phase]
     peak, peak_kind = measured_hbm_peak()
-    achieved = algo / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1), "peak": peak,
-            "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": ncu_traffic(kernel), "algorithmic_bytes": int(algo), "ms_per_launch": round(ms, 4)}
+    hbm_achieved = algo / (ms / 1e3) / 1e9
+    prof = ncu_kernel(kernel)
+    hbm = {"achieved": round(hbm_achieved, 1), "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+           "frac": round(hbm_achieved / peak, 4)}
+    if prof is None:
+        return {"bound": "hbm", "kernel": kernel, **hbm, "traffic": None, "algorithmic_bytes": int(algo),
+                "ms_per_launch": round(ms, 4)}
+    ipk, mhz = issue_peak(sm_count)
+    achieved = prof["inst_executed_per_launch"] / (ms / 1e3)
+    return {"bound": "alu", "kernel": kernel, "achieved": round(achieved / 1e9, 1), "peak": round(ipk / 1e9, 1),
+            "peak_source": f"derived: {sm_count} SMs x {ISSUE_PER_SM_CYCLE} warp instructions/cycle x {mhz:.0f} MHz",
+            "unit": "G warp instructions/s", "frac": round(achieved / ipk, 4),
+            "traffic": prof["dram_bytes_per_launch"], "algorithmic_bytes": int(algo), "ms_per_launch": round(ms, 4),
+            "instructions_per_launch": prof["inst_executed_per_launch"], "hbm": hbm}
 
 
 # ---------------------------------------------------------------- workloads
@@ -394,7 +423,7 @@ def run_kc(args):
 
     # roofline of the dominant kernel (per-launch means over the timed steps)
     st = c.stats()
-    roofline = roofline_of(st, phases, rs, w)
+    roofline = roofline_of(st, phases, rs, w, torch.cuda.get_device_properties(dev).multi_processor_count)
     strategy = {1: "direct", 2: "partitioned"}.get(st["strategy"], "?")
 
     # CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
