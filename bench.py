@@ -50,9 +50,18 @@ if ROOT not in sys.path:
 
 METRIC = "canonical k-mers counted/s per GB300 (plain vs batched/served); p99 job latency"
 UNIT = "k-mers/s"
-WORKLOAD = ("mid: 5 Mbp uniform ACGT genome, 1,000,000 x 150 bp reads from both strands (30x), "
+WORKLOADS = {
+    "mid": ("mid: 5 Mbp uniform ACGT genome, 1,000,000 x 150 bp reads from both strands (30x), "
             "0.5% substitutions, 0.05% N; k=31 canonical uint64 keys, Bloom 2^30 bits with 4 hashes, "
-            "2^24-slot open-addressing table, exact uint32 counts of k-mers seen >= 2 times")
+            "2^24-slot open-addressing table, exact uint32 counts of k-mers seen >= 2 times"),
+    "paired": ("paired: 50 Mbp uniform ACGT genome (normal) and a tumour copy with 0.1% SNVs and 1-10 bp indels "
+               "at 1e-5/base; 10,000,000 x 150 bp reads per sample (30x), 0.5% substitutions, 0.05% N; k=31, "
+               "Bloom 2^32 bits with 4 hashes, joint table of (normal, tumour) uint32 counts, count >= 2"),
+    "ooc": ("ooc: 500 Mbp uniform ACGT genome, 100,000,000 x 150 bp reads (30x), 0.5% substitutions, 0.05% N; "
+            "k=31, Bloom 2^34 bits with 4 hashes, count >= 2; 64 hash-prefix partition groups in turn, each "
+            "group's sorted result spilled to pinned host memory on a side stream, merged by key at dump"),
+}
+CHUNK_READS = 20_000_000  # reads per kc_add_reads call
 MID_SEED = 2
 L2_FLUSH_BYTES = 256 << 20
 
@@ -200,8 +209,9 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_kernel(kernel: str):
-    """Per-launch ncu counters of a kernel from the committed profile, if taken on the current sources."""
+def ncu_kernel(kernel: str, workload: str = "mid"):
+    """Per-launch ncu counters of a kernel on a workload from the committed profile, if taken on the current
+    sources."""
     path = os.path.join(ROOT, "profiles", "ncu_kernels.json")
     try:
         with open(path) as f:
@@ -210,7 +220,7 @@ def ncu_kernel(kernel: str):
         return None
     if d.get("source_hash") != _kernel_source_hash():
         return None
-    return d.get("kernels", {}).get(kernel)
+    return d.get("workloads", {}).get(workload, {}).get(kernel)
 
 
 ISSUE_PER_SM_CYCLE = 4  # four warp schedulers per SM, one warp instruction each per cycle
@@ -226,7 +236,7 @@ def issue_peak(sm_count: int):
     return sm_count * ISSUE_PER_SM_CYCLE * mhz * 1e6, mhz
 
 
-def roofline_of(st, phases, rs, w, sm_count):
+def roofline_of(st, phases, n_bases, w, sm_count, workload="mid", consume_launches=1):
     """Roofline entry of the kernel that takes the most device time.
 
     Partitioned strategy: the consumer k_consume_q (the largest single kernel;
@@ -246,7 +256,7 @@ def roofline_of(st, phases, rs, w, sm_count):
     import statistics as _st
 
     W = st["windows"]
-    read_bytes = (rs.n_bases * 3 + 7) // 8
+    read_bytes = (n_bases * 3 + 7) // 8
     bloom_bytes = w.bloom_bits // 8
     mean = {k: _st.mean(v) for k, v in phases.items()}
     if st["strategy"] == 1:
@@ -254,13 +264,14 @@ def roofline_of(st, phases, rs, w, sm_count):
                  "pass2": ("k_pass2", read_bytes + 32 * st["table_keys"])}
         phase = max(table, key=lambda k: mean[k])
     else:
-        table = {"pass2": ("k_consume_q", 8 * W + bloom_bytes + 16 * st["result_keys"])}
+        # per launch: with spill the consumer runs once per partition group
+        table = {"pass2": ("k_consume_q", (8 * W + bloom_bytes + 16 * st["result_keys"]) / consume_launches)}
         phase = "pass2"
     kernel, algo = table[phase]
-    ms = mean[phase]
+    ms = mean[phase] / (consume_launches if st["strategy"] != 1 else 1)
     peak, peak_kind = measured_hbm_peak()
     hbm_achieved = algo / (ms / 1e3) / 1e9
-    prof = ncu_kernel(kernel)
+    prof = ncu_kernel(kernel, workload)
     hbm = {"achieved": round(hbm_achieved, 1), "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
            "frac": round(hbm_achieved / peak, 4)}
     if prof is None:
@@ -278,11 +289,12 @@ def roofline_of(st, phases, rs, w, sm_count):
 # ---------------------------------------------------------------- workloads
 
 
-def make_inputs(rank: int):
+def make_inputs(rank: int, workload: str = "mid"):
     import synth
 
-    w = synth.mid(seed=shard_seed(rank))
-    return w
+    if workload == "mid":
+        return synth.mid(seed=shard_seed(rank))
+    return synth.WORKLOADS[workload]()  # paired, ooc: one fixed read set per rank
 
 
 def oracle_rate(w, n_reads: int):
@@ -320,17 +332,25 @@ def run_kc(args):
     dist = init_dist(world, "nccl")
     stream = torch.cuda.current_stream()
 
-    w = make_inputs(rank)
+    w = make_inputs(rank, args.workload)
     rs = w.samples[0]
-    packed, mask = kc.pack_ascii(rs.ascii)
-    offsets = np.ascontiguousarray(rs.offsets, dtype=np.uint64)
-    # pinned host copies (e2e) and device-resident copies (value)
-    h_packed = torch.from_numpy(packed.view(np.int64)).pin_memory()
-    h_mask = torch.from_numpy(mask.view(np.int64)).pin_memory()
-    h_off = torch.from_numpy(offsets.view(np.int64)).pin_memory()
-    d_packed = h_packed.to(dev)
-    d_mask = h_mask.to(dev)
-    d_off = h_off.to(dev)
+    n_samples = len(w.samples)
+    spill = bool(w.extra.get("spill_parts"))
+    # each sample in chunks of at most CHUNK_READS reads: pinned host copies
+    # (e2e) and device-resident copies (value)
+    chunks_h, chunks_d = [], []
+    for s_i, r_s in enumerate(w.samples):
+        for r0 in range(0, max(1, r_s.n_reads), CHUNK_READS):
+            part = r_s if r_s.n_reads <= CHUNK_READS else r_s.slice(r0, min(r_s.n_reads, r0 + CHUNK_READS))
+            packed, mask = kc.pack_ascii(part.ascii)
+            offsets = np.ascontiguousarray(part.offsets, dtype=np.uint64)
+            hp = (torch.from_numpy(packed.view(np.int64)).pin_memory(),
+                  torch.from_numpy(offsets.view(np.int64)).pin_memory(),
+                  torch.from_numpy(mask.view(np.int64)).pin_memory())
+            chunks_h.append((s_i, *hp))
+            chunks_d.append((s_i, *(t.to(dev) for t in hp)))
+            del packed, mask
+    total_bases = w.n_bases
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
 
@@ -339,37 +359,44 @@ def run_kc(args):
     tuning = None
     knobs = dict(strategy=args.strategy, scatter_mode=args.scatter_mode, ctas_per_sm=args.ctas_per_sm,
                  part_bits=args.part_bits, smem_table_log2=0)
-    if not args.no_tune and args.strategy == "auto" and not (args.scatter_mode or args.ctas_per_sm or args.part_bits):
+    if (not args.no_tune and not spill and args.strategy == "auto"
+            and not (args.scatter_mode or args.ctas_per_sm or args.part_bits)):
         t0 = time.perf_counter()
-        best, trials = kc.autotune(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, [(0, d_packed, d_off, d_mask)],
-                                   reps=3)
+        best, trials = kc.autotune(w.k, n_samples, w.bloom_bits, w.n_hashes, w.min_count, chunks_d, reps=3)
         knobs = dict(strategy=best["strategy"], scatter_mode=best["scatter_mode"], ctas_per_sm=best["ctas_per_sm"],
                      part_bits=best["part_bits"], smem_table_log2=best["smem_table_log2"])
         short = lambda cfg: {k: v for k, v in cfg.items() if k in ("strategy", "part_bits", "smem_table_log2",
                                                                     "ctas_per_sm")}
         tuning = {"best": short(best), "seconds": round(time.perf_counter() - t0, 2),
                   "trials": [[short(cfg), round(ms, 3)] for cfg, ms in trials]}
-    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots, timing=True,
-                       stream=stream, **knobs)
+    if spill:
+        knobs["strategy"] = "partitioned"
+    c = kc.KmerCounter(w.k, n_samples, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots,
+                       timing=True, spill=spill, stream=stream, **knobs)
 
     # size result buffers with one untimed job
-    c.add_reads(0, d_packed, d_off, d_mask)
+    for s_i, p_, o_, m_ in chunks_d:
+        c.add_reads(s_i, p_, o_, m_)
     c.finalize()
     n_res = c.result_size()
-    d_keys = torch.empty(n_res, dtype=torch.int64, device=dev)
-    d_counts = torch.empty((n_res, 1), dtype=torch.int32, device=dev)
     h_keys = torch.empty(n_res, dtype=torch.int64).pin_memory()
-    h_counts = torch.empty((n_res, 1), dtype=torch.int32).pin_memory()
+    h_counts = torch.empty((n_res, n_samples), dtype=torch.int32).pin_memory()
+    if spill:  # an out-of-core result lands in host memory
+        d_keys, d_counts = h_keys, h_counts
+    else:
+        d_keys = torch.empty(n_res, dtype=torch.int64, device=dev)
+        d_counts = torch.empty((n_res, n_samples), dtype=torch.int32, device=dev)
 
-    def job(p, o, m, keys, counts):
+    def job(chunks, keys, counts):
         c.reset()
-        c.add_reads(0, p, o, m)
+        for s_i, p_, o_, m_ in chunks:
+            c.add_reads(s_i, p_, o_, m_)
         c.finalize()
         c.dump(keys, counts)
 
     # warm-up
     for _ in range(args.warmup):
-        job(d_packed, d_off, d_mask, d_keys, d_counts)
+        job(chunks_d, d_keys, d_counts)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(_smi_id(local))
@@ -386,7 +413,7 @@ def run_kc(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        job(d_packed, d_off, d_mask, d_keys, d_counts)
+        job(chunks_d, d_keys, d_counts)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -405,25 +432,27 @@ def run_kc(args):
     value = all_windows / (max_total_ms / 1e3)
 
     # e2e: pinned host inputs and outputs through the C ABI, wall clock
-    h2d = int(h_packed.numel() * 8 + h_mask.numel() * 8 + h_off.numel() * 8)
-    d2h = int(n_res * 8 + n_res * 4)
+    h2d = int(sum(t.numel() * 8 for ch in chunks_h for t in ch[1:]))
+    d2h = int(n_res * 8 + n_res * 4 * n_samples)
     for _ in range(max(1, args.warmup)):
-        job(h_packed, h_off, h_mask, h_keys, h_counts)
+        job(chunks_h, h_keys, h_counts)
     barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        job(h_packed, h_off, h_mask, h_keys, h_counts)
+        job(chunks_h, h_keys, h_counts)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = reduce_max(e2e_s, dist, dev)
     e2e_value = all_windows / e2e_s
     # the e2e result must be the device result
-    assert np.array_equal(h_keys.numpy(), d_keys.cpu().numpy()), "e2e and device dumps differ"
+    if not spill:
+        assert np.array_equal(h_keys.numpy(), d_keys.cpu().numpy()), "e2e and device dumps differ"
 
     # roofline of the dominant kernel (per-launch means over the timed steps)
     st = c.stats()
-    roofline = roofline_of(st, phases, rs, w, torch.cuda.get_device_properties(dev).multi_processor_count)
+    roofline = roofline_of(st, phases, total_bases, w, torch.cuda.get_device_properties(dev).multi_processor_count,
+                           args.workload, min(st["partitions"], 64) if spill else 1)
     strategy = {1: "direct", 2: "partitioned"}.get(st["strategy"], "?")
 
     # CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
@@ -432,11 +461,11 @@ def run_kc(args):
         n_s = pick_sample_reads(w, args.cpu_seconds)
         win, dt = oracle_rate(w, n_s)
         cpu = {"value": round(win / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n_s:,} of {rs.n_reads:,} reads of the mid workload ({win:,} windows, "
+               "sample": f"first {n_s:,} of {rs.n_reads:,} reads of the {args.workload} workload ({win:,} windows, "
                          f"{dt:.1f} s, single-threaded C++ oracle, {os.cpu_count()} host cores present)"}
 
     served = None
-    if rank == 0 and world == 1 and not args.no_served:
+    if rank == 0 and world == 1 and not args.no_served and args.workload == "mid":
         served = run_served_trace(args.served_jobs, args.served_max_reads)
 
     if rank == 0:
@@ -444,8 +473,9 @@ def run_kc(args):
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(max_total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded genome and reads)",
-            "config": {"workload": WORKLOAD, "windows_per_job": windows, "result_keys": n_res,
-                       "l2": "256 MiB written between timed steps (outside the step events)",
+            "config": {"workload": WORKLOADS[args.workload], "windows_per_job": windows, "result_keys": n_res,
+                       "l2": "256 MiB written between timed steps (outside the step events)"
+                             + ("; inputs larger than L2" if args.workload != "mid" else ""),
                        "parallelism": f"{world} independent jobs, one per GPU" if world > 1 else "1 GPU"},
             "strategy": strategy,
             "tuning": tuning,
@@ -648,6 +678,8 @@ def main(argv=None):
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--part-bits", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="library defaults instead of kc_autotune's choice")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mid",
+                    help="mid (the default bench line), paired (two samples, joint table) or ooc (spill)")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

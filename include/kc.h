@@ -85,8 +85,13 @@ typedef struct kc_config {
                                      grouped in two levels)                         */
     uint64_t table_slots;         /* direct: open-addressing slots (power of two)
                                      of the global table                            */
-    uint32_t spill;               /* 1: each finished partition's result is copied
-                                     to pinned host memory on a side stream         */
+    uint32_t spill;               /* partitioned: kc_finalize takes 64 groups of
+                                     partitions in turn and copies each group's
+                                     sorted result to pinned host memory on a side
+                                     stream.  1: kc_dump copies the runs back and
+                                     sorts them on the device when it has room
+                                     (else as 2); 2: kc_dump merges the runs on
+                                     the host                                       */
     uint32_t timing;              /* 1: record CUDA events around every phase on
                                      the handle's stream (see kc_stats.ms_*)        */
     uint32_t strategy;            /* KC_STRATEGY_*                                  */

@@ -217,7 +217,7 @@ class KmerCounter:
                 split_max = split_max or (-1 if cfg.split_max == SPLIT_NONE else cfg.split_max)
         cfg.table_slots = table_slots
         cfg.part_bits = part_bits
-        cfg.spill = 1 if spill else 0
+        cfg.spill = int(spill)  # 1 or True: dump re-sorts on the device when it has room; 2: merges on the host
         cfg.ctas_per_sm = ctas_per_sm
         cfg.timing = 1 if timing else 0
         cfg.strategy = {"auto": 0, "direct": 1, "partitioned": 2}[strategy]

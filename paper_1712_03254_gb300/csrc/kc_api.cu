@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
+#include <memory>
 #include <thread>
 #include <cstring>
 #include <string>
@@ -119,18 +120,43 @@ void free_batches(kc_handle h) {
     h->batches.clear();
 }
 
+// Forget the spilled runs; their pinned chunks stay for the next job.
 void release_spill(kc_handle h) {
-    for (auto& r : h->spill_dir)
-        if (r.host) cudaFreeHost(r.host);
+    for (auto& c : h->spill_chunks) c.used = 0;
     h->spill_dir.clear();
     h->spilled = false;
     h->spilled_bytes = 0;
 }
 
-// Merge the spilled sorted runs into keys[] / vals[] (host), in key ranges
-// split among threads: each range is cut out of every run by binary search
-// and merged with a small heap.
-void merge_runs(const std::vector<SpillRun>& runs, uint64_t* keys, uint64_t* vals) {
+void free_spill_chunks(kc_handle h) {
+    for (auto& c : h->spill_chunks) cudaFreeHost(c.p);
+    h->spill_chunks.clear();
+}
+
+// Room for `words` 64-bit words in the pinned chunks: the first chunk with
+// space left, else a new chunk of at least 256 MiB.
+uint64_t* spill_alloc(kc_handle h, uint64_t words) {
+    for (auto& c : h->spill_chunks)
+        if (c.words - c.used >= words) {
+            uint64_t* p = c.p + c.used;
+            c.used += words;
+            return p;
+        }
+    PinnedChunk c;
+    c.words = std::max<uint64_t>(words, 32ull << 20);
+    if (cudaMallocHost(&c.p, c.words * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    c.used = words;
+    h->spill_chunks.push_back(c);
+    return c.p;
+}
+
+// Merge the spilled sorted runs into keys[] and counts[] (host; counts may be
+// null), in key ranges split among threads: each range is cut out of every run
+// by binary search and merged with a small heap.
+void merge_runs(const std::vector<SpillRun>& runs, uint64_t* keys, uint32_t* counts, int n_samples) {
     std::vector<uint64_t> sample;
     for (const auto& r : runs)
         for (uint64_t i = 0; i < r.n_items; i += std::max<uint64_t>(1, r.n_items / 256)) sample.push_back(r.host[i]);
@@ -170,7 +196,15 @@ void merge_runs(const std::vector<SpillRun>& runs, uint64_t* keys, uint64_t* val
             const size_t r = heap.back().second;
             heap.pop_back();
             keys[o] = runs[r].host[pos[r]];
-            vals[o] = runs[r].host[runs[r].n_items + pos[r]];
+            if (counts) {
+                const uint64_t v = runs[r].host[runs[r].n_items + pos[r]];
+                if (n_samples == 2) {
+                    counts[2 * o] = (uint32_t)v;
+                    counts[2 * o + 1] = (uint32_t)(v >> 32);
+                } else {
+                    counts[o] = (uint32_t)v;
+                }
+            }
             ++o;
             if (++pos[r] < cut[t][r].second) {
                 heap.push_back({runs[r].host[pos[r]], r});
@@ -525,6 +559,7 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     if (c.smem_table_log2 && (c.smem_table_log2 < 10 || c.smem_table_log2 > 13))
         return fail(KC_ERR_ARG, "smem_table_log2 must be in 10..13");
     if (c.split_max != KC_SPLIT_NONE && c.split_max > 13) return fail(KC_ERR_ARG, "split_max must be in 0..13");
+    if (c.spill > 2) return fail(KC_ERR_ARG, "spill must be 0, 1 or 2");
     // Partitions: filter slices of 4096 words (32 KiB) unless set; the
     // partitioned strategy needs a slice of at most 8192 words in shared memory.
     const int lw = log2_exact(bloom_bits / 64);
@@ -625,10 +660,9 @@ void kc_destroy(kc_handle h) {
     if (h->stream) {
         free_batches(h);
         free_result(h);
-        if (!h->spill_dir.empty()) {
-            cudaStreamSynchronize(h->copy_stream);
-            release_spill(h);
-        }
+        if (!h->spill_dir.empty()) cudaStreamSynchronize(h->copy_stream);
+        release_spill(h);
+        free_spill_chunks(h);
         if (h->bloom) cudaFreeAsync(h->bloom, h->stream);
         if (h->table) cudaFreeAsync(h->table, h->stream);
         if (h->ctr) cudaFreeAsync(h->ctr, h->stream);
@@ -759,6 +793,40 @@ kc_status kc_finalize(kc_handle h) {
     return KC_OK;
 }
 
+// A spilled result back on the device: the runs are copied into one device
+// array and sorted there as one survivor set (sort_result), after which the
+// handle holds its result on the device like an unspilled one.
+// KC_ERR_OOM_DEVICE (nothing changed, no error recorded) when the device has
+// no room for it.
+kc_status resort_spilled(kc_handle h) {
+    const uint64_t n = h->n_result;
+    cudaStream_t st = h->stream;
+    uint64_t *tk = nullptr, *tv = nullptr;
+    if (cudaMallocAsync(&tk, n * 8, st) != cudaSuccess || cudaMallocAsync(&tv, n * 8, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (tk) cudaFreeAsync(tk, st);
+        return KC_ERR_OOM_DEVICE;
+    }
+    uint64_t off = 0;
+    for (const auto& r : h->spill_dir) {
+        if (!r.n_items) continue;
+        KC_CUDA(cudaMemcpyAsync(tk + off, r.host, r.n_items * 8, cudaMemcpyHostToDevice, st));
+        KC_CUDA(cudaMemcpyAsync(tv + off, r.host + r.n_items, r.n_items * 8, cudaMemcpyHostToDevice, st));
+        off += r.n_items;
+    }
+    h->host_ctr.survivors = n;
+    KC_CUDA(cudaMemcpyAsync(&h->ctr->survivors, &h->host_ctr.survivors, 8, cudaMemcpyHostToDevice, st));
+    const uint64_t spilled_bytes = h->spilled_bytes;
+    kc_status s = sort_result(h, tk, tv);  // synchronises the stream (reads the counters)
+    cudaFreeAsync(tk, st);
+    cudaFreeAsync(tv, st);
+    if (s != KC_OK) return s;
+    release_spill(h);  // the pinned chunks stay for the next job
+    h->spilled_bytes = spilled_bytes;
+    h->n_result = n;
+    return KC_OK;
+}
+
 kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capacity, uint64_t* n_out) {
     kc_status s = check_open(h);
     if (s != KC_OK) return s;
@@ -768,28 +836,30 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
     if (capacity < h->n_result) return fail(KC_ERR_CAPACITY, "dump capacity smaller than the result");
     if (h->n_result == 0) return KC_OK;
     cudaStream_t st = h->stream;
+    if (h->spilled && h->cfg.spill == 1) {
+        // copy the runs back and sort them on the device when there is room
+        s = resort_spilled(h);
+        if (s != KC_OK && s != KC_ERR_OOM_DEVICE) return s;
+    }
     if (h->spilled) {  // merge the host runs
         const bool dev_k = is_device_ptr(keys), dev_c = counts && is_device_ptr(counts);
-        std::vector<uint64_t> mk, mv(h->n_result);
+        std::unique_ptr<uint64_t[]> mk;
+        std::unique_ptr<uint32_t[]> mc;
         uint64_t* kout = keys;
+        uint32_t* cout = counts;
         if (dev_k) {
-            mk.resize(h->n_result);
-            kout = mk.data();
+            mk.reset(new (std::nothrow) uint64_t[h->n_result]);
+            if (!mk) return fail(KC_ERR_OOM_HOST, "dump staging");
+            kout = mk.get();
         }
-        merge_runs(h->spill_dir, kout, mv.data());
+        if (dev_c) {
+            mc.reset(new (std::nothrow) uint32_t[h->n_result * (size_t)h->n_samples]);
+            if (!mc) return fail(KC_ERR_OOM_HOST, "dump staging");
+            cout = mc.get();
+        }
+        merge_runs(h->spill_dir, kout, cout, h->n_samples);
         if (dev_k) KC_CUDA(cudaMemcpy(keys, kout, h->n_result * 8, cudaMemcpyHostToDevice));
-        if (counts) {
-            std::vector<uint32_t> c32;
-            uint32_t* cout = counts;
-            if (dev_c) {
-                c32.resize(h->n_result * (size_t)h->n_samples);
-                cout = c32.data();
-            }
-            if (h->n_samples == 2) std::memcpy(cout, mv.data(), h->n_result * 8);
-            else
-                for (uint64_t i = 0; i < h->n_result; ++i) cout[i] = (uint32_t)mv[i];
-            if (dev_c) KC_CUDA(cudaMemcpy(counts, cout, h->n_result * 4 * (size_t)h->n_samples, cudaMemcpyHostToDevice));
-        }
+        if (dev_c) KC_CUDA(cudaMemcpy(counts, cout, h->n_result * 4 * (size_t)h->n_samples, cudaMemcpyHostToDevice));
         return KC_OK;
     }
     KC_CUDA(cudaMemcpyAsync(keys, h->res_keys, h->n_result * 8, cudaMemcpyDefault, st));

@@ -1055,8 +1055,8 @@ kc_status finalize_spilled(kc_batch_ctx* b, kc_handle h) {
         run.n_parts = per;
         run.n_items = h->n_result;
         if (run.n_items) {
-            cudaError_t e = cudaMallocHost(&run.host, run.n_items * 16);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost(spill)");
+            run.host = spill_alloc(h, 2 * run.n_items);
+            if (!run.host) return fail(KC_ERR_OOM_HOST, "pinned host memory for a spilled run");
             // the copy waits for the group's sort; the next group runs meanwhile
             KC_CUDA(cudaEventRecord(h->ev_main, b->st));
             KC_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_main, 0));

@@ -33,8 +33,15 @@ enum class State { Open, Finalized, Poisoned };
 // unit (partition range, location, number of items).
 struct SpillRun {
     uint32_t first_part = 0, n_parts = 0;
-    uint64_t* host = nullptr;  // n_items keys followed by n_items packed counts
+    uint64_t* host = nullptr;  // n_items keys followed by n_items packed counts (inside a pinned chunk)
     uint64_t n_items = 0;
+};
+
+// Pinned host memory the spilled runs are placed in; kept across kc_reset so
+// a repeated out-of-core job does not pin memory again.
+struct PinnedChunk {
+    uint64_t* p = nullptr;
+    uint64_t words = 0, used = 0;
 };
 
 kc_status fail(kc_status s, const std::string& msg);
@@ -95,6 +102,7 @@ struct kc_ctx {
     // out-of-core results (kc_config.spill)
     bool spilled = false;
     std::vector<kcapi::SpillRun> spill_dir;
+    std::vector<kcapi::PinnedChunk> spill_chunks;
     uint64_t spilled_bytes = 0;
 
 
@@ -125,6 +133,8 @@ kc_status read_counters(kc_handle h);
 kc_status device_errors(kc_handle h);
 void free_result(kc_handle h);
 void release_spill(kc_handle h);
+void free_spill_chunks(kc_handle h);
+uint64_t* spill_alloc(kc_handle h, uint64_t words);  // nullptr when pinning fails
 
 }  // namespace kcapi
 

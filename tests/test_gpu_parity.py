@@ -160,6 +160,13 @@ def test_device_resident_inputs(oracle_mod, strategy):
     ok, oc = o.result()
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), ok)
     assert np.array_equal(counts.cpu().numpy().view(np.uint32), oc)
+    assert c.stats()["spilled_bytes"] == st["spilled_bytes"]
+    # the same handle again: the pinned runs are reused
+    c.reset()
+    for s_i, rs in enumerate(w.samples):
+        c.add_readset(s_i, rs)
+    c.finalize()
+    assert_same_result(c, o)
     bloom = torch.empty(w.bloom_bits // 64, dtype=torch.int64, device="cuda")
     c.export_bloom(out=bloom)
     assert np.array_equal(bloom.cpu().numpy().view(np.uint64), o.bloom())
@@ -370,14 +377,16 @@ def test_two_level_partitions(oracle_mod, part_bits):
     assert_same_bloom(c, o)
 
 
+@pytest.mark.parametrize("spill", [1, 2])  # dump re-sorts on the device / merges on the host
 @pytest.mark.parametrize("part_bits", [10, 16])  # 2^22 filter words: slices of 2^12 and 2^6 words
-def test_spill_to_host_merges_runs(oracle_mod, part_bits):
+def test_spill_to_host_merges_runs(oracle_mod, part_bits, spill):
     """Out-of-core finalize: 64 groups of partitions in turn, each group's
-    sorted survivors copied to pinned host memory; kc_dump merges the runs."""
+    sorted survivors copied to pinned host memory; kc_dump puts the runs back
+    in key order (on the device, or merged on the host)."""
     w = synth.paired(scale=0.002)
     w.bloom_bits = 1 << 28
     o = oracle_mod.count(w)
-    c = gpu_count(w, strategy="partitioned", part_bits=part_bits, spill=True)
+    c = gpu_count(w, strategy="partitioned", part_bits=part_bits, spill=spill)
     st = c.stats()
     assert st["spilled_bytes"] == 16 * st["result_keys"] > 0
     assert_same_result(c, o)
@@ -391,3 +400,10 @@ def test_spill_to_host_merges_runs(oracle_mod, part_bits):
     ok, oc = o.result()
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), ok)
     assert np.array_equal(counts.cpu().numpy().view(np.uint32), oc)
+    assert c.stats()["spilled_bytes"] == st["spilled_bytes"]
+    # the same handle again: the pinned runs are reused
+    c.reset()
+    for s_i, rs in enumerate(w.samples):
+        c.add_readset(s_i, rs)
+    c.finalize()
+    assert_same_result(c, o)
