@@ -267,6 +267,10 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[(uint64_t)blockIdx.x * P + i] = s_cnt[i];
 }
 
+constexpr int kLinThreads = 1024;
+constexpr int kLinPerThread = 4;
+constexpr uint32_t kRetryCap = 2048;  // hashes one retry list holds
+
 // Staged scatter of hashes already in memory.  CTA c moves segment c
 // (seg[c] = {offset into src, length, group}) into its padded runs, 4 hashes
 // per thread per round; full 4-entry stages leave as aligned 32-byte sectors.
@@ -274,23 +278,31 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
 // segment belongs to level-1 group `group`, hashes of another group (the
 // level-1 run padding) are skipped, and the run padding written here carries
 // the prefix of another level-2 partition.
-constexpr int kLinThreads = 1024;
-constexpr int kLinPerThread = 4;
-
+//
+// A hash whose stage is full goes to a retry list in shared memory and is
+// staged again, first thing, in the next round, so the warp that held it
+// takes its next rows at once (a warp loads new rows only when all its lanes
+// are free, which keeps the loads coalesced).  Two lists alternate between
+// rounds.  Hashes failing again go to the front of the other list (at most as
+// many as the list held), new failures to its back, as long as the space the
+// front may still need is left; beyond that a hash stays with its thread.
 __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64_t* __restrict__ src,
                                                                     const SegDesc* __restrict__ segs, int a1, int a2,
                                                                     const uint64_t* __restrict__ base,
                                                                     uint64_t* __restrict__ out) {
     extern __shared__ unsigned long long s_stage[];
+    __shared__ unsigned s_front[2], s_back[2];  // entries at the front / back of each retry list
     const uint32_t P = 1u << a2;
     const uint32_t D = stage_depth(a2);  // entries staged per bucket, a multiple of 4
     uint32_t* fill = reinterpret_cast<uint32_t*>(s_stage + (size_t)D * P);
     uint64_t* cursor = reinterpret_cast<uint64_t*>(fill + P);  // next output position of each run
+    uint64_t* retry = cursor + P;                              // two lists of kRetryCap hashes
     const uint64_t* my_base = base + (uint64_t)blockIdx.x * P;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
         fill[i] = 0;
         cursor[i] = __ldg(my_base + i);
     }
+    if (threadIdx.x == 0) s_front[0] = s_back[0] = s_front[1] = s_back[1] = 0;
     __syncthreads();
     const SegDesc sd = segs[blockIdx.x];
     const uint64_t s0 = sd.off, len = sd.len;
@@ -311,7 +323,20 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
         }
         next += blockDim.x;
     }
+    int par = 0;  // retry list read this round
     for (;;) {
+        const unsigned n_front = min(s_front[par], kRetryCap), n_back = min(s_back[par], kRetryCap);
+        const unsigned n_in = n_front + n_back;
+        const uint64_t* rin = retry + (size_t)par * kRetryCap;
+        uint64_t* rout = retry + (size_t)(par ^ 1) * kRetryCap;
+        // the retry list first: a failure goes to the front of the other list
+        for (unsigned i = threadIdx.x; i < n_in; i += blockDim.x) {
+            const uint64_t h = rin[i < n_front ? i : kRetryCap - 1 - (i - n_front)];
+            const uint32_t b = (uint32_t)(h >> shift) & (P - 1);
+            const uint32_t pos = atomicAdd(&fill[b], 1u);
+            if (pos < D) s_stage[(size_t)b * D + pos] = h;
+            else rout[atomicAdd(&s_front[par ^ 1], 1u)] = h;  // at most n_in of these
+        }
         // Warp-uniform: a warp takes its next rows only when none of its lanes
         // still holds a pending hash, so every load stays coalesced.
         if (__all_sync(kFull, pend == 0)) {
@@ -339,10 +364,21 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
                 if (pos < D) {
                     s_stage[(size_t)b * D + pos] = h;
                     pend &= ~(1u << e);
-                }  // else the stage is full: retry next round
+                } else {
+                    // the back of the other list, leaving the n_in entries the
+                    // front may take; past that the hash stays and retries
+                    const unsigned k = atomicAdd(&s_back[par ^ 1], 1u);
+                    if (k < kRetryCap - n_in) {
+                        rout[kRetryCap - 1 - k] = h;
+                        pend &= ~(1u << e);
+                    } else {
+                        atomicSub(&s_back[par ^ 1], 1u);
+                    }
+                }
             }
         }
         __syncthreads();
+        if (threadIdx.x == 0) s_front[par] = s_back[par] = 0;  // read by every thread above
         if (D == 4) {
             // shallow stages (many buckets): a thread per bucket, one sector
             for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
@@ -369,12 +405,13 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
                 if (lane == 0) {
                     for (uint32_t i = whole; i < f; ++i) st[i - whole] = st[i];
                     cursor[b] += whole;
-                    fill[b] = f - whole;  // windows beyond D retry next round
+                    fill[b] = f - whole;  // hashes beyond D went to the retry list
                 }
                 __syncwarp();
             }
         }
-        if (!__syncthreads_or(pend != 0 || nval != 0)) break;
+        par ^= 1;
+        if (!__syncthreads_or(pend != 0 || nval != 0 || s_front[par] != 0 || s_back[par] != 0)) break;
     }
     for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
         const uint32_t f = min(fill[b], D);
@@ -580,9 +617,10 @@ void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_uni
                                                reinterpret_cast<unsigned long long*>(g_cursor), seg, lin);
 }
 
-// stage, fill count and 64-bit output cursor per bucket
+// stage, fill count and 64-bit output cursor per bucket, then the two retry lists
 size_t staged_seg_smem(int a) {
-    return ((size_t)stage_depth(a) * sizeof(uint64_t) + sizeof(uint32_t) + sizeof(uint64_t)) << a;
+    return (((size_t)stage_depth(a) * sizeof(uint64_t) + sizeof(uint32_t) + sizeof(uint64_t)) << a) +
+           2 * kRetryCap * sizeof(uint64_t);
 }
 
 void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,

@@ -160,13 +160,6 @@ def test_device_resident_inputs(oracle_mod, strategy):
     ok, oc = o.result()
     assert np.array_equal(keys.cpu().numpy().view(np.uint64), ok)
     assert np.array_equal(counts.cpu().numpy().view(np.uint32), oc)
-    assert c.stats()["spilled_bytes"] == st["spilled_bytes"]
-    # the same handle again: the pinned runs are reused
-    c.reset()
-    for s_i, rs in enumerate(w.samples):
-        c.add_readset(s_i, rs)
-    c.finalize()
-    assert_same_result(c, o)
     bloom = torch.empty(w.bloom_bits // 64, dtype=torch.int64, device="cuda")
     c.export_bloom(out=bloom)
     assert np.array_equal(bloom.cpu().numpy().view(np.uint64), o.bloom())
