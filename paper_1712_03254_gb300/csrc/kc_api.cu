@@ -379,14 +379,14 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
 
 // Sort the survivors held in tk/tv (count in host_ctr.survivors, already
 // read back) into res_keys/res_vals: bucket by the top bits of the 2k-bit
-// key (about 64 keys a bucket), then sort every bucket: one warp per bucket
+// key (at most about 32 keys a bucket), then sort every bucket: one warp per bucket
 // in registers, larger buckets in shared memory or, rarely, global memory.
 kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
     cudaStream_t st = h->stream;
     const uint64_t n = h->host_ctr.survivors;
     const uint64_t cap = std::max<uint64_t>(1, n);
     int bits = 0;
-    while (bits < 22 && bits < 2 * h->k && (cap >> bits) > 64) ++bits;
+    while (bits < 24 && bits < 2 * h->k && (cap >> bits) > 32) ++bits;
     const uint64_t n_buckets = 1ull << bits;
     const int prefix_shift = 2 * h->k - bits;
     uint64_t *starts = nullptr, *cursor = nullptr;

@@ -949,14 +949,14 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         }
     }
 
-    // sort: per job, bucket bits for about 64 survivors a bucket
+    // sort: per job, bucket bits for at most about 32 survivors a bucket
     uint64_t n_buckets = 0;
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
         kc::JobDesc& J = b->jobs[j];
         const uint64_t nsv = std::min<uint64_t>(cnt[2 * j], work[j].sv_cap);
         int bits = 0;
-        while (bits < 22 && bits < 2 * h->k && (std::max<uint64_t>(1, nsv) >> bits) > 64) ++bits;
+        while (bits < 24 && bits < 2 * h->k && (std::max<uint64_t>(1, nsv) >> bits) > 32) ++bits;
         J.sort_bits = bits;
         J.bucket_base = n_buckets;
         J.n_buckets = 1ull << bits;

@@ -195,16 +195,15 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&k)[R], uint64_t (&v)[R],
                 const int rs = stride >> 5;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    if ((r & rs) == 0) {
+                    if ((r & rs) == 0) {  // compile-time: pairs within the lane
                         const int q = r | rs;
                         const bool asc = (((r << 5) | lane) & size) == 0;
-                        if ((k[r] > k[q]) == asc) {
-                            const uint64_t tk = k[r], tv = v[r];
-                            k[r] = k[q];
-                            v[r] = v[q];
-                            k[q] = tk;
-                            v[q] = tv;
-                        }
+                        const bool sw = (k[r] > k[q]) == asc;  // selects, no branch: lanes stay converged
+                        const uint64_t ka = k[r], kb = k[q], va = v[r], vb = v[q];
+                        k[r] = sw ? kb : ka;
+                        k[q] = sw ? ka : kb;
+                        v[r] = sw ? vb : va;
+                        v[q] = sw ? va : vb;
                     }
                 }
             } else {
@@ -215,11 +214,11 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&k)[R], uint64_t (&v)[R],
                     const uint64_t ov = __shfl_xor_sync(0xffffffffu, v[r], stride);
                     const bool asc = (i & size) == 0;
                     const bool lower = (i & stride) == 0;
-                    const bool take_other = lower ? (asc ? ok < k[r] : ok > k[r]) : (asc ? ok > k[r] : ok < k[r]);
-                    if (take_other) {
-                        k[r] = ok;
-                        v[r] = ov;
-                    }
+                    // keep the smaller key when this lane's end of the pair should hold it
+                    const bool want_min = lower == asc;
+                    const bool take_other = want_min ? ok < k[r] : ok > k[r];
+                    k[r] = take_other ? ok : k[r];
+                    v[r] = take_other ? ov : v[r];
                 }
             }
         }
