@@ -99,6 +99,37 @@ __device__ __forceinline__ uint64_t canonical_key(uint64_t fwd, const PassParams
     return fwd < rc ? fwd : rc;
 }
 
+// Rolling codes over the 64 window starts of a unit: the forward and
+// reverse-complement codes of window j, updated by one base per step instead
+// of being cut out of the unit's words for every window.  `x` and `y` hold the
+// bases entering at the next steps (base j + k first, as the top two bits of
+// x), taken from the unit's words w0, w1 and the following word w2.
+struct RollingWindow {
+    uint64_t fwd, rc, x, y;
+};
+
+__device__ __forceinline__ RollingWindow rolling_start(uint64_t w0, uint64_t w1, uint64_t w2, const PassParams& p) {
+    RollingWindow r;
+    const int kk = 64 - p.rc_shift;  // 2k, in 2..62
+    r.fwd = w0 >> p.rc_shift;
+    r.rc = reverse_pairs(r.fwd ^ p.kmask) >> p.rc_shift;
+    r.x = (w0 << kk) | (w1 >> p.rc_shift);
+    r.y = (w1 << kk) | (w2 >> p.rc_shift);
+    return r;
+}
+
+// Window j -> window j + 1: the base leaving is dropped by the mask (forward)
+// or shifted out (reverse complement), the entering base b adds b at the low
+// end of the forward code and its complement 3 - b at the high end of the
+// reverse complement.
+__device__ __forceinline__ void rolling_step(RollingWindow& r, const PassParams& p) {
+    const uint64_t b = r.x >> 62;
+    r.fwd = ((r.fwd << 2) | b) & p.kmask;
+    r.rc = (r.rc >> 2) | ((b ^ 3ull) << (62 - p.rc_shift));
+    r.x = (r.x << 2) | (r.y >> 62);
+    r.y <<= 2;
+}
+
 // Bits of one key in its filter word: bit (g >> 6i) & 63 for i < n_hashes,
 // assembled in two 32-bit halves.
 template <int NH>

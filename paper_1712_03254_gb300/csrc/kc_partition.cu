@@ -239,28 +239,29 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
     const unsigned lt = (1u << lane) - 1u;
     for (uint64_t g = lo + (uint64_t)wid * 32; g < hi; g += (uint64_t)nwarps * 32) {
         const UnitWords uw = load_unit(pw, vw, g + lane, hi, lane);
-        uint64_t vm = uw.v;
+        const uint64_t vm = uw.v;
         const unsigned nv = (unsigned)__popcll(vm);
-        const int n_iter = __reduce_max_sync(kFull, nv);
         // the warp's windows of these 32 units get consecutive positions,
-        // claimed once; each round's stores are coalesced
+        // claimed once; each step's stores are coalesced
         const unsigned tot = __reduce_add_sync(kFull, nv);
+        if (tot == 0) continue;
         unsigned wb = 0;
         if (lane == 0) wb = atomicAdd(&s_pos, tot);
         wb = __shfl_sync(kFull, wb, 0);
-        for (int it = 0; it < n_iter; ++it) {
-            const bool has = vm != 0;
+        // every lane walks the 64 window starts of its unit with rolling codes
+        RollingWindow rw = rolling_start(uw.w0, uw.w1, uw.w2, p);
+#pragma unroll 4
+        for (int j = 0; j < 64; ++j) {
+            const bool has = (vm >> (63 - j)) & 1ull;
             uint64_t h = 0;
             if (has) {
-                const int j = __clzll(vm);
-                vm &= ~(0x8000000000000000ull >> j);
-                const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
-                h = mixer64(key);
+                h = mixer64(rw.fwd < rw.rc ? rw.fwd : rw.rc);
                 atomicAdd(&s_cnt[(uint32_t)(h >> (64 - a))], 1u);
             }
             const unsigned ballot = __ballot_sync(kFull, has);
             if (has) lin[base + wb + __popc(ballot & lt)] = h;
             wb += __popc(ballot);
+            rolling_step(rw, p);
         }
     }
     __syncthreads();
