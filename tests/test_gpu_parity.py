@@ -130,6 +130,19 @@ def test_several_batches_and_offset_base(oracle_mod, strategy):
     assert_same_bloom(c, o)
 
 
+def test_many_batches_full_recount(oracle_mod):
+    """40 read batches per sample: a partition spans more batches than the
+    consumer's window bitmap covers, so the second pass recounts every window
+    instead of only the first pass's uncounted ones; same result either way."""
+    w = synth.paired(scale=0.001)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, batches=40, strategy="partitioned")
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    c = gpu_count(w, batches=7, strategy="partitioned")
+    assert_same_result(c, o)
+
+
 def test_two_samples_joint_table(oracle_mod, strategy):
     w = synth.paired(scale=0.002)
     o = oracle_mod.count(w)
