@@ -636,8 +636,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = make_inputs(0)
-    budget_s = 150.0
+    w = make_inputs(0, args.workload)
+    budget_s = args.ref_seconds
     per_step = budget_s / max(1, args.steps + args.warmup)
     n_s = pick_sample_reads(w, per_step)
     for _ in range(args.warmup):
@@ -649,13 +649,14 @@ def run_reference(args):
         wins = win
     total = sum(times)
     value = wins * args.steps / total
-    sample = (f"first {n_s:,} of {w.samples[0].n_reads:,} reads of the mid workload per step ({wins:,} windows), "
+    sample = (f"first {n_s:,} of {w.samples[0].n_reads:,} reads of the {args.workload} workload per step "
+              f"({wins:,} windows), "
               f"single-threaded C++ oracle, {os.cpu_count()} host cores present")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic (seeded genome and reads)", "config": {"workload": WORKLOAD},
+        "data": "synthetic (seeded genome and reads)", "config": {"workload": WORKLOADS[args.workload]},
         "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -670,6 +671,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["kc", "reference"], default="kc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0, help="--impl reference: CPU seconds for the whole run")
     ap.add_argument("--strategy", choices=["auto", "direct", "partitioned"], default="auto")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream comparison")
     ap.add_argument("--served-jobs", type=int, default=64)
