@@ -698,8 +698,7 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
         b0 = ends[0];
         b1 = ends[1];
     } else {
-        for (uint64_t r = 0; r < n_reads; ++r)
-            if (offsets[r + 1] < offsets[r]) return fail(KC_ERR_ARG, "read offsets decrease");
+        // the full check of host offsets runs below, while the copies are in flight
         b0 = offsets[0];
         b1 = offsets[n_reads];
     }
@@ -742,6 +741,15 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     KC_CUDA(cudaMemsetAsync(b.pw + n_pwords_src, 0, (n_pwords - n_pwords_src) * 8, cs));
     KC_CUDA(cudaMemcpyAsync(nm, n_mask + B / 64, n_units * 8, cudaMemcpyDefault, cs));
     KC_CUDA(cudaMemcpyAsync(doff, offsets, (n_reads + 1) * 8, cudaMemcpyDefault, cs));
+    if (!off_dev) {
+        bool decreasing = false;
+        for (uint64_t r = 0; r < n_reads && !decreasing; ++r) decreasing = offsets[r + 1] < offsets[r];
+        if (decreasing) {
+            KC_CUDA(cudaStreamSynchronize(cs));
+            for (void* q : {(void*)b.pw, (void*)b.vw, (void*)nm, (void*)bd, (void*)doff}) cudaFreeAsync(q, cs);
+            return fail(KC_ERR_ARG, "read offsets decrease");
+        }
+    }
     if (any_host) {
         KC_CUDA(cudaEventRecord(h->ev_copy, cs));
         KC_CUDA(cudaStreamWaitEvent(st, h->ev_copy, 0));
