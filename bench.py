@@ -21,7 +21,7 @@ With N ranks (torchrun) every rank counts its own job (independent read set),
 no collective is on the data path, and value = all ranks' windows / the
 slowest rank's time ("weak" scaling).
 
-The "served" field replays a Poisson stream of 64 jobs of mixed size (1-20
+The "served" field replays a Poisson stream of 256 jobs of mixed size (1-20
 Mbp genomes, 10^4-2x10^5 reads, k 25 or 31, filters of 8 bits per expected
 distinct k-mer) through one-at-a-time plain jobs and through the
 continuous-batching server, at 0.7 and 0.9 of the plain capacity and all at
@@ -613,16 +613,18 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
                                     for x in ("queue", "ingest", "batch_wait", "finalize")}},
             "results_equal_alone": same,
         })
-    # saturation: every job submitted at once
-    srv = kc.KcServer(budget_bytes, max_batch=64)
-    start = time.perf_counter()
-    ids = [srv.submit(j["w"].k, j["w"].bloom_bits, j["w"].n_hashes, j["w"].min_count,
-                      [(j["packed"], j["offsets"], j["mask"])]) for j in jobs]
-    for i in ids:
-        srv.wait(i, timeout_s=600)
-    span = time.perf_counter() - start
-    st = srv.stats()
-    srv.close()
+    # saturation: every job submitted at once (one untimed pass first, so the
+    # timed one runs with warm pinned result blocks and captured sort graphs)
+    for timed in (False, True):
+        srv = kc.KcServer(budget_bytes, max_batch=64)
+        start = time.perf_counter()
+        ids = [srv.submit(j["w"].k, j["w"].bloom_bits, j["w"].n_hashes, j["w"].min_count,
+                          [(j["packed"], j["offsets"], j["mask"])]) for j in jobs]
+        for i in ids:
+            srv.wait(i, timeout_s=600)
+        span = time.perf_counter() - start
+        st = srv.stats()
+        srv.close()
     out["saturated"] = {"served_jobs_per_s": round(len(jobs) / span, 2), "plain_jobs_per_s": round(plain_cap, 2),
                         "served_k_mers_per_s": round(windows / span, 1),
                         "plain_k_mers_per_s": round(windows * plain_cap / len(jobs), 1),
@@ -677,7 +679,7 @@ def main(argv=None):
     ap.add_argument("--ref-seconds", type=float, default=150.0, help="--impl reference: CPU seconds for the whole run")
     ap.add_argument("--strategy", choices=["auto", "direct", "partitioned"], default="auto")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream comparison")
-    ap.add_argument("--served-jobs", type=int, default=64)
+    ap.add_argument("--served-jobs", type=int, default=256)
     ap.add_argument("--served-max-reads", type=int, default=200_000)
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)

@@ -180,15 +180,17 @@ kc_status kc_batch_finalize(kc_batch b, kc_handle* handles, int n);
 void kc_batch_destroy(kc_batch b);
 
 /*
- * Job server with continuous batching (host-submitted jobs).  An ingest
- * thread admits queued jobs in arrival order as soon as their estimated
- * device footprint fits device_budget_bytes and adds their reads on their own
- * streams; a finalize thread repeatedly finalizes every job ingested so far
- * (at most max_batch) as one batch (kc_batch_finalize), copies the results to
- * host memory and releases the jobs' device memory.  Jobs that arrive while a
- * batch runs are ingested at once and join the next batch.  Each job's result
- * is the one kc_finalize would give it alone.  All kc_server_* calls are
- * thread-safe.
+ * Job server with continuous batching (host-submitted jobs).  Two ingest
+ * threads admit queued jobs in arrival order as soon as their estimated
+ * device footprint fits device_budget_bytes and add their reads on their own
+ * streams; two finalize threads, each with its own batch object, repeatedly
+ * take every job ingested so far (at most max_batch) as one batch
+ * (kc_batch_finalize), copy the results into pinned host blocks (one pool
+ * per process, reused across jobs and servers and kept until the process
+ * exits, up to 8 GiB; ordinary host memory past that) and release the jobs'
+ * device memory.  Jobs that arrive while a batch runs are ingested at
+ * once and join a next batch.  Each job's result is the one kc_finalize would
+ * give it alone.  All kc_server_* calls are thread-safe.
  */
 typedef struct kc_server_ctx* kc_server;
 

@@ -63,6 +63,11 @@ bool is_device_ptr(const void* p) {
 
 namespace kc {
 void set_last_error(const std::string& msg) { kcapi::g_last_error = msg; }
+
+std::mutex& sync_api_mutex() {
+    static std::mutex m;
+    return m;
+}
 }  // namespace kc
 
 
@@ -129,6 +134,7 @@ void release_spill(kc_handle h) {
 }
 
 void free_spill_chunks(kc_handle h) {
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     for (auto& c : h->spill_chunks) cudaFreeHost(c.p);
     h->spill_chunks.clear();
 }
@@ -144,6 +150,7 @@ uint64_t* spill_alloc(kc_handle h, uint64_t words) {
         }
     PinnedChunk c;
     c.words = std::max<uint64_t>(words, 32ull << 20);
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     if (cudaMallocHost(&c.p, c.words * 8) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -297,7 +304,7 @@ kc_status regroup_batch(kc_handle h, Batch& b, cudaStream_t st) {
     kc::launch_regroup_base(rel, starts, dsegs, nv, a2, st);
     kc::launch_scatter_staged_seg(b.hdata, dsegs, (int)nv, a1, a2, rel, out, st);
     h->launches += 5;
-    KC_CUDA(cudaGetLastError());
+    KC_LAUNCHED("second-level bucketing launches");
     for (void* q : {(void*)counts, (void*)total, (void*)dvlo, (void*)rel, (void*)cursor, (void*)dsegs})
         cudaFreeAsync(q, st);
     cudaFreeAsync(b.hdata, st);
@@ -411,7 +418,7 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
     kc::launch_bucket_sort_warp(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, h->grid, st);
     phase_end(h, kSort, t0);
     h->launches += 4;
-    KC_CUDA(cudaGetLastError());
+    KC_LAUNCHED("sort launches");
     kc_status s = read_counters(h);
     if (s != KC_OK) return s;
     if (h->host_ctr.err & kc::DERR_INTERNAL) {
@@ -421,7 +428,7 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
     if (h->host_ctr.err & kc::DERR_SORT_MEDIUM) {
         kc::launch_bucket_sort(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, st);
         h->launches += 1;
-        KC_CUDA(cudaGetLastError());
+        KC_LAUNCHED("medium sort launch");
         if ((s = read_counters(h)) != KC_OK) return s;
     }
     if (h->host_ctr.err & kc::DERR_SORT_BUCKET) {
@@ -439,7 +446,7 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
                 kc::launch_bitonic_global(h->res_keys + hs[i], h->res_vals + hs[i], m, st);
                 h->launches += steps;
             }
-        KC_CUDA(cudaGetLastError());
+        KC_LAUNCHED("global sort launches");
     }
     if (h->host_ctr.err & (kc::DERR_SORT_MEDIUM | kc::DERR_SORT_BUCKET)) {
         unsigned zero = 0;
@@ -461,7 +468,7 @@ kc_status finalize_direct(kc_handle h) {
         kc::launch_pass2(b.pw, b.vw, b.n_units, h->params(b.sample), h->table, h->ctr, h->grid, st);
     phase_end(h, kPass2, t0);
     h->launches += h->batches.size();
-    KC_CUDA(cudaGetLastError());
+    KC_LAUNCHED("direct recount launch");
     kc_status s = read_counters(h);
     if (s != KC_OK) return s;
     if ((s = device_errors(h)) != KC_OK) return s;
@@ -477,7 +484,7 @@ kc_status finalize_direct(kc_handle h) {
     kc::launch_compact(h->table, h->n_slots, h->n_samples, h->min_count, tk, tv, h->ctr, nullptr, 0, h->grid, st);
     phase_end(h, kCompact, t0);
     h->launches += 1;
-    KC_CUDA(cudaGetLastError());
+    KC_LAUNCHED("direct compaction launches");
     if ((s = read_counters(h)) != KC_OK) return s;
     s = sort_result(h, tk, tv);
     cudaFreeAsync(tk, st);
@@ -774,7 +781,7 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
         h->launches += 2;
     }
     phase_end(h, kPass1, t0);
-    KC_CUDA(cudaGetLastError());
+    KC_LAUNCHED("ingest launches");
     cudaFreeAsync(nm, st);
     cudaFreeAsync(bd, st);
     cudaFreeAsync(doff, st);
@@ -866,8 +873,10 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
             cout = mc.get();
         }
         merge_runs(h->spill_dir, kout, cout, h->n_samples);
-        if (dev_k) KC_CUDA(cudaMemcpy(keys, kout, h->n_result * 8, cudaMemcpyHostToDevice));
-        if (dev_c) KC_CUDA(cudaMemcpy(counts, cout, h->n_result * 4 * (size_t)h->n_samples, cudaMemcpyHostToDevice));
+        if (dev_k) KC_CUDA(cudaMemcpyAsync(keys, kout, h->n_result * 8, cudaMemcpyHostToDevice, st));
+        if (dev_c)
+            KC_CUDA(cudaMemcpyAsync(counts, cout, h->n_result * 4 * (size_t)h->n_samples, cudaMemcpyHostToDevice, st));
+        if (dev_k || dev_c) KC_CUDA(cudaStreamSynchronize(st));  // the staging buffers go out of scope
         return KC_OK;
     }
     KC_CUDA(cudaMemcpyAsync(keys, h->res_keys, h->n_result * 8, cudaMemcpyDefault, st));

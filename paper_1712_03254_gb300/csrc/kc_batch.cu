@@ -495,6 +495,7 @@ template <class T>
 kc_status grow(T*& p, size_t& cap, size_t need) {
     if (need <= cap) return KC_OK;
     size_t n = std::max<size_t>(need, cap * 2);
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
@@ -506,6 +507,7 @@ kc_status grow(T*& p, size_t& cap, size_t need) {
 kc_status ensure_jobs(kc_batch_ctx* b, size_t n_jobs, size_t n_items) {
     if (n_jobs > b->jobs_cap) {
         size_t n = std::max<size_t>(n_jobs, b->jobs_cap * 2);
+        std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
         if (b->d_jobs) cudaFree(b->d_jobs);
         if (b->d_counters) cudaFree(b->d_counters);
         b->d_jobs = nullptr;
@@ -524,6 +526,7 @@ kc_status ensure_jobs(kc_batch_ctx* b, size_t n_jobs, size_t n_items) {
 kc_status ensure_buckets(kc_batch_ctx* b, uint64_t n_buckets) {
     if (n_buckets <= b->buckets_cap) return KC_OK;
     const uint64_t n = std::max<uint64_t>(n_buckets, 1ull << 16);
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     if (b->d_hist) cudaFree(b->d_hist);
     if (b->d_starts) cudaFree(b->d_starts);
     if (b->d_cursor) cudaFree(b->d_cursor);
@@ -548,6 +551,7 @@ kc_status ensure_buckets(kc_batch_ctx* b, uint64_t n_buckets) {
 
 // Capture the sort sequence once; it reads everything else from d_desc.
 kc_status capture_sort_graph(kc_batch_ctx* b) {
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     cudaGraph_t g = nullptr;
     KC_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
     const dim3 grid2((unsigned)b->sm_count * 4, 32);
@@ -611,7 +615,7 @@ void release_work(kc_batch_ctx* b, std::vector<JobWork>& w) {
 
 template <int NH>
 cudaError_t launch_consume_nh(int n_ctas, size_t smem, const kc::BatchDesc* d, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(kc::k_consume_q<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = kc::allow_max_dynamic_smem(kc::k_consume_q<NH>);
     if (e != cudaSuccess) return e;
     kc::k_consume_q<NH><<<n_ctas, kc::kConsumeThreads, smem, st>>>(d);
     return cudaGetLastError();
@@ -706,7 +710,7 @@ kc_status run_fallbacks(kc_batch_ctx* b, JobWork& x, uint32_t j, uint32_t n_fail
         for (size_t t = 0; t < nb; ++t) kc::launch_fb_recount(F, (int)t, b->st);
         kc::launch_fb_compact(F, b->st);
         h->launches += 2 * nb + 1;
-        KC_CUDA(cudaGetLastError());
+        KC_LAUNCHED("fallback launches");
         cudaFreeAsync(table, b->st);
     }
     h->fallback_partitions += n_failed;
@@ -735,9 +739,12 @@ kc_status kc_batch_create_internal(cudaStream_t st, kc_batch_ctx** out) {
             return bail(cuda_fail(e, "cudaStreamCreate"));
         b->own_stream = true;
     }
-    if ((e = cudaMalloc(&b->d_desc, sizeof(kc::BatchDesc))) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_flags, 2 * sizeof(unsigned int))) != cudaSuccess)
-        return bail(cuda_fail(e, "cudaMalloc(batch descriptor)"));
+    {
+        std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
+        if ((e = cudaMalloc(&b->d_desc, sizeof(kc::BatchDesc))) != cudaSuccess ||
+            (e = cudaMalloc(&b->d_flags, 2 * sizeof(unsigned int))) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMalloc(batch descriptor)"));
+    }
     *out = b;
     return KC_OK;
 }
@@ -746,6 +753,7 @@ void kc_batch_destroy_internal(kc_batch_ctx* b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
     if (b->sort_graph) cudaGraphExecDestroy(b->sort_graph);
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     cudaFree(b->d_desc);
     cudaFree(b->d_flags);
     cudaFree(b->d_jobs);
@@ -913,7 +921,7 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         return fail(KC_ERR_CUDA, "consumer launch");
     }
     if (timed) phase_end(hs[0], kPass2, t0, st);
-    KC_CUDA(cudaGetLastError());
+    KC_LAUNCHED("consumer launch");
     std::vector<unsigned long long> cnt(2 * (size_t)n);
     KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
     KC_CUDA(cudaStreamSynchronize(st));
@@ -996,7 +1004,7 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     }
     if (err & kc::DERR_SORT_MEDIUM) {
         kc::k_medium_sort_q<<<(unsigned)b->sm_count * 4, 256, 0, st>>>(b->d_desc);
-        KC_CUDA(cudaGetLastError());
+        KC_LAUNCHED("batched medium sort launch");
         KC_CUDA(cudaMemcpyAsync(&err, b->d_flags + 1, 4, cudaMemcpyDeviceToHost, st));
         KC_CUDA(cudaStreamSynchronize(st));
         for (int j = 0; j < n; ++j) hs[j]->launches += 1;
@@ -1016,7 +1024,7 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
                 }
             }
         }
-        KC_CUDA(cudaGetLastError());
+        KC_LAUNCHED("batched global sort launches");
     }
     if (timed) phase_end(hs[0], kSort, t0, st);
     release_work(b, work);

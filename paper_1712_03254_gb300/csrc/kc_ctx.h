@@ -53,6 +53,13 @@ kc_status cuda_fail(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return kcapi::cuda_fail(e_, #call); \
     } while (0)
 
+// After kernel launches: the launch error, named by where it happened.
+#define KC_LAUNCHED(where)                                          \
+    do {                                                            \
+        cudaError_t e_ = cudaGetLastError();                        \
+        if (e_ != cudaSuccess) return kcapi::cuda_fail(e_, where);  \
+    } while (0)
+
 }  // namespace kcapi
 
 struct kc_ctx {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "kc_device.cuh"
@@ -12,6 +13,12 @@ namespace kc {
 
 // Message returned by kc_last_error() on this thread.
 void set_last_error(const std::string& msg);
+
+// Held while a stream is being captured into a graph and around every CUDA
+// call that may synchronise the device or the legacy stream (cudaMalloc,
+// cudaFree, cudaMallocHost, cudaFreeHost, cudaMemcpy), so that none of them
+// lands inside another host thread's capture.
+std::mutex& sync_api_mutex();
 
 struct Grid {
     int sm_count = 152;
@@ -125,5 +132,22 @@ void launch_fb_recount(const FallbackArgs& F, int bt, cudaStream_t st);
 void launch_fb_compact(const FallbackArgs& F, cudaStream_t st);
 void launch_prefix_hist(const uint64_t* keys, DevCounters* ctr, uint64_t cap, int shift, uint64_t n_buckets,
                         uint32_t* hist, const Grid& g, cudaStream_t st);
+
+// The device's opt-in shared memory per block (cached per device).
+int max_optin_smem();
+
+// Let func launch with as much dynamic shared memory as the device allows
+// beside its static shared memory.  The attribute belongs to the function and
+// is shared by every host thread, so it is always set to the same value, the
+// maximum, never to one launch's need: jobs launching on other threads cannot
+// lower it under each other.
+template <typename F>
+inline cudaError_t allow_max_dynamic_smem(F func) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_optin_smem() - (int)fa.sharedSizeBytes);
+}
 
 }  // namespace kc

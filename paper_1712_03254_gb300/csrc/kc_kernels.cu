@@ -15,6 +15,8 @@
 // Sort        bucket by top key bits, then sort each bucket in shared memory
 //             (bitonic network), giving ascending keys.
 
+#include <atomic>
+
 #include "kc_internal.h"
 
 namespace kc {
@@ -533,7 +535,7 @@ void launch_bucket_sort(uint64_t* keys, uint64_t* vals, const uint64_t* starts, 
     const size_t smem = 2 * sizeof(uint64_t) * kSortCap;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_bucket_sort);
         attr_set = true;
     }
     k_bucket_sort<<<(unsigned)n_buckets, kSortThreads, smem, st>>>(keys, vals, starts, ctr);
@@ -554,6 +556,18 @@ void launch_bitonic_global(uint64_t* keys, uint64_t* vals, uint64_t n, cudaStrea
 void launch_counts_narrow(const uint64_t* vals, uint64_t n, uint32_t* out, cudaStream_t st) {
     if (n == 0) return;
     k_counts_narrow<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(vals, n, out);
+}
+
+int max_optin_smem() {
+    static std::atomic<int> cache[64];  // per device; 0 = not queried yet
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int v = dev >= 0 && dev < 64 ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (!v) {
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (dev >= 0 && dev < 64) cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
 }
 
 }  // namespace kc

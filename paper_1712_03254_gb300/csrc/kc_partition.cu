@@ -604,7 +604,7 @@ size_t staged_scatter_smem(int a) {
 void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                          int n_ctas, const PassParams& p, int a, uint32_t* counts, cudaStream_t st) {
     const size_t smem = bucket_pass_smem(a);
-    cudaFuncSetAttribute(k_bucket_pass<kCountPerCta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_dynamic_smem(k_bucket_pass<kCountPerCta>);
     k_bucket_pass<kCountPerCta><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts, nullptr,
                                                            nullptr, nullptr);
 }
@@ -613,7 +613,7 @@ void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_uni
                           int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, SegDesc* seg,
                           uint64_t* lin, cudaStream_t st) {
     const size_t smem = bucket_pass_smem(a);
-    cudaFuncSetAttribute(k_extract_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_dynamic_smem(k_extract_count);
     k_extract_count<<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
                                                reinterpret_cast<unsigned long long*>(g_cursor), seg, lin);
 }
@@ -627,14 +627,14 @@ size_t staged_seg_smem(int a) {
 void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,
                                const uint64_t* base, uint64_t* out, cudaStream_t st) {
     const size_t smem = staged_seg_smem(a2);
-    cudaFuncSetAttribute(k_scatter_staged_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_dynamic_smem(k_scatter_staged_seg);
     k_scatter_staged_seg<<<n_segs, kLinThreads, smem, st>>>(src, segs, a1, a2, base, out);
 }
 
 void launch_count_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2, uint32_t* counts,
                       cudaStream_t st) {
     const size_t smem = bucket_pass_smem(a2);
-    cudaFuncSetAttribute(k_count_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_dynamic_smem(k_count_seg);
     k_count_seg<<<n_segs, 1024, smem, st>>>(src, segs, a1, a2, counts);
 }
 
@@ -670,14 +670,14 @@ void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_un
                            uint64_t* out, cudaStream_t st) {
     if (mode == kScatterStaged) {
         const size_t smem = staged_scatter_smem(a);
-        cudaFuncSetAttribute(k_bucket_scatter_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_bucket_scatter_staged);
         k_bucket_scatter_staged<<<n_ctas, kStagedThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, base, out);
     } else if (mode == kScatterCursor) {
         k_bucket_pass<kScatterCursor><<<n_ctas, 512, 0, st>>>(pw, vw, n_units, units_per_cta, p, a, nullptr, nullptr,
                                                              reinterpret_cast<unsigned long long*>(cursor), out);
     } else {
         const size_t smem = bucket_pass_smem(a);
-        cudaFuncSetAttribute(k_bucket_pass<kScatterRegion>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_dynamic_smem(k_bucket_pass<kScatterRegion>);
         k_bucket_pass<kScatterRegion><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, nullptr, base,
                                                                  nullptr, out);
     }

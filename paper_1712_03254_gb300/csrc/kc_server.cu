@@ -30,10 +30,13 @@
 #include <cuda_runtime.h>
 
 #include "../../include/kc.h"
+#include "kc_internal.h"
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kIngestThreads = 2;
+constexpr int kFinalizeThreads = 2;
 
 struct Job {
     uint64_t id = 0;
@@ -44,9 +47,77 @@ struct Job {
     kc_status status = KC_OK;
     std::string error;
     bool done = false;
-    std::vector<uint64_t> keys;
-    std::vector<uint32_t> counts;
+    // the result in host memory: pinned pool blocks (class >= 0) or, past the
+    // pool's cap, ordinary host memory (class -1)
+    uint64_t* keys = nullptr;
+    uint32_t* counts = nullptr;
+    int keys_class = -1, counts_class = -1;
+    uint64_t n_keys = 0;
 };
+
+// Pinned host blocks for results, in power-of-two size classes, reused across
+// jobs and across servers (one pool per process, kept until it exits): the
+// device-to-host copy of a result runs at full speed on the finalize thread,
+// and the copy into the caller's memory happens later in kc_server_result, on
+// the caller's thread.
+struct PinnedPool {
+    std::mutex mu;
+    std::map<int, std::vector<void*>> free_blocks;
+    uint64_t held = 0;
+    uint64_t cap = 8ull << 30;
+    static int size_class(uint64_t bytes) {
+        int c = 20;  // 1 MiB at least
+        while (c < 63 && (1ull << c) < bytes) ++c;
+        return c;
+    }
+    // A block of at least `bytes`; *cls = its class, or -1 (ordinary memory)
+    void* get(uint64_t bytes, int* cls) {
+        const int c = size_class(bytes);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = free_blocks.find(c);
+            if (it != free_blocks.end() && !it->second.empty()) {
+                void* p = it->second.back();
+                it->second.pop_back();
+                *cls = c;
+                return p;
+            }
+            if (held + (1ull << c) <= cap) {
+                void* p = nullptr;
+                std::lock_guard<std::mutex> sync_lk(kc::sync_api_mutex());
+                if (cudaMallocHost(&p, 1ull << c) == cudaSuccess) {
+                    held += 1ull << c;
+                    *cls = c;
+                    return p;
+                }
+                cudaGetLastError();
+            }
+        }
+        *cls = -1;
+        return ::operator new(bytes, std::nothrow);
+    }
+    void put(void* p, int cls) {
+        if (!p) return;
+        if (cls < 0) {
+            ::operator delete(p);
+            return;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        free_blocks[cls].push_back(p);
+    }
+};
+
+PinnedPool& result_pool() {
+    static PinnedPool* pool = new PinnedPool();  // never destroyed: the CUDA context may be gone at exit
+    return *pool;
+}
+
+void free_result(PinnedPool& pool, Job& j) {
+    pool.put(j.keys, j.keys_class);
+    pool.put(j.counts, j.counts_class);
+    j.keys = nullptr;
+    j.counts = nullptr;
+}
 
 }  // namespace
 
@@ -61,9 +132,13 @@ struct kc_server_ctx {
     std::map<uint64_t, std::shared_ptr<Job>> jobs;
     uint64_t next_id = 1, in_use = 0, peak = 0;
     bool stop = false;
-    std::thread t_ingest, t_final;
-    kc_batch batch = nullptr;
+    // two ingest threads (pageable host copies run in parallel) and two
+    // finalize threads, each with its own batch object, so one batch's
+    // copy-out overlaps the next batch's kernels
+    std::vector<std::thread> t_ingest, t_final;
+    std::vector<kc_batch> batch;
     int device = 0;
+    PinnedPool& pool = result_pool();
     // statistics
     std::vector<double> latencies_ms;
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_jobs = 0;
@@ -149,7 +224,7 @@ void ingest_loop(kc_server_ctx* S) {
     }
 }
 
-void finalize_loop(kc_server_ctx* S) {
+void finalize_loop(kc_server_ctx* S, int idx) {
     cudaSetDevice(S->device);
     for (;;) {
         std::vector<std::shared_ptr<Job>> run;
@@ -168,23 +243,30 @@ void finalize_loop(kc_server_ctx* S) {
             hs.push_back(j->h);
             j->t_fstart = t_start;
         }
-        kc_status st = kc_batch_finalize(S->batch, hs.data(), (int)hs.size());
+        kc_status st = kc_batch_finalize(S->batch[idx], hs.data(), (int)hs.size());
         for (auto& j : run) {
             kc_status js = st;
             uint64_t n = 0;
             if (js == KC_OK) js = kc_dump(j->h, nullptr, nullptr, 0, &n);
             if (js == KC_OK) {
-                j->keys.resize(n);
-                j->counts.resize(n * (size_t)j->spec.n_samples);
-                if (n) js = kc_dump(j->h, j->keys.data(), j->counts.data(), n, &n);
+                j->keys = static_cast<uint64_t*>(S->pool.get(std::max<uint64_t>(1, n) * 8, &j->keys_class));
+                j->counts = static_cast<uint32_t*>(
+                    S->pool.get(std::max<uint64_t>(1, n * (size_t)j->spec.n_samples) * 4, &j->counts_class));
+                if (!j->keys || !j->counts) js = KC_ERR_OOM_HOST;
+                else if (n) js = kc_dump(j->h, j->keys, j->counts, n, &n);
+                j->n_keys = n;
+            }
+            if (js == KC_OK) {
+                kc_destroy(j->h);  // outside the lock: it waits for the job's stream
+                j->h = nullptr;
+            } else {
+                free_result(S->pool, *j);
             }
             std::lock_guard<std::mutex> lk(S->mu);
             if (js != KC_OK) {
                 fail_job(S, j, js);
                 continue;
             }
-            kc_destroy(j->h);
-            j->h = nullptr;
             j->t_done = Clock::now();
             j->done = true;
             S->in_use -= j->footprint;
@@ -232,13 +314,19 @@ kc_status kc_server_create_ex(uint64_t device_budget_bytes, int max_batch, uint3
     S->max_batch = max_batch;
     S->flags = flags;
     cudaGetDevice(&S->device);
-    kc_status st = kc_batch_create(nullptr, &S->batch);
+    kc_status st = KC_OK;
+    for (int i = 0; st == KC_OK && i < kFinalizeThreads; ++i) {
+        kc_batch b = nullptr;
+        st = kc_batch_create(nullptr, &b);
+        if (st == KC_OK) S->batch.push_back(b);
+    }
     if (st != KC_OK) {
+        for (kc_batch b : S->batch) kc_batch_destroy(b);
         delete S;
         return st;
     }
-    S->t_ingest = std::thread(ingest_loop, S);
-    S->t_final = std::thread(finalize_loop, S);
+    for (int i = 0; i < kIngestThreads; ++i) S->t_ingest.emplace_back(ingest_loop, S);
+    for (int i = 0; i < kFinalizeThreads; ++i) S->t_final.emplace_back(finalize_loop, S, i);
     *out = S;
     return KC_OK;
 }
@@ -291,7 +379,8 @@ kc_status kc_server_wait(kc_server S, uint64_t job_id, double timeout_s, uint64_
     } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
         return KC_ERR_TIMEOUT;
     }
-    if (n_keys) *n_keys = j->keys.size();
+    if (j->status != KC_OK) kc::set_last_error(j->error);  // the job's own message, for this thread
+    if (n_keys) *n_keys = j->n_keys;
     if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
     return j->status;
 }
@@ -305,11 +394,12 @@ kc_status kc_server_result(kc_server S, uint64_t job_id, uint64_t* keys, uint32_
     std::shared_ptr<Job> j = it->second;
     if (!j->done) return KC_ERR_STATE;
     if (j->status != KC_OK) return j->status;
-    if (n_out) *n_out = j->keys.size();
+    if (n_out) *n_out = j->n_keys;
     if (!keys) return KC_OK;
-    if (capacity < j->keys.size()) return KC_ERR_CAPACITY;
-    std::memcpy(keys, j->keys.data(), j->keys.size() * 8);
-    if (counts) std::memcpy(counts, j->counts.data(), j->counts.size() * 4);
+    if (capacity < j->n_keys) return KC_ERR_CAPACITY;
+    std::memcpy(keys, j->keys, j->n_keys * 8);
+    if (counts) std::memcpy(counts, j->counts, j->n_keys * (size_t)j->spec.n_samples * 4);
+    free_result(S->pool, *j);
     S->jobs.erase(it);  // the result has been handed over
     return KC_OK;
 }
@@ -348,11 +438,12 @@ void kc_server_destroy(kc_server S) {
     }
     S->cv_ingest.notify_all();
     S->cv_final.notify_all();
-    if (S->t_ingest.joinable()) S->t_ingest.join();
-    if (S->t_final.joinable()) S->t_final.join();
+    for (auto& t : S->t_ingest) t.join();
+    for (auto& t : S->t_final) t.join();
     for (auto& d : S->ingested)
         if (d->h) kc_destroy(d->h);
-    kc_batch_destroy(S->batch);
+    for (auto& kv : S->jobs) free_result(S->pool, *kv.second);  // results never collected
+    for (kc_batch b : S->batch) kc_batch_destroy(b);
     delete S;
 }
 

@@ -79,6 +79,7 @@ kc_status batch_bases(const kc_tune_input& in, uint64_t* out) {
     if (!in.n_reads) return KC_OK;
     if (!in.offsets) return tune_fail(KC_ERR_ARG, "tuning input without offsets");
     uint64_t ends[2];
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     if (cudaMemcpy(&ends[0], in.offsets, 8, cudaMemcpyDefault) != cudaSuccess ||
         cudaMemcpy(&ends[1], in.offsets + in.n_reads, 8, cudaMemcpyDefault) != cudaSuccess) {
         cudaGetLastError();
