@@ -143,6 +143,54 @@ def test_many_batches_full_recount(oracle_mod):
     assert_same_result(c, o)
 
 
+@pytest.mark.parametrize("n_hashes", [1, 7, 10])
+def test_bits_per_key_extremes(oracle_mod, n_hashes, strategy):
+    """One and ten filter bits per key (the smallest and largest accepted), and
+    an odd count in between: the filter words and the counts."""
+    w = synth.tiny(scale=0.3)
+    w.n_hashes = n_hashes
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy=strategy)
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+
+
+def test_smallest_filter_many_false_positives(oracle_mod, strategy):
+    """A 4096-bit filter (the minimum) for about 136,000 windows: almost every window
+    is a candidate, the exact recount still drops every singleton."""
+    w = synth.tiny(scale=0.1)
+    w.bloom_bits = 1 << 12
+    w.table_slots = 1 << 20  # direct: every distinct key becomes a candidate
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy=strategy, part_bits=1 if strategy == "partitioned" else 0)
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    assert c.stats()["candidates"] > 0.9 * o.windows
+
+
+def test_largest_partition_count(oracle_mod):
+    """20 partition bits (the maximum: 2^20 partitions in two levels) over a
+    2^34-bit filter (2 GiB, slices of 256 words)."""
+    w = synth.tiny(scale=0.3)
+    w.bloom_bits = 1 << 34
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy="partitioned", part_bits=20)
+    assert c.stats()["partitions"] == 1 << 20
+    assert_same_result(c, o)
+    nw = w.bloom_bits // 64
+    for first in (0, nw // 3, nw - 4096):  # three stretches of the 2^28 filter words
+        assert np.array_equal(c.export_bloom(first, 4096), o.bloom(first, 4096))
+
+
+def test_high_min_count_keeps_nothing(oracle_mod, strategy):
+    w = synth.tiny(scale=0.2)
+    w.min_count = 1000
+    o = oracle_mod.count(w)
+    c = gpu_count(w, strategy=strategy)
+    assert c.result_size() == 0 == len(o.result()[0])
+    assert_same_bloom(c, o)
+
+
 def test_two_samples_joint_table(oracle_mod, strategy):
     w = synth.paired(scale=0.002)
     o = oracle_mod.count(w)
