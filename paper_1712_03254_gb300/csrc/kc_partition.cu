@@ -353,6 +353,9 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
                     nx[e] = __ldcg(src + s0 + next);
                     nval |= 1u << e;
                 }
+                // the rows after these start their way into L2 now
+                const uint64_t ahead = next + kLinPerThread * blockDim.x;
+                if (ahead < len) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + s0 + ahead));
                 next += blockDim.x;
             }
         }
