@@ -333,7 +333,9 @@ def run_kc(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = init_dist(world, "nccl")
-    stream = torch.cuda.current_stream()
+    # the library's work and the step events share one stream (a real one:
+    # the legacy default stream would give the handle a stream of its own)
+    stream = torch.cuda.Stream()
 
     w = make_inputs(rank, args.workload)
     rs = w.samples[0]
@@ -412,7 +414,8 @@ def run_kc(args):
     barrier(dist)
     torch.cuda.synchronize()
     for _ in range(args.steps):
-        flush.zero_()  # write 256 MiB between steps: the next step starts with a cold L2
+        with torch.cuda.stream(stream):
+            flush.zero_()  # write 256 MiB between steps: the next step starts with a cold L2
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
