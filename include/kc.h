@@ -79,7 +79,9 @@ typedef enum kc_status {
 typedef struct kc_config {
     uint32_t struct_size;         /* sizeof(kc_config), for ABI growth             */
     uint32_t block_threads;       /* threads per CTA of the streaming kernels       */
-    uint32_t ctas_per_sm;         /* resident CTAs per SM for grid sizing           */
+    uint32_t ctas_per_sm;         /* resident CTAs per SM for grid sizing (<= 64);
+                                     partitioned: extraction CTAs per SM, i.e. the
+                                     reads each extraction CTA takes               */
     uint32_t part_bits;           /* partitioned: log2 of the number of hash-prefix
                                      partitions (1..20; above 12 the hashes are
                                      grouped in two levels)                         */

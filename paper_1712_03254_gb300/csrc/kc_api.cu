@@ -567,6 +567,7 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
         return fail(KC_ERR_ARG, "smem_table_log2 must be in 10..13");
     if (c.split_max != KC_SPLIT_NONE && c.split_max > 13) return fail(KC_ERR_ARG, "split_max must be in 0..13");
     if (c.spill > 2) return fail(KC_ERR_ARG, "spill must be 0, 1 or 2");
+    if (c.ctas_per_sm > 64) return fail(KC_ERR_ARG, "ctas_per_sm must be in 0..64");
     // Partitions: filter slices of 4096 words (32 KiB) unless set; the
     // partitioned strategy needs a slice of at most 8192 words in shared memory.
     const int lw = log2_exact(bloom_bits / 64);

@@ -108,3 +108,13 @@ def test_partitioned_slice_limit(bloom_log2, part_bits, ok):
     with pytest.raises(kc.KcError) as e:
         kc.KmerCounter(31, 1, 1 << bloom_log2, 4, 2, strategy="partitioned", part_bits=part_bits)
     assert e.value.name == "KC_ERR_ARG"
+
+
+@pytest.mark.parametrize("kw", [dict(ctas_per_sm=65), dict(smem_table_log2=9), dict(smem_table_log2=14),
+                                dict(split_max=14), dict(spill=3), dict(scatter_mode=5), dict(table_slots=1000),
+                                dict(strategy="direct", table_slots=512)])
+def test_config_knobs_out_of_range(kw):
+    """Tuning knobs outside their documented ranges are rejected before any CUDA call."""
+    with pytest.raises(kc.KcError) as e:
+        kc.KmerCounter(31, 1, 1 << 24, 4, 2, **kw)
+    assert e.value.name == "KC_ERR_ARG"
