@@ -411,9 +411,10 @@ class KcServer:
     def wait(self, job_id: int, timeout_s: float = -1.0):
         n = ctypes.c_uint64()
         lat = ctypes.c_double()
-        _check(self._L.kc_server_wait(self._s, job_id, timeout_s, ctypes.byref(n), ctypes.byref(lat)),
-               "kc_server_wait")
-        self._keep.pop(job_id, None)
+        st = self._L.kc_server_wait(self._s, job_id, timeout_s, ctypes.byref(n), ctypes.byref(lat))
+        if STATUS[st] != "KC_ERR_TIMEOUT":  # the job is done: the server no longer reads its inputs
+            self._keep.pop(job_id, None)
+        _check(st, "kc_server_wait")
         return n.value, lat.value
 
     def result(self, job_id: int):

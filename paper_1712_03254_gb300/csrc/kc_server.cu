@@ -342,12 +342,16 @@ static bool host_memory(const void* p) {
 }
 
 kc_status kc_server_submit(kc_server S, const kc_job_spec* spec, uint64_t* job_id) {
-    if (!S || !spec || !job_id) return KC_ERR_ARG;
-    if (spec->n_samples < 1 || spec->n_samples > 2) return KC_ERR_ARG;
+    const auto bad = [](const char* msg) {
+        kc::set_last_error(msg);
+        return KC_ERR_ARG;
+    };
+    if (!S || !spec || !job_id) return bad("kc_server_submit: null argument");
+    if (spec->n_samples < 1 || spec->n_samples > 2) return bad("n_samples must be 1 or 2");
     for (int i = 0; i < spec->n_samples; ++i) {
-        if (spec->n_reads[i] && !spec->offsets[i]) return KC_ERR_ARG;
+        if (spec->n_reads[i] && !spec->offsets[i]) return bad("a sample with reads has no offsets");
         if (!host_memory(spec->offsets[i]) || !host_memory(spec->packed[i]) || !host_memory(spec->n_mask[i]))
-            return KC_ERR_ARG;
+            return bad("server jobs take host arrays");
     }
     auto j = std::make_shared<Job>();
     j->spec = *spec;

@@ -101,3 +101,24 @@ def test_wait_timeout_and_unknown_job():
         srv.wait(12345, timeout_s=0.01)
     assert e.value.name == "KC_ERR_ARG"
     srv.close()
+
+
+def test_failed_job_reports_its_error_and_others_complete(oracle_mod):
+    """A job the library rejects (k = 40) fails with its own status and
+    message; the jobs around it complete with their exact results."""
+    good = _jobs(9, 2)
+    srv = kc.KcServer(device_budget_bytes=4 << 30, max_batch=4)
+    packed, mask = kc.pack_ascii(good[0].samples[0].ascii)
+    bad_id = srv.submit(40, good[0].bloom_bits, 4, 2, [(packed, good[0].samples[0].offsets, mask)])
+    ids = [srv.submit_workload(w) for w in good]
+    with pytest.raises(kc.KcError) as e:
+        srv.wait(bad_id, timeout_s=120)
+    assert e.value.name == "KC_ERR_ARG" and "k must be" in str(e.value)
+    for i, w in zip(ids, good):
+        srv.wait(i, timeout_s=120)
+        keys, counts = srv.result(i)
+        ok, oc = oracle_mod.count(w).result()
+        assert np.array_equal(keys, ok) and np.array_equal(counts, oc)
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == len(good)
+    srv.close()
