@@ -472,6 +472,12 @@ def run_kc(args):
 
     served = None
     if rank == 0 and world == 1 and not args.no_served and args.workload == "mid":
+        # the mid job's buffers are not needed any more: the stream of jobs
+        # starts from a device holding only what it allocates itself
+        c.close()
+        del chunks_d, d_keys, d_counts, flush
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
         served = run_served_trace(args.served_jobs, args.served_max_reads)
 
     if rank == 0:
