@@ -66,6 +66,14 @@ def _load():
         lib.orc_partitions.restype = i
         lib.orc_canonical.argtypes = [ctypes.c_char_p, i]
         lib.orc_canonical.restype = u64
+        lib.orc_items16.argtypes = [p, p, u64]
+        lib.orc_items16.restype = ctypes.c_int64
+        lib.orc_spectrum.argtypes = [p, u32, p]
+        lib.orc_spectrum.restype = i
+        lib.orc_filter_select.argtypes = [p, i, u32, u32, u32, p, p, u64]
+        lib.orc_filter_select.restype = ctypes.c_int64
+        lib.orc_filter_reads.argtypes = [p, i, u32, u32, u32, p, p, u64, p]
+        lib.orc_filter_reads.restype = ctypes.c_int64
         lib.orc_destroy.argtypes = [p]
         lib.orc_destroy.restype = None
         _lib = lib
@@ -162,6 +170,49 @@ class Oracle:
 
     def bloom_pattern(self, key: int) -> int:
         return int(self._lib.orc_bloom_pattern(self._h, key))
+
+
+    def items16(self) -> np.ndarray:
+        """The result as 16-byte items (uint8[n, 16]): key, two clamped 16-bit counts, padding."""
+        n = int(self._lib.orc_result_size(self._h))
+        out = np.zeros((n, 16), dtype=np.uint8)
+        if self._lib.orc_items16(self._h, out.ctypes.data, n) != n:
+            raise RuntimeError("oracle: items16")
+        return out
+
+    def spectrum(self, cap: int) -> np.ndarray:
+        """Joint count spectrum, uint64[(cap+1)] or uint64[cap+1, cap+1] (clamped counts)."""
+        shape = (cap + 1,) if self.n_samples == 1 else (cap + 1, cap + 1)
+        out = np.zeros(shape, dtype=np.uint64)
+        if self._lib.orc_spectrum(self._h, cap, out.ctypes.data) != 0:
+            raise ValueError("oracle: spectrum")
+        return out
+
+    def filter_select(self, tumor: int = 1, min_tumor: int = 2, max_normal: int = 0, ratio: int = 0):
+        """(keys uint64[n], counts uint32[n, 2]) of the selected result keys, ascending."""
+        n = self._lib.orc_filter_select(self._h, tumor, min_tumor, max_normal, ratio, None, None, 0)
+        if n < 0:
+            raise ValueError("oracle: filter_select")
+        keys = np.zeros(n, dtype=np.uint64)
+        counts = np.zeros((n, 2), dtype=np.uint32)
+        got = self._lib.orc_filter_select(self._h, tumor, min_tumor, max_normal, ratio, keys.ctypes.data,
+                                          counts.ctypes.data, n)
+        if got != n:
+            raise RuntimeError("oracle: filter_select size changed")
+        return keys, counts
+
+    def filter_reads(self, reads, tumor: int = 1, min_tumor: int = 2, max_normal: int = 0, ratio: int = 0):
+        """(hits uint32[n_reads], number of candidate reads) for a read set."""
+        ascii = np.ascontiguousarray(reads.ascii, dtype=np.uint8)
+        offs = np.ascontiguousarray(reads.offsets, dtype=np.uint64)
+        n_reads = len(offs) - 1
+        hits = np.zeros(max(1, n_reads), dtype=np.uint32)
+        got = self._lib.orc_filter_reads(self._h, tumor, min_tumor, max_normal, ratio,
+                                         ascii.ctypes.data if ascii.size else None, offs.ctypes.data, n_reads,
+                                         hits.ctypes.data)
+        if got < 0:
+            raise ValueError("oracle: filter_reads")
+        return hits[:n_reads], int(got)
 
 
 def count(workload, restrict=None):

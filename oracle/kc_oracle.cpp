@@ -13,8 +13,8 @@
 //     A/C/G/T is skipped: the reads' quality screen (Section III-A) is read
 //     as "drop windows over unknown bases".
 //  2. Each base takes 2 bits, A=0 C=1 G=2 T=3, first base most significant, so
-//     a k-mer is one 64-bit word (Section II-A, "64 bits per k-mer -- 2 bits
-//     per each base") and numeric order equals lexicographic order.
+//     a k-mer is one 64-bit word (Section II-A: two bits per base, one 64-bit
+//     number per k-mer) and numeric order equals lexicographic order.
 //  3. A k-mer and its reverse complement are the same key: key = min(fwd, rc),
 //     rc being the encoding of the reversed, complemented string.  (The paper
 //     does not discuss strands; canonical keys are this library's reading.)
@@ -32,6 +32,26 @@
 //     "Fast splittable pseudorandom number generators", OOPSLA 2014): add the
 //     golden-ratio increment, then two xor-shift/multiply rounds and a final
 //     xor-shift.  The paper names no hash function; this is the library's.
+//
+// Downstream of the count (Section II-B: the Count unit's table is read by
+// the Filter unit; Section III-D: the table's 16-byte k-mer items):
+//
+//  7. 16-byte items: per result key, in ascending order, 8 bytes of key, then
+//     the two per-sample counts as 16-bit numbers (both counts share 4 bytes
+//     in the paper's item), each clamped to 65535, then 4 zero bytes of padding.
+//     A one-sample job writes 0 as the second count.
+//  8. Joint spectrum: hist[min(c0, cap) * (cap + 1) + min(c1, cap)] = number
+//     of result keys with those clamped counts (two samples), hist[min(c0,
+//     cap)] for one sample.
+//  9. Filter selection (Section II-B, Filter unit: k-mers whose frequencies
+//     differ between the samples).  The paper states no threshold; the
+//     library's reading: with t the tumoral sample and n the other, a result
+//     key is selected iff
+//        count[t] >= min_tumor  and  count[n] <= max_normal  and
+//        count[t] >= ratio * count[n]      (ratio 0: no ratio test).
+// 10. Filter read hits (the Filter unit reads the input again and looks its
+//     k-mers up in the table): hits[r] = number of valid windows of read r
+//     whose key is selected; a read is a candidate iff hits[r] > 0.
 //
 // Partition-restricted runs (for inputs too large to count in full here):
 // when a keep-set over the top q bits of h is given, windows whose key falls
@@ -159,6 +179,23 @@ struct Oracle {
         }
     }
 
+    bool selected(const std::vector<uint32_t>& c, int tumor, uint32_t min_tumor, uint32_t max_normal,
+                  uint32_t ratio) const {
+        uint64_t t = c[tumor], n = c[1 - tumor];
+        if (t < min_tumor) return false;
+        if (n > max_normal) return false;
+        if (t < (uint64_t)ratio * n) return false;
+        return true;
+    }
+
+    // Result keys selected by the filter, ascending.
+    std::vector<uint64_t> filter_keys(int tumor, uint32_t min_tumor, uint32_t max_normal, uint32_t ratio) const {
+        std::vector<uint64_t> out;
+        for (uint64_t key : result_keys())
+            if (selected(counts.at(key), tumor, min_tumor, max_normal, ratio)) out.push_back(key);
+        return out;
+    }
+
     std::vector<uint64_t> result_keys() const {
         std::vector<uint64_t> keys;
         for (const auto& kv : counts) {
@@ -281,6 +318,98 @@ uint64_t orc_canonical(const char* s, int k) {
     std::vector<char> rc((size_t)k);
     for (int t = 0; t < k; ++t) rc[t] = complement_base(s[k - 1 - t]);
     return std::min(encode(s, k), encode(rc.data(), k));
+}
+
+// 16-byte items of the result (item 7 above): 16 bytes per key written to out
+// (little-endian fields at byte offsets 0, 8, 10, 12).  Returns the number of
+// items, -1 if capacity (in items) is too small.
+int64_t orc_items16(void* h, uint8_t* out, uint64_t capacity) {
+    Oracle* o = (Oracle*)h;
+    std::vector<uint64_t> ks = o->result_keys();
+    if (ks.size() > capacity) return -1;
+    for (size_t i = 0; i < ks.size(); ++i) {
+        const auto& c = o->counts.at(ks[i]);
+        uint16_t c16[2] = {0, 0};
+        for (int s = 0; s < o->n_samples; ++s) c16[s] = c[s] > 65535u ? 65535u : (uint16_t)c[s];
+        uint32_t pad = 0;
+        uint8_t* item = out + 16 * i;
+        std::memcpy(item, &ks[i], 8);
+        std::memcpy(item + 8, &c16[0], 2);
+        std::memcpy(item + 10, &c16[1], 2);
+        std::memcpy(item + 12, &pad, 4);
+    }
+    return (int64_t)ks.size();
+}
+
+// Joint spectrum of the result (item 8): hist has (cap+1)^n_samples entries.
+int orc_spectrum(void* h, uint32_t cap, uint64_t* hist) {
+    Oracle* o = (Oracle*)h;
+    if (!o || cap < 1 || !hist) return -1;
+    const uint64_t side = (uint64_t)cap + 1;
+    const uint64_t n_bins = o->n_samples == 2 ? side * side : side;
+    for (uint64_t b = 0; b < n_bins; ++b) hist[b] = 0;
+    for (uint64_t key : o->result_keys()) {
+        const auto& c = o->counts.at(key);
+        uint64_t bin = std::min<uint64_t>(c[0], cap);
+        if (o->n_samples == 2) bin = bin * side + std::min<uint64_t>(c[1], cap);
+        ++hist[bin];
+    }
+    return 0;
+}
+
+// Filter selection (item 9): keys and counts (n_samples per key) of the
+// selected result keys, ascending.  keys == nullptr: size only.  Returns the
+// number of keys; -1 for invalid arguments or too small a capacity.
+int64_t orc_filter_select(void* h, int tumor, uint32_t min_tumor, uint32_t max_normal, uint32_t ratio,
+                          uint64_t* keys, uint32_t* counts, uint64_t capacity) {
+    Oracle* o = (Oracle*)h;
+    if (!o || o->n_samples != 2 || tumor < 0 || tumor > 1) return -1;
+    std::vector<uint64_t> ks = o->filter_keys(tumor, min_tumor, max_normal, ratio);
+    if (!keys) return (int64_t)ks.size();
+    if (ks.size() > capacity) return -1;
+    for (size_t i = 0; i < ks.size(); ++i) {
+        keys[i] = ks[i];
+        const auto& c = o->counts.at(ks[i]);
+        counts[2 * i] = c[0];
+        counts[2 * i + 1] = c[1];
+    }
+    return (int64_t)ks.size();
+}
+
+// Filter read hits (item 10) of n_reads ASCII reads: hits[r] per read.
+// Returns the number of candidate reads (hits > 0), -1 on invalid arguments.
+int64_t orc_filter_reads(void* h, int tumor, uint32_t min_tumor, uint32_t max_normal, uint32_t ratio,
+                         const char* ascii, const uint64_t* offsets, uint64_t n_reads, uint32_t* hits) {
+    Oracle* o = (Oracle*)h;
+    if (!o || o->n_samples != 2 || tumor < 0 || tumor > 1 || !offsets || (n_reads && !hits)) return -1;
+    if (!ascii && n_reads && offsets[n_reads] != offsets[0]) return -1;
+    std::vector<uint64_t> ks = o->filter_keys(tumor, min_tumor, max_normal, ratio);
+    std::unordered_map<uint64_t, bool> sel;
+    for (uint64_t key : ks) sel[key] = true;
+    const int k = o->k;
+    std::vector<char> rc_buf((size_t)k);
+    int64_t candidates = 0;
+    for (uint64_t r = 0; r < n_reads; ++r) {
+        if (offsets[r + 1] < offsets[r]) return -1;
+        const char* s = ascii + offsets[r];
+        const uint64_t len = offsets[r + 1] - offsets[r];
+        uint32_t n_hits = 0;
+        for (uint64_t j = 0; len >= (uint64_t)k && j + (uint64_t)k <= len; ++j) {
+            bool valid = true;
+            for (int t = 0; t < k; ++t)
+                if (base_code(s[j + t]) < 0) {
+                    valid = false;
+                    break;
+                }
+            if (!valid) continue;
+            for (int t = 0; t < k; ++t) rc_buf[t] = complement_base(s[j + k - 1 - t]);
+            const uint64_t key = std::min(encode(s + j, k), encode(rc_buf.data(), k));
+            if (sel.count(key)) ++n_hits;
+        }
+        hits[r] = n_hits;
+        if (n_hits) ++candidates;
+    }
+    return candidates;
 }
 
 void orc_destroy(void* h) { delete (Oracle*)h; }
