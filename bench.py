@@ -27,6 +27,11 @@ distinct k-mer) through one-at-a-time plain jobs and through the
 continuous-batching server, at 0.7 and 0.9 of the plain capacity and all at
 once; latencies count from each job's scheduled arrival.
 
+The "filter" field times the Filter unit downstream of the count on a
+paired normal/tumour job of 2 x 1,000,000 reads: the selection of imbalanced
+k-mers once, then per step both samples' reads rescanned against it (hits per
+read and the candidate reads), device-resident and from pinned host memory.
+
 --impl reference times the CPU oracle (single thread, as it stands) on a
 bounded sample of the same workload.
 """
@@ -289,6 +294,149 @@ def roofline_of(st, phases, n_bases, w, sm_count, workload="mid", consume_launch
             "instructions_per_launch": prof["inst_executed_per_launch"], "hbm": hbm}
 
 
+FILTER_SOURCES = ("kc_filter.cu", "kc_device.cuh", "kc_internal.h", "kc_kernels.cu")
+FILTER_SPEC = (1, 4, 0, 0)  # tumour sample 1: k-mers seen >= 4 times in the tumour and never in the normal
+FILTER_WORKLOAD = ("paired normal/tumour at 1/10 size: 5 Mbp uniform ACGT genome and a tumour copy with 0.1% SNVs "
+                   "and 1-10 bp indels at 1e-5/base, 1,000,000 x 150 bp reads per sample (30x), 0.5% substitutions, "
+                   "0.05% N; k=31, Bloom 2^32 bits, 4 hashes, count >= 2; selection count[tumour] >= 4 and "
+                   "count[normal] = 0; both samples rescanned")
+
+
+def ncu_filter_kernel(kernel: str, workload: str):
+    """Per-launch ncu counters of a filter-unit kernel, if taken on the current filter sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_filter.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1712_03254_gb300", "csrc")
+    for f in FILTER_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    if d.get("source_hash") != h.hexdigest()[:16]:
+        return None
+    return d.get("workloads", {}).get(workload, {}).get(kernel)
+
+
+def filter_roofline(ms_per_launch, n_bases, n_reads, table_bytes, sm_count, workload):
+    """Roofline of k_filter_hits (one launch per read set).  Algorithmic bytes:
+    2 bits (packed base) + 1 bit (valid-window bit) per base, the 8-byte read
+    offsets read once, the selection's lookup table read once, 4 bytes of hit
+    count written per read."""
+    algo = (n_bases * 3 + 7) // 8 + 8 * (n_reads + 1) + table_bytes + 4 * n_reads
+    peak, peak_kind = measured_hbm_peak()
+    hbm_achieved = algo / (ms_per_launch / 1e3) / 1e9
+    hbm = {"achieved": round(hbm_achieved, 1), "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+           "frac": round(hbm_achieved / peak, 4)}
+    prof = ncu_filter_kernel("k_filter_hits", workload)
+    if prof is None:
+        return {"bound": "hbm", "kernel": "k_filter_hits", **hbm, "traffic": None, "algorithmic_bytes": int(algo),
+                "ms_per_launch": round(ms_per_launch, 4)}
+    ipk, mhz = issue_peak(sm_count)
+    achieved = prof["inst_executed_per_launch"] / (ms_per_launch / 1e3)
+    return {"bound": "alu", "kernel": "k_filter_hits", "achieved": round(achieved / 1e9, 1),
+            "peak": round(ipk / 1e9, 1),
+            "peak_source": f"derived: {sm_count} SMs x {ISSUE_PER_SM_CYCLE} warp instructions/cycle x {mhz:.0f} MHz",
+            "unit": "G warp instructions/s", "frac": round(achieved / ipk, 4),
+            "traffic": prof["dram_bytes_per_launch"], "algorithmic_bytes": int(algo),
+            "ms_per_launch": round(ms_per_launch, 4), "instructions_per_launch": prof["inst_executed_per_launch"],
+            "hbm": hbm}
+
+
+def run_filter_bench(dev, stream, steps: int, warmup: int, flush):
+    """Filter unit on a paired job: selection once, then every timed step
+    rescans both samples' device-resident reads (kc_filter_reads, hits and
+    candidate list into device buffers); e2e does the same from pinned host
+    reads into pinned host hits."""
+    import torch
+
+    import paper_1712_03254_gb300 as kc
+    import synth
+
+    w = synth.paired(scale=0.1)
+    c = kc.KmerCounter(w.k, 2, w.bloom_bits, w.n_hashes, w.min_count, timing=True, stream=stream)
+    ins_h, ins_d, outs_d, outs_h = [], [], [], []
+    for s_i, rs in enumerate(w.samples):
+        packed, mask = kc.pack_ascii(rs.ascii)
+        offsets = np.ascontiguousarray(rs.offsets, dtype=np.uint64)
+        hp = tuple(torch.from_numpy(a.view(np.int64)).pin_memory() for a in (packed, offsets, mask))
+        ins_h.append(hp)
+        ins_d.append(tuple(t.to(dev) for t in hp))
+        outs_d.append((torch.empty(rs.n_reads, dtype=torch.int32, device=dev),
+                       torch.empty(rs.n_reads, dtype=torch.int64, device=dev)))
+        outs_h.append((torch.empty(rs.n_reads, dtype=torch.int32).pin_memory(),
+                       torch.empty(rs.n_reads, dtype=torch.int64).pin_memory()))
+    torch.cuda.synchronize()
+    for s_i, (p_, o_, m_) in enumerate(ins_d):
+        c.add_reads(s_i, p_, o_, m_)
+    c.finalize()
+    t0 = time.perf_counter()
+    n_sel = c.filter_select(*FILTER_SPEC)
+    select_wall_ms = (time.perf_counter() - t0) * 1e3
+    st0 = c.stats()
+
+    def step(ins, outs):
+        n_c = 0
+        for (p_, o_, m_), (hits, cand) in zip(ins, outs):
+            n_c += c.filter_reads(p_, o_, m_, hits=hits, candidates=cand)[2]
+        return n_c
+
+    for _ in range(warmup):
+        step(ins_d, outs_d)
+    torch.cuda.synchronize()
+    base = c.stats()
+    ms, n_cand = [], 0
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # cold L2: the reads and the table are below its size
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n_cand = step(ins_d, outs_d)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = c.stats()
+    windows = (st["filter_windows"] - base["filter_windows"]) // steps
+    kernel_ms = (st["ms_filter_reads"] - base["ms_filter_reads"]) / (steps * 2)
+    launches = (st["launches"] - base["launches"]) // steps
+    for _ in range(max(1, warmup)):
+        step(ins_h, outs_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step(ins_h, outs_h)
+    e2e_s = (time.perf_counter() - t0) / steps
+    # the host hits must be the device ones
+    for (hh, _), (dh, _) in zip(outs_h, outs_d):
+        assert torch.equal(hh, dh.cpu()), "filter: host and device hits differ"
+    n_reads = sum(rs.n_reads for rs in w.samples)
+    lb = 8  # the selection's lookup table: 2^lb buckets of four keys, at most half full
+    while (4 << lb) < 2 * n_sel:
+        lb += 1
+    table_bytes = 32 << lb
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {
+        "workload": FILTER_WORKLOAD, "spec": dict(zip(("tumor", "min_tumor", "max_normal", "ratio"), FILTER_SPEC)),
+        "selected_keys": n_sel, "result_keys": st0["result_keys"], "candidate_reads": n_cand,
+        "reads": n_reads, "windows_per_step": int(windows),
+        "value": round(windows / (statistics.mean(ms) / 1e3), 1), "unit": "windows rescanned/s",
+        "ms_per_step": round(statistics.mean(ms), 4), "kernel_ms": round(kernel_ms, 4),
+        "select_ms": round(st0["ms_filter_select"], 4), "select_wall_ms": round(select_wall_ms, 3),
+        "gpu_launches_per_step": int(launches),
+        "roofline": filter_roofline(kernel_ms, w.n_bases // 2, n_reads // 2, table_bytes, sm_count, "paired-filter"),
+        "e2e": {"value": round(windows / e2e_s, 1), "unit": "windows rescanned/s",
+                "h2d_bytes_per_step": int(sum(t.numel() * 8 for ins in ins_h for t in ins)),
+                "d2h_bytes_per_step": int(sum(h.numel() * 4 for h, _ in outs_h) + n_cand * 8),
+                "ms_per_step": round(e2e_s * 1e3, 4)},
+        "l2": "256 MiB written between timed steps (outside the step events)",
+    }
+    c.close()
+    return out
+
+
 # ---------------------------------------------------------------- workloads
 
 
@@ -470,6 +618,10 @@ def run_kc(args):
                "sample": f"first {n_s:,} of {rs.n_reads:,} reads of the {args.workload} workload ({win:,} windows, "
                          f"{dt:.1f} s, single-threaded C++ oracle, {os.cpu_count()} host cores present)"}
 
+    filt = None
+    if rank == 0 and world == 1 and not args.no_filter and args.workload == "mid":
+        filt = run_filter_bench(dev, stream, args.steps, args.warmup, flush)
+
     served = None
     if rank == 0 and world == 1 and not args.no_served and args.workload == "mid":
         # the mid job's buffers are not needed any more; the stream of jobs
@@ -501,6 +653,7 @@ def run_kc(args):
             "clocks": clk,
             "gpu_launches": int(launches),
             "served": served,
+            "filter": filt,
         }
         print(json.dumps(line), flush=True)
     c.close()
@@ -709,6 +862,7 @@ def main(argv=None):
     ap.add_argument("--ref-seconds", type=float, default=150.0, help="--impl reference: CPU seconds for the whole run")
     ap.add_argument("--strategy", choices=["auto", "direct", "partitioned"], default="auto")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream comparison")
+    ap.add_argument("--no-filter", action="store_true", help="skip the Filter-unit measurement")
     ap.add_argument("--served-jobs", type=int, default=256)
     ap.add_argument("--served-max-reads", type=int, default=2_000_000)
     ap.add_argument("--scatter-mode", type=int, default=0)

@@ -159,6 +159,12 @@ typedef struct kc_stats {
     uint32_t fallback_partitions;   /* partitions whose table left shared memory    */
     uint32_t split_partitions;      /* partitions counted as sub-ranges (split_max) */
     uint32_t split_level;           /* finest split level any partition needed      */
+    /* Filter unit (kc_filter_*; timing as above): device time of the last
+     * selection (compaction and lookup table) and of the rescan kernels of
+     * all kc_filter_reads calls since create / reset; selected keys, valid
+     * windows rescanned and windows whose key was selected. */
+    double ms_filter_select, ms_filter_reads;
+    uint64_t filter_selected, filter_windows, filter_hits;
 } kc_stats;
 
 /*
@@ -353,6 +359,77 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
 kc_status kc_export_bloom(kc_handle h, uint64_t* words, uint64_t first_word, uint64_t n_words);
 
 kc_status kc_stats_get(kc_handle h, kc_stats* out);
+
+/*
+ * Downstream of the count: the result in the paper's item form, its joint
+ * count spectrum, and the Filter unit.  All need a finalized handle; a result
+ * spilled to host memory (kc_config.spill) is first copied back and sorted on
+ * the device (KC_ERR_OOM_DEVICE if it does not fit).  Output arrays may be
+ * host or device memory; every call blocks until its output is written.
+ */
+
+/* One k-mer item of the joint table in the 16-byte form of Section III-D:
+ * 8 bytes of k-mer, the two samples' counts in 4 bytes, 4 bytes of padding.
+ * count[s] = min(count of sample s, 65535); count[1] = 0 for one sample;
+ * pad = 0. */
+typedef struct kc_item16 {
+    uint64_t key;
+    uint16_t count[2];
+    uint32_t pad;
+} kc_item16;
+
+/* Write the result as items, ascending keys (same order and keys as kc_dump).
+ * items == NULL: size query (*n_out).  capacity in items; a smaller capacity
+ * than the result gives KC_ERR_CAPACITY.  Device items must be 16-byte
+ * aligned (KC_ERR_ARG otherwise). */
+kc_status kc_export_items(kc_handle h, kc_item16* items, uint64_t capacity, uint64_t* n_out);
+
+/* Joint count spectrum of the result: with two samples
+ * hist[min(c0, cap) * (cap + 1) + min(c1, cap)] = number of result keys with
+ * those clamped counts ((cap + 1)^2 entries); with one sample hist[min(c0,
+ * cap)] (cap + 1 entries).  hist is overwritten.  1 <= cap <=
+ * KC_SPECTRUM_MAX_CAP. */
+#define KC_SPECTRUM_MAX_CAP 1023u
+kc_status kc_spectrum(kc_handle h, uint32_t cap, uint64_t* hist);
+
+/*
+ * Filter unit (Section II-B): select the k-mers whose counts differ between
+ * the normal and the tumoral sample, then read the input again and look every
+ * k-mer up among the selected ones, which finds the reads that carry them.
+ * The paper gives no threshold; a result key is selected iff, with t = tumor
+ * and n = the other sample,
+ *     count[t] >= min_tumor  and  count[n] <= max_normal  and
+ *     count[t] >= ratio * count[n]          (ratio 0: no ratio test)
+ * Only keys of the result (count summed over samples >= min_count) can be
+ * selected.  Two-sample handles only (KC_ERR_STATE otherwise).
+ */
+typedef struct kc_filter_spec {
+    int tumor;            /* sample holding the tumoral reads: 0 or 1        */
+    uint32_t min_tumor;
+    uint32_t max_normal;
+    uint32_t ratio;
+} kc_filter_spec;
+
+/* Select the keys (replacing an earlier selection); *n_selected = how many.
+ * KC_ERR_ARG for tumor outside 0..1. */
+kc_status kc_filter_select(kc_handle h, const kc_filter_spec* spec, uint64_t* n_selected);
+
+/* Copy the selected keys, ascending, with their counts (counts[i * 2 + s]),
+ * as kc_dump does for the result.  KC_ERR_STATE before kc_filter_select. */
+kc_status kc_filter_keys(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capacity, uint64_t* n_out);
+
+/*
+ * Rescan n_reads reads (packed format above, any sample or any other read
+ * set; the arrays are not kept) against the selection:
+ *   hits        n_reads uint32, overwritten: hits[r] = number of valid
+ *               windows of read r whose canonical key is selected
+ *   candidates  NULL, or room for n_reads uint64: the indices r (0-based in
+ *               this call) with hits[r] > 0, ascending
+ *   n_candidates  number of reads with hits[r] > 0
+ * KC_ERR_STATE before kc_filter_select; KC_ERR_ARG for decreasing offsets.
+ */
+kc_status kc_filter_reads(kc_handle h, const uint64_t* packed_reads, const uint64_t* offsets, const uint64_t* n_mask,
+                          uint64_t n_reads, uint32_t* hits, uint64_t* candidates, uint64_t* n_candidates);
 
 /* Forget all reads and results but keep the allocations, for a new job with
  * the same parameters. */

@@ -18,7 +18,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["KmerCounter", "KcBatch", "KcServer", "KcError", "pack_ascii", "lib", "build", "Config", "Stats",
-           "autotune", "tune_lookup", "tune_cache_save", "tune_cache_load", "tune_cache_clear"]
+           "FilterSpec", "ITEM16", "autotune", "tune_lookup", "tune_cache_save", "tune_cache_load", "tune_cache_clear"]
 
 _lock = threading.Lock()
 _lib = None
@@ -50,10 +50,22 @@ class Stats(ctypes.Structure):
                 ("ms_ingest", ctypes.c_double), ("ms_pass1", ctypes.c_double), ("ms_pass2", ctypes.c_double),
                 ("ms_compact", ctypes.c_double), ("ms_sort", ctypes.c_double), ("strategy", ctypes.c_uint32),
                 ("fallback_partitions", ctypes.c_uint32), ("split_partitions", ctypes.c_uint32),
-                ("split_level", ctypes.c_uint32)]
+                ("split_level", ctypes.c_uint32), ("ms_filter_select", ctypes.c_double),
+                ("ms_filter_reads", ctypes.c_double), ("filter_selected", ctypes.c_uint64),
+                ("filter_windows", ctypes.c_uint64), ("filter_hits", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class FilterSpec(ctypes.Structure):
+    _fields_ = [("tumor", ctypes.c_int), ("min_tumor", ctypes.c_uint32), ("max_normal", ctypes.c_uint32),
+                ("ratio", ctypes.c_uint32)]
+
+
+# kc_item16: the 16-byte k-mer item of the joint table
+ITEM16 = np.dtype([("key", "<u8"), ("count", "<u2", (2,)), ("pad", "<u4")])
+assert ITEM16.itemsize == 16
 
 
 class TuneInput(ctypes.Structure):
@@ -153,6 +165,16 @@ def lib():
             L.kc_tune_cache_load.restype = st
             L.kc_tune_cache_clear.argtypes = []
             L.kc_tune_cache_clear.restype = None
+            L.kc_export_items.argtypes = [p, p, u64, ctypes.POINTER(u64)]
+            L.kc_export_items.restype = st
+            L.kc_spectrum.argtypes = [p, u32, p]
+            L.kc_spectrum.restype = st
+            L.kc_filter_select.argtypes = [p, ctypes.POINTER(FilterSpec), ctypes.POINTER(u64)]
+            L.kc_filter_select.restype = st
+            L.kc_filter_keys.argtypes = [p, p, p, u64, ctypes.POINTER(u64)]
+            L.kc_filter_keys.restype = st
+            L.kc_filter_reads.argtypes = [p, p, p, p, u64, p, p, ctypes.POINTER(u64)]
+            L.kc_filter_reads.restype = st
             _lib = L
     return _lib
 
@@ -289,6 +311,62 @@ class KmerCounter:
         s = Stats()
         _check(self._L.kc_stats_get(self._h, ctypes.byref(s)), "kc_stats_get")
         return s.as_dict()
+
+    def export_items(self, out=None):
+        """The result as 16-byte items (numpy ITEM16 records), or written into out
+        (a device tensor of n * 16 bytes, 16-byte aligned)."""
+        n = ctypes.c_uint64()
+        _check(self._L.kc_export_items(self._h, None, 0, ctypes.byref(n)), "kc_export_items")
+        if out is None:
+            out = np.empty(n.value, dtype=ITEM16)
+            cap = n.value
+        else:
+            cap = (out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes) // 16
+        _check(self._L.kc_export_items(self._h, _ptr(out), cap, ctypes.byref(n)), "kc_export_items")
+        return out
+
+    def spectrum(self, cap: int, out=None):
+        """Joint count spectrum: uint64[cap+1] (one sample) or uint64[cap+1, cap+1] (two)."""
+        if out is None:
+            out = np.empty((cap + 1,) * self.n_samples, dtype=np.uint64)
+        _check(self._L.kc_spectrum(self._h, cap, _ptr(out)), "kc_spectrum")
+        return out
+
+    def filter_select(self, tumor: int = 1, min_tumor: int = 2, max_normal: int = 0, ratio: int = 0) -> int:
+        """Filter unit: select the imbalanced result keys; returns how many."""
+        spec = FilterSpec(tumor, min_tumor, max_normal, ratio)
+        n = ctypes.c_uint64()
+        _check(self._L.kc_filter_select(self._h, ctypes.byref(spec), ctypes.byref(n)), "kc_filter_select")
+        return n.value
+
+    def filter_keys(self):
+        """(keys uint64[n], counts uint32[n, 2]) of the selection, ascending keys."""
+        n = ctypes.c_uint64()
+        _check(self._L.kc_filter_keys(self._h, None, None, 0, ctypes.byref(n)), "kc_filter_keys")
+        keys = np.empty(n.value, dtype=np.uint64)
+        counts = np.empty((n.value, 2), dtype=np.uint32)
+        _check(self._L.kc_filter_keys(self._h, _ptr(keys), _ptr(counts), n.value, ctypes.byref(n)), "kc_filter_keys")
+        return keys, counts
+
+    def filter_reads(self, packed, offsets, n_mask, hits=None, candidates=None, want_candidates: bool = True):
+        """Rescan reads against the selection: (hits uint32[n_reads], candidate read indices or None,
+        number of candidates).  hits / candidates may be given (numpy or torch, host or device)."""
+        if isinstance(offsets, np.ndarray):
+            offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        n_reads = max(0, (offsets.numel() if hasattr(offsets, "numel") else len(offsets)) - 1)
+        if hits is None:
+            hits = np.empty(n_reads, dtype=np.uint32)
+        if candidates is None and want_candidates:
+            candidates = np.empty(max(1, n_reads), dtype=np.uint64)
+        n = ctypes.c_uint64()
+        _check(self._L.kc_filter_reads(self._h, _ptr(packed), _ptr(offsets), _ptr(n_mask), n_reads, _ptr(hits),
+                                       _ptr(candidates), ctypes.byref(n)), "kc_filter_reads")
+        return hits, (candidates[: n.value] if candidates is not None else None), n.value
+
+    def filter_readset(self, readset, **kw):
+        """filter_reads on a synth.ReadSet-like object (ascii + offsets), packed on the host."""
+        packed, mask = pack_ascii(readset.ascii)
+        return self.filter_reads(packed, np.ascontiguousarray(readset.offsets, dtype=np.uint64), mask, **kw)
 
     def reset(self):
         _check(self._L.kc_reset(self._h), "kc_reset")

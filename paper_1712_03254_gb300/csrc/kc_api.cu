@@ -507,6 +507,40 @@ kc_status finalize_partitioned(kc_handle h) {
     return kc_batch_finalize_internal(g_engines[h->device], &h, 1);
 }
 
+// A spilled result back on the device: the runs are copied into one device
+// array and sorted there as one survivor set (sort_result), after which the
+// handle holds its result on the device like an unspilled one.
+// KC_ERR_OOM_DEVICE (nothing changed, no error recorded) when the device has
+// no room for it.
+kc_status resort_spilled(kc_handle h) {
+    const uint64_t n = h->n_result;
+    cudaStream_t st = h->stream;
+    uint64_t *tk = nullptr, *tv = nullptr;
+    if (cudaMallocAsync(&tk, n * 8, st) != cudaSuccess || cudaMallocAsync(&tv, n * 8, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (tk) cudaFreeAsync(tk, st);
+        return KC_ERR_OOM_DEVICE;
+    }
+    uint64_t off = 0;
+    for (const auto& r : h->spill_dir) {
+        if (!r.n_items) continue;
+        KC_CUDA(cudaMemcpyAsync(tk + off, r.host, r.n_items * 8, cudaMemcpyHostToDevice, st));
+        KC_CUDA(cudaMemcpyAsync(tv + off, r.host + r.n_items, r.n_items * 8, cudaMemcpyHostToDevice, st));
+        off += r.n_items;
+    }
+    h->host_ctr.survivors = n;
+    KC_CUDA(cudaMemcpyAsync(&h->ctr->survivors, &h->host_ctr.survivors, 8, cudaMemcpyHostToDevice, st));
+    const uint64_t spilled_bytes = h->spilled_bytes;
+    kc_status s = sort_result(h, tk, tv);  // synchronises the stream (reads the counters)
+    cudaFreeAsync(tk, st);
+    cudaFreeAsync(tv, st);
+    if (s != KC_OK) return s;
+    release_spill(h);  // the pinned chunks stay for the next job
+    h->spilled_bytes = spilled_bytes;
+    h->n_result = n;
+    return KC_OK;
+}
+
 }  // namespace kcapi
 
 using namespace kcapi;
@@ -642,6 +676,8 @@ kc_status kc_reset(kc_handle h) {
     if (!h) return fail(KC_ERR_ARG, "null handle");
     free_batches(h);
     free_result(h);
+    free_selection(h);
+    h->filter_windows = h->filter_hits = 0;
     if (!h->spill_dir.empty()) {
         cudaStreamSynchronize(h->copy_stream);
         release_spill(h);
@@ -668,6 +704,7 @@ void kc_destroy(kc_handle h) {
     if (h->stream) {
         free_batches(h);
         free_result(h);
+        free_selection(h);
         if (!h->spill_dir.empty()) cudaStreamSynchronize(h->copy_stream);
         release_spill(h);
         free_spill_chunks(h);
@@ -809,40 +846,6 @@ kc_status kc_finalize(kc_handle h) {
     return KC_OK;
 }
 
-// A spilled result back on the device: the runs are copied into one device
-// array and sorted there as one survivor set (sort_result), after which the
-// handle holds its result on the device like an unspilled one.
-// KC_ERR_OOM_DEVICE (nothing changed, no error recorded) when the device has
-// no room for it.
-kc_status resort_spilled(kc_handle h) {
-    const uint64_t n = h->n_result;
-    cudaStream_t st = h->stream;
-    uint64_t *tk = nullptr, *tv = nullptr;
-    if (cudaMallocAsync(&tk, n * 8, st) != cudaSuccess || cudaMallocAsync(&tv, n * 8, st) != cudaSuccess) {
-        cudaGetLastError();
-        if (tk) cudaFreeAsync(tk, st);
-        return KC_ERR_OOM_DEVICE;
-    }
-    uint64_t off = 0;
-    for (const auto& r : h->spill_dir) {
-        if (!r.n_items) continue;
-        KC_CUDA(cudaMemcpyAsync(tk + off, r.host, r.n_items * 8, cudaMemcpyHostToDevice, st));
-        KC_CUDA(cudaMemcpyAsync(tv + off, r.host + r.n_items, r.n_items * 8, cudaMemcpyHostToDevice, st));
-        off += r.n_items;
-    }
-    h->host_ctr.survivors = n;
-    KC_CUDA(cudaMemcpyAsync(&h->ctr->survivors, &h->host_ctr.survivors, 8, cudaMemcpyHostToDevice, st));
-    const uint64_t spilled_bytes = h->spilled_bytes;
-    kc_status s = sort_result(h, tk, tv);  // synchronises the stream (reads the counters)
-    cudaFreeAsync(tk, st);
-    cudaFreeAsync(tv, st);
-    if (s != KC_OK) return s;
-    release_spill(h);  // the pinned chunks stay for the next job
-    h->spilled_bytes = spilled_bytes;
-    h->n_result = n;
-    return KC_OK;
-}
-
 kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capacity, uint64_t* n_out) {
     kc_status s = check_open(h);
     if (s != KC_OK) return s;
@@ -925,6 +928,7 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->spilled_bytes = h->spilled_bytes;
     out->strategy = (uint32_t)h->strategy;
     size_t bytes = h->fixed_bytes + h->res_cap * 16;
+    if (h->has_selection) bytes += std::max<uint64_t>(1, h->n_sel) * 16 + (32ull << h->sel_buckets_log2);
     for (const auto& b : h->batches) {
         if (b.pw) bytes += (2 * b.n_units + 2) * 8 + b.n_units * 8;
         if (b.hdata) bytes += b.hcap * 8 + ((1ull << h->part_bits) + 1) * 8;
@@ -936,6 +940,11 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->ms_pass2 = h->ms[kPass2];
     out->ms_compact = h->ms[kCompact];
     out->ms_sort = h->ms[kSort];
+    out->ms_filter_select = h->ms[kFilterSelect];
+    out->ms_filter_reads = h->ms[kFilterReads];
+    out->filter_selected = h->has_selection ? h->n_sel : 0;
+    out->filter_windows = h->filter_windows;
+    out->filter_hits = h->filter_hits;
     return KC_OK;
 }
 

@@ -102,7 +102,7 @@ struct kc_ctx {
     };
     std::vector<cudaEvent_t> ev_pool;
     std::vector<Mark> marks;
-    double ms[5] = {0, 0, 0, 0, 0};
+    double ms[7] = {0, 0, 0, 0, 0, 0, 0};
     uint64_t launches = 0;
     uint32_t fallback_partitions = 0;
 
@@ -111,6 +111,16 @@ struct kc_ctx {
     std::vector<kcapi::SpillRun> spill_dir;
     std::vector<kcapi::PinnedChunk> spill_chunks;
     uint64_t spilled_bytes = 0;
+
+    // Filter unit (kc_filter.cu): the selected result keys in key order and
+    // their lookup table (2^sel_buckets_log2 buckets of four keys)
+    uint64_t* sel_keys = nullptr;
+    uint64_t* sel_vals = nullptr;
+    uint64_t* sel_table = nullptr;
+    uint64_t n_sel = 0;
+    int sel_buckets_log2 = 0;
+    bool has_selection = false;
+    uint64_t filter_windows = 0, filter_hits = 0;  // summed over kc_filter_reads calls
 
 
     kc::PassParams params(int sample) const {
@@ -130,7 +140,7 @@ struct kc_ctx {
 
 namespace kcapi {
 
-enum Phase { kIngest = 0, kPass1 = 1, kPass2 = 2, kCompact = 3, kSort = 4 };
+enum Phase { kIngest = 0, kPass1 = 1, kPass2 = 2, kCompact = 3, kSort = 4, kFilterSelect = 5, kFilterReads = 6 };
 
 // Phase timing events, recorded on stream st (the handle's stream if null).
 cudaEvent_t phase_begin(kc_handle h, cudaStream_t st = nullptr);
@@ -142,6 +152,12 @@ void free_result(kc_handle h);
 void release_spill(kc_handle h);
 void free_spill_chunks(kc_handle h);
 uint64_t* spill_alloc(kc_handle h, uint64_t words);  // nullptr when pinning fails
+kc_status check_open(kc_handle h);                   // KC_ERR_ARG / KC_ERR_STATE for null or poisoned
+bool is_device_ptr(const void* p);
+// Copy a spilled result back to the device and sort it there
+// (KC_ERR_OOM_DEVICE, nothing changed, when it does not fit).
+kc_status resort_spilled(kc_handle h);
+void free_selection(kc_handle h);
 
 }  // namespace kcapi
 
