@@ -324,8 +324,8 @@ def ncu_filter_kernel(kernel: str, workload: str):
 def filter_roofline(ms_per_launch, n_bases, n_reads, table_bytes, sm_count, workload):
     """Roofline of k_filter_hits (one launch per read set).  Algorithmic bytes:
     2 bits (packed base) + 1 bit (valid-window bit) per base, the 8-byte read
-    offsets read once, the selection's lookup table read once, 4 bytes of hit
-    count written per read."""
+    offsets read once, the selection's fingerprint words read once, 4 bytes of
+    hit count written per read."""
     algo = (n_bases * 3 + 7) // 8 + 8 * (n_reads + 1) + table_bytes + 4 * n_reads
     peak, peak_kind = measured_hbm_peak()
     hbm_achieved = algo / (ms_per_launch / 1e3) / 1e9
@@ -413,10 +413,10 @@ def run_filter_bench(dev, stream, steps: int, warmup: int, flush):
     for (hh, _), (dh, _) in zip(outs_h, outs_d):
         assert torch.equal(hh, dh.cpu()), "filter: host and device hits differ"
     n_reads = sum(rs.n_reads for rs in w.samples)
-    lb = 8  # the selection's lookup table: 2^lb buckets of four keys, at most half full
-    while (4 << lb) < 2 * n_sel:
+    lb = 8  # the selection's lookup table: 2^lb buckets of four 32-bit fingerprints, 2^lb >= 2 x selected keys
+    while (1 << lb) < 2 * n_sel:
         lb += 1
-    table_bytes = 32 << lb
+    table_bytes = 16 << lb  # the fingerprint words (the 64-bit codes are read only on a fingerprint match)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     out = {
         "workload": FILTER_WORKLOAD, "spec": dict(zip(("tumor", "min_tumor", "max_normal", "ratio"), FILTER_SPEC)),
@@ -863,6 +863,8 @@ def main(argv=None):
     ap.add_argument("--strategy", choices=["auto", "direct", "partitioned"], default="auto")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream comparison")
     ap.add_argument("--no-filter", action="store_true", help="skip the Filter-unit measurement")
+    ap.add_argument("--filter-only", action="store_true",
+                    help="print only the Filter-unit measurement (one JSON object), for profiling it alone")
     ap.add_argument("--served-jobs", type=int, default=256)
     ap.add_argument("--served-max-reads", type=int, default=2_000_000)
     ap.add_argument("--scatter-mode", type=int, default=0)
@@ -875,6 +877,13 @@ def main(argv=None):
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.filter_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        print(json.dumps(run_filter_bench(dev, torch.cuda.Stream(), args.steps, args.warmup, flush)), flush=True)
     else:
         run_kc(args)
 

@@ -928,7 +928,7 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->spilled_bytes = h->spilled_bytes;
     out->strategy = (uint32_t)h->strategy;
     size_t bytes = h->fixed_bytes + h->res_cap * 16;
-    if (h->has_selection) bytes += std::max<uint64_t>(1, h->n_sel) * 16 + (32ull << h->sel_buckets_log2);
+    if (h->has_selection) bytes += std::max<uint64_t>(1, h->n_sel) * 16 + (48ull << h->sel_buckets_log2) + (h->sel_pre ? 4ull * 49152 : 0);
     for (const auto& b : h->batches) {
         if (b.pw) bytes += (2 * b.n_units + 2) * 8 + b.n_units * 8;
         if (b.hdata) bytes += b.hcap * 8 + ((1ull << h->part_bits) + 1) * 8;

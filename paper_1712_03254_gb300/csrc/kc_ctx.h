@@ -113,12 +113,14 @@ struct kc_ctx {
     uint64_t spilled_bytes = 0;
 
     // Filter unit (kc_filter.cu): the selected result keys in key order and
-    // their lookup table (2^sel_buckets_log2 buckets of four keys)
+    // their lookup table (2^sel_buckets_log2 buckets of four slots: 32-bit
+    // fingerprints, then the slots' 64-bit codes)
     uint64_t* sel_keys = nullptr;
     uint64_t* sel_vals = nullptr;
     uint64_t* sel_table = nullptr;
     uint64_t n_sel = 0;
     int sel_buckets_log2 = 0;
+    bool sel_pre = false;  // a shared-memory prefilter follows the table
     bool has_selection = false;
     uint64_t filter_windows = 0, filter_hits = 0;  // summed over kc_filter_reads calls
 

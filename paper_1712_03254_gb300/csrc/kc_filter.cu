@@ -13,12 +13,14 @@
 //           to find the reads that carry selected k-mers.  Selection:
 //           count[t] >= min_tumor, count[n] <= max_normal, count[t] >=
 //           ratio * count[n] (the paper gives no threshold).  The selected
-//           keys are compacted in key order and stored in a lookup table of
-//           32-byte buckets (four keys, one sector); the rescan computes every
-//           valid window's canonical key and probes the table, and a hit adds
-//           one to its read's count.
+//           keys are compacted in key order and both orientations of each are
+//           stored in a lookup table of 16-byte buckets of four fingerprints;
+//           the rescan rolls every valid window's forward code and probes
+//           the table; hits are marked per 64-base unit and then counted per
+//           read.
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "kc_ctx.h"
@@ -26,7 +28,6 @@
 namespace kc {
 namespace {
 
-constexpr unsigned long long kSelEmpty = ~0ull;  // keys are below 4^31: never a key
 constexpr int kTileThreads = 256;
 constexpr int kTileRounds = 16;
 constexpr uint64_t kTileItems = (uint64_t)kTileThreads * kTileRounds;
@@ -116,87 +117,200 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_write(Pred pred, Write wr
     }
 }
 
-// Lookup table of the selected keys: n_buckets buckets of four keys (one
-// 32-byte sector), kSelEmpty = free.  A key goes to the first free slot of
-// its bucket (h >> (64 - log2 buckets)) or of the buckets after it, so slots
-// of a bucket fill in order and a bucket whose last slot is free ends every
-// probe sequence through it.
-__global__ void k_sel_insert(const uint64_t* __restrict__ keys, uint64_t n, unsigned long long* __restrict__ table,
-                             int bucket_shift, uint64_t bucket_mask, DevCounters* __restrict__ ctr) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned long long key = keys[i];
-        uint64_t b = mixer64(key) >> bucket_shift;
-        bool placed = false;
-        for (uint64_t probe = 0; probe <= bucket_mask && !placed; ++probe) {
-            for (int s = 0; s < 4 && !placed; ++s) {
-                const unsigned long long prev = atomicCAS(table + 4 * b + s, kSelEmpty, key);
-                placed = prev == kSelEmpty || prev == key;
-            }
-            b = (b + 1) & bucket_mask;
-        }
-        if (!placed) atomicOr(&ctr->err, DERR_INTERNAL);  // cannot happen: the table is at most half full
-    }
+// Selection table.  It holds both orientations of every selected k-mer (the
+// forward code of a window then finds its canonical key without the reverse
+// complement): 2^lb buckets of four slots.  A slot is a 32-bit fingerprint
+// (0 = free) in the bucket's 16-byte fingerprint word, with the 64-bit code
+// in a parallel array, read only when a fingerprint matches; at most a
+// quarter of the slots are taken.  A code goes to the first free slot of its
+// bucket or of the buckets after it, so slots fill in order and a bucket
+// whose last slot is free ends every probe through it.
+// Hash: Fibonacci hashing, h = code * 2^64/golden ratio; bucket = top lb bits
+// of h, fingerprint = the 32 bits below them with the lowest bit set.
+//
+// Small selections also get a prefilter that the rescan keeps in shared
+// memory: kPreWords 32-bit words, each entry setting two bits of one word
+// (word from the top 32 bits of h, bits from h's bits 14..18 and 20..24).  A
+// window whose two bits are not both set is not in the table, and most
+// windows are rejected there instead of by a random global load.
+constexpr uint32_t kPreWords = 49152;                 // 192 KiB of shared memory
+constexpr uint64_t kPreMaxEntries = kPreWords * 32 / 4;  // at most a quarter of its bits per entry pair
+
+struct SelTable {
+    unsigned int* fp;      // 4 per bucket
+    unsigned long long* code;  // 4 per bucket
+    unsigned int* pre;     // kPreWords prefilter words (null: no prefilter)
+    int lb;
+    uint64_t mask;         // buckets - 1
+};
+
+__device__ __forceinline__ uint64_t sel_h(uint64_t code) { return code * 0x9e3779b97f4a7c15ull; }
+
+__device__ __forceinline__ void sel_hash(uint64_t code, int lb, uint64_t& bucket, unsigned& fp) {
+    const uint64_t h = sel_h(code);
+    bucket = h >> (64 - lb);
+    fp = (unsigned)(h >> (32 - lb)) | 1u;  // never 0 (0 marks a free slot)
 }
 
-__device__ __forceinline__ bool sel_contains(const unsigned long long* __restrict__ table, uint64_t b,
-                                             uint64_t bucket_mask, unsigned long long key) {
-    for (uint64_t probe = 0; probe <= bucket_mask; ++probe) {
-        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(table + 4 * b);
-        const ulonglong2 a = __ldg(q), c = __ldg(q + 1);
-        if (a.x == key || a.y == key || c.x == key || c.y == key) return true;
-        if (c.y == kSelEmpty) return false;
-        b = (b + 1) & bucket_mask;
+__device__ __forceinline__ uint32_t pre_word(uint64_t h) {
+    return (uint32_t)(((h >> 32) * (uint64_t)kPreWords) >> 32);
+}
+
+__device__ __forceinline__ uint32_t pre_bits(uint64_t h) {
+    return (1u << ((uint32_t)(h >> 20) & 31u)) | (1u << ((uint32_t)(h >> 14) & 31u));
+}
+
+__device__ __forceinline__ bool sel_insert(const SelTable& T, uint64_t code) {
+    uint64_t b;
+    unsigned fp;
+    sel_hash(code, T.lb, b, fp);
+    if (T.pre) {
+        const uint64_t h = sel_h(code);
+        atomicOr(T.pre + pre_word(h), pre_bits(h));
+    }
+    for (uint64_t probe = 0; probe <= T.mask; ++probe) {
+        for (int s = 0; s < 4; ++s)
+            if (atomicCAS(T.fp + 4 * b + s, 0u, fp) == 0u) {
+                T.code[4 * b + s] = code;
+                return true;
+            }
+        b = (b + 1) & T.mask;
     }
     return false;
 }
 
-// Upper bound: the read whose base range holds position pos (offsets are the
-// caller's, non-decreasing, n_reads + 1 of them, offsets[0] <= pos).
-__device__ __forceinline__ uint64_t read_of(const uint64_t* __restrict__ offsets, uint64_t n_reads, uint64_t pos) {
-    uint64_t lo = 0, hi = n_reads;  // invariant: offsets[lo] <= pos < offsets[hi]
-    while (hi - lo > 1) {
-        const uint64_t mid = lo + ((hi - lo) >> 1);
-        if (offsets[mid] <= pos) lo = mid;
-        else hi = mid;
+// Both orientations of every selected canonical key.
+__global__ void k_sel_insert(const uint64_t* __restrict__ keys, uint64_t n, SelTable T, PassParams p,
+                             DevCounters* __restrict__ ctr) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t key = keys[i];
+        const uint64_t rc = reverse_pairs(key ^ p.kmask) >> p.rc_shift;
+        bool ok = sel_insert(T, key);
+        if (rc != key) ok = ok && sel_insert(T, rc);  // an even-k palindrome is its own reverse complement
+        if (!ok) atomicOr(&ctr->err, DERR_INTERNAL);  // cannot happen: the table is at most half full
     }
-    return lo;
 }
 
-// Filter rescan: one lane per 64-base unit, as the recount pass; every valid
-// window's canonical key probes the selection, and a hit adds one to its
-// read.  Hits are rare, so the read lookup and the atomic add cost little.
-__global__ void __launch_bounds__(256) k_filter_hits(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw,
-                                                     uint64_t n_units, PassParams p, uint64_t base_pos,
-                                                     const unsigned long long* __restrict__ table, int bucket_shift,
-                                                     uint64_t bucket_mask, const uint64_t* __restrict__ offsets,
-                                                     uint64_t n_reads, unsigned int* __restrict__ hits,
-                                                     DevCounters* __restrict__ ctr) {
+// Matching slots of a bucket word: confirm against the stored codes.
+__device__ __forceinline__ bool sel_confirm(const SelTable& T, uint64_t b, uint4 q, unsigned fp, uint64_t code) {
+    const unsigned f[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (f[s] == fp && __ldg(T.code + 4 * b + s) == code) return true;
+    return false;
+}
+
+// Probe from the bucket after b on (rare: b's slots are all taken).
+__device__ __forceinline__ bool sel_probe_rest(const SelTable& T, uint64_t b, unsigned fp, uint64_t code) {
+    for (uint64_t probe = 0; probe < T.mask; ++probe) {
+        b = (b + 1) & T.mask;
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(T.fp) + b);
+        if ((q.x == fp || q.y == fp || q.z == fp || q.w == fp) && sel_confirm(T, b, q, fp, code)) return true;
+        if (q.w == 0u) return false;
+    }
+    return false;
+}
+
+// Filter rescan: one lane per 64-base unit; the lane walks its unit's 64
+// window starts with the rolling forward code and probes the selection for
+// four windows at a time (four 16-byte bucket loads in flight).  PRE: one
+// 1024-thread CTA per SM holds the prefilter in shared memory and loads a
+// bucket only for windows that pass it.  Hits go to the unit's hit mask (bit
+// 63 - j: the window starting at base j of the unit, as the valid-window
+// bits), written once per unit; k_read_hits turns the masks into hits per
+// read.
+constexpr int kFilterThreads = 256;
+constexpr int kFilterThreadsPre = 1024;
+
+template <bool PRE>
+__global__ void __launch_bounds__(PRE ? kFilterThreadsPre : kFilterThreads, PRE ? 1 : 4)
+    k_filter_hits(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw, uint64_t n_units, PassParams p,
+                  SelTable T, uint64_t* __restrict__ hitmask, DevCounters* __restrict__ ctr) {
+    extern __shared__ uint4 s_pre4[];
+    const uint32_t* s_pre = reinterpret_cast<const uint32_t*>(s_pre4);
+    if (PRE) {
+        const uint4* g = reinterpret_cast<const uint4*>(T.pre);
+        for (uint32_t i = threadIdx.x; i < kPreWords / 4; i += blockDim.x) s_pre4[i] = __ldg(g + i);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int kk = 64 - p.rc_shift;  // 2k
+    const uint4* fpw = reinterpret_cast<const uint4*>(T.fp);
     unsigned long long found = 0;
     for (uint64_t base = warp * 32; base < n_units; base += n_warps * 32) {
         const uint64_t u = base + lane;
         const UnitWords uw = load_unit(pw, vw, u, n_units, lane);
-        uint64_t vm = uw.v;
-        const int n_iter = __reduce_max_sync(0xffffffffu, (unsigned)__popcll(vm));
-        for (int it = 0; it < n_iter; ++it) {
-            if (vm) {
-                const int j = __clzll(vm);
-                vm &= ~(0x8000000000000000ull >> j);
-                const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
-                if (sel_contains(table, mixer64(key) >> bucket_shift, bucket_mask, key)) {
-                    const uint64_t r = read_of(offsets, n_reads, base_pos + u * 64 + (uint64_t)j);
-                    atomicAdd(hits + r, 1u);
-                    ++found;
+        uint64_t vm = uw.v, hm = 0;
+        // forward code of window j, and the bases entering at the next steps
+        uint64_t fwd = uw.w0 >> p.rc_shift;
+        uint64_t x = (uw.w0 << kk) | (uw.w1 >> p.rc_shift);
+        uint64_t y = (uw.w1 << kk) | (uw.w2 >> p.rc_shift);
+        for (int j0 = 0; j0 < 64 && vm; j0 += 4, vm <<= 4) {
+            uint64_t code[4], b[4];
+            unsigned fp[4];
+            bool probe[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                code[t] = fwd;
+                const uint64_t h = sel_h(fwd);
+                b[t] = h >> (64 - T.lb);
+                fp[t] = (unsigned)(h >> (32 - T.lb)) | 1u;
+                probe[t] = (vm >> (63 - t)) & 1ull;
+                if (PRE && probe[t]) {
+                    const uint32_t m = pre_bits(h);
+                    probe[t] = (s_pre[pre_word(h)] & m) == m;
                 }
+                fwd = ((fwd << 2) | (x >> 62)) & p.kmask;
+                x = (x << 2) | (y >> 62);
+                y <<= 2;
             }
-            __syncwarp();
+            if (!(probe[0] || probe[1] || probe[2] || probe[3])) continue;
+            uint4 q[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                q[t] = make_uint4(0u, 0u, 0u, 0u);
+                if (probe[t]) q[t] = __ldg(fpw + b[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const bool match = q[t].x == fp[t] || q[t].y == fp[t] || q[t].z == fp[t] || q[t].w == fp[t];
+                if (!match && q[t].w == 0u) continue;  // not in the table (skipped windows read as empty)
+                bool hit = match && sel_confirm(T, b[t], q[t], fp[t], code[t]);
+                if (!hit && q[t].w != 0u) hit = sel_probe_rest(T, b[t], fp[t], code[t]);
+                if (hit) hm |= 0x8000000000000000ull >> (j0 + t);
+            }
         }
+        if (u < n_units) hitmask[u] = hm;
+        found += __popcll(hm);
     }
     found = warp_sum(found);
     if (lane == 0 && found) atomicAdd(&ctr->candidates, found);
+}
+
+// hits[r] = hit-mask bits inside read r's bases (local positions o0 .. o1 - 1;
+// the mask has bits only at valid window starts, which lie inside reads).
+// Thread per read.
+__global__ void k_read_hits(const uint64_t* __restrict__ offsets, uint64_t n_reads, uint64_t base,
+                            uint64_t n_units, const uint64_t* __restrict__ hitmask, unsigned int* __restrict__ hits) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_reads; r += stride) {
+        const uint64_t o0 = offsets[r] - base, o1 = offsets[r + 1] - base;
+        unsigned n = 0;
+        if (o1 > o0) {
+            const uint64_t u0 = o0 >> 6, u1 = (o1 - 1) >> 6;
+            for (uint64_t u = u0; u <= u1 && u < n_units; ++u) {
+                uint64_t m = hitmask[u];
+                if (u == u0) m &= ~0ull >> (o0 & 63);                 // from base o0 on
+                const int e = (int)((o1 - 1) & 63);
+                if (u == u1 && e < 63) m &= ~(~0ull >> (e + 1));      // up to base o1 - 1
+                n += (unsigned)__popcll(m);
+            }
+        }
+        hits[r] = n;
+    }
 }
 
 __global__ void k_items16(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals, uint64_t n,
@@ -248,6 +362,35 @@ unsigned grid_of(uint64_t n, unsigned block, unsigned cap) {
     return (unsigned)g;
 }
 
+// Resident CTAs of k_filter_hits<false> per SM: its grid fills the SMs
+// once, no partial second wave.
+int filter_blocks_per_sm() {
+    static std::atomic<int> cached{0};
+    int v = cached.load(std::memory_order_relaxed);
+    if (!v) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_filter_hits<false>, kFilterThreads, 0) !=
+                cudaSuccess ||
+            v < 1) {
+            cudaGetLastError();
+            v = 4;
+        }
+        cached.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+// k_filter_hits<true> takes 192 KiB of dynamic shared memory (set once per
+// device; the value is the same for every caller).
+cudaError_t filter_pre_smem_attr() {
+    static std::atomic<int> done[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    cudaError_t e = allow_max_dynamic_smem(k_filter_hits<true>);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev].store(1, std::memory_order_relaxed);
+    return e;
+}
+
 }  // namespace
 }  // namespace kc
 
@@ -260,10 +403,27 @@ void free_selection(kc_handle h) {
     h->sel_keys = h->sel_vals = h->sel_table = nullptr;
     h->n_sel = 0;
     h->sel_buckets_log2 = 0;
+    h->sel_pre = false;
     h->has_selection = false;
 }
 
 namespace {
+
+// Bytes per selection bucket: four 32-bit fingerprints and four 64-bit codes.
+constexpr uint64_t kSelBucketBytes = 16 + 32;
+
+kc::SelTable sel_table_of(kc_handle h) {
+    kc::SelTable T;
+    const uint64_t n_buckets = 1ull << h->sel_buckets_log2;
+    T.fp = reinterpret_cast<unsigned int*>(h->sel_table);
+    T.code = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->sel_table) + 16 * n_buckets);
+    T.pre = h->sel_pre ? reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(h->sel_table) +
+                                                          kSelBucketBytes * n_buckets)
+                       : nullptr;
+    T.lb = h->sel_buckets_log2;
+    T.mask = n_buckets - 1;
+    return T;
+}
 
 // The result on the device: a spilled result is copied back and sorted there.
 kc_status device_result(kc_handle h, const char* who) {
@@ -387,18 +547,27 @@ kc_status kc_filter_select(kc_handle h, const kc_filter_spec* spec, uint64_t* n_
     s = compact_ordered(h, pred, kc::SelectWrite{}, n, &kept, false);
     if (s != KC_OK) return s;
     const uint64_t cap = std::max<uint64_t>(1, kept);
-    int lb = 8;  // buckets of four keys, at most half full
-    while ((4ull << lb) < 2 * kept) ++lb;
+    // buckets of four slots for both orientations of every key, at most a
+    // quarter full: about 2 % of the buckets are full and make a miss probe on
+    int lb = 8;
+    while ((1ull << lb) < 2 * kept) ++lb;
+    if (lb > 32) return fail(KC_ERR_CAPACITY, "selection larger than 2^31 keys");
     const uint64_t n_buckets = 1ull << lb;
     cudaError_t e;
+    const bool pre = 2 * kept <= kc::kPreMaxEntries;
+    const uint64_t table_bytes = n_buckets * kSelBucketBytes + (pre ? kc::kPreWords * 4ull : 0);
     if ((e = cudaMallocAsync(&h->sel_keys, cap * 8, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&h->sel_vals, cap * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&h->sel_table, n_buckets * 32, st)) != cudaSuccess) {
+        (e = cudaMallocAsync(&h->sel_table, table_bytes, st)) != cudaSuccess) {
         free_selection(h);
         return cuda_fail(e, "cudaMallocAsync(selection)");
     }
     h->sel_buckets_log2 = lb;
-    KC_CUDA(cudaMemsetAsync(h->sel_table, 0xff, n_buckets * 32, st));
+    h->sel_pre = pre;
+    KC_CUDA(cudaMemsetAsync(h->sel_table, 0, n_buckets * 16, st));  // fingerprints: all slots free
+    if (pre)
+        KC_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(h->sel_table) + n_buckets * kSelBucketBytes, 0,
+                                kc::kPreWords * 4ull, st));
     if (kept) {
         s = compact_ordered(h, pred, kc::SelectWrite{h->res_keys, h->res_vals, h->sel_keys, h->sel_vals}, n, &kept,
                             true);
@@ -407,7 +576,7 @@ kc_status kc_filter_select(kc_handle h, const kc_filter_spec* spec, uint64_t* n_
             return s;
         }
         kc::k_sel_insert<<<kc::grid_of(kept, 256, h->grid.sm_count * 8), 256, 0, st>>>(
-            h->sel_keys, kept, reinterpret_cast<unsigned long long*>(h->sel_table), 64 - lb, n_buckets - 1, h->ctr);
+            h->sel_keys, kept, sel_table_of(h), h->params(0), h->ctr);
         h->launches += 1;
         KC_LAUNCHED("selection table launch");
     }
@@ -466,6 +635,7 @@ kc_status kc_filter_reads(kc_handle h, const uint64_t* packed_reads, const uint6
     }
     if (b1 < b0) return fail(KC_ERR_ARG, "read offsets decrease");
     if (b1 > b0 && (!packed_reads || !n_mask)) return fail(KC_ERR_ARG, "packed_reads or n_mask is null");
+    if (n_reads >= (1ull << 32)) return fail(KC_ERR_ARG, "at most 2^32 - 1 reads per kc_filter_reads call");
 
     const bool hits_dev = is_device_ptr(hits);
     const bool cand_dev = candidates && is_device_ptr(candidates);
@@ -477,9 +647,10 @@ kc_status kc_filter_reads(kc_handle h, const uint64_t* packed_reads, const uint6
 
     uint64_t *pw = nullptr, *vw = nullptr, *nm = nullptr, *bd = nullptr, *doff = nullptr, *dcand = nullptr;
     uint32_t* dhits = hits_dev ? hits : nullptr;
+    uint64_t* hitmask = nullptr;
     kc::DevCounters* fctr = nullptr;
     auto release = [&]() {
-        for (void* q : {(void*)pw, (void*)vw, (void*)nm, (void*)bd, (void*)doff, (void*)fctr})
+        for (void* q : {(void*)pw, (void*)vw, (void*)nm, (void*)bd, (void*)doff, (void*)fctr, (void*)hitmask})
             if (q) cudaFreeAsync(q, st);
         if (dhits && !hits_dev) cudaFreeAsync(dhits, st);
         if (dcand && !cand_dev) cudaFreeAsync(dcand, st);
@@ -491,6 +662,7 @@ kc_status kc_filter_reads(kc_handle h, const uint64_t* packed_reads, const uint6
         (e = cudaMallocAsync(&bd, n_units * 8, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&doff, (n_reads + 1) * 8, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&fctr, sizeof(kc::DevCounters), st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&hitmask, n_units * 8, st)) != cudaSuccess ||
         (!hits_dev && (e = cudaMallocAsync(&dhits, n_reads * 4, st)) != cudaSuccess) ||
         (candidates && !cand_dev && (e = cudaMallocAsync(&dcand, n_reads * 8, st)) != cudaSuccess)) {
         release();
@@ -499,7 +671,6 @@ kc_status kc_filter_reads(kc_handle h, const uint64_t* packed_reads, const uint6
     if (cand_dev) dcand = candidates;
     auto run = [&]() -> kc_status {
         KC_CUDA(cudaMemsetAsync(fctr, 0, sizeof(kc::DevCounters), st));
-        KC_CUDA(cudaMemsetAsync(dhits, 0, n_reads * 4, st));
         KC_CUDA(cudaMemsetAsync(pw, 0, n_pwords * 8, st));
         KC_CUDA(cudaMemsetAsync(nm, 0, n_units * 8, st));
         if (n_pwords_src) KC_CUDA(cudaMemcpyAsync(pw, packed_reads + B / 32, n_pwords_src * 8, cudaMemcpyDefault, st));
@@ -508,12 +679,25 @@ kc_status kc_filter_reads(kc_handle h, const uint64_t* packed_reads, const uint6
         KC_CUDA(cudaMemsetAsync(bd, 0, n_units * 8, st));
         kc::launch_mark_read_starts(doff, n_reads, B, n_local, bd, fctr, st);
         kc::launch_build_valid(nm, bd, n_units, b0 - B, n_local, h->k, vw, fctr, h->grid, st);
-        cudaEvent_t t0 = phase_begin(h);
-        kc::k_filter_hits<<<kc::grid_of(n_units, 256, h->grid.sm_count * 8), 256, 0, st>>>(
-            pw, vw, n_units, h->params(0), B, reinterpret_cast<const unsigned long long*>(h->sel_table),
-            64 - h->sel_buckets_log2, (1ull << h->sel_buckets_log2) - 1, doff, n_reads, dhits, fctr);
-        phase_end(h, kFilterReads, t0);
-        h->launches += 3;
+        const kc::SelTable T = sel_table_of(h);
+        if (T.pre) {
+            KC_CUDA(kc::filter_pre_smem_attr());
+            const unsigned grid = kc::grid_of(n_units, kc::kFilterThreadsPre, (unsigned)h->grid.sm_count);
+            cudaEvent_t t0 = phase_begin(h);
+            kc::k_filter_hits<true><<<grid, kc::kFilterThreadsPre, kc::kPreWords * 4, st>>>(
+                pw, vw, n_units, h->params(0), T, hitmask, fctr);
+            phase_end(h, kFilterReads, t0);
+        } else {
+            const unsigned grid = kc::grid_of(n_units, kc::kFilterThreads,
+                                              (unsigned)(h->grid.sm_count * kc::filter_blocks_per_sm()));
+            cudaEvent_t t0 = phase_begin(h);
+            kc::k_filter_hits<false><<<grid, kc::kFilterThreads, 0, st>>>(pw, vw, n_units, h->params(0), T,
+                                                                         hitmask, fctr);
+            phase_end(h, kFilterReads, t0);
+        }
+        kc::k_read_hits<<<kc::grid_of(n_reads, 256, h->grid.sm_count * 8), 256, 0, st>>>(doff, n_reads, B, n_units,
+                                                                                         hitmask, dhits);
+        h->launches += 4;
         KC_LAUNCHED("filter rescan launches");
         kc::DevCounters c{};
         KC_CUDA(cudaMemcpyAsync(&c, fctr, sizeof(c), cudaMemcpyDeviceToHost, st));

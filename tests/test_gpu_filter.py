@@ -123,6 +123,21 @@ def test_filter_parity(paired_small, strategy, spec):
     assert st["filter_windows"] == o.windows  # both samples rescanned once
 
 
+def test_filter_parity_large_selection(oracle_mod):
+    """Selections of more than 196,608 keys (both orientations above 2^18 x 1.5
+    table entries) are probed without the shared-memory prefilter; smaller
+    ones with it.  Both give the oracle's hits."""
+    w = synth.paired(scale=0.006)  # 300 kbp genomes, 2 x 60,000 reads
+    o = oracle_mod.count(w)
+    c = gpu_count(w)
+    big = (1, 1, 1 << 31, 0)  # every result key
+    _check_filter(c, o, w, big)
+    assert 2 * c.filter_keys()[0].size > 49152 * 32 // 4
+    small = (1, 3, 0, 0)
+    _check_filter(c, o, w, small)
+    assert 2 * c.filter_keys()[0].size <= 49152 * 32 // 4
+
+
 def test_filter_reselect_and_other_read_sets(paired_small):
     """A new selection replaces the old one; any read set may be rescanned."""
     w, o = paired_small
