@@ -74,6 +74,8 @@ def _load():
         lib.orc_filter_select.restype = ctypes.c_int64
         lib.orc_filter_reads.argtypes = [p, i, u32, u32, u32, p, p, u64, p]
         lib.orc_filter_reads.restype = ctypes.c_int64
+        lib.orc_stems.argtypes = [p, p, u64]
+        lib.orc_stems.restype = ctypes.c_int64
         lib.orc_destroy.argtypes = [p]
         lib.orc_destroy.restype = None
         _lib = lib
@@ -186,6 +188,16 @@ class Oracle:
         out = np.zeros(shape, dtype=np.uint64)
         if self._lib.orc_spectrum(self._h, cap, out.ctypes.data) != 0:
             raise ValueError("oracle: spectrum")
+        return out
+
+    def stems(self) -> np.ndarray:
+        """Stem-grouped items (uint8[n, 72]): stem code, 16 counts per sample (uint16, clamped)."""
+        n = self._lib.orc_stems(self._h, None, 0)
+        if n < 0:
+            raise ValueError("oracle: stems need k >= 3")
+        out = np.zeros((n, 72), dtype=np.uint8)
+        if self._lib.orc_stems(self._h, out.ctypes.data, n) != n:
+            raise RuntimeError("oracle: stems")
         return out
 
     def filter_select(self, tumor: int = 1, min_tumor: int = 2, max_normal: int = 0, ratio: int = 0):

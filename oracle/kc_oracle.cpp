@@ -52,6 +52,16 @@
 // 10. Filter read hits (the Filter unit reads the input again and looks its
 //     k-mers up in the table): hits[r] = number of valid windows of read r
 //     whose key is selected; a read is a candidate iff hits[r] > 0.
+// 11. Stem-grouped items (Section II-A: a k-mer's stem is its middle k-2
+//     bases; Section III-D: the Filter unit's 72-byte item, 8 bytes of stem
+//     and a 16-bit count per sample for each of the 16 k-mers that extend
+//     the stem by one base on each side).  With canonical keys the library
+//     reads it as: one item per canonical stem c (the smaller of a stem and
+//     its reverse complement) that has a non-zero entry, ascending by c;
+//     entry (x, y), stored at index 4*code(x) + code(y), holds the counts,
+//     clamped to 65535, of the canonical key of the k-mer x c y (0 if that key
+//     is not in the result).  Layout: 8 bytes of stem code, then 16 counts of
+//     sample 0, then 16 of sample 1 (zero for one sample).  Needs k >= 3.
 //
 // Partition-restricted runs (for inputs too large to count in full here):
 // when a keep-set over the top q bits of h is given, windows whose key falls
@@ -60,6 +70,8 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -410,6 +422,48 @@ int64_t orc_filter_reads(void* h, int tumor, uint32_t min_tumor, uint32_t max_no
         if (n_hits) ++candidates;
     }
     return candidates;
+}
+
+// Stem-grouped items (item 11): 72 bytes per item into out.  Every result
+// key is spelled out as a string in both orientations; an orientation whose
+// stem is canonical (not larger than its reverse complement) fills entry
+// (first base, last base) of that stem's item.  Returns the number of items,
+// -1 if k < 3 or capacity (in items) is too small; out == nullptr: size only.
+int64_t orc_stems(void* h, uint8_t* out, uint64_t capacity) {
+    Oracle* o = (Oracle*)h;
+    if (!o || o->k < 3) return -1;
+    const int k = o->k;
+    const char letters[4] = {'A', 'C', 'G', 'T'};
+    struct Item {
+        uint16_t c[2][16];
+    };
+    std::map<uint64_t, Item> items;
+    for (uint64_t key : o->result_keys()) {
+        std::string fwd((size_t)k, 'A');
+        for (int t = 0; t < k; ++t) fwd[t] = letters[(key >> (2 * (k - 1 - t))) & 3];
+        std::string rc((size_t)k, 'A');
+        for (int t = 0; t < k; ++t) rc[t] = complement_base(fwd[k - 1 - t]);
+        const auto& cnt = o->counts.at(key);
+        for (const std::string& kmer : {fwd, rc}) {
+            const std::string stem = kmer.substr(1, k - 2);
+            std::string stem_rc(stem.size(), 'A');
+            for (size_t t = 0; t < stem.size(); ++t) stem_rc[t] = complement_base(stem[stem.size() - 1 - t]);
+            if (stem > stem_rc) continue;  // not the canonical stem: the other orientation fills the entry
+            const uint64_t code = encode(stem.data(), k - 2);
+            Item& it = items[code];  // value-initialised: all counts 0
+            const int e = 4 * base_code(kmer[0]) + base_code(kmer[k - 1]);
+            for (int s = 0; s < o->n_samples; ++s) it.c[s][e] = cnt[s] > 65535u ? 65535u : (uint16_t)cnt[s];
+        }
+    }
+    if (!out) return (int64_t)items.size();
+    if (items.size() > capacity) return -1;
+    size_t i = 0;
+    for (const auto& kv : items) {
+        uint8_t* item = out + 72 * i++;
+        std::memcpy(item, &kv.first, 8);
+        std::memcpy(item + 8, kv.second.c, 64);
+    }
+    return (int64_t)items.size();
 }
 
 void orc_destroy(void* h) { delete (Oracle*)h; }

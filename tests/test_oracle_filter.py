@@ -1,10 +1,14 @@
 """Pins for the oracle's downstream functions: 16-byte items, joint spectrum,
-Filter-unit selection and read hits.
+Filter-unit selection and read hits, stem-grouped 72-byte items.
 
 * brute force by string operations on tiny random inputs (tests/_brute.py);
 * the item layout of Section III-D (8-byte key, two counts in 4 bytes, 4
   bytes of padding) written with struct, and the clamp of a count above
   65535;
+* the paper's stem example (Section II-A: the stem of ACGGCAGC is CGGCAG)
+  and the stem item layout (8-byte stem, 16 + 16 two-byte counts, Section
+  III-D); stem items rebuilt from brute force by enumerating the 16
+  extensions of every canonical stem;
 * a closed form: a tumour genome that differs from the normal one by one
   substitution, read by reads at every start on both strands, has exactly the
   k windows over the substitution as tumour-only k-mers, with counts and read
@@ -188,3 +192,76 @@ def test_filter_needs_two_samples(oracle_mod):
     o = _oracle(oracle_mod, [["ACGTACGT"]], 3, 1)
     with pytest.raises(ValueError):
         o.filter_select(1, 2, 0, 0)
+
+
+def _stem_items_brute(samples, k, min_count):
+    """Stem items from brute-force counts: every canonical stem that a result
+    k-mer has (in either orientation), each of its 16 one-base extensions
+    looked up by its canonical string."""
+    counts = {_brute.as_str(key, k): c for key, c in _brute.count(samples, k, min_count)}
+    stems = set()
+    for kmer in counts:
+        for o in (kmer, _brute.revcomp_str(kmer)):
+            st = o[1:-1]
+            stems.add(min(st, _brute.revcomp_str(st)))
+    out = []
+    for st in sorted(stems):
+        per = [[0] * 16 for _ in range(2)]
+        for xi, x in enumerate("ACGT"):
+            for yi, y in enumerate("ACGT"):
+                c = counts.get(_brute.canonical_str(x + st + y))
+                if c:
+                    for s_i, v in enumerate(c):
+                        per[s_i][4 * xi + yi] = min(v, 65535)
+        out.append(struct.pack("<Q16H16H", _brute.as_int(st), *per[0], *per[1]))
+    return b"".join(out)
+
+
+def test_stem_paper_example(oracle_mod):
+    """Section II-A: the stem of ACGGCAGC is CGGCAG.  Alone, the k-mer gives one
+    item: stem CGGCAG (its own canonical form), count 1 at (first A, last C)."""
+    o = _oracle(oracle_mod, [["ACGGCAGC"]], 8, 1)
+    items = o.stems()
+    assert items.shape == (1, 72)
+    stem, *counts = struct.unpack("<Q16H16H", items[0].tobytes())
+    assert _brute.as_str(stem, 6) == "CGGCAG"
+    assert counts[: 16] == [0, 1] + [0] * 14 and counts[16:] == [0] * 16
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 8])
+@pytest.mark.parametrize("n_samples,min_count", [(1, 1), (2, 1), (2, 2)])
+def test_stems_bruteforce(oracle_mod, k, n_samples, min_count):
+    rng = random.Random(17 * k + 3 * n_samples + min_count)
+    alphabet = "ACG" if k > 4 else "ACGT"  # repeats for larger k; even k also meets palindromic stems
+    samples = [_random_reads(rng, 40, 40, 0.02, alphabet=alphabet) for _ in range(n_samples)]
+    o = _oracle(oracle_mod, samples, k, min_count)
+    got = o.stems()
+    assert got.shape[1] == 72  # Section III-D: 8 bytes of stem, 2 bytes per count, 16 + 16 counts
+    assert got.tobytes() == _stem_items_brute(samples, k, min_count)
+
+
+def test_stems_palindromic_stems(oracle_mod):
+    """k = 4: stem AT is its own reverse complement; AATG and its reverse complement
+    CATT both extend it, so the item holds the count at (A, G) and at (C, T)."""
+    o = _oracle(oracle_mod, [["AATG", "AATG"]], 4, 1)
+    items = o.stems()
+    assert items.tobytes() == _stem_items_brute([["AATG", "AATG"]], 4, 1)
+    rows = {_brute.as_str(struct.unpack("<Q", it[:8].tobytes())[0], 2): it for it in items}
+    c = struct.unpack("<16H", rows["AT"][8:40].tobytes())
+    assert c[4 * 0 + 2] == 2 and c[4 * 1 + 3] == 2  # (A, G) and (C, T)
+
+
+def test_stems_need_k3(oracle_mod):
+    o = _oracle(oracle_mod, [["ACGT"]], 2, 1)
+    with pytest.raises(ValueError):
+        o.stems()
+
+
+def test_stems_count_clamp(oracle_mod):
+    """AAA seen 69,998 times: its stem item (stem A, entry (A, A)) holds 65535."""
+    samples = [["A" * 70_000, "CAGT"], ["AAAC"]]
+    o = _oracle(oracle_mod, samples, 3, 1)
+    items = o.stems()
+    assert items.tobytes() == _stem_items_brute(samples, 3, 1)
+    stem, *counts = struct.unpack("<Q16H16H", items[0].tobytes())
+    assert stem == 0 and counts[0] == 65535 and counts[16] == 1
