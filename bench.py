@@ -346,6 +346,18 @@ def filter_roofline(ms_per_launch, n_bases, n_reads, table_bytes, sm_count, work
             "hbm": hbm}
 
 
+def stem_hbm(n_keys: int, n_items: int, ms: float):
+    """HBM roofline of the stem-table build (all its kernels): algorithmic bytes
+    = the result read once (16 B per key) + the items written (72 B each)."""
+    if ms <= 0:
+        return None
+    algo = 16 * n_keys + 72 * n_items
+    peak, kind = measured_hbm_peak()
+    achieved = algo / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "peak_source": kind, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "algorithmic_bytes": algo}
+
+
 def run_filter_bench(dev, stream, steps: int, warmup: int, flush):
     """Filter unit on a paired job: selection once, then every timed step
     rescans both samples' device-resident reads (kc_filter_reads, hits and
@@ -412,6 +424,12 @@ def run_filter_bench(dev, stream, steps: int, warmup: int, flush):
     # the host hits must be the device ones
     for (hh, _), (dh, _) in zip(outs_h, outs_d):
         assert torch.equal(hh, dh.cpu()), "filter: host and device hits differ"
+    # the stem-grouped table of the same result (built once on the device, then copied out)
+    b0 = c.stats()
+    t0 = time.perf_counter()
+    stems = c.export_stems()
+    stems_wall_ms = (time.perf_counter() - t0) * 1e3
+    stems_ms = c.stats()["ms_stems"] - b0["ms_stems"]
     n_reads = sum(rs.n_reads for rs in w.samples)
     lb = 8  # the selection's lookup table: 2^lb buckets of four 32-bit fingerprints, 2^lb >= 2 x selected keys
     while (1 << lb) < 2 * n_sel:
@@ -432,6 +450,10 @@ def run_filter_bench(dev, stream, steps: int, warmup: int, flush):
                 "d2h_bytes_per_step": int(sum(h.numel() * 4 for h, _ in outs_h) + n_cand * 8),
                 "ms_per_step": round(e2e_s * 1e3, 4)},
         "l2": "256 MiB written between timed steps (outside the step events)",
+        "stems": {"items": int(stems.size), "result_keys": st0["result_keys"], "device_ms": round(stems_ms, 4),
+                  "wall_ms": round(stems_wall_ms, 3),
+                  "keys_per_s": round(st0["result_keys"] / (stems_ms / 1e3), 1) if stems_ms > 0 else None,
+                  "hbm": stem_hbm(st0["result_keys"], int(stems.size), stems_ms)},
     }
     c.close()
     return out

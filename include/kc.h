@@ -165,6 +165,10 @@ typedef struct kc_stats {
      * windows rescanned and windows whose key was selected. */
     double ms_filter_select, ms_filter_reads;
     uint64_t filter_selected, filter_windows, filter_hits;
+    /* Stem table (kc_export_stems; timing as above): device time of building
+     * it, and its number of items. */
+    double ms_stems;
+    uint64_t stem_items;
 } kc_stats;
 
 /*
@@ -391,6 +395,25 @@ kc_status kc_export_items(kc_handle h, kc_item16* items, uint64_t capacity, uint
  * KC_SPECTRUM_MAX_CAP. */
 #define KC_SPECTRUM_MAX_CAP 1023u
 kc_status kc_spectrum(kc_handle h, uint32_t cap, uint64_t* hist);
+
+/* One item of the stem-grouped table (Section II-A: a stem is the middle k-2
+ * bases of a k-mer; Section III-D: a 72-byte item of 8 bytes of stem and a
+ * 2-byte count per sample for each of the 16 k-mers that extend the stem by
+ * one base on each side).  With canonical keys: one item per canonical stem
+ * c (the smaller of a stem and its reverse complement, as a 2(k-2)-bit code)
+ * with at least one non-zero entry; count[s][4 * code(x) + code(y)] =
+ * min(count of sample s of the canonical key of the k-mer x c y, 65535), 0
+ * if that key is not in the result; count[1][*] = 0 for one sample. */
+typedef struct kc_stem_item {
+    uint64_t stem;
+    uint16_t count[2][16];
+} kc_stem_item;
+
+/* Write the stem-grouped table, ascending stems.  Built on the device at the
+ * first call after kc_finalize and kept until kc_reset.  items == NULL: size
+ * query.  KC_ERR_STATE for k < 3; KC_ERR_CAPACITY when capacity (in items) is
+ * smaller than the table. */
+kc_status kc_export_stems(kc_handle h, kc_stem_item* items, uint64_t capacity, uint64_t* n_out);
 
 /*
  * Filter unit (Section II-B): select the k-mers whose counts differ between

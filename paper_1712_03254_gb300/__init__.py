@@ -18,7 +18,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["KmerCounter", "KcBatch", "KcServer", "KcError", "pack_ascii", "lib", "build", "Config", "Stats",
-           "FilterSpec", "ITEM16", "autotune", "tune_lookup", "tune_cache_save", "tune_cache_load", "tune_cache_clear"]
+           "FilterSpec", "ITEM16", "STEM_ITEM", "autotune", "tune_lookup", "tune_cache_save", "tune_cache_load", "tune_cache_clear"]
 
 _lock = threading.Lock()
 _lib = None
@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("fallback_partitions", ctypes.c_uint32), ("split_partitions", ctypes.c_uint32),
                 ("split_level", ctypes.c_uint32), ("ms_filter_select", ctypes.c_double),
                 ("ms_filter_reads", ctypes.c_double), ("filter_selected", ctypes.c_uint64),
-                ("filter_windows", ctypes.c_uint64), ("filter_hits", ctypes.c_uint64)]
+                ("filter_windows", ctypes.c_uint64), ("filter_hits", ctypes.c_uint64),
+                ("ms_stems", ctypes.c_double), ("stem_items", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -66,6 +67,9 @@ class FilterSpec(ctypes.Structure):
 # kc_item16: the 16-byte k-mer item of the joint table
 ITEM16 = np.dtype([("key", "<u8"), ("count", "<u2", (2,)), ("pad", "<u4")])
 assert ITEM16.itemsize == 16
+# kc_stem_item: stem code, then 16 counts per sample (entry 4 * first base + last base)
+STEM_ITEM = np.dtype([("stem", "<u8"), ("count", "<u2", (2, 16))])
+assert STEM_ITEM.itemsize == 72
 
 
 class TuneInput(ctypes.Structure):
@@ -167,6 +171,8 @@ def lib():
             L.kc_tune_cache_clear.restype = None
             L.kc_export_items.argtypes = [p, p, u64, ctypes.POINTER(u64)]
             L.kc_export_items.restype = st
+            L.kc_export_stems.argtypes = [p, p, u64, ctypes.POINTER(u64)]
+            L.kc_export_stems.restype = st
             L.kc_spectrum.argtypes = [p, u32, p]
             L.kc_spectrum.restype = st
             L.kc_filter_select.argtypes = [p, ctypes.POINTER(FilterSpec), ctypes.POINTER(u64)]
@@ -323,6 +329,18 @@ class KmerCounter:
         else:
             cap = (out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes) // 16
         _check(self._L.kc_export_items(self._h, _ptr(out), cap, ctypes.byref(n)), "kc_export_items")
+        return out
+
+    def export_stems(self, out=None):
+        """The stem-grouped table (numpy STEM_ITEM records), or written into out (72 bytes per item)."""
+        n = ctypes.c_uint64()
+        _check(self._L.kc_export_stems(self._h, None, 0, ctypes.byref(n)), "kc_export_stems")
+        if out is None:
+            out = np.empty(n.value, dtype=STEM_ITEM)
+            cap = n.value
+        else:
+            cap = (out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes) // 72
+        _check(self._L.kc_export_stems(self._h, _ptr(out), cap, ctypes.byref(n)), "kc_export_stems")
         return out
 
     def spectrum(self, cap: int, out=None):

@@ -384,54 +384,61 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
     return KC_OK;
 }
 
-// Sort the survivors held in tk/tv (count in host_ctr.survivors, already
-// read back) into res_keys/res_vals: bucket by the top bits of the 2k-bit
-// key (at most about 32 keys a bucket), then sort every bucket: one warp per bucket
-// in registers, larger buckets in shared memory or, rarely, global memory.
-kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
+// Sort n (key, value) pairs held in tk/tv, keys below 2^key_bits, into
+// out_k/out_v (n entries each): bucket by the top key bits (at most about 32
+// keys a bucket), then sort every bucket: one warp per bucket in registers,
+// larger buckets in shared memory or, rarely, global memory.  ctr->survivors
+// must hold n on the device; ctr->err collects the kernels' flags (and is
+// cleared of the sort flags again).  Synchronises the stream.  Device time
+// goes to `phase`.
+kc_status sort_pairs(kc_handle h, const uint64_t* tk, const uint64_t* tv, uint64_t n, int key_bits,
+                     kc::DevCounters* ctr, uint64_t* out_k, uint64_t* out_v, int phase) {
     cudaStream_t st = h->stream;
-    const uint64_t n = h->host_ctr.survivors;
     const uint64_t cap = std::max<uint64_t>(1, n);
     int bits = 0;
-    while (bits < 24 && bits < 2 * h->k && (cap >> bits) > 32) ++bits;
+    while (bits < 24 && bits < key_bits && (cap >> bits) > 32) ++bits;
     const uint64_t n_buckets = 1ull << bits;
-    const int prefix_shift = 2 * h->k - bits;
+    const int prefix_shift = key_bits - bits;
     uint64_t *starts = nullptr, *cursor = nullptr;
     uint32_t* hist = nullptr;
     cudaError_t e;
-    if ((e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&hist, n_buckets * 4, st)) != cudaSuccess ||
+    if ((e = cudaMallocAsync(&hist, n_buckets * 4, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&starts, (n_buckets + 1) * 8, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&cursor, n_buckets * 8, st)) != cudaSuccess) {
         if (hist) cudaFreeAsync(hist, st);
         if (starts) cudaFreeAsync(starts, st);
-        free_result(h);
         return cuda_fail(e, "cudaMallocAsync(sort buffers)");
     }
-    h->res_cap = cap;
+    auto release = [&]() {
+        cudaFreeAsync(hist, st);
+        cudaFreeAsync(starts, st);
+        cudaFreeAsync(cursor, st);
+    };
     cudaEvent_t t0 = phase_begin(h);
     KC_CUDA(cudaMemsetAsync(hist, 0, n_buckets * 4, st));
-    kc::launch_prefix_hist(tk, h->ctr, n, prefix_shift, n_buckets, hist, h->grid, st);
+    kc::launch_prefix_hist(tk, ctr, n, prefix_shift, n_buckets, hist, h->grid, st);
     KC_CUDA(kc::launch_scan(hist, n_buckets, starts, cursor, st));
-    kc::launch_scatter(tk, tv, h->ctr, n, prefix_shift, n_buckets, cursor, h->res_keys, h->res_vals, h->grid, st);
-    kc::launch_bucket_sort_warp(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, h->grid, st);
-    phase_end(h, kSort, t0);
+    kc::launch_scatter(tk, tv, ctr, n, prefix_shift, n_buckets, cursor, out_k, out_v, h->grid, st);
+    kc::launch_bucket_sort_warp(out_k, out_v, starts, n_buckets, ctr, h->grid, st);
+    phase_end(h, phase, t0);
     h->launches += 4;
     KC_LAUNCHED("sort launches");
-    kc_status s = read_counters(h);
-    if (s != KC_OK) return s;
-    if (h->host_ctr.err & kc::DERR_INTERNAL) {
+    unsigned err = 0;
+    KC_CUDA(cudaMemcpyAsync(&err, &ctr->err, 4, cudaMemcpyDeviceToHost, st));
+    KC_CUDA(cudaStreamSynchronize(st));
+    if (err & kc::DERR_INTERNAL) {
+        release();
         h->state = State::Poisoned;
         return fail(KC_ERR_INTERNAL, "sort: key outside its bucket range");
     }
-    if (h->host_ctr.err & kc::DERR_SORT_MEDIUM) {
-        kc::launch_bucket_sort(h->res_keys, h->res_vals, starts, n_buckets, h->ctr, st);
+    if (err & kc::DERR_SORT_MEDIUM) {
+        kc::launch_bucket_sort(out_k, out_v, starts, n_buckets, ctr, st);
         h->launches += 1;
         KC_LAUNCHED("medium sort launch");
-        if ((s = read_counters(h)) != KC_OK) return s;
+        KC_CUDA(cudaMemcpyAsync(&err, &ctr->err, 4, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
     }
-    if (h->host_ctr.err & kc::DERR_SORT_BUCKET) {
+    if (err & kc::DERR_SORT_BUCKET) {
         // Rare: a bucket larger than the shared-memory tile; sort it in global memory.
         std::vector<uint64_t> hs(n_buckets + 1);
         KC_CUDA(cudaMemcpyAsync(hs.data(), starts, (n_buckets + 1) * 8, cudaMemcpyDeviceToHost, st));
@@ -443,19 +450,36 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
                 while (m2 < m) m2 <<= 1;
                 for (uint64_t size = 2; size <= m2; size <<= 1)
                     for (uint64_t stride = size >> 1; stride > 0; stride >>= 1) ++steps;
-                kc::launch_bitonic_global(h->res_keys + hs[i], h->res_vals + hs[i], m, st);
+                kc::launch_bitonic_global(out_k + hs[i], out_v + hs[i], m, st);
                 h->launches += steps;
             }
         KC_LAUNCHED("global sort launches");
     }
-    if (h->host_ctr.err & (kc::DERR_SORT_MEDIUM | kc::DERR_SORT_BUCKET)) {
-        unsigned zero = 0;
-        KC_CUDA(cudaMemcpyAsync(&h->ctr->err, &zero, 4, cudaMemcpyHostToDevice, st));
+    if (err & (kc::DERR_SORT_MEDIUM | kc::DERR_SORT_BUCKET)) {
+        const unsigned keep = err & ~(kc::DERR_SORT_MEDIUM | kc::DERR_SORT_BUCKET);
+        KC_CUDA(cudaMemcpyAsync(&ctr->err, &keep, 4, cudaMemcpyHostToDevice, st));
     }
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(starts, st);
-    cudaFreeAsync(cursor, st);
+    release();
     KC_CUDA(cudaStreamSynchronize(st));
+    return KC_OK;
+}
+
+// Sort the survivors held in tk/tv (count in host_ctr.survivors, already
+// read back and on the device in ctr->survivors) into res_keys/res_vals.
+kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
+    cudaStream_t st = h->stream;
+    const uint64_t n = h->host_ctr.survivors;
+    const uint64_t cap = std::max<uint64_t>(1, n);
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess) {
+        free_result(h);
+        return cuda_fail(e, "cudaMallocAsync(result)");
+    }
+    h->res_cap = cap;
+    kc_status s = sort_pairs(h, tk, tv, n, 2 * h->k, h->ctr, h->res_keys, h->res_vals, kSort);
+    if (s != KC_OK) return s;
+    if ((s = read_counters(h)) != KC_OK) return s;
     phase_collect(h);
     h->n_result = n;
     return KC_OK;
@@ -677,6 +701,7 @@ kc_status kc_reset(kc_handle h) {
     free_batches(h);
     free_result(h);
     free_selection(h);
+    free_stems(h);
     h->filter_windows = h->filter_hits = 0;
     if (!h->spill_dir.empty()) {
         cudaStreamSynchronize(h->copy_stream);
@@ -705,6 +730,7 @@ void kc_destroy(kc_handle h) {
         free_batches(h);
         free_result(h);
         free_selection(h);
+        free_stems(h);
         if (!h->spill_dir.empty()) cudaStreamSynchronize(h->copy_stream);
         release_spill(h);
         free_spill_chunks(h);
@@ -928,6 +954,7 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->spilled_bytes = h->spilled_bytes;
     out->strategy = (uint32_t)h->strategy;
     size_t bytes = h->fixed_bytes + h->res_cap * 16;
+    if (h->has_stems) bytes += std::max<uint64_t>(1, h->n_stems) * sizeof(kc_stem_item);
     if (h->has_selection) bytes += std::max<uint64_t>(1, h->n_sel) * 16 + (48ull << h->sel_buckets_log2) + (h->sel_pre ? 4ull * 49152 : 0);
     for (const auto& b : h->batches) {
         if (b.pw) bytes += (2 * b.n_units + 2) * 8 + b.n_units * 8;
@@ -945,6 +972,8 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->filter_selected = h->has_selection ? h->n_sel : 0;
     out->filter_windows = h->filter_windows;
     out->filter_hits = h->filter_hits;
+    out->ms_stems = h->ms[kStems];
+    out->stem_items = h->has_stems ? h->n_stems : 0;
     return KC_OK;
 }
 

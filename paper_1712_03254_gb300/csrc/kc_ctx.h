@@ -102,7 +102,7 @@ struct kc_ctx {
     };
     std::vector<cudaEvent_t> ev_pool;
     std::vector<Mark> marks;
-    double ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t launches = 0;
     uint32_t fallback_partitions = 0;
 
@@ -124,6 +124,11 @@ struct kc_ctx {
     bool has_selection = false;
     uint64_t filter_windows = 0, filter_hits = 0;  // summed over kc_filter_reads calls
 
+    // stem-grouped items of the result (kc_export_stems), built on first use
+    kc_stem_item* stem_items = nullptr;
+    uint64_t n_stems = 0;
+    bool has_stems = false;
+
 
     kc::PassParams params(int sample) const {
         kc::PassParams p{};
@@ -142,7 +147,16 @@ struct kc_ctx {
 
 namespace kcapi {
 
-enum Phase { kIngest = 0, kPass1 = 1, kPass2 = 2, kCompact = 3, kSort = 4, kFilterSelect = 5, kFilterReads = 6 };
+enum Phase {
+    kIngest = 0,
+    kPass1 = 1,
+    kPass2 = 2,
+    kCompact = 3,
+    kSort = 4,
+    kFilterSelect = 5,
+    kFilterReads = 6,
+    kStems = 7
+};
 
 // Phase timing events, recorded on stream st (the handle's stream if null).
 cudaEvent_t phase_begin(kc_handle h, cudaStream_t st = nullptr);
@@ -160,6 +174,11 @@ bool is_device_ptr(const void* p);
 // (KC_ERR_OOM_DEVICE, nothing changed, when it does not fit).
 kc_status resort_spilled(kc_handle h);
 void free_selection(kc_handle h);
+void free_stems(kc_handle h);
+// Sort n (key, value) pairs (keys below 2^key_bits) from tk/tv into out_k/out_v;
+// ctr->survivors holds n on the device; synchronises the stream.
+kc_status sort_pairs(kc_handle h, const uint64_t* tk, const uint64_t* tv, uint64_t n, int key_bits,
+                     kc::DevCounters* ctr, uint64_t* out_k, uint64_t* out_v, int phase);
 
 }  // namespace kcapi
 

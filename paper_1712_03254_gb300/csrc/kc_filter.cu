@@ -355,6 +355,101 @@ __global__ void __launch_bounds__(256) k_spectrum(const uint64_t* __restrict__ v
             if (local[b]) atomicAdd(hist + b, (unsigned long long)local[b]);
 }
 
+// Stem-grouped items.  A result key K = x S y (first base x, stem S of k-2
+// bases, last base y) fills entry (x, y) of stem S when S is canonical (not
+// above its reverse complement S'); otherwise its reverse complement
+// y' S' x' (complements y', x') fills entry (y', x') of stem S'.  A stem that
+// is its own reverse complement gets both entries.  One record per entry:
+// key = stem << 4 | entry, value = the key's packed counts; records are
+// claimed with one atomic per warp.
+__global__ void k_stem_records(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals, uint64_t n,
+                               int k, uint64_t* __restrict__ rec_keys, uint64_t* __restrict__ rec_vals,
+                               DevCounters* __restrict__ ctr) {
+    const int lane = threadIdx.x & 31;
+    const int sb = 2 * (k - 2);  // stem bits, 2..58
+    const uint64_t smask = (1ull << sb) - 1ull;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_round = (n + 31) & ~31ull;  // whole warps take part in every round
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        uint64_t r0 = 0, r1 = 0, v = 0;
+        int cnt = 0;
+        if (i < n) {
+            const uint64_t K = keys[i];
+            v = vals[i];
+            const uint64_t x = K >> (2 * k - 2), y = K & 3ull;
+            const uint64_t S = (K >> 2) & smask;
+            const uint64_t Sr = reverse_pairs(S ^ smask) >> (64 - sb);
+            const uint64_t e_fwd = 4 * x + y, e_rev = 4 * (3 - y) + (3 - x);
+            if (S < Sr) {
+                r0 = (S << 4) | e_fwd;
+                cnt = 1;
+            } else if (S > Sr) {
+                r0 = (Sr << 4) | e_rev;
+                cnt = 1;
+            } else {
+                r0 = (S << 4) | e_fwd;
+                r1 = (S << 4) | e_rev;
+                cnt = e_rev == e_fwd ? 1 : 2;  // equal only for a k-mer that is its own reverse complement
+            }
+        }
+        // warp-aggregated claim of cnt slots per lane
+        unsigned incl = (unsigned)cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && total) base = atomicAdd(&ctr->survivors, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        const uint64_t pos = base + incl - cnt;
+        if (cnt >= 1) {
+            rec_keys[pos] = r0;
+            rec_vals[pos] = v;
+        }
+        if (cnt == 2) {
+            rec_keys[pos + 1] = r1;
+            rec_vals[pos + 1] = v;
+        }
+    }
+}
+
+// A sorted record starts an item when its stem differs from the previous one.
+struct StemStartPred {
+    const uint64_t* rec_keys;
+    __device__ bool operator()(uint64_t i) const { return i == 0 || (rec_keys[i] >> 4) != (rec_keys[i - 1] >> 4); }
+};
+
+// One thread per item: its records are starts[j] .. starts[j+1] - 1 (n_rec
+// for the last); 72 bytes = stem, 16 counts of sample 0, 16 of sample 1, as
+// nine 64-bit words (count e of a sample in bits 16 (e % 4) of word e / 4).
+__global__ void k_stem_items(const uint64_t* __restrict__ rec_keys, const uint64_t* __restrict__ rec_vals,
+                             uint64_t n_rec, const uint64_t* __restrict__ starts, uint64_t n_items, int n_samples,
+                             uint64_t* __restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_items; j += stride) {
+        const uint64_t s0 = starts[j], s1 = j + 1 < n_items ? starts[j + 1] : n_rec;
+        uint64_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint64_t r = s0; r < s1; ++r) {
+            const int e = (int)(rec_keys[r] & 15ull);
+            const uint64_t v = rec_vals[r];
+            const uint64_t lo = (uint32_t)v, hi = n_samples == 2 ? v >> 32 : 0ull;
+            const uint64_t c0 = lo < 65535u ? lo : 65535u, c1 = hi < 65535u ? hi : 65535u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((e >> 2) == q) {  // registers stay registers: the word is chosen by unrolled compares
+                    w[q] |= c0 << (16 * (e & 3));
+                    w[4 + q] |= c1 << (16 * (e & 3));
+                }
+        }
+        uint64_t* o = out + 9 * j;
+        o[0] = rec_keys[s0] >> 4;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[1 + q] = w[q];
+    }
+}
+
 unsigned grid_of(uint64_t n, unsigned block, unsigned cap) {
     uint64_t g = (n + block - 1) / block;
     if (g < 1) g = 1;
@@ -405,6 +500,13 @@ void free_selection(kc_handle h) {
     h->sel_buckets_log2 = 0;
     h->sel_pre = false;
     h->has_selection = false;
+}
+
+void free_stems(kc_handle h) {
+    if (h->stem_items) cudaFreeAsync(h->stem_items, h->stream);
+    h->stem_items = nullptr;
+    h->n_stems = 0;
+    h->has_stems = false;
 }
 
 namespace {
@@ -528,6 +630,83 @@ kc_status kc_spectrum(kc_handle h, uint32_t cap, uint64_t* hist) {
         cudaFreeAsync(out, st);
     }
     KC_CUDA(cudaStreamSynchronize(st));
+    return KC_OK;
+}
+
+// Build the stem items of the result on the device (kept until kc_reset).
+static kc_status build_stems(kc_handle h) {
+    cudaStream_t st = h->stream;
+    const uint64_t n = h->n_result;
+    const uint64_t cap = std::max<uint64_t>(1, 2 * n);
+    uint64_t *rk = nullptr, *rv = nullptr, *sk = nullptr, *sv = nullptr, *starts = nullptr;
+    kc::DevCounters* sctr = nullptr;
+    auto release = [&]() {
+        for (void* q : {(void*)rk, (void*)rv, (void*)sk, (void*)sv, (void*)starts, (void*)sctr})
+            if (q) cudaFreeAsync(q, st);
+    };
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&rk, cap * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&rv, cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&sk, cap * 8, st)) != cudaSuccess || (e = cudaMallocAsync(&sv, cap * 8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&sctr, sizeof(kc::DevCounters), st)) != cudaSuccess) {
+        release();
+        return cuda_fail(e, "cudaMallocAsync(stem records)");
+    }
+    auto run = [&]() -> kc_status {
+        KC_CUDA(cudaMemsetAsync(sctr, 0, sizeof(kc::DevCounters), st));
+        cudaEvent_t t0 = phase_begin(h);
+        if (n)
+            kc::k_stem_records<<<kc::grid_of(n, 256, h->grid.sm_count * 8), 256, 0, st>>>(
+                h->res_keys, h->res_vals, n, h->k, rk, rv, sctr);
+        phase_end(h, kStems, t0);
+        h->launches += 1;
+        KC_LAUNCHED("stem record launch");
+        uint64_t n_rec = 0;
+        KC_CUDA(cudaMemcpyAsync(&n_rec, &sctr->survivors, 8, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        if (n_rec > cap) {
+            h->state = State::Poisoned;
+            return fail(KC_ERR_INTERNAL, "stem records: more than two per key");
+        }
+        kc_status s = sort_pairs(h, rk, rv, n_rec, 2 * (h->k - 2) + 4, sctr, sk, sv, kStems);
+        if (s != KC_OK) return s;
+        KC_CUDA(cudaMallocAsync(&starts, std::max<uint64_t>(1, n_rec) * 8, st));
+        uint64_t n_items = 0;
+        t0 = phase_begin(h);
+        s = compact_ordered(h, kc::StemStartPred{sk}, kc::IndexWrite{starts}, n_rec, &n_items, true);
+        if (s != KC_OK) return s;
+        KC_CUDA(cudaMallocAsync(&h->stem_items, std::max<uint64_t>(1, n_items) * sizeof(kc_stem_item), st));
+        if (n_items)
+            kc::k_stem_items<<<kc::grid_of(n_items, 256, h->grid.sm_count * 8), 256, 0, st>>>(
+                sk, sv, n_rec, starts, n_items, h->n_samples, reinterpret_cast<uint64_t*>(h->stem_items));
+        phase_end(h, kStems, t0);
+        h->launches += 1;
+        KC_LAUNCHED("stem item launch");
+        KC_CUDA(cudaStreamSynchronize(st));
+        phase_collect(h);
+        h->n_stems = n_items;
+        h->has_stems = true;
+        return KC_OK;
+    };
+    kc_status s = run();
+    if (s != KC_OK) {
+        cudaStreamSynchronize(st);
+        free_stems(h);
+    }
+    release();
+    return s;
+}
+
+kc_status kc_export_stems(kc_handle h, kc_stem_item* items, uint64_t capacity, uint64_t* n_out) {
+    kc_status s = device_result(h, "kc_export_stems");
+    if (s != KC_OK) return s;
+    if (h->k < 3) return fail(KC_ERR_STATE, "kc_export_stems needs k >= 3 (a stem is the middle k - 2 bases)");
+    if (!h->has_stems && (s = build_stems(h)) != KC_OK) return s;
+    if (n_out) *n_out = h->n_stems;
+    if (!items) return KC_OK;
+    if (capacity < h->n_stems) return fail(KC_ERR_CAPACITY, "item capacity smaller than the stem table");
+    if (h->n_stems == 0) return KC_OK;
+    KC_CUDA(cudaMemcpyAsync(items, h->stem_items, h->n_stems * sizeof(kc_stem_item), cudaMemcpyDefault, h->stream));
+    KC_CUDA(cudaStreamSynchronize(h->stream));
     return KC_OK;
 }
 

@@ -72,6 +72,7 @@ def test_null_handle_calls_fail_cleanly():
     assert L.kc_add_reads(None, 0, None, None, None, 0) == 1
     assert L.kc_export_items(None, None, 0, ctypes.byref(n)) == 1
     assert L.kc_spectrum(None, 4, None) == 1
+    assert L.kc_export_stems(None, None, 0, ctypes.byref(n)) == 1
     spec = kc.FilterSpec(1, 2, 0, 0)
     assert L.kc_filter_select(None, ctypes.byref(spec), ctypes.byref(n)) == 1
     assert L.kc_filter_keys(None, None, None, 0, ctypes.byref(n)) == 1
@@ -83,12 +84,14 @@ def test_item16_layout_matches_the_header(tmp_path):
     """kc_item16 is the 16-byte item of Section III-D: key at 0, counts at 8 and 10, padding at 12."""
     src = tmp_path / "layout.c"
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "kc.h"\n'
-                   'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(kc_item16), offsetof(kc_item16, key),'
-                   ' offsetof(kc_item16, count), offsetof(kc_item16, pad), sizeof(kc_filter_spec)); return 0; }\n')
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(kc_item16), offsetof(kc_item16, key),'
+                   ' offsetof(kc_item16, count), offsetof(kc_item16, pad), sizeof(kc_filter_spec),'
+                   ' sizeof(kc_stem_item), offsetof(kc_stem_item, count)); return 0; }\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    assert [int(x) for x in out] == [16, 0, 8, 12, ctypes.sizeof(kc.FilterSpec)]
+    assert [int(x) for x in out] == [16, 0, 8, 12, ctypes.sizeof(kc.FilterSpec), 72, 8]
+    assert kc.STEM_ITEM.itemsize == 72 and kc.STEM_ITEM.fields["count"][1] == 8
     assert kc.ITEM16.itemsize == 16 and kc.ITEM16.fields["count"][1] == 8 and kc.ITEM16.fields["pad"][1] == 12
 
 

@@ -295,3 +295,84 @@ def test_filter_bench_size_properties(oracle_mod):
     ok, oc = o.filter_select(*spec)
     mine = np.isin(oracle_mod.partitions(sk, q), parts)
     assert np.array_equal(sk[mine], ok) and np.array_equal(sc[mine], oc)
+
+
+def test_stems_parity_two_samples(paired_small, strategy):
+    w, o = paired_small
+    c = gpu_count(w, strategy=strategy)
+    got = c.export_stems()
+    assert got.tobytes() == o.stems().tobytes()
+    assert c.stats()["stem_items"] == got.size
+
+
+@pytest.mark.parametrize("k", [3, 4, 8, 16, 31])
+def test_stems_parity_ragged_even_and_odd_k(oracle_mod, k):
+    """Even k: stems of even length can be their own reverse complement (two
+    entries per key); odd k: never."""
+    rng = random.Random(400 + k)
+    alphabet = "AT" if k <= 8 else "ACGT"
+    reads = ["".join("N" if rng.random() < 0.01 else rng.choice(alphabet) for _ in range(rng.randint(0, 200)))
+             for _ in range(600)]
+    w = synth.Workload("ragged", [synth.ReadSet.from_strings(reads)], k, 1 << 20, 3, 1)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, table_slots=1 << 18)
+    assert c.export_stems().tobytes() == o.stems().tobytes()
+
+
+def test_stems_clamp_device_buffer_and_errors(oracle_mod):
+    torch = pytest.importorskip("torch")
+    normal = ["A" * 70_000, "ACGTTGCA" * 3]
+    tumour = ["AAAC", "ACGTTGCA" * 3, "C" * 40]
+    w = synth.Workload("clamp", [synth.ReadSet.from_strings(normal), synth.ReadSet.from_strings(tumour)],
+                       3, 1 << 16, 4, 2)
+    o = oracle_mod.count(w)
+    c = gpu_count(w, table_slots=1 << 12)
+    items = c.export_stems()
+    assert items.tobytes() == o.stems().tobytes()
+    assert items[0]["stem"] == 0 and items[0]["count"][0][0] == 65535
+    out = torch.empty(9 * items.size, dtype=torch.int64, device="cuda")
+    c.export_stems(out)
+    assert out.cpu().numpy().view(np.uint8).tobytes() == o.stems().tobytes()
+    with pytest.raises(kc.KcError) as e:
+        c.export_stems(out[: 9 * (items.size - 1)])
+    assert e.value.name == "KC_ERR_CAPACITY"
+    # after a reset the table is rebuilt for the new job
+    c.reset()
+    c.add_readset(0, w.samples[1])
+    c.finalize()
+    o2 = oracle_mod.Oracle(3, 2, 1 << 16, 4, 2)
+    o2.add_reads(0, w.samples[1])
+    assert c.export_stems().tobytes() == o2.stems().tobytes()
+    # k < 3 has no stems
+    c2 = kc.KmerCounter(2, 1, 1 << 16, 4, 1)
+    c2.add_readset(0, synth.ReadSet.from_strings(["ACGTACGT"]))
+    c2.finalize()
+    with pytest.raises(kc.KcError) as e:
+        c2.export_stems()
+    assert e.value.name == "KC_ERR_STATE"
+
+
+@pytest.mark.parametrize("spill", [1, 2])
+def test_stems_of_a_spilled_result(paired_small, spill):
+    w, o = paired_small
+    w2 = synth.Workload(w.name, w.samples, w.k, 1 << 28, w.n_hashes, w.min_count)
+    c = gpu_count(w2, strategy="partitioned", part_bits=10, spill=spill)
+    assert c.export_stems().tobytes() == o.stems().tobytes()
+
+
+def test_stems_bench_size_properties():
+    """Paired shape of the benchmark (2 x 1,000,000 reads, k = 31): a stem of
+    29 bases is never its own reverse complement, so every result key fills
+    exactly one entry: the entries add up to the dump's counts per sample,
+    stems are strictly ascending and every item has an entry."""
+    w = synth.paired(scale=0.1)
+    c = gpu_count(w)
+    keys, counts = c.dump()
+    items = c.export_stems()
+    cnt = items["count"].astype(np.uint64)  # [n, 2, 16]
+    assert counts.max() < 65535
+    for s in range(2):
+        assert int(cnt[:, s, :].sum()) == int(counts[:, s].sum(dtype=np.uint64))
+    assert int(((cnt[:, 0, :] + cnt[:, 1, :]) > 0).sum()) == keys.size
+    assert np.all(np.diff(items["stem"].astype(np.uint64)) > 0)
+    assert np.all((cnt.sum(axis=(1, 2))) > 0)
