@@ -76,6 +76,8 @@ def _load():
         lib.orc_filter_reads.restype = ctypes.c_int64
         lib.orc_stems.argtypes = [p, p, u64]
         lib.orc_stems.restype = ctypes.c_int64
+        lib.orc_bloom2_bounds.argtypes = [p, p, p, u64, u64]
+        lib.orc_bloom2_bounds.restype = i
         lib.orc_destroy.argtypes = [p]
         lib.orc_destroy.restype = None
         _lib = lib
@@ -163,6 +165,17 @@ class Oracle:
         if self._lib.orc_bloom(self._h, out.ctypes.data, first, n) != 0:
             raise ValueError("oracle: bloom range")
         return out
+
+    def bloom2_bounds(self, first: int = 0, n: int | None = None):
+        """(lower, upper) word arrays that bound the Prune chain's second filter for any insertion order."""
+        nw = self.bloom_bits // 64
+        if n is None:
+            n = nw - first
+        lo = np.zeros(n, dtype=np.uint64)
+        hi = np.zeros(n, dtype=np.uint64)
+        if self._lib.orc_bloom2_bounds(self._h, lo.ctypes.data, hi.ctypes.data, first, n) != 0:
+            raise ValueError("oracle: bloom2 bounds")
+        return lo, hi
 
     def bloom_query(self, key: int) -> bool:
         return bool(self._lib.orc_bloom_query(self._h, key))

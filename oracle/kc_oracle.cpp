@@ -62,6 +62,20 @@
 //     clamped to 65535, of the canonical key of the k-mer x c y (0 if that key
 //     is not in the result).  Layout: 8 bytes of stem code, then 16 counts of
 //     sample 0, then 16 of sample 1 (zero for one sample).  Needs k >= 3.
+// 12. Two-filter Prune chain (Section III, Prune unit: every k-mer goes into
+//     a first filter; one already present there, or a false positive, goes
+//     into a second filter, which then holds the k-mers seen more than once;
+//     the Count unit counts only k-mers found in the second filter).  The
+//     second filter's content depends on the order of the insertions: a key
+//     seen once lands in it only if other keys set all its bits in the first
+//     filter before it.  For every order of the windows it lies between
+//        lower = OR of pattern(key) at word(key) over keys with summed count >= 2
+//        upper = lower OR, for every key with summed count 1 whose pattern is
+//                inside the OR of the other keys' patterns at its word, its
+//                pattern at its word
+//     (same words and patterns as item 6).  The counting result is the same
+//     as without the chain: the count pass is exact for the keys of the
+//     second filter and keeps those whose count reaches min_count.
 //
 // Partition-restricted runs (for inputs too large to count in full here):
 // when a keep-set over the top q bits of h is given, windows whose key falls
@@ -464,6 +478,39 @@ int64_t orc_stems(void* h, uint8_t* out, uint64_t capacity) {
         std::memcpy(item + 8, kv.second.c, 64);
     }
     return (int64_t)items.size();
+}
+
+// Bounds of the Prune chain's second filter (item 12), words [first, first +
+// n) of each.  Unrestricted runs only.  Returns 0, or -1 for a bad range.
+int orc_bloom2_bounds(void* h, uint64_t* lower, uint64_t* upper, uint64_t first, uint64_t n) {
+    Oracle* o = (Oracle*)h;
+    const uint64_t nw = o->bloom_bits / 64;
+    if (o->restrict_bits != 0 || first > nw || n > nw - first) return -1;
+    std::unordered_map<uint64_t, std::vector<uint64_t>> by_word;  // word -> keys counted there
+    for (const auto& kv : o->counts) by_word[o->word_of(kv.first)].push_back(kv.first);
+    for (uint64_t i = 0; i < n; ++i) lower[i] = upper[i] = 0;
+    for (const auto& wk : by_word) {
+        const uint64_t w = wk.first;
+        if (w < first || w >= first + n) continue;
+        uint64_t lo = 0, hi = 0;
+        for (uint64_t key : wk.second) {
+            uint64_t total = 0;
+            for (uint32_t c : o->counts.at(key)) total += c;
+            const uint64_t pat = o->pattern_of(key);
+            if (total >= 2) {
+                lo |= pat;
+                hi |= pat;
+                continue;
+            }
+            uint64_t others = 0;
+            for (uint64_t other : wk.second)
+                if (other != key) others |= o->pattern_of(other);
+            if ((others & pat) == pat) hi |= pat;
+        }
+        lower[w - first] = lo;
+        upper[w - first] = hi;
+    }
+    return 0;
 }
 
 void orc_destroy(void* h) { delete (Oracle*)h; }
