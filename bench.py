@@ -27,6 +27,9 @@ distinct k-mer) through one-at-a-time plain jobs and through the
 continuous-batching server, at 0.7 and 0.9 of the plain capacity and all at
 once; latencies count from each job's scheduled arrival.
 
+The "prune_chain" field times the paper's two-filter Prune chain (direct
+strategy) on the mid job beside the direct strategy without it.
+
 The "filter" field times the Filter unit downstream of the count on a
 paired normal/tumour job of 2 x 1,000,000 reads: the selection of imbalanced
 k-mers once, then per step both samples' reads rescanned against it (hits per
@@ -346,6 +349,50 @@ def filter_roofline(ms_per_launch, n_bases, n_reads, table_bytes, sm_count, work
             "hbm": hbm}
 
 
+def run_chain_bench(w, chunks_d, stream, steps: int, warmup: int, flush):
+    """The paper's two-filter Prune chain (direct strategy) on the same job,
+    beside the direct strategy without it: device-resident inputs, CUDA events
+    on the library's stream, the same L2 flush between steps."""
+    import torch
+
+    import paper_1712_03254_gb300 as kc
+
+    out = {}
+    for name, chain in (("direct", False), ("direct_prune_chain", True)):
+        c = kc.KmerCounter(w.k, len(w.samples), w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots,
+                           strategy="direct", timing=True, prune_chain=chain, stream=stream)
+
+        def job():
+            c.reset()
+            for s_i, p_, o_, m_ in chunks_d:
+                c.add_reads(s_i, p_, o_, m_)
+            c.finalize()
+
+        for _ in range(max(1, warmup)):
+            job()
+        ms, phases = [], {"pass1": [], "pass2": []}
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            job()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            st = c.stats()
+            for k in phases:
+                phases[k].append(st["ms_" + k])
+        st = c.stats()
+        out[name] = {"ms_per_job": round(statistics.mean(ms), 4),
+                     "k_mers_per_s": round(st["windows"] / (statistics.mean(ms) / 1e3), 1),
+                     "pass1_ms": round(statistics.mean(phases["pass1"]), 4),
+                     "pass2_ms": round(statistics.mean(phases["pass2"]), 4),
+                     "result_keys": st["result_keys"], "table_keys": st["table_keys"]}
+        c.close()
+    return out
+
+
 def stem_hbm(n_keys: int, n_items: int, ms: float):
     """HBM roofline of the stem-table build (all its kernels): algorithmic bytes
     = the result read once (16 B per key) + the items written (72 B each)."""
@@ -640,9 +687,10 @@ def run_kc(args):
                "sample": f"first {n_s:,} of {rs.n_reads:,} reads of the {args.workload} workload ({win:,} windows, "
                          f"{dt:.1f} s, single-threaded C++ oracle, {os.cpu_count()} host cores present)"}
 
-    filt = None
+    filt = chain = None
     if rank == 0 and world == 1 and not args.no_filter and args.workload == "mid":
         filt = run_filter_bench(dev, stream, args.steps, args.warmup, flush)
+        chain = run_chain_bench(w, chunks_d, stream, min(args.steps, 5), args.warmup, flush)
 
     served = None
     if rank == 0 and world == 1 and not args.no_served and args.workload == "mid":
@@ -676,6 +724,7 @@ def run_kc(args):
             "gpu_launches": int(launches),
             "served": served,
             "filter": filt,
+            "prune_chain": chain,
         }
         print(json.dumps(line), flush=True)
     c.close()

@@ -111,7 +111,16 @@ typedef struct kc_config {
                                      its filter slice before it falls back to a
                                      global table (0 = 6; at most the slice's
                                      log2 words; KC_SPLIT_NONE = never split)       */
-    uint64_t reserved[4];
+    uint32_t prune_chain;         /* 1: the paper's two-filter Prune chain (direct
+                                     strategy; KC_ERR_ARG with the partitioned one):
+                                     kc_add_reads puts every window into the filter
+                                     and a window whose bits were all set already
+                                     into a second filter of the same size;
+                                     kc_finalize counts, in one exact pass, the
+                                     windows whose key is in the second filter (see
+                                     kc_export_bloom2).  The result is the same.    */
+    uint32_t reserved32;
+    uint64_t reserved[3];
 } kc_config;
 
 #define KC_SPLIT_NONE 0xffffffffu
@@ -361,6 +370,13 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
  * checkpoints).  Blocks until pending work is done.  With the partitioned
  * strategy the filter is built by kc_finalize (all zero before). */
 kc_status kc_export_bloom(kc_handle h, uint64_t* words, uint64_t first_word, uint64_t n_words);
+
+/* Copy words [first_word, first_word + n_words) of the Prune chain's second
+ * filter (kc_config.prune_chain = 1; KC_ERR_STATE otherwise).  Its content
+ * depends on the order in which concurrent windows reach the first filter: it
+ * holds every key seen at least twice, and a key seen once only if other keys
+ * had set all of its bits before it. */
+kc_status kc_export_bloom2(kc_handle h, uint64_t* words, uint64_t first_word, uint64_t n_words);
 
 kc_status kc_stats_get(kc_handle h, kc_stats* out);
 

@@ -39,7 +39,8 @@ class Config(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("part_bits", ctypes.c_uint32),
                 ("table_slots", ctypes.c_uint64), ("spill", ctypes.c_uint32), ("timing", ctypes.c_uint32),
                 ("strategy", ctypes.c_uint32), ("smem_table_log2", ctypes.c_uint32),
-                ("scatter_mode", ctypes.c_uint32), ("split_max", ctypes.c_uint32), ("reserved", ctypes.c_uint64 * 4)]
+                ("scatter_mode", ctypes.c_uint32), ("split_max", ctypes.c_uint32), ("prune_chain", ctypes.c_uint32),
+                ("reserved32", ctypes.c_uint32), ("reserved", ctypes.c_uint64 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -126,6 +127,8 @@ def lib():
             L.kc_dump.restype = st
             L.kc_export_bloom.argtypes = [p, p, u64, u64]
             L.kc_export_bloom.restype = st
+            L.kc_export_bloom2.argtypes = [p, p, u64, u64]
+            L.kc_export_bloom2.restype = st
             L.kc_stats_get.argtypes = [p, ctypes.POINTER(Stats)]
             L.kc_stats_get.restype = st
             L.kc_reset.argtypes = [p]
@@ -227,7 +230,7 @@ class KmerCounter:
     def __init__(self, k: int, n_samples: int, bloom_bits: int, n_hashes: int = 4, min_count: int = 2,
                  table_slots: int = 0, part_bits: int = 0, spill: bool = False, ctas_per_sm: int = 0,
                  timing: bool = False, strategy: str = "auto", smem_table_log2: int = 0, scatter_mode: int = 0,
-                 split_max: int = 0, tune_bases: int = 0, stream=None):
+                 split_max: int = 0, tune_bases: int = 0, prune_chain: bool = False, stream=None):
         L = lib()
         cfg = Config()
         L.kc_default_config(ctypes.byref(cfg))
@@ -252,6 +255,7 @@ class KmerCounter:
         cfg.smem_table_log2 = smem_table_log2
         cfg.scatter_mode = scatter_mode
         cfg.split_max = SPLIT_NONE if split_max < 0 else split_max  # -1: never split an overflowing partition
+        cfg.prune_chain = int(prune_chain)  # the paper's two-filter chain (direct strategy)
         h = ctypes.c_void_p()
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
@@ -311,6 +315,16 @@ class KmerCounter:
         if out is None:
             out = np.empty(n, dtype=np.uint64)
         _check(self._L.kc_export_bloom(self._h, _ptr(out), first, n), "kc_export_bloom")
+        return out
+
+    def export_bloom2(self, first: int = 0, n: int | None = None, out=None):
+        """Words of the Prune chain's second filter (prune_chain=True handles)."""
+        nw = self.bloom_bits // 64
+        if n is None:
+            n = nw - first
+        if out is None:
+            out = np.empty(n, dtype=np.uint64)
+        _check(self._L.kc_export_bloom2(self._h, _ptr(out), first, n), "kc_export_bloom2")
         return out
 
     def stats(self) -> dict:

@@ -488,8 +488,13 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
 kc_status finalize_direct(kc_handle h) {
     cudaStream_t st = h->stream;
     cudaEvent_t t0 = phase_begin(h);
-    for (const auto& b : h->batches)
-        kc::launch_pass2(b.pw, b.vw, b.n_units, h->params(b.sample), h->table, h->ctr, h->grid, st);
+    for (const auto& b : h->batches) {
+        if (h->bloom2)
+            kc::launch_count_chain(b.pw, b.vw, b.n_units, h->params(b.sample), h->bloom2, h->table, h->ctr, h->grid,
+                                   st);
+        else
+            kc::launch_pass2(b.pw, b.vw, b.n_units, h->params(b.sample), h->table, h->ctr, h->grid, st);
+    }
     phase_end(h, kPass2, t0);
     h->launches += h->batches.size();
     KC_LAUNCHED("direct recount launch");
@@ -626,6 +631,9 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     if (c.split_max != KC_SPLIT_NONE && c.split_max > 13) return fail(KC_ERR_ARG, "split_max must be in 0..13");
     if (c.spill > 2) return fail(KC_ERR_ARG, "spill must be 0, 1 or 2");
     if (c.ctas_per_sm > 64) return fail(KC_ERR_ARG, "ctas_per_sm must be in 0..64");
+    if (c.prune_chain > 1) return fail(KC_ERR_ARG, "prune_chain must be 0 or 1");
+    if (c.prune_chain && c.strategy == KC_STRATEGY_PARTITIONED)
+        return fail(KC_ERR_ARG, "prune_chain runs on the direct strategy");
     // Partitions: filter slices of 4096 words (32 KiB) unless set; the
     // partitioned strategy needs a slice of at most 8192 words in shared memory.
     const int lw = log2_exact(bloom_bits / 64);
@@ -633,7 +641,8 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     pb = std::min(pb, lw);
     const bool part_ok = lw - pb <= 13 && pb >= 1;
     int strategy = (int)c.strategy;
-    if (strategy == KC_STRATEGY_AUTO) strategy = part_ok ? KC_STRATEGY_PARTITIONED : KC_STRATEGY_DIRECT;
+    if (strategy == KC_STRATEGY_AUTO)
+        strategy = part_ok && !c.prune_chain ? KC_STRATEGY_PARTITIONED : KC_STRATEGY_DIRECT;
     if (strategy == KC_STRATEGY_PARTITIONED && !part_ok)
         return fail(KC_ERR_ARG, "partitioned strategy: filter slice per partition exceeds 8192 words");
 
@@ -687,9 +696,11 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
         return bail(cuda_fail(e, "cudaMallocAsync(filter)"));
     if (table_bytes && (e = cudaMallocAsync(&h->table, table_bytes, h->stream)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMallocAsync(table)"));
+    if (c.prune_chain && (e = cudaMallocAsync(&h->bloom2, bloom_bytes, h->stream)) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMallocAsync(second filter)"));
     if ((e = cudaMallocAsync(&h->ctr, sizeof(kc::DevCounters), h->stream)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMallocAsync(counters)"));
-    h->fixed_bytes = bloom_bytes + table_bytes + sizeof(kc::DevCounters);
+    h->fixed_bytes = bloom_bytes * (c.prune_chain ? 2 : 1) + table_bytes + sizeof(kc::DevCounters);
     kc_status s = kc_reset(h);
     if (s != KC_OK) return bail(s);
     *out = h;
@@ -708,6 +719,7 @@ kc_status kc_reset(kc_handle h) {
         release_spill(h);
     }
     KC_CUDA(cudaMemsetAsync(h->bloom, 0, h->bloom_bits / 8, h->stream));
+    if (h->bloom2) KC_CUDA(cudaMemsetAsync(h->bloom2, 0, h->bloom_bits / 8, h->stream));
     if (h->table) KC_CUDA(cudaMemsetAsync(h->table, 0, h->n_slots * sizeof(kc::Slot), h->stream));
     KC_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(kc::DevCounters), h->stream));
     h->bases = 0;
@@ -735,6 +747,7 @@ void kc_destroy(kc_handle h) {
         release_spill(h);
         free_spill_chunks(h);
         if (h->bloom) cudaFreeAsync(h->bloom, h->stream);
+        if (h->bloom2) cudaFreeAsync(h->bloom2, h->stream);
         if (h->table) cudaFreeAsync(h->table, h->stream);
         if (h->ctr) cudaFreeAsync(h->ctr, h->stream);
     }
@@ -832,7 +845,10 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     phase_end(h, kIngest, t0);
     t0 = phase_begin(h);
     if (h->strategy == KC_STRATEGY_DIRECT) {
-        kc::launch_pass1(b.pw, b.vw, n_units, h->params(sample), h->bloom, h->table, h->ctr, h->grid, st);
+        if (h->bloom2)
+            kc::launch_prune(b.pw, b.vw, n_units, h->params(sample), h->bloom, h->bloom2, h->ctr, h->grid, st);
+        else
+            kc::launch_pass1(b.pw, b.vw, n_units, h->params(sample), h->bloom, h->table, h->ctr, h->grid, st);
         h->launches += 3;
     } else {
         s = bucket_batch(h, b, n_local, st);
@@ -931,6 +947,16 @@ kc_status kc_export_bloom(kc_handle h, uint64_t* words, uint64_t first_word, uin
     const uint64_t nw = h->bloom_bits / 64;
     if (!words || first_word > nw || n_words > nw - first_word) return fail(KC_ERR_ARG, "filter range");
     KC_CUDA(cudaMemcpyAsync(words, h->bloom + first_word, n_words * 8, cudaMemcpyDefault, h->stream));
+    KC_CUDA(cudaStreamSynchronize(h->stream));
+    return KC_OK;
+}
+
+kc_status kc_export_bloom2(kc_handle h, uint64_t* words, uint64_t first_word, uint64_t n_words) {
+    if (!h) return fail(KC_ERR_ARG, "null handle");
+    if (!h->bloom2) return fail(KC_ERR_STATE, "no second filter: the handle was not created with prune_chain = 1");
+    const uint64_t nw = h->bloom_bits / 64;
+    if (!words || first_word > nw || n_words > nw - first_word) return fail(KC_ERR_ARG, "filter range");
+    KC_CUDA(cudaMemcpyAsync(words, h->bloom2 + first_word, n_words * 8, cudaMemcpyDefault, h->stream));
     KC_CUDA(cudaStreamSynchronize(h->stream));
     return KC_OK;
 }

@@ -12,6 +12,15 @@
 
 struct kc_batch_ctx;
 
+namespace kc {
+// The Prune chain (kc_prune.cu): filter and second-filter update over the
+// resident reads, then the exact count of the second filter's keys.
+void launch_prune(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, const PassParams& p, uint64_t* bf1,
+                  uint64_t* bf2, DevCounters* ctr, const Grid& g, cudaStream_t st);
+void launch_count_chain(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, const PassParams& p,
+                        const uint64_t* bf2, Slot* table, DevCounters* ctr, const Grid& g, cudaStream_t st);
+}  // namespace kc
+
 namespace kcapi {
 
 struct Batch {
@@ -80,6 +89,7 @@ struct kc_ctx {
     int slice_log2 = 0;  // partitioned: filter words per partition
 
     uint64_t* bloom = nullptr;
+    uint64_t* bloom2 = nullptr;  // the Prune chain's second filter (kc_config.prune_chain)
     kc::Slot* table = nullptr;
     kc::DevCounters* ctr = nullptr;
     std::vector<kcapi::Batch> batches;

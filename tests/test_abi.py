@@ -73,6 +73,7 @@ def test_null_handle_calls_fail_cleanly():
     assert L.kc_export_items(None, None, 0, ctypes.byref(n)) == 1
     assert L.kc_spectrum(None, 4, None) == 1
     assert L.kc_export_stems(None, None, 0, ctypes.byref(n)) == 1
+    assert L.kc_export_bloom2(None, None, 0, 0) == 1
     spec = kc.FilterSpec(1, 2, 0, 0)
     assert L.kc_filter_select(None, ctypes.byref(spec), ctypes.byref(n)) == 1
     assert L.kc_filter_keys(None, None, None, 0, ctypes.byref(n)) == 1
@@ -145,7 +146,8 @@ def test_partitioned_slice_limit(bloom_log2, part_bits, ok):
 
 @pytest.mark.parametrize("kw", [dict(ctas_per_sm=65), dict(smem_table_log2=9), dict(smem_table_log2=14),
                                 dict(split_max=14), dict(spill=3), dict(scatter_mode=5), dict(table_slots=1000),
-                                dict(strategy="direct", table_slots=512)])
+                                dict(strategy="direct", table_slots=512), dict(prune_chain=2),
+                                dict(prune_chain=True, strategy="partitioned")])
 def test_config_knobs_out_of_range(kw):
     """Tuning knobs outside their documented ranges are rejected before any CUDA call."""
     with pytest.raises(kc.KcError) as e:
