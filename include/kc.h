@@ -2,7 +2,7 @@
  * kc.h -- C ABI of libkc, a GB300 (sm_103a) k-mer frequency counter.
  *
  * The library counts canonical k-mers of DNA reads per sample, drops k-mers
- * seen only once with a Bloom filter, and returns the exact counts of the
+ * that occur once with a Bloom filter, and returns the exact counts of the
  * survivors in ascending key order.  This is the counting step of the
  * reference-free variant caller described in "Accelerating K-mer Frequency
  * Counting with GPU and Non-Volatile Memory" (Cadenelli, Polo, Carrera):
@@ -329,7 +329,7 @@ void kc_tune_cache_clear(void);
  *   bloom_bits power of two, >= 4096
  *   n_hashes   bits per key in its filter word, 1..10
  *   min_count  keys whose count summed over samples is below this are dropped
- *              (2 drops the k-mers seen only once; 1 keeps every key)
+ *              (2 drops the k-mers that occur once; 1 keeps every key)
  * Returns KC_ERR_ARG on out-of-range arguments.
  */
 kc_status kc_create(int k, int n_samples, uint64_t bloom_bits, int n_hashes, uint32_t min_count,

@@ -20,7 +20,7 @@
 //     does not discuss strands; canonical keys are this library's reading.)
 //  4. count[key][sample] = number of valid windows with that key, per sample.
 //  5. The result keeps the keys whose count summed over samples is at least
-//     min_count: k-mers seen only once are dropped (Section II-B, Count unit;
+//     min_count: k-mers that occur once are dropped (Section II-B, Count unit;
 //     Section III, Prune), and Bloom false positives are removed (Section III,
 //     Unify).  Keys are listed in ascending order.
 //  6. The Bloom filter is the OR over every valid window of the window key's
