@@ -168,10 +168,11 @@ typedef struct kc_stats {
     uint32_t fallback_partitions;   /* partitions whose table left shared memory    */
     uint32_t split_partitions;      /* partitions counted as sub-ranges (split_max) */
     uint32_t split_level;           /* finest split level any partition needed      */
-    /* Filter unit (kc_filter_*; timing as above): device time of the last
-     * selection (compaction and lookup table) and of the rescan kernels of
-     * all kc_filter_reads calls since create / reset; selected keys, valid
-     * windows rescanned and windows whose key was selected. */
+    /* Filter unit (kc_filter_*; timing as above): time on the handle's
+     * stream of all selections (compaction and lookup table, from the first
+     * kernel to the last, host gaps included) and of the rescan kernels of
+     * all kc_filter_reads calls since create / reset; keys of the current
+     * selection, valid windows rescanned and windows whose key was selected. */
     double ms_filter_select, ms_filter_reads;
     uint64_t filter_selected, filter_windows, filter_hits;
     /* Stem table (kc_export_stems; timing as above): device time of building
