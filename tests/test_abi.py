@@ -153,3 +153,15 @@ def test_config_knobs_out_of_range(kw):
     with pytest.raises(kc.KcError) as e:
         kc.KmerCounter(31, 1, 1 << 24, 4, 2, **kw)
     assert e.value.name == "KC_ERR_ARG"
+
+
+def test_plain_c_client_compiles_and_links(tmp_path):
+    """The boundary is a C ABI: a C99 program using only include/kc.h builds and
+    links against libkc.so (it runs on a GPU; here it is only built)."""
+    lib = kc.build()
+    exe = tmp_path / "kc_count"
+    src = os.path.join(ROOT, "tests", "c_client", "kc_count.c")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", INCLUDE, src, "-o", str(exe),
+                    "-L", os.path.dirname(lib), "-l:" + os.path.basename(lib),
+                    "-Wl,-rpath," + os.path.dirname(lib)], check=True, capture_output=True)
+    assert exe.exists()
