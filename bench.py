@@ -670,7 +670,8 @@ def run_kc(args):
     e2e_value = all_windows / e2e_s
     # the e2e result must be the device result
     if not spill:
-        assert np.array_equal(h_keys.numpy(), d_keys.cpu().numpy()), "e2e and device dumps differ"
+        assert np.array_equal(h_keys.numpy(), d_keys.cpu().numpy()), "e2e and device dumps differ (keys)"
+        assert np.array_equal(h_counts.numpy(), d_counts.cpu().numpy()), "e2e and device dumps differ (counts)"
 
     # roofline of the dominant kernel (per-launch means over the timed steps)
     st = c.stats()

@@ -21,7 +21,10 @@
  *                   whose most significant 2 bits are the window's first base
  *                   (library: canonical keys), so 1 <= k <= 31 fits a uint64.
  *   result          keys whose count summed over samples is >= min_count,
- *                   ascending, with one uint32 count per sample.
+ *                   ascending, with one uint32 count per sample.  A count
+ *                   that would pass 2^32-1 is an error, never a wrapped or
+ *                   clamped number: kc_finalize returns KC_ERR_CAPACITY (it
+ *                   takes more than 4.29e9 copies of one k-mer in one sample).
  *   Bloom filter    bloom_bits / 64 words; key sets n_hashes bits of ONE word
  *                   (library: word-blocked, so a single atomic decides whether
  *                   a key was seen before):
@@ -494,10 +497,14 @@ const char* kc_status_string(kc_status s);
  * given.
  *
  *   packed_reads, offsets, n_mask  inputs in the packed format above; all in
- *                  device memory (KC_ERR_ARG otherwise)
- *   bloom_out      bloom_bits / 64 words of device memory, overwritten
+ *                  device memory of the current device, or managed memory
+ *                  (KC_ERR_ARG otherwise: host memory and another GPU's memory
+ *                  are refused, since nothing is copied first)
+ *   bloom_out      bloom_bits / 64 words of such memory, overwritten
  *   stream         cudaStream_t as void*, NULL for the default stream; the call
- *                  returns after its work on this stream is done
+ *                  synchronises this stream twice (it reads the read range
+ *                  back before its launches and the error bits after them) and
+ *                  returns after its work on the stream is done
  *
  * Everything intermediate lives in one fixed scratch array inside the library
  * (a file-scope __device__ array of about 4 MiB that every GPU loading the

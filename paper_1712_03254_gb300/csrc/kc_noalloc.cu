@@ -75,13 +75,22 @@ __global__ void __launch_bounds__(256) k_bloom_only(const uint64_t* __restrict__
     }
 }
 
+// Memory this call's kernels may read and write directly: device memory of
+// the current device, or managed memory.  Device memory of another GPU is
+// refused (peer access may be off, and nothing here copies it first).
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Device address of the scratch array on the current device.
@@ -117,9 +126,10 @@ extern "C" kc_status kc_bloom_build_noalloc(int k, uint64_t bloom_bits, int n_ha
     if (k < 1 || k > 31) return noalloc_fail(KC_ERR_ARG, "k must be in 1..31");
     if (bloom_bits < 4096 || (bloom_bits & (bloom_bits - 1))) return noalloc_fail(KC_ERR_ARG, "bloom_bits must be a power of two >= 4096");
     if (n_hashes < 1 || n_hashes > 10) return noalloc_fail(KC_ERR_ARG, "n_hashes must be in 1..10");
-    if (!bloom_out || !on_device(bloom_out)) return noalloc_fail(KC_ERR_ARG, "bloom_out must be device memory");
+    if (!bloom_out || !on_device(bloom_out))
+        return noalloc_fail(KC_ERR_ARG, "bloom_out must be device memory of the current device");
     if (n_reads && (!offsets || !on_device(offsets)))
-        return noalloc_fail(KC_ERR_ARG, "offsets must be device memory");
+        return noalloc_fail(KC_ERR_ARG, "offsets must be device memory of the current device");
     cudaStream_t st = (cudaStream_t)stream;
     uint64_t* scratch = nullptr;
     kc_status s = scratch_address(&scratch);
@@ -135,7 +145,7 @@ extern "C" kc_status kc_bloom_build_noalloc(int k, uint64_t bloom_bits, int n_ha
     if (b1 < b0) return noalloc_fail(KC_ERR_ARG, "read offsets decrease");
     if (b1 == b0) return KC_OK;
     if (!packed_reads || !n_mask || !on_device(packed_reads) || !on_device(n_mask))
-        return noalloc_fail(KC_ERR_ARG, "packed_reads and n_mask must be device memory");
+        return noalloc_fail(KC_ERR_ARG, "packed_reads and n_mask must be device memory of the current device");
     const uint64_t B = (b0 / 64) * 64;
     const uint64_t n_local = b1 - B;
     if (n_local > kMaxBases)
