@@ -17,9 +17,13 @@ library defaults.
          device copy of the reads and the device to host copy of the result
          inside the timed region (wall clock)
 
-With N ranks (torchrun) every rank counts its own job (independent read set),
-no collective is on the data path, and value = all ranks' windows / the
-slowest rank's time ("weak" scaling).
+With N ranks (torchrun) the one job is sharded by key: the hash space is cut
+into 64 shards and rank r owns a contiguous range of them (kc_config.own_bits,
+own_lo, own_hi).  Every rank scans all the reads and counts only the keys it
+owns, with its own filter slice and tables; no collective is on the data path,
+and value = the job's windows / the slowest rank's time ("strong" scaling).
+After the timed steps the ranks' results are gathered on rank 0, merged by key
+(kc_merge_results) and compared with the whole job counted on one GPU.
 
 The "served" field replays a Poisson stream of 256 jobs of mixed size (1-20
 Mbp genomes, 10^4-2x10^6 reads, k 25 or 31, filters of 8 bits per expected
@@ -84,9 +88,18 @@ def dist_env():
     return rank, world, local
 
 
-def shard_seed(rank: int) -> int:
-    """Seed of the read set counted by a rank (rank 0: the canonical workload)."""
-    return MID_SEED + 7919 * rank
+OWN_BITS = 6  # hash shards the job is split into across ranks
+
+
+def owner_knobs(rank: int, world: int) -> dict:
+    """kc_config ownership of rank `rank` of `world`: a contiguous range of the 2^OWN_BITS hash shards
+    (nothing with one rank: the handle owns every key)."""
+    if world <= 1:
+        return {}
+    import paper_1712_03254_gb300 as kc
+
+    lo, hi = kc.owned_shards(rank, world, OWN_BITS)
+    return {"own_bits": OWN_BITS, "own_lo": lo, "own_hi": hi}
 
 
 def init_dist(world: int, backend: str):
@@ -106,16 +119,6 @@ def reduce_max(x: float, dist, device) -> float:
 
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def reduce_sum(x: float, dist, device) -> float:
-    if dist is None:
-        return x
-    import torch
-
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -247,54 +250,96 @@ def issue_peak(sm_count: int):
     return sm_count * ISSUE_PER_SM_CYCLE * mhz * 1e6, mhz
 
 
-def roofline_of(st, phases, n_bases, w, sm_count, workload="mid", consume_launches=1):
-    """Roofline entry of the kernel that takes the most device time.
+def algorithmic_bytes(n_bases: int, windows: int, bloom_bits: int, table_slots: int, result_keys: int,
+                      n_samples: int) -> dict:
+    """Compulsory DRAM bytes of one counting job (two passes over the reads), term by term:
+      reads   3 bits per base (2-bit code + N mask) read once per pass
+      filter  zeroed, then read and written once: 3 x its bytes
+      table   zeroed, updated, read by the compaction: 3 x its bytes (16 B slots)
+      output  8 B key + 4 B count per sample per result key
+    The materialised hash stream of the partitioned strategy (8 B per window
+    written and read per grouping pass) is implementation traffic, never
+    counted here."""
+    terms = {"reads": 2 * ((n_bases * 3 + 7) // 8), "filter": 3 * (bloom_bits // 8), "table": 3 * 16 * table_slots,
+             "output": (8 + 4 * n_samples) * result_keys}
+    total = sum(terms.values())
+    return {"total": int(total), "per_window": round(total / max(1, windows), 3), "terms": terms}
+
+
+def atomic_ceiling(rates: dict, strategy: int) -> dict:
+    """Windows per second the random updates allow.  Per window the partitioned
+    path makes 3 random shared-memory 32-bit adds (extraction histogram,
+    scatter stage fill, recount) and 1 shared-memory 64-bit OR (the filter
+    slice); the direct strategy makes 1 global 64-bit OR into the filter
+    (beyond L2) and its table probes."""
+    if strategy == 1:
+        per = {"hbm_or64": 1}
+        t = 1.0 / rates["hbm_or64_per_s"]
+    else:
+        per = {"smem_add32": 3, "smem_or64": 1}
+        t = 3.0 / rates["smem_add32_per_s"] + 1.0 / rates["smem_or64_per_s"]
+    return {"windows_per_s": round(1.0 / t, 1), "updates_per_window": per,
+            "rates_per_s": {k: round(v, 1) for k, v in rates.items()}}
+
+
+def roofline_of(st, phases, n_bases, w, sm_count, step_ms, workload="mid", consume_launches=1, rates=None):
+    """Roofline entry of the kernel that takes the most device time, against HBM.
 
     Partitioned strategy: the consumer k_consume_q (the largest single kernel;
-    the "pass2" phase events bracket exactly its one launch).  Direct strategy:
-    the larger of k_pass1 / k_pass2.  Algorithmic bytes are compulsory traffic:
-      reads      2 bits (packed base) + 1 bit (valid-window bit) per base
-      direct     pass1: reads + filter read and written once + 32 B per claimed
-                 key; pass2: reads + 32 B per claimed key
-      consumer   8 B hash read per window + filter written once + 16 B per
-                 result key
-    When the committed ncu counters match the current sources, the kernel's
-    DRAM traffic and instruction count come from them; the kernel then reports
-    against the SM issue limit ("alu": warp instructions issued per second
-    over 152 SMs x 4 schedulers x the maximum SM clock), with the HBM figures
-    beside it.  Otherwise it reports against HBM bandwidth alone.
+    the "pass2" phase events bracket exactly its one launch).  Direct
+    strategy: the larger of k_pass1 / k_pass2.  achieved = the job's
+    algorithmic bytes per window (algorithmic_bytes: reads, filter, the
+    configuration's table, output) x the windows one launch processes / the
+    launch's mean CUDA-event time.  Beside it: the same bytes over the whole
+    step, the atomic ceiling (atomic_ceiling) and HBM ceiling in windows/s,
+    and, when the committed ncu counters match the current sources, the
+    kernel's DRAM traffic and its fraction of the SM issue limit (a diagnosis
+    of what binds it, not the headline).
     """
     import statistics as _st
 
     W = st["windows"]
-    read_bytes = (n_bases * 3 + 7) // 8
-    bloom_bytes = w.bloom_bits // 8
     mean = {k: _st.mean(v) for k, v in phases.items()}
+    algo = algorithmic_bytes(n_bases, W, w.bloom_bits, w.table_slots, st["result_keys"], len(w.samples))
     if st["strategy"] == 1:
-        table = {"pass1": ("k_pass1", read_bytes + 2 * bloom_bytes + 32 * st["table_keys"]),
-                 "pass2": ("k_pass2", read_bytes + 32 * st["table_keys"])}
-        phase = max(table, key=lambda k: mean[k])
+        phase = "pass1" if mean["pass1"] >= mean["pass2"] else "pass2"
+        kernel = "k_pass1" if phase == "pass1" else "k_pass2"
+        ms = mean[phase]
     else:
-        # per launch: with spill the consumer runs once per partition group
-        table = {"pass2": ("k_consume_q", (8 * W + bloom_bytes + 16 * st["result_keys"]) / consume_launches)}
-        phase = "pass2"
-    kernel, algo = table[phase]
-    ms = mean[phase] / (consume_launches if st["strategy"] != 1 else 1)
+        phase, kernel = "pass2", "k_consume_q"
+        ms = mean[phase] / consume_launches  # with spill the consumer runs once per partition group
+    per_launch = algo["total"] / (consume_launches if st["strategy"] != 1 else 1)
     peak, peak_kind = measured_hbm_peak()
-    hbm_achieved = algo / (ms / 1e3) / 1e9
+    achieved = per_launch / (ms / 1e3) / 1e9
+    step_achieved = algo["total"] / (step_ms / 1e3) / 1e9
     prof = ncu_kernel(kernel, workload)
-    hbm = {"achieved": round(hbm_achieved, 1), "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-           "frac": round(hbm_achieved / peak, 4)}
-    if prof is None:
-        return {"bound": "hbm", "kernel": kernel, **hbm, "traffic": None, "algorithmic_bytes": int(algo),
-                "ms_per_launch": round(ms, 4)}
-    ipk, mhz = issue_peak(sm_count)
-    achieved = prof["inst_executed_per_launch"] / (ms / 1e3)
-    return {"bound": "alu", "kernel": kernel, "achieved": round(achieved / 1e9, 1), "peak": round(ipk / 1e9, 1),
-            "peak_source": f"derived: {sm_count} SMs x {ISSUE_PER_SM_CYCLE} warp instructions/cycle x {mhz:.0f} MHz",
-            "unit": "G warp instructions/s", "frac": round(achieved / ipk, 4),
-            "traffic": prof["dram_bytes_per_launch"], "algorithmic_bytes": int(algo), "ms_per_launch": round(ms, 4),
-            "instructions_per_launch": prof["inst_executed_per_launch"], "hbm": hbm}
+    out = {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1), "peak": peak,
+           "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+           "traffic": prof["dram_bytes_per_launch"] if prof else None,
+           "algorithmic_bytes": int(per_launch), "algorithmic_bytes_per_window": algo["per_window"],
+           "algorithmic_terms": algo["terms"], "ms_per_launch": round(ms, 4),
+           "implementation_bytes": (16 * W if st["strategy"] != 1 else 0),
+           "step": {"ms": round(step_ms, 4), "achieved": round(step_achieved, 1),
+                    "frac": round(step_achieved / peak, 4)}}
+    hbm_windows = peak * 1e9 / algo["per_window"]
+    ceil = {"hbm_windows_per_s": round(hbm_windows, 1)}
+    if rates:
+        a = atomic_ceiling(rates, st["strategy"])
+        ceil["atomic"] = a
+        lo = min(hbm_windows, a["windows_per_s"])
+        ceil["min_windows_per_s"] = round(lo, 1)
+        ceil["bound_by"] = "atomic" if a["windows_per_s"] < hbm_windows else "hbm"
+        ceil["step_frac_of_min"] = round(W / (step_ms / 1e3) / lo, 4)
+    out["ceilings"] = ceil
+    if prof is not None:
+        ipk, mhz = issue_peak(sm_count)
+        ach = prof["inst_executed_per_launch"] / (ms / 1e3)
+        out["issue"] = {"achieved": round(ach / 1e9, 1), "peak": round(ipk / 1e9, 1), "unit": "G warp instructions/s",
+                        "frac": round(ach / ipk, 4),
+                        "peak_source": f"derived: {sm_count} SMs x {ISSUE_PER_SM_CYCLE} warp instructions/cycle x "
+                                       f"{mhz:.0f} MHz",
+                        "instructions_per_launch": prof["inst_executed_per_launch"]}
+    return out
 
 
 FILTER_SOURCES = ("kc_filter.cu", "kc_device.cuh", "kc_internal.h", "kc_kernels.cu")
@@ -509,12 +554,13 @@ def run_filter_bench(dev, stream, steps: int, warmup: int, flush):
 # ---------------------------------------------------------------- workloads
 
 
-def make_inputs(rank: int, workload: str = "mid"):
+def make_inputs(workload: str = "mid"):
+    """The workload's read sets (every rank of a sharded run holds all of them)."""
     import synth
 
     if workload == "mid":
-        return synth.mid(seed=shard_seed(rank))
-    return synth.WORKLOADS[workload]()  # paired, ooc: one fixed read set per rank
+        return synth.mid(seed=MID_SEED)
+    return synth.WORKLOADS[workload]()
 
 
 def oracle_rate(w, n_reads: int):
@@ -554,7 +600,7 @@ def run_kc(args):
     # the legacy default stream would give the handle a stream of its own)
     stream = torch.cuda.Stream()
 
-    w = make_inputs(rank, args.workload)
+    w = make_inputs(args.workload)
     rs = w.samples[0]
     n_samples = len(w.samples)
     spill = bool(w.extra.get("spill_parts"))
@@ -592,6 +638,9 @@ def run_kc(args):
         tuning = {"best": short(best), "seconds": round(time.perf_counter() - t0, 2),
                   "trials": [[short(cfg), round(ms, 3)] for cfg, ms in trials]}
     if spill:
+        knobs["strategy"] = "partitioned"
+    knobs.update(owner_knobs(rank, world))  # N > 1: this rank's hash-shard range of the one job
+    if world > 1:
         knobs["strategy"] = "partitioned"
     c = kc.KmerCounter(w.k, n_samples, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots,
                        timing=True, spill=spill, stream=stream, **knobs)
@@ -651,7 +700,9 @@ def run_kc(args):
 
     total_ms = sum(step_ms)
     max_total_ms = reduce_max(total_ms, dist, dev)
-    all_windows = reduce_sum(float(windows * args.steps), dist, dev)
+    # every rank scans all the job's windows (and counts the keys it owns):
+    # the work is the job's windows, whatever the number of ranks
+    all_windows = float(windows * args.steps)
     value = all_windows / (max_total_ms / 1e3)
 
     # e2e: pinned host inputs and outputs through the C ABI, wall clock
@@ -673,10 +724,33 @@ def run_kc(args):
         assert np.array_equal(h_keys.numpy(), d_keys.cpu().numpy()), "e2e and device dumps differ (keys)"
         assert np.array_equal(h_counts.numpy(), d_counts.cpu().numpy()), "e2e and device dumps differ (counts)"
 
-    # roofline of the dominant kernel (per-launch means over the timed steps)
+    # N > 1: the owners' results, merged by key on rank 0, must be the whole job's
+    merged_check = None
+    if dist is not None:
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (h_keys.numpy().copy(), h_counts.numpy().view(np.uint32).copy()))
+        if rank == 0:
+            mk, mc = kc.merge_results(gathered, n_samples)
+            whole = kc.KmerCounter(w.k, n_samples, w.bloom_bits, w.n_hashes, w.min_count, table_slots=w.table_slots,
+                                   spill=spill, stream=stream,
+                                   **{k: v for k, v in knobs.items() if not k.startswith("own_")})
+            for s_i, p_, o_, m_ in chunks_d:
+                whole.add_reads(s_i, p_, o_, m_)
+            whole.finalize()
+            wk, wc = whole.dump()
+            whole.close()
+            merged_check = bool(np.array_equal(mk, wk) and np.array_equal(mc, wc))
+            assert merged_check, "merged owner results differ from the whole job"
+
+    # roofline of the dominant kernel (per-launch means over the timed steps),
+    # with the measured random-atomic ceilings beside it
     st = c.stats()
+    try:
+        rates = kc.atomic_ceilings(stream)
+    except kc.KcError:
+        rates = None
     roofline = roofline_of(st, phases, total_bases, w, torch.cuda.get_device_properties(dev).multi_processor_count,
-                           args.workload, min(st["partitions"], 64) if spill else 1)
+                           max_total_ms / args.steps, args.workload, min(st["partitions"], 64) if spill else 1, rates)
     strategy = {1: "direct", 2: "partitioned"}.get(st["strategy"], "?")
 
     # CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
@@ -709,11 +783,15 @@ def run_kc(args):
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(max_total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded genome and reads)",
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded genome and reads)",
             "config": {"workload": WORKLOADS[args.workload], "windows_per_job": windows, "result_keys": n_res,
                        "l2": "256 MiB written between timed steps (outside the step events)"
                              + ("; inputs larger than L2" if args.workload != "mid" else ""),
-                       "parallelism": f"{world} independent jobs, one per GPU" if world > 1 else "1 GPU"},
+                       "parallelism": (f"one job sharded over {world} GPUs by hash range ({1 << OWN_BITS} shards, "
+                                       "a contiguous range per rank, reads replicated, no collective on the data "
+                                       "path); e2e and result_keys are rank 0's; results merged by key after the "
+                                       "timed steps" if world > 1 else "1 GPU")},
+            "merged_equals_whole_job": merged_check,
             "strategy": strategy,
             "tuning": tuning,
             "phase_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
@@ -896,7 +974,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = make_inputs(0, args.workload)
+    w = make_inputs(args.workload)
     budget_s = args.ref_seconds
     per_step = budget_s / max(1, args.steps + args.warmup)
     n_s = pick_sample_reads(w, per_step)

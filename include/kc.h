@@ -122,8 +122,39 @@ typedef struct kc_config {
                                      kc_finalize counts, in one exact pass, the
                                      windows whose key is in the second filter (see
                                      kc_export_bloom2).  The result is the same.    */
-    uint32_t reserved32;
-    uint64_t reserved[3];
+    uint32_t own_bits;            /* partitioned: hash-range ownership.  0: the
+                                     handle counts every key.  Else the keys are
+                                     split into 2^own_bits shards by the top
+                                     own_bits bits of h = mixer64(key) and the
+                                     handle counts only the shards own_lo ..
+                                     own_hi - 1: its result, filter words and
+                                     kc_stats.owned_windows cover those keys alone
+                                     (a contiguous slice of the filter; the other
+                                     words stay 0).  Handles owning disjoint
+                                     ranges of the same reads give disjoint
+                                     results whose union, merged by key
+                                     (kc_merge_results), is the whole job's, and
+                                     whose filters OR to the whole filter: the
+                                     second level of partitioning of Section
+                                     II-B, one owner per range with its own
+                                     structures and no synchronisation.  Needs
+                                     own_bits <= the partition bits (1..20)       */
+    uint32_t own_lo;              /* first owned shard                              */
+    uint32_t own_hi;              /* one past the last owned shard (0 = 2^own_bits) */
+    uint64_t device_budget;       /* partitioned: device bytes the job may hold
+                                     (filter, resident batches, result).  0: the
+                                     device's free memory when the call runs.  A
+                                     kc_add_reads whose window hashes would pass
+                                     the budget keeps the batch's packed reads
+                                     instead (about 0.4 byte per base rather than
+                                     8 per window); kc_finalize then extracts and
+                                     groups those reads again, one hash range at a
+                                     time, and spills the sorted result of every
+                                     range to pinned host memory as with spill = 1
+                                     (Section III-D: tables swapped out when they
+                                     outgrow memory).  A job whose result would
+                                     not fit is spilled the same way.            */
+    uint64_t reserved[1];
 } kc_config;
 
 #define KC_SPLIT_NONE 0xffffffffu
@@ -182,6 +213,13 @@ typedef struct kc_stats {
      * it, and its number of items. */
     double ms_stems;
     uint64_t stem_items;
+    /* Windows whose key the handle owns (= windows without own_bits; complete
+     * after kc_finalize), batches kept as packed reads because their hashes
+     * would have passed the device budget, and the hash ranges kc_finalize
+     * extracted those batches in (0 when none was kept). */
+    uint64_t owned_windows;
+    uint32_t deferred_batches;
+    uint32_t scan_groups;
 } kc_stats;
 
 /*
@@ -479,6 +517,42 @@ kc_status kc_filter_reads(kc_handle h, const uint64_t* packed_reads, const uint6
 kc_status kc_reset(kc_handle h);
 
 void kc_destroy(kc_handle h);
+
+/*
+ * kc_merge_results -- merge n_runs results, each sorted by key with keys
+ * unique across runs (as handles owning disjoint hash ranges of one job give
+ * them), into one ascending result.  Host memory only; no GPU is used.
+ *   keys[r], counts[r]  run r: n[r] keys and n[r] x n_samples counts (row-major)
+ *   out_keys, out_counts  sum of n[r] entries each; out_counts may be NULL
+ * KC_ERR_ARG for null arrays, n_samples outside 1..2 or a run that is not
+ * strictly ascending; KC_ERR_ARG also when two runs hold the same key (the
+ * ranges were not disjoint).  Runs of more than 2^20 keys in all are merged on
+ * several host threads.
+ */
+kc_status kc_merge_results(int n_runs, const uint64_t* const* keys, const uint32_t* const* counts, const uint64_t* n,
+                           int n_samples, uint64_t* out_keys, uint32_t* out_counts);
+
+/*
+ * kc_atomic_ceilings -- measured ceilings of the random atomic updates the
+ * counting kernels are made of (the paper finds random updates of its filters
+ * and tables to bound counting, Section IV-C).  Each field is updates per
+ * second over the whole GPU, one kind of update at random addresses:
+ *   smem_or64_per_s   64-bit atomicOr into a 4096-word shared-memory array
+ *                     per CTA (the partition consumer's filter slice)
+ *   smem_add32_per_s  32-bit atomicAdd into 4096 shared-memory counters per
+ *                     CTA (the extraction and scatter histograms, the
+ *                     consumer's counts)
+ *   l2_or64_per_s     64-bit atomicOr into a 16 MiB global array (held in L2)
+ *   hbm_or64_per_s    64-bit atomicOr into a 4 GiB global array (beyond L2:
+ *                     the direct strategy's filter update)
+ * Allocates about 4 GiB of device memory for the call; work is ordered on
+ * stream (cudaStream_t as void*, NULL = the legacy default stream) and the
+ * call returns when it is done.  A measurement aid, not a step of the path.
+ */
+typedef struct kc_atomic_rates {
+    double smem_or64_per_s, smem_add32_per_s, l2_or64_per_s, hbm_or64_per_s;
+} kc_atomic_rates;
+kc_status kc_atomic_ceilings(kc_atomic_rates* out, void* stream);
 
 /* Message of the last error on this thread ("" if none). */
 const char* kc_last_error(void);

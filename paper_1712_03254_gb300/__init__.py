@@ -18,6 +18,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["KmerCounter", "KcBatch", "KcServer", "KcError", "pack_ascii", "lib", "build", "Config", "Stats",
+           "merge_results", "owned_shards", "atomic_ceilings",
            "FilterSpec", "ITEM16", "STEM_ITEM", "autotune", "tune_lookup", "tune_cache_save", "tune_cache_load", "tune_cache_clear"]
 
 _lock = threading.Lock()
@@ -40,7 +41,11 @@ class Config(ctypes.Structure):
                 ("table_slots", ctypes.c_uint64), ("spill", ctypes.c_uint32), ("timing", ctypes.c_uint32),
                 ("strategy", ctypes.c_uint32), ("smem_table_log2", ctypes.c_uint32),
                 ("scatter_mode", ctypes.c_uint32), ("split_max", ctypes.c_uint32), ("prune_chain", ctypes.c_uint32),
-                ("reserved32", ctypes.c_uint32), ("reserved", ctypes.c_uint64 * 3)]
+                ("own_bits", ctypes.c_uint32), ("own_lo", ctypes.c_uint32), ("own_hi", ctypes.c_uint32),
+                ("device_budget", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 1)]
+
+
+assert ctypes.sizeof(Config) == 80
 
 
 class Stats(ctypes.Structure):
@@ -54,10 +59,17 @@ class Stats(ctypes.Structure):
                 ("split_level", ctypes.c_uint32), ("ms_filter_select", ctypes.c_double),
                 ("ms_filter_reads", ctypes.c_double), ("filter_selected", ctypes.c_uint64),
                 ("filter_windows", ctypes.c_uint64), ("filter_hits", ctypes.c_uint64),
-                ("ms_stems", ctypes.c_double), ("stem_items", ctypes.c_uint64)]
+                ("ms_stems", ctypes.c_double), ("stem_items", ctypes.c_uint64),
+                ("owned_windows", ctypes.c_uint64), ("deferred_batches", ctypes.c_uint32),
+                ("scan_groups", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class AtomicRates(ctypes.Structure):
+    _fields_ = [("smem_or64_per_s", ctypes.c_double), ("smem_add32_per_s", ctypes.c_double),
+                ("l2_or64_per_s", ctypes.c_double), ("hbm_or64_per_s", ctypes.c_double)]
 
 
 class FilterSpec(ctypes.Structure):
@@ -184,6 +196,10 @@ def lib():
             L.kc_filter_keys.restype = st
             L.kc_filter_reads.argtypes = [p, p, p, p, u64, p, p, ctypes.POINTER(u64)]
             L.kc_filter_reads.restype = st
+            L.kc_merge_results.argtypes = [i, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(u64), i, p, p]
+            L.kc_merge_results.restype = st
+            L.kc_atomic_ceilings.argtypes = [ctypes.POINTER(AtomicRates), p]
+            L.kc_atomic_ceilings.restype = st
             _lib = L
     return _lib
 
@@ -219,6 +235,39 @@ def pack_ascii(ascii: np.ndarray):
     return packed, mask
 
 
+def merge_results(results, n_samples: int):
+    """Merge per-owner results [(keys uint64[n], counts uint32[n, n_samples]), ...] (each ascending, keys
+    disjoint across them) into one ascending result (kc_merge_results, host memory)."""
+    runs = [(np.ascontiguousarray(k, dtype=np.uint64), np.ascontiguousarray(c, dtype=np.uint32)) for k, c in results]
+    n_total = sum(k.size for k, _ in runs)
+    keys = np.empty(n_total, dtype=np.uint64)
+    counts = np.empty((n_total, n_samples), dtype=np.uint32)
+    m = len(runs)
+    kp = (ctypes.c_void_p * max(1, m))(*[k.ctypes.data if k.size else None for k, _ in runs])
+    cp = (ctypes.c_void_p * max(1, m))(*[c.ctypes.data if c.size else None for _, c in runs])
+    ns = (ctypes.c_uint64 * max(1, m))(*[k.size for k, _ in runs])
+    _check(lib().kc_merge_results(m, kp, cp, ns, n_samples, keys.ctypes.data if n_total else None,
+                                  counts.ctypes.data if n_total else None), "kc_merge_results")
+    return keys, counts
+
+
+def atomic_ceilings(stream=None) -> dict:
+    """Measured random-atomic update rates (kc_atomic_ceilings), updates per second."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    r = AtomicRates()
+    _check(lib().kc_atomic_ceilings(ctypes.byref(r), stream), "kc_atomic_ceilings")
+    return {name: getattr(r, name) for name, _ in r._fields_}
+
+
+def owned_shards(rank: int, world: int, own_bits: int):
+    """[lo, hi) of the 2^own_bits hash shards that rank `rank` of `world` owns: contiguous, as even as possible."""
+    n = 1 << own_bits
+    if not 0 <= rank < world <= n:
+        raise ValueError("need 0 <= rank < world <= 2^own_bits")
+    return rank * n // world, (rank + 1) * n // world
+
+
 SPLIT_NONE = 0xFFFFFFFF  # kc_config.split_max: overflowing partitions go straight to the global table
 STRATEGY_NAMES = {0: "auto", 1: "direct", 2: "partitioned"}
 SERVER_TUNED = 1  # kc_server_create_ex flag
@@ -230,7 +279,8 @@ class KmerCounter:
     def __init__(self, k: int, n_samples: int, bloom_bits: int, n_hashes: int = 4, min_count: int = 2,
                  table_slots: int = 0, part_bits: int = 0, spill: bool = False, ctas_per_sm: int = 0,
                  timing: bool = False, strategy: str = "auto", smem_table_log2: int = 0, scatter_mode: int = 0,
-                 split_max: int = 0, tune_bases: int = 0, prune_chain: bool = False, stream=None):
+                 split_max: int = 0, tune_bases: int = 0, prune_chain: bool = False, own_bits: int = 0,
+                 own_lo: int = 0, own_hi: int = 0, device_budget: int = 0, stream=None):
         L = lib()
         cfg = Config()
         L.kc_default_config(ctypes.byref(cfg))
@@ -256,6 +306,8 @@ class KmerCounter:
         cfg.scatter_mode = scatter_mode
         cfg.split_max = SPLIT_NONE if split_max < 0 else split_max  # -1: never split an overflowing partition
         cfg.prune_chain = int(prune_chain)  # the paper's two-filter chain (direct strategy)
+        cfg.own_bits, cfg.own_lo, cfg.own_hi = own_bits, own_lo, own_hi  # hash shards [own_lo, own_hi) of 2^own_bits
+        cfg.device_budget = device_budget  # bytes; 0: the device's free memory
         h = ctypes.c_void_p()
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream

@@ -318,8 +318,12 @@ kc_status regroup_batch(kc_handle h, Batch& b, cudaStream_t st) {
 // Partitioned strategy, ingest: group the batch's window hashes by partition
 // (count pass, per-partition prefix over CTAs, scan, scatter pass).  With more
 // than 12 partition bits the hashes are first grouped by the top l1_bits, then
-// every group is re-bucketed by the next 12 bits (regroup_batch).
-kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st) {
+// every group is re-bucketed by the next 12 bits (regroup_batch).  Only
+// windows whose hash lies in [p.h_lo, p.h_hi] are kept.  exact: the grouped
+// hashes get exactly the room they need, read back after the scan (one
+// synchronisation), instead of one slot per base of the batch.
+kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st, const kc::PassParams& p,
+                       bool exact) {
     const int a = h->l1_bits;
     const uint64_t P = 1ull << a;
     int mode = h->cfg.scatter_mode ? (int)h->cfg.scatter_mode : 4;
@@ -354,21 +358,27 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
         (e = cudaMallocAsync(&total, P * 4, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&cursor, P * 8, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&b.hstarts, (P + 1) * 8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, b.hcap) * 8, st)) != cudaSuccess)
+        (!exact && (e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, b.hcap) * 8, st)) != cudaSuccess))
         return bail(e);
     if (mode == 4 && ((e = cudaMallocAsync(&lin, std::max<uint64_t>(1, n_local) * 8, st)) != cudaSuccess ||
                       (e = cudaMallocAsync(&seg, (size_t)n_ctas * sizeof(kc::SegDesc), st)) != cudaSuccess ||
                       (e = cudaMallocAsync(&g_cursor, 8, st)) != cudaSuccess))
         return bail(e);
-    const kc::PassParams p = h->params(b.sample);
     if (mode == 4) {
         KC_CUDA(cudaMemsetAsync(g_cursor, 0, 8, st));
-        kc::launch_extract_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, g_cursor, seg, lin, st);
+        kc::launch_extract_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, g_cursor, seg, lin, h->ctr, st);
     } else {
         kc::launch_bucket_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, st);
     }
     kc::launch_bucket_offsets(counts, n_ctas, a, mode >= 3 ? 1 : 0, rel, total, st);
     if ((e = kc::launch_scan(total, P, b.hstarts, cursor, st)) != cudaSuccess) return bail(e);
+    if (exact) {  // the grouped hashes need exactly hstarts[P] slots
+        uint64_t need = 0;
+        KC_CUDA(cudaMemcpyAsync(&need, b.hstarts + P, 8, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        b.hcap = need;
+        if ((e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, need) * 8, st)) != cudaSuccess) return bail(e);
+    }
     if (mode != 1) kc::launch_bucket_base(rel, b.hstarts, n_ctas, a, st);
     if (mode == 4) kc::launch_scatter_staged_seg(lin, seg, n_ctas, 0, a, rel, b.hdata, st);
     else kc::launch_bucket_scatter(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, mode, rel, cursor, b.hdata, st);
@@ -382,6 +392,51 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st)
     if (g_cursor) cudaFreeAsync(g_cursor, st);
     if (h->l1_bits != h->part_bits) return regroup_batch(h, b, st);
     return KC_OK;
+}
+
+// Device bytes the handle holds now: filter, table and counters, resident
+// batches (reads and grouped hashes) and its result.
+uint64_t held_bytes(kc_handle h) {
+    uint64_t bytes = h->fixed_bytes + h->res_cap * 16;
+    for (const auto& b : h->batches) {
+        if (b.pw) bytes += (2 * b.n_units + 2) * 8 + b.n_units * 8;
+        if (b.hdata) bytes += b.hcap * 8 + ((1ull << h->part_bits) + 1) * 8;
+    }
+    return bytes;
+}
+
+// Bytes the handle may still allocate: kc_config.device_budget minus what it
+// holds, or (no budget) the device's free memory plus what the stream-ordered
+// pool has cached and not handed out, less a 1 GiB margin.
+uint64_t room_bytes(kc_handle h) {
+    const uint64_t held = held_bytes(h);
+    if (h->cfg.device_budget) return h->cfg.device_budget > held ? h->cfg.device_budget - held : 0;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return ~0ull;  // unknown: do not defer
+    }
+    uint64_t cached = 0;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+        uint64_t reserved = 0, used = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+            cached = reserved - used;
+        else
+            cudaGetLastError();
+    }
+    const uint64_t avail = (uint64_t)free_b + cached, margin = 1ull << 30;
+    return avail > margin ? avail - margin : 0;
+}
+
+// Device bytes bucket_batch needs for a batch of n_local bases: the linear
+// hashes and the grouped hashes (8 bytes per window each, at most one window
+// per base), and the run padding of up to 3 per (CTA, partition).
+uint64_t bucket_bytes(kc_handle h, uint64_t n_local) {
+    const int max_ctas = h->grid.sm_count * (h->cfg.ctas_per_sm ? (int)h->cfg.ctas_per_sm : 1);
+    return 16 * n_local + 24ull * (uint64_t)max_ctas * (1ull << h->l1_bits) +
+           (uint64_t)max_ctas * (1ull << h->l1_bits) * 12;
 }
 
 // Sort n (key, value) pairs held in tk/tv, keys below 2^key_bits, into
@@ -646,6 +701,16 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     if (strategy == KC_STRATEGY_PARTITIONED && !part_ok)
         return fail(KC_ERR_ARG, "partitioned strategy: filter slice per partition exceeds 8192 words");
 
+    if (c.own_bits) {
+        if (strategy != KC_STRATEGY_PARTITIONED)
+            return fail(KC_ERR_ARG, "own_bits needs the partitioned strategy");
+        if ((int)c.own_bits > pb) return fail(KC_ERR_ARG, "own_bits must not exceed the partition bits");
+        const uint64_t n_shards = 1ull << c.own_bits, hi = c.own_hi ? c.own_hi : n_shards;
+        if (c.own_lo >= hi || hi > n_shards) return fail(KC_ERR_ARG, "owned shards must satisfy own_lo < own_hi <= 2^own_bits");
+    } else if (c.own_lo || c.own_hi) {
+        return fail(KC_ERR_ARG, "own_lo / own_hi need own_bits");
+    }
+
     kc_ctx* h = new (std::nothrow) kc_ctx();
     if (!h) return fail(KC_ERR_OOM_HOST, "host allocation");
     h->k = k;
@@ -660,6 +725,17 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     h->l1_bits = pb <= 12 ? pb : pb - 12;
     h->slice_log2 = lw - pb;
     if (strategy == KC_STRATEGY_PARTITIONED) slots = 0;
+    h->own_plo = 0;
+    h->own_phi = strategy == KC_STRATEGY_PARTITIONED ? (1u << pb) : 0u;
+    if (c.own_bits) {
+        const int ob = (int)c.own_bits;
+        const uint64_t hi = c.own_hi ? c.own_hi : (1ull << ob);
+        h->owner = true;
+        h->own_h_lo = (uint64_t)c.own_lo << (64 - ob);
+        h->own_h_hi = (hi << (64 - ob)) - 1ull;  // hi = 2^ob wraps to 0, giving ~0
+        h->own_plo = c.own_lo << (pb - ob);
+        h->own_phi = (uint32_t)(hi << (pb - ob));
+    }
     h->n_slots = slots;
     h->log2_slots = slots ? log2_exact(slots) : 0;
 
@@ -732,6 +808,7 @@ kc_status kc_reset(kc_handle h) {
     for (double& x : h->ms) x = 0.0;
     h->launches = 0;
     h->fallback_partitions = 0;
+    h->deferred = h->scan_groups = 0;
     h->state = State::Open;
     return KC_OK;
 }
@@ -850,8 +927,14 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
         else
             kc::launch_pass1(b.pw, b.vw, n_units, h->params(sample), h->bloom, h->table, h->ctr, h->grid, st);
         h->launches += 3;
+    } else if (bucket_bytes(h, n_local) > room_bytes(h)) {
+        // the window hashes would not fit the device budget: keep the packed
+        // reads (about 3 bits per base), extracted again at kc_finalize one
+        // hash range at a time
+        b.deferred = true;
+        ++h->deferred;
     } else {
-        s = bucket_batch(h, b, n_local, st);
+        s = bucket_batch(h, b, n_local, st, h->params(sample), false);
         if (s != KC_OK) {
             cudaFreeAsync(nm, st);
             cudaFreeAsync(bd, st);
@@ -865,7 +948,7 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     cudaFreeAsync(nm, st);
     cudaFreeAsync(bd, st);
     cudaFreeAsync(doff, st);
-    if (h->strategy != KC_STRATEGY_DIRECT) {
+    if (h->strategy != KC_STRATEGY_DIRECT && !b.deferred) {
         // the hashes replace the reads: nothing rescans them
         cudaFreeAsync(b.pw, st);
         cudaFreeAsync(b.vw, st);
@@ -897,7 +980,7 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
     if (capacity < h->n_result) return fail(KC_ERR_CAPACITY, "dump capacity smaller than the result");
     if (h->n_result == 0) return KC_OK;
     cudaStream_t st = h->stream;
-    if (h->spilled && h->cfg.spill == 1) {
+    if (h->spilled && h->cfg.spill != 2) {
         // copy the runs back and sort them on the device when there is room
         s = resort_spilled(h);
         if (s != KC_OK && s != KC_ERR_OOM_DEVICE) return s;
@@ -979,6 +1062,9 @@ kc_status kc_stats_get(kc_handle h, kc_stats* out) {
     out->split_level = h->host_ctr.split_hint;
     out->spilled_bytes = h->spilled_bytes;
     out->strategy = (uint32_t)h->strategy;
+    out->owned_windows = h->owner ? h->host_ctr.kept : h->host_ctr.windows;
+    out->deferred_batches = h->deferred;
+    out->scan_groups = h->scan_groups;
     size_t bytes = h->fixed_bytes + h->res_cap * 16;
     if (h->has_stems) bytes += std::max<uint64_t>(1, h->n_stems) * sizeof(kc_stem_item);
     if (h->has_selection) bytes += std::max<uint64_t>(1, h->n_sel) * 16 + (48ull << h->sel_buckets_log2) + (h->sel_pre ? 4ull * 49152 : 0);

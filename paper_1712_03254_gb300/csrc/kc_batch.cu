@@ -817,7 +817,9 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         JobWork& x = work[j];
         kc_handle h = x.h;
         const uint64_t P = 1ull << h->part_bits;
-        const uint64_t p_lo = std::min<uint64_t>(part_lo, P), p_hi = std::min<uint64_t>(part_hi, P);
+        // the requested partitions that the handle owns (kc_config.own_bits)
+        const uint64_t p_lo = std::max<uint64_t>(std::min<uint64_t>(part_lo, P), h->own_plo);
+        const uint64_t p_hi = std::max<uint64_t>(p_lo, std::min<uint64_t>(std::min<uint64_t>(part_hi, P), h->own_phi));
         const size_t nb = h->batches.size();
         for (uint64_t p = p_lo; p < p_hi; ++p) {
             uint64_t w = 0;
@@ -1051,34 +1053,35 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
 // of partitions, host location, items).  kc_dump merges the sorted runs.
 constexpr uint32_t kSpillGroups = 64;
 
-kc_status finalize_spilled(kc_batch_ctx* b, kc_handle h) {
-    const uint32_t P = 1u << h->part_bits;
-    const uint32_t G = std::min(P, kSpillGroups), per = P / G;
-    release_spill(h);
-    for (uint32_t g = 0; g < G; ++g) {
-        kc_status s = finalize_core(b, &h, 1, g * per, (g + 1) * per, g + 1 == G);
-        if (s != KC_OK) return s;
-        SpillRun run;
-        run.first_part = g * per;
-        run.n_parts = per;
-        run.n_items = h->n_result;
-        if (run.n_items) {
-            run.host = spill_alloc(h, 2 * run.n_items);
-            if (!run.host) return fail(KC_ERR_OOM_HOST, "pinned host memory for a spilled run");
-            // the copy waits for the group's sort; the next group runs meanwhile
-            KC_CUDA(cudaEventRecord(h->ev_main, b->st));
-            KC_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_main, 0));
-            KC_CUDA(cudaMemcpyAsync(run.host, h->res_keys, run.n_items * 8, cudaMemcpyDeviceToHost, h->copy_stream));
-            KC_CUDA(cudaMemcpyAsync(run.host + run.n_items, h->res_vals, run.n_items * 8, cudaMemcpyDeviceToHost,
-                                    h->copy_stream));
-        }
-        if (h->res_keys) cudaFreeAsync(h->res_keys, h->copy_stream);
-        if (h->res_vals) cudaFreeAsync(h->res_vals, h->copy_stream);
-        h->res_keys = h->res_vals = nullptr;
-        h->res_cap = 0;
-        h->spill_dir.push_back(run);
-        h->spilled_bytes += run.n_items * 16;
+// Finalize partitions [part_lo, part_hi) of h and copy their sorted result to
+// pinned host memory on the handle's side stream (one spill run).
+kc_status spill_group(kc_batch_ctx* b, kc_handle h, uint32_t part_lo, uint32_t part_hi, bool last) {
+    kc_status s = finalize_core(b, &h, 1, part_lo, part_hi, last);
+    if (s != KC_OK) return s;
+    SpillRun run;
+    run.first_part = part_lo;
+    run.n_parts = part_hi - part_lo;
+    run.n_items = h->n_result;
+    if (run.n_items) {
+        run.host = spill_alloc(h, 2 * run.n_items);
+        if (!run.host) return fail(KC_ERR_OOM_HOST, "pinned host memory for a spilled run");
+        // the copy waits for the group's sort; the next group runs meanwhile
+        KC_CUDA(cudaEventRecord(h->ev_main, b->st));
+        KC_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_main, 0));
+        KC_CUDA(cudaMemcpyAsync(run.host, h->res_keys, run.n_items * 8, cudaMemcpyDeviceToHost, h->copy_stream));
+        KC_CUDA(cudaMemcpyAsync(run.host + run.n_items, h->res_vals, run.n_items * 8, cudaMemcpyDeviceToHost,
+                                h->copy_stream));
     }
+    if (h->res_keys) cudaFreeAsync(h->res_keys, h->copy_stream);
+    if (h->res_vals) cudaFreeAsync(h->res_vals, h->copy_stream);
+    h->res_keys = h->res_vals = nullptr;
+    h->res_cap = 0;
+    h->spill_dir.push_back(run);
+    h->spilled_bytes += run.n_items * 16;
+    return KC_OK;
+}
+
+kc_status finish_spill(kc_handle h) {
     KC_CUDA(cudaStreamSynchronize(h->copy_stream));
     uint64_t total = 0;
     for (const auto& r : h->spill_dir) total += r.n_items;
@@ -1088,11 +1091,127 @@ kc_status finalize_spilled(kc_batch_ctx* b, kc_handle h) {
     return KC_OK;
 }
 
+// Spill groups of partitions [g * per, (g + 1) * per) that the handle owns.
+std::vector<uint32_t> owned_groups(kc_handle h, uint32_t G, uint32_t per, uint32_t g_lo, uint32_t g_hi) {
+    std::vector<uint32_t> out;
+    for (uint32_t g = g_lo; g < g_hi; ++g)
+        if ((g + 1) * per > h->own_plo && g * per < h->own_phi) out.push_back(g);
+    return out;
+}
+
+kc_status finalize_spilled(kc_batch_ctx* b, kc_handle h) {
+    const uint32_t P = 1u << h->part_bits;
+    const uint32_t G = std::min(P, kSpillGroups), per = P / G;
+    release_spill(h);
+    const std::vector<uint32_t> groups = owned_groups(h, G, per, 0, G);
+    for (size_t i = 0; i < groups.size(); ++i) {
+        const uint32_t g = groups[i];
+        kc_status s = spill_group(b, h, g * per, (g + 1) * per, i + 1 == groups.size());
+        if (s != KC_OK) return s;
+    }
+    return finish_spill(h);
+}
+
+// Out-of-core finalize of a handle with batches kept as reads (their hashes
+// would have passed the device budget).  The hash space is cut into S scan
+// ranges, S a power of two chosen so that one range's grouped hashes fit the
+// room left; for each range every kept batch is extracted and grouped again
+// in pieces, keeping only the range's windows, and the range's spill groups
+// are finalized and spilled as by finalize_spilled.  Batches grouped at
+// kc_add_reads take part in every range as they are.
+kc_status finalize_grouped(kc_batch_ctx* b, kc_handle h) {
+    const uint32_t P = 1u << h->part_bits;
+    const uint32_t G = std::min(P, kSpillGroups), per = P / G;
+    uint64_t kept_bases = 0;
+    for (const auto& bt : h->batches)
+        if (bt.deferred) kept_bases += bt.n_units * 64;
+    // one range: its grouped hashes (8 bytes per window) plus the linear
+    // hashes of the piece being grouped, about as large, plus the survivors
+    // of one spill group; S = G at most
+    const uint64_t room = room_bytes(h);
+    uint32_t S = 1;
+    while (S < G && 3 * (8 * kept_bases / S) > room) S <<= 1;
+    h->scan_groups = S;
+    const uint64_t piece_units = std::max<uint64_t>(1ull << 16, (kept_bases / 64) / S + 1);
+    release_spill(h);
+    std::vector<Batch> kept = h->batches;
+    std::vector<uint32_t> all_groups = owned_groups(h, G, per, 0, G);
+    const uint32_t last_group = all_groups.empty() ? 0 : all_groups.back();
+    cudaStream_t st = h->stream;
+    kc_status s = KC_OK;
+    for (uint32_t r = 0; r < S && s == KC_OK; ++r) {
+        const std::vector<uint32_t> groups = owned_groups(h, G, per, r * (G / S), (r + 1) * (G / S));
+        if (groups.empty()) continue;
+        // hash range of scan range r, within the handle's own range
+        const int pb = h->part_bits;
+        const uint64_t p0 = (uint64_t)r * (P / S), p1 = (uint64_t)(r + 1) * (P / S);
+        kc::PassParams base = h->params(0);
+        base.h_lo = std::max<uint64_t>(h->own_h_lo, p0 << (64 - pb));
+        base.h_hi = std::min<uint64_t>(h->own_h_hi, (p1 << (64 - pb)) - 1ull);  // p1 = P wraps to 0: ~0
+        std::vector<Batch> pieces;
+        cudaEvent_t t0 = phase_begin(h);
+        for (const Batch& bt : kept) {
+            if (!bt.deferred) {
+                pieces.push_back(bt);
+                continue;
+            }
+            for (uint64_t u0 = 0; u0 < bt.n_units && s == KC_OK; u0 += piece_units) {
+                Batch pc;
+                pc.sample = bt.sample;
+                pc.pw = bt.pw + 2 * u0;  // the word after the piece is the next unit's first word (or padding)
+                pc.vw = bt.vw + u0;
+                pc.n_units = std::min(piece_units, bt.n_units - u0);
+                kc::PassParams p = base;
+                p.sample = bt.sample;
+                s = bucket_batch(h, pc, pc.n_units * 64, st, p, true);
+                h->launches += 5;
+                pc.pw = pc.vw = nullptr;  // the piece borrows the kept reads
+                pc.deferred = true;       // marks hashes to free after the range
+                if (s == KC_OK) pieces.push_back(pc);
+            }
+        }
+        phase_end(h, kPass1, t0);
+        if (s == KC_OK) {
+            h->batches = pieces;
+            for (uint32_t g : groups) {
+                s = spill_group(b, h, g * per, (g + 1) * per, g == last_group);
+                if (s != KC_OK) break;
+            }
+        }
+        for (Batch& pc : pieces)
+            if (pc.deferred) {
+                if (pc.hdata) cudaFreeAsync(pc.hdata, st);
+                if (pc.hstarts) cudaFreeAsync(pc.hstarts, st);
+            }
+        h->batches = kept;
+    }
+    if (s != KC_OK) return s;
+    return finish_spill(h);
+}
+
 kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
-    if (n == 1 && hs && hs[0] && hs[0]->cfg.spill && hs[0]->strategy == KC_STRATEGY_PARTITIONED &&
-        hs[0]->state == State::Open)
-        return finalize_spilled(b, hs[0]);
-    return finalize_core(b, hs, n, 0, 0xffffffffu, true);
+    if (n == 1 && hs && hs[0] && hs[0]->strategy == KC_STRATEGY_PARTITIONED && hs[0]->state == State::Open) {
+        kc_handle h = hs[0];
+        if (h->deferred) return finalize_grouped(b, h);
+        if (h->cfg.spill) return finalize_spilled(b, h);
+        // survivors and sorted result, 16 bytes each per key, at most one
+        // key per min_count windows (and per base): spill when they would
+        // not fit
+        if (32 * (h->bases / std::max<uint32_t>(1, h->min_count)) > room_bytes(h)) return finalize_spilled(b, h);
+    }
+    if (!hs || n <= 1) return finalize_core(b, hs, n, 0, 0xffffffffu, true);
+    // handles whose reads passed the device budget are finalized alone, in
+    // hash ranges; the others together
+    std::vector<kc_handle> rest;
+    for (int j = 0; j < n; ++j) {
+        if (hs[j] && hs[j]->deferred && hs[j]->strategy == KC_STRATEGY_PARTITIONED && hs[j]->state == State::Open) {
+            kc_status s = finalize_grouped(b, hs[j]);
+            if (s != KC_OK) return s;
+        } else {
+            rest.push_back(hs[j]);
+        }
+    }
+    return finalize_core(b, rest.data(), (int)rest.size(), 0, 0xffffffffu, true);
 }
 
 extern "C" {

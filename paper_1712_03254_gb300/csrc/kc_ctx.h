@@ -33,6 +33,9 @@ struct Batch {
     uint64_t* hdata = nullptr;    // capacity: one per base of the batch
     uint64_t* hstarts = nullptr;  // partition starts, 2^part_bits + 1
     uint64_t hcap = 0;
+    // partitioned, over the device budget: the reads are kept (pw, vw) and
+    // extracted again at kc_finalize, one hash range at a time
+    bool deferred = false;
 };
 
 enum class State { Open, Finalized, Poisoned };
@@ -140,8 +143,18 @@ struct kc_ctx {
     bool has_stems = false;
 
 
+    // hash-range ownership (kc_config.own_bits): keys with own_h_lo <= h <=
+    // own_h_hi, i.e. partitions own_plo .. own_phi - 1
+    uint64_t own_h_lo = 0, own_h_hi = ~0ull;
+    uint32_t own_plo = 0, own_phi = 0;
+    bool owner = false;
+    // device budget (kc_config.device_budget) and the batches kept as reads
+    uint32_t deferred = 0, scan_groups = 0;
+
     kc::PassParams params(int sample) const {
         kc::PassParams p{};
+        p.h_lo = own_h_lo;
+        p.h_hi = own_h_hi;
         p.k = k;
         p.rc_shift = 64 - 2 * k;
         p.kmask = (1ull << (2 * k)) - 1ull;
@@ -185,6 +198,12 @@ bool is_device_ptr(const void* p);
 kc_status resort_spilled(kc_handle h);
 void free_selection(kc_handle h);
 void free_stems(kc_handle h);
+// Group a batch's window hashes (those in [p.h_lo, p.h_hi]) by partition
+// into b.hdata / b.hstarts; exact: size b.hdata after one read-back.
+kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st, const kc::PassParams& p,
+                       bool exact);
+uint64_t held_bytes(kc_handle h);
+uint64_t room_bytes(kc_handle h);
 // Sort n (key, value) pairs (keys below 2^key_bits) from tk/tv into out_k/out_v;
 // ctr->survivors holds n on the device; synchronises the stream.
 kc_status sort_pairs(kc_handle h, const uint64_t* tk, const uint64_t* tv, uint64_t n, int key_bits,

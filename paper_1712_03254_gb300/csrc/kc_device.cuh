@@ -27,8 +27,11 @@ struct DevCounters {
     unsigned int err;               // DERR_* bits
     unsigned int split_parts;       // partitions counted in sub-ranges
     unsigned int split_hint;        // split level the job's partitions start at
-    unsigned int pad[5];
+    unsigned int pad0;
+    unsigned long long kept;        // windows kept by hash-range restricted extractions
+    unsigned int pad[2];
 };
+static_assert(sizeof(DevCounters) == 64, "device counters: 64 bytes");
 
 enum : unsigned int {
     DERR_TABLE_FULL = 1u,      // a probe sequence visited every slot
@@ -50,6 +53,10 @@ struct PassParams {
     unsigned long long table_mask;
     int all_candidates;      // min_count <= 1: every window goes to the table
     int sample;
+    // Hash range kept by the partitioned extraction: a window is kept iff
+    // h_lo <= h <= h_hi (0 and ~0: every window).  It restricts a handle to the
+    // keys it owns, or to one hash range of an out-of-core job at a time.
+    unsigned long long h_lo, h_hi;
 };
 
 // SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014): golden-ratio

@@ -107,10 +107,12 @@ struct SegDesc {
     uint64_t off, len, group, pad;
 };
 // mode 4: the extraction pass writes every CTA's hashes to its own segment of
-// a linear array (plus counts); the staged scatter then moves the segments
+// a linear array (plus counts); the staged scatter then moves the segments.
+// Windows outside [p.h_lo, p.h_hi] are dropped (their number kept goes to
+// ctr->kept when the range is not the whole hash space).
 void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                           int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, SegDesc* seg,
-                          uint64_t* lin, cudaStream_t st);
+                          uint64_t* lin, DevCounters* ctr, cudaStream_t st);
 // Staged scatter of segs[c] into its runs: bucket (h >> (64 - a1 - a2)) mod
 // 2^a2; with a1 > 0 only hashes of the segment's level-1 group.
 void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,

@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(512) k_bucket_pass(const uint64_t* __restrict_
                 const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
                 const uint64_t h = mixer64(key);
                 const uint32_t b = (uint32_t)(h >> (64 - a));
-                if (kMode == kScatterCursor) {
+                if (h < p.h_lo || h > p.h_hi) {
+                    // outside the kept hash range
+                } else if (kMode == kScatterCursor) {
                     const unsigned long long pos = atomicAdd(cursor + b, 1ull);
                     out[pos] = h;
                 } else {
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kStagedThreads) k_bucket_scatter_staged(
             const uint64_t key = canonical_key(window_code(uw.w0, uw.w1, uw.w2, j, p.rc_shift), p);
             ph = mixer64(key);
             pb = (uint32_t)(ph >> (64 - a));
-            pend = true;
+            pend = ph >= p.h_lo && ph <= p.h_hi;  // only the kept hash range
         }
         if (pend) {
             const uint32_t pos = atomicAdd(&fill[pb], 1u);
@@ -204,14 +206,22 @@ __global__ void __launch_bounds__(kStagedThreads) k_bucket_scatter_staged(
 // contiguous segment per CTA of a linear array (warp-aggregated positions, so
 // the stores are coalesced), and the CTA's histogram over partitions goes to
 // counts[cta][*].  seg[cta] = {segment start, its length}.
+//
+// kRange: only windows with p.h_lo <= h <= p.h_hi are kept (a handle owning
+// a hash range, or one range of an out-of-core job).  The CTA still reserves
+// room for all its windows, but a warp claims positions step by step for the
+// windows it keeps, so the segment holds the kept hashes contiguously and its
+// length is set at the end; the kept total goes to ctr->kept.
 constexpr int kExtractThreads = 1024;
 
+template <bool kRange>
 __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_t* __restrict__ pw,
                                                        const uint64_t* __restrict__ vw, uint64_t n_units,
                                                        uint64_t units_per_cta, PassParams p, int a,
                                                        uint32_t* __restrict__ counts,
                                                        unsigned long long* __restrict__ g_cursor,
-                                                       SegDesc* __restrict__ seg, uint64_t* __restrict__ lin) {
+                                                       SegDesc* __restrict__ seg, uint64_t* __restrict__ lin,
+                                                       DevCounters* __restrict__ ctr) {
     extern __shared__ uint32_t s_cnt[];
     __shared__ unsigned long long s_base;
     __shared__ unsigned s_pos;
@@ -246,26 +256,37 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
         const unsigned tot = __reduce_add_sync(kFull, nv);
         if (tot == 0) continue;
         unsigned wb = 0;
-        if (lane == 0) wb = atomicAdd(&s_pos, tot);
-        wb = __shfl_sync(kFull, wb, 0);
+        if (!kRange) {
+            if (lane == 0) wb = atomicAdd(&s_pos, tot);
+            wb = __shfl_sync(kFull, wb, 0);
+        }
         // every lane walks the 64 window starts of its unit with rolling codes
         RollingWindow rw = rolling_start(uw.w0, uw.w1, uw.w2, p);
 #pragma unroll 4
         for (int j = 0; j < 64; ++j) {
-            const bool has = (vm >> (63 - j)) & 1ull;
+            bool has = (vm >> (63 - j)) & 1ull;
             uint64_t h = 0;
             if (has) {
                 h = mixer64(rw.fwd < rw.rc ? rw.fwd : rw.rc);
-                atomicAdd(&s_cnt[(uint32_t)(h >> (64 - a))], 1u);
+                if (kRange) has = h >= p.h_lo && h <= p.h_hi;
+                if (has) atomicAdd(&s_cnt[(uint32_t)(h >> (64 - a))], 1u);
             }
             const unsigned ballot = __ballot_sync(kFull, has);
+            if (kRange && ballot) {  // warp-uniform: positions for this step's kept windows
+                if (lane == 0) wb = atomicAdd(&s_pos, (unsigned)__popc(ballot));
+                wb = __shfl_sync(kFull, wb, 0);
+            }
             if (has) lin[base + wb + __popc(ballot & lt)] = h;
-            wb += __popc(ballot);
+            if (!kRange) wb += __popc(ballot);
             rolling_step(rw, p);
         }
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[(uint64_t)blockIdx.x * P + i] = s_cnt[i];
+    if (kRange && threadIdx.x == 0) {
+        seg[blockIdx.x].len = s_pos;
+        if (s_pos) atomicAdd(&ctr->kept, (unsigned long long)s_pos);
+    }
 }
 
 constexpr int kLinThreads = 1024;
@@ -614,11 +635,18 @@ void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_unit
 
 void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                           int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, SegDesc* seg,
-                          uint64_t* lin, cudaStream_t st) {
+                          uint64_t* lin, DevCounters* ctr, cudaStream_t st) {
     const size_t smem = bucket_pass_smem(a);
-    allow_max_dynamic_smem(k_extract_count);
-    k_extract_count<<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
-                                               reinterpret_cast<unsigned long long*>(g_cursor), seg, lin);
+    unsigned long long* cur = reinterpret_cast<unsigned long long*>(g_cursor);
+    if (p.h_lo == 0ull && p.h_hi == ~0ull) {
+        allow_max_dynamic_smem(k_extract_count<false>);
+        k_extract_count<false><<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
+                                                                      cur, seg, lin, ctr);
+    } else {
+        allow_max_dynamic_smem(k_extract_count<true>);
+        k_extract_count<true><<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
+                                                                     cur, seg, lin, ctr);
+    }
 }
 
 // stage, fill count and 64-bit output cursor per bucket, then the two retry lists

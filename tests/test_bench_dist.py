@@ -1,12 +1,16 @@
 """Host logic of the multi-GPU benchmark, with two gloo ranks on the CPU.
 
-Each rank counts its own read set (no collective on the data path); the
-benchmark only reduces the timing (max over ranks) and the work (sum over
-ranks).  Here two CPU processes check the seed assignment and both reductions.
+The one job is sharded by hash range: each rank owns a contiguous range of
+the 64 hash shards (no collective on the data path); the benchmark reduces
+only the timing (max over ranks), counts the job's windows once, and after
+the timed steps gathers the ranks' results for a merge by key.  Here two CPU
+processes check the shard assignment, the reduction and the gather + merge
+of disjoint sorted results.
 """
 import os
 import socket
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -23,24 +27,26 @@ def _worker(rank, world, port, q):
     os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
                        "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
     import bench
+    import paper_1712_03254_gb300 as kc
 
     r, w, local = bench.dist_env()
     dist = bench.init_dist(w, "gloo")
     dev = torch.device("cpu")
-    seed = bench.shard_seed(r)
-    # per-rank "measurements": rank 1 is slower and counts more windows
-    t = 1.0 + r
-    windows = 1000 * (r + 1)
-    t_max = bench.reduce_max(t, dist, dev)
-    w_sum = bench.reduce_sum(float(windows), dist, dev)
-    seeds = [torch.zeros(1, dtype=torch.int64) for _ in range(w)]
-    dist.all_gather(seeds, torch.tensor([seed], dtype=torch.int64))
+    knobs = bench.owner_knobs(r, w)
+    # per-rank "measurements": rank 1 is slower
+    t_max = bench.reduce_max(1.0 + r, dist, dev)
+    # each rank's result: the keys of its own shards (here: keys = shard * 1000 + i, i < 3)
+    keys = np.array([s * 1000 + i for s in range(knobs["own_lo"], knobs["own_hi"]) for i in range(3)], np.uint64)
+    counts = (keys % 7 + 2).astype(np.uint32).reshape(-1, 1)
+    gathered = [None] * w
+    dist.all_gather_object(gathered, (keys, counts))
+    mk, mc = kc.merge_results(gathered, 1)
     bench.barrier(dist)
-    q.put((r, w, local, t_max, w_sum, [int(s.item()) for s in seeds]))
+    q.put((r, w, local, knobs, t_max, mk.tolist(), mc[:, 0].tolist()))
     dist.destroy_process_group()
 
 
-def test_two_rank_reductions_and_seeds():
+def test_two_rank_shards_reduction_and_merge():
     world = 2
     port = _free_port()
     ctx = mp.get_context("spawn")
@@ -52,15 +58,17 @@ def test_two_rank_reductions_and_seeds():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    out.sort()
-    for r, (rank, w, local, t_max, w_sum, seeds) in enumerate(out):
+    out.sort(key=lambda x: x[0])
+    import bench
+
+    assert [o[3] for o in out] == [{"own_bits": bench.OWN_BITS, "own_lo": 0, "own_hi": 32},
+                                   {"own_bits": bench.OWN_BITS, "own_lo": 32, "own_hi": 64}]
+    want = [s * 1000 + i for s in range(64) for i in range(3)]
+    for r, (rank, w, local, knobs, t_max, mk, mc) in enumerate(out):
         assert rank == r and w == world and local == r
         assert t_max == 2.0  # the slowest rank's time
-        assert w_sum == 3000.0  # windows of all ranks
-        assert seeds[0] == 2  # rank 0 counts the canonical workload
-        assert len(set(seeds)) == world  # every rank has its own read set
-    # the aggregate the benchmark prints: all ranks' work over the slowest time
-    assert out[0][4] / out[0][3] == 1500.0
+        assert mk == want  # the union of both ranks' shards, in key order
+        assert mc == [k % 7 + 2 for k in want]
 
 
 def test_single_process_needs_no_process_group():
@@ -68,5 +76,5 @@ def test_single_process_needs_no_process_group():
 
     assert bench.init_dist(1, "gloo") is None
     assert bench.reduce_max(3.5, None, None) == 3.5
-    assert bench.reduce_sum(2.0, None, None) == 2.0
+    assert bench.owner_knobs(0, 1) == {}
     bench.barrier(None)

@@ -66,3 +66,45 @@ def test_stem_hbm():
     assert r["algorithmic_bytes"] == algo
     assert r["frac"] == pytest.approx(algo / 2e-3 / 1e9 / peak, abs=1e-4)
     assert bench.stem_hbm(10, 10, 0.0) is None
+
+
+def test_algorithmic_bytes_of_the_mid_job_is_the_stated_11_7_per_window():
+    """Reads 2 x 3 bits/base, filter and table 3 x their bytes, 12 B per result key: about 11.7 B per
+    window on the mid job (1e6 x 150 bp reads, 118,157,762 windows, 2^30-bit filter, 2^24 slots,
+    5,260,097 result keys)."""
+    a = bench.algorithmic_bytes(150_000_000, 118_157_762, 1 << 30, 1 << 24, 5_260_097, 1)
+    assert a["terms"]["reads"] == 2 * ((150_000_000 * 3 + 7) // 8)
+    assert a["terms"]["filter"] == 3 * (1 << 27)
+    assert a["terms"]["table"] == 3 * 16 * (1 << 24)
+    assert a["terms"]["output"] == 12 * 5_260_097
+    assert a["per_window"] == pytest.approx(11.71, abs=0.01)
+
+
+def test_atomic_ceiling_combines_the_updates_of_a_window():
+    rates = {"smem_or64_per_s": 2e12, "smem_add32_per_s": 6e12, "l2_or64_per_s": 1e11, "hbm_or64_per_s": 2e10}
+    part = bench.atomic_ceiling(rates, 2)
+    assert part["windows_per_s"] == pytest.approx(1 / (3 / 6e12 + 1 / 2e12), rel=1e-6)
+    direct = bench.atomic_ceiling(rates, 1)
+    assert direct["windows_per_s"] == pytest.approx(2e10, rel=1e-6)
+
+
+def test_roofline_hbm_form_and_ceilings(monkeypatch):
+    monkeypatch.setattr(bench, "ncu_kernel", lambda kernel, workload: None)
+
+    class W:
+        bloom_bits, table_slots, samples = 1 << 30, 1 << 24, [None]
+
+    st = {"windows": 118_157_762, "strategy": 2, "result_keys": 5_260_097}
+    phases = {"pass1": [1.2], "pass2": [1.15], "ingest": [0.05], "compact": [0.0], "sort": [0.49]}
+    rates = {"smem_or64_per_s": 2e12, "smem_add32_per_s": 6e12, "l2_or64_per_s": 1e11, "hbm_or64_per_s": 2e10}
+    r = bench.roofline_of(st, phases, 150_000_000, W, 152, 3.2, rates=rates)
+    peak, _ = bench.measured_hbm_peak()
+    algo = bench.algorithmic_bytes(150_000_000, st["windows"], W.bloom_bits, W.table_slots, st["result_keys"], 1)
+    assert r["bound"] == "hbm" and r["kernel"] == "k_consume_q" and r["traffic"] is None
+    assert r["achieved"] == pytest.approx(algo["total"] / 1.15e-3 / 1e9, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak, abs=1e-4)
+    assert r["step"]["frac"] == pytest.approx(algo["total"] / 3.2e-3 / 1e9 / peak, abs=1e-4)
+    c = r["ceilings"]
+    assert c["min_windows_per_s"] == min(c["hbm_windows_per_s"], c["atomic"]["windows_per_s"])
+    assert c["step_frac_of_min"] == pytest.approx(st["windows"] / 3.2e-3 / c["min_windows_per_s"], abs=1e-4)
+    assert r["implementation_bytes"] == 16 * st["windows"]
