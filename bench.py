@@ -31,6 +31,11 @@ distinct k-mer) through one-at-a-time plain jobs and through the
 continuous-batching server, at 0.7 and 0.9 of the plain capacity and all at
 once; latencies count from each job's scheduled arrival.
 
+The "paired" and "ooc" fields run this benchmark on the two-sample job
+(2 x 10,000,000 reads, joint table; tuned) and on the out-of-core job
+(100,000,000 reads, 64 partition groups spilled to pinned host memory), each
+in a process of its own (--no-other-workloads skips them).
+
 The "prune_chain" field times the paper's two-filter Prune chain (direct
 strategy) on the mid job beside the direct strategy without it.
 
@@ -767,6 +772,12 @@ def run_kc(args):
         filt = run_filter_bench(dev, stream, args.steps, args.warmup, flush)
         chain = run_chain_bench(w, chunks_d, stream, min(args.steps, 5), args.warmup, flush)
 
+    # the two-sample and out-of-core configurations, each in a process of its own
+    others = {}
+    if rank == 0 and world == 1 and args.workload == "mid" and not args.no_other_workloads:
+        others["paired"] = run_workload_subprocess("paired", min(args.steps, 5), 3)
+        others["ooc"] = run_workload_subprocess("ooc", 3, 3, ["--part-bits", "18"])
+
     served = None
     if rank == 0 and world == 1 and not args.no_served and args.workload == "mid":
         # the mid job's buffers are not needed any more; the stream of jobs
@@ -804,6 +815,7 @@ def run_kc(args):
             "served": served,
             "filter": filt,
             "prune_chain": chain,
+            **others,
         }
         print(json.dumps(line), flush=True)
     c.close()
@@ -957,6 +969,19 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
     return out
 
 
+def run_workload_subprocess(workload: str, steps: int, warmup: int, extra=()):
+    """This benchmark on another workload, in a fresh Python process: its JSON line (or the error)."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", workload, "--steps", str(steps), "--warmup",
+           str(warmup), "--no-cpu-baseline", *extra]
+    r = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT)
+    if r.returncode != 0:
+        return {"error": r.stderr[-2000:]}
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    keep = ("value", "unit", "ms_per_step", "config", "strategy", "tuning", "phase_ms", "roofline", "e2e", "clocks",
+            "gpu_launches", "steps", "warmup")
+    return {k: line.get(k) for k in keep}
+
+
 def run_served_subprocess(n_jobs: int, max_reads: int):
     """run_served_trace in a fresh Python process; its result (a JSON line)."""
     code = ("import json, sys; sys.path.insert(0, %r); import bench; "
@@ -1013,6 +1038,8 @@ def main(argv=None):
     ap.add_argument("--strategy", choices=["auto", "direct", "partitioned"], default="auto")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream comparison")
     ap.add_argument("--no-filter", action="store_true", help="skip the Filter-unit measurement")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the paired and ooc fields of the default (mid) line")
     ap.add_argument("--filter-only", action="store_true",
                     help="print only the Filter-unit measurement (one JSON object), for profiling it alone")
     ap.add_argument("--served-jobs", type=int, default=256)

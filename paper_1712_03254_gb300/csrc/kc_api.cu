@@ -474,7 +474,7 @@ kc_status sort_pairs(kc_handle h, const uint64_t* tk, const uint64_t* tv, uint64
     kc::launch_prefix_hist(tk, ctr, n, prefix_shift, n_buckets, hist, h->grid, st);
     KC_CUDA(kc::launch_scan(hist, n_buckets, starts, cursor, st));
     kc::launch_scatter(tk, tv, ctr, n, prefix_shift, n_buckets, cursor, out_k, out_v, h->grid, st);
-    kc::launch_bucket_sort_warp(out_k, out_v, starts, n_buckets, ctr, h->grid, st);
+    kc::launch_bucket_sort_warp(out_k, out_v, starts, n_buckets, prefix_shift, ctr, h->grid, st);
     phase_end(h, phase, t0);
     h->launches += 4;
     KC_LAUNCHED("sort launches");
@@ -525,6 +525,7 @@ kc_status sort_result(kc_handle h, uint64_t* tk, uint64_t* tv) {
     cudaStream_t st = h->stream;
     const uint64_t n = h->host_ctr.survivors;
     const uint64_t cap = std::max<uint64_t>(1, n);
+    free_result(h);
     cudaError_t e;
     if ((e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess) {
@@ -786,7 +787,7 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
 kc_status kc_reset(kc_handle h) {
     if (!h) return fail(KC_ERR_ARG, "null handle");
     free_batches(h);
-    free_result(h);
+    h->n_result = 0;  // the result arrays stay allocated for the next job (finalize reuses them)
     free_selection(h);
     free_stems(h);
     h->filter_windows = h->filter_hits = 0;

@@ -45,6 +45,7 @@ struct JobDesc {
     uint64_t* res_keys;
     uint64_t* res_vals;
     uint64_t res_cap;
+    uint64_t flat_base;  // this job's first survivor in the batch's survivors, in job order (set by the plan)
 };
 
 struct BatchDesc {
@@ -61,6 +62,9 @@ struct BatchDesc {
     uint64_t* cursor;
     unsigned long long* tiles;
     uint64_t n_tiles;
+    uint64_t buckets_cap;  // room of hist / starts / cursor
+    int all_packable;      // set by the plan: every job's small buckets sort packed (k_warp_sort_q)
+    uint64_t n_flat;       // set by the plan: survivors of all jobs
 };
 
 namespace {
@@ -251,17 +255,114 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
     }
 }
 
+// Start of a batch: the queue head, the sort error bits and every job's
+// survivor and failed-partition counters at zero.
+__global__ void k_reset_q(const BatchDesc* __restrict__ D) {
+    for (uint32_t i = threadIdx.x; i < 2 * D->n_jobs; i += blockDim.x) D->counters[i] = 0ull;
+    if (threadIdx.x == 0) {
+        *D->head = 0u;
+        *D->err = 0u;
+    }
+}
+
+// Sort plan, on the device once the survivors are counted: per job, bucket
+// bits for at most about 32 survivors a bucket and the job's first bucket in
+// the flat arrays; the total into D->n_buckets.  More buckets than the arrays
+// hold (never, when the host sized them from the survivor capacities) is an
+// internal error and sorts nothing.
+__global__ void k_plan_q(BatchDesc* __restrict__ D) {
+    if (threadIdx.x != 0) return;
+    JobDesc* jobs = const_cast<JobDesc*>(D->jobs);
+    uint64_t total = 0, flat = 0;
+    int packable = 1;
+    for (uint32_t j = 0; j < D->n_jobs; ++j) {
+        JobDesc& J = jobs[j];
+        uint64_t nsv = D->counters[2 * j];
+        if (nsv > J.sv_cap) nsv = J.sv_cap;
+        J.flat_base = flat;
+        flat += nsv;
+        if (nsv < 1) nsv = 1;
+        int bits = 0;
+        while (bits < 24 && bits < J.key_bits && (nsv >> bits) > 32) ++bits;
+        J.sort_bits = bits;
+        J.bucket_base = total;
+        J.n_buckets = 1ull << bits;
+        total += J.n_buckets;
+        if (J.key_bits - bits > 58) packable = 0;
+    }
+    D->all_packable = packable;
+    D->n_flat = flat;
+    *D->err = 0u;
+    if (total > D->buckets_cap) {
+        atomicOr(D->err, DERR_INTERNAL);
+        total = 0;
+    }
+    D->n_buckets = total;
+}
+
+__global__ void k_zero_hist_q(const BatchDesc* __restrict__ D) {
+    const uint64_t n = D->n_buckets;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) D->hist[i] = 0u;
+}
+
+// Job owning the batch's survivor number i (jobs are in survivor order).
+__device__ __forceinline__ uint32_t job_of_survivor(const BatchDesc* D, uint64_t i) {
+    uint32_t lo = 0, hi = D->n_jobs;  // invariant: jobs[lo].flat_base <= i
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (D->jobs[mid].flat_base <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// A thread's view of the job that owns its current survivor: the fields the
+// histogram and scatter use, reloaded only when the survivor index passes
+// into a later job (a thread's indices only grow).
+struct SurvivorJob {
+    uint32_t j;
+    uint64_t lo, hi;  // flat survivor range of job j
+    const uint64_t* keys;
+    const uint64_t* vals;
+    int shift;
+    uint64_t n_buckets, bucket_base;
+    uint64_t* res_keys;
+    uint64_t* res_vals;
+    uint64_t res_cap;
+    __device__ void load(const BatchDesc* D, uint32_t jj) {
+        j = jj;
+        const JobDesc& J = D->jobs[jj];
+        lo = J.flat_base;
+        hi = jj + 1 < D->n_jobs ? D->jobs[jj + 1].flat_base : D->n_flat;
+        keys = J.sv_keys;
+        vals = J.sv_vals;
+        shift = J.key_bits - J.sort_bits;
+        n_buckets = J.n_buckets;
+        bucket_base = J.bucket_base;
+        res_keys = J.res_keys;
+        res_vals = J.res_vals;
+        res_cap = J.res_cap;
+    }
+    __device__ void seek(const BatchDesc* D, uint64_t i) {
+        while (i >= hi && j + 1 < D->n_jobs) load(D, j + 1);
+    }
+};
+
+// The survivors of all jobs as one flat range: every thread takes survivors
+// across job boundaries, so one job or many keep the whole grid busy.
 __global__ void k_prefix_hist_q(const BatchDesc* __restrict__ D) {
-    for (uint32_t j = blockIdx.y; j < D->n_jobs; j += gridDim.y) {
-        const JobDesc& J = D->jobs[j];
-        const uint64_t n = min((uint64_t)D->counters[2 * j], J.sv_cap);
-        const int shift = J.key_bits - J.sort_bits;
-        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-            const uint64_t b = J.sv_keys[i] >> shift;
-            if (b < J.n_buckets) atomicAdd(D->hist + J.bucket_base + b, 1u);
-            else atomicOr(D->err, DERR_INTERNAL);
-        }
+    const uint64_t n = D->n_flat;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    SurvivorJob S;
+    S.load(D, job_of_survivor(D, i));
+    for (; i < n; i += stride) {
+        S.seek(D, i);
+        const uint64_t b = S.keys[i - S.lo] >> S.shift;
+        if (b < S.n_buckets) atomicAdd(D->hist + S.bucket_base + b, 1u);
+        else atomicOr(D->err, DERR_INTERNAL);
     }
 }
 
@@ -346,27 +447,33 @@ __global__ void __launch_bounds__(1024) k_scan_apply_q(const BatchDesc* __restri
 }
 
 __global__ void k_scatter_q(const BatchDesc* __restrict__ D) {
-    for (uint32_t j = blockIdx.y; j < D->n_jobs; j += gridDim.y) {
-        const JobDesc& J = D->jobs[j];
-        const uint64_t n = min((uint64_t)D->counters[2 * j], J.sv_cap);
-        const int shift = J.key_bits - J.sort_bits;
-        const uint64_t job0 = D->starts[J.bucket_base];
-        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-            const uint64_t key = J.sv_keys[i];
-            const uint64_t b = key >> shift;
-            if (b >= J.n_buckets) {
-                atomicOr(D->err, DERR_INTERNAL);
-                continue;
-            }
-            const uint64_t pos = atomicAdd(reinterpret_cast<unsigned long long*>(D->cursor) + J.bucket_base + b, 1ull) - job0;
-            if (pos >= J.res_cap) {
-                atomicOr(D->err, DERR_INTERNAL);
-                continue;
-            }
-            J.res_keys[pos] = key;
-            J.res_vals[pos] = J.sv_vals[i];
+    const uint64_t n = D->n_flat;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    SurvivorJob S;
+    S.load(D, job_of_survivor(D, i));
+    uint64_t job0 = D->starts[S.bucket_base];
+    for (; i < n; i += stride) {
+        if (i >= S.hi) {
+            S.seek(D, i);
+            job0 = D->starts[S.bucket_base];
         }
+        const uint64_t k = i - S.lo;
+        const uint64_t key = S.keys[k];
+        const uint64_t val = S.vals[k];
+        const uint64_t b = key >> S.shift;
+        if (b >= S.n_buckets) {
+            atomicOr(D->err, DERR_INTERNAL);
+            continue;
+        }
+        const uint64_t pos = atomicAdd(reinterpret_cast<unsigned long long*>(D->cursor) + S.bucket_base + b, 1ull) - job0;
+        if (pos >= S.res_cap) {
+            atomicOr(D->err, DERR_INTERNAL);
+            continue;
+        }
+        S.res_keys[pos] = key;
+        S.res_vals[pos] = val;
     }
 }
 
@@ -381,25 +488,61 @@ __device__ __forceinline__ uint32_t job_of_bucket(const BatchDesc* D, uint64_t f
     return lo;
 }
 
-__global__ void __launch_bounds__(256, 2) k_warp_sort_q(const BatchDesc* __restrict__ D) {
+// Buckets of 2..64 keys (nearly all of them: the bits are chosen for about
+// 32 keys a bucket on average, and canonical keys, the smaller of two
+// orientations, are up to twice as dense at the low end of the key space):
+// one warp each, packed (warp_sort32_packed / warp_sort64_packed), small
+// enough in registers for six 256-thread CTAs per SM, so the loads of many
+// buckets are in flight.
+__global__ void __launch_bounds__(256, 6) k_warp_sort_q(const BatchDesc* __restrict__ D) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nb = D->n_buckets;
+    if (!D->all_packable) return;  // every bucket goes to k_warp_sort_big_q
     for (uint64_t fb = warp; fb < nb; fb += n_warps) {
         const uint64_t n64 = D->starts[fb + 1] - D->starts[fb];
-        if (n64 <= 1) continue;
-        if (n64 > 256) {
-            if (lane == 0) atomicOr(D->err, DERR_SORT_MEDIUM);
-            continue;
-        }
+        if (n64 <= 1 || n64 > 64) continue;  // larger ones: k_warp_sort_big_q
         const JobDesc& J = D->jobs[job_of_bucket(D, fb)];
+        const int shift = J.key_bits - J.sort_bits;  // the bucket's keys share the bits above shift (<= 58)
         const uint64_t lo = D->starts[fb] - D->starts[J.bucket_base];
-        const int n = (int)n64;
-        if (n <= 32) warp_sort_bucket<1>(J.res_keys, J.res_vals, lo, n, lane);
-        else if (n <= 64) warp_sort_bucket<2>(J.res_keys, J.res_vals, lo, n, lane);
-        else if (n <= 128) warp_sort_bucket<4>(J.res_keys, J.res_vals, lo, n, lane);
-        else warp_sort_bucket<8>(J.res_keys, J.res_vals, lo, n, lane);
+        if (n64 <= 32) warp_sort32_packed(J.res_keys, J.res_vals, lo, (int)n64, lane, shift);
+        else warp_sort64_packed(J.res_keys, J.res_vals, lo, (int)n64, lane, shift);
+    }
+}
+
+// Buckets of 65..256 keys in registers of one warp, and every bucket of a
+// batch whose bucket bits leave too many key bits to pack; larger ones are
+// flagged for the shared-memory sort.
+// The lanes of a warp look at 32 buckets at once; the warp then sorts the
+// ones it has to, one after the other.
+__global__ void __launch_bounds__(256, 2) k_warp_sort_big_q(const BatchDesc* __restrict__ D) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t nb = D->n_buckets;
+    const bool all_pack = D->all_packable != 0;
+    for (uint64_t base = warp * 32; base < nb; base += n_warps * 32) {
+        const uint64_t fb = base + (uint64_t)lane;
+        const uint64_t m64 = fb < nb ? D->starts[fb + 1] - D->starts[fb] : 0ull;
+        unsigned todo = __ballot_sync(kFull, m64 > 64 || (m64 > 1 && !all_pack));
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint64_t b = base + (uint64_t)src;
+            const uint64_t n64 = __shfl_sync(kFull, m64, src);
+            if (n64 > 256) {
+                if (lane == 0) atomicOr(D->err, DERR_SORT_MEDIUM);
+                continue;
+            }
+            const JobDesc& J = D->jobs[job_of_bucket(D, b)];
+            const uint64_t lo = D->starts[b] - D->starts[J.bucket_base];
+            const int n = (int)n64;
+            if (n <= 32) warp_sort_bucket<1>(J.res_keys, J.res_vals, lo, n, lane);
+            else if (n <= 64) warp_sort_bucket<2>(J.res_keys, J.res_vals, lo, n, lane);
+            else if (n <= 128) warp_sort_bucket<4>(J.res_keys, J.res_vals, lo, n, lane);
+            else warp_sort_bucket<8>(J.res_keys, J.res_vals, lo, n, lane);
+        }
     }
 }
 
@@ -484,6 +627,13 @@ struct kc_batch_ctx {
     unsigned long long* d_tiles = nullptr;
     uint64_t buckets_cap = 0, tiles_cap = 0;
     cudaGraphExec_t sort_graph = nullptr;
+    // captured consumer launches, one per launch shape
+    struct ConsumeGraph {
+        int nh, n_ctas;
+        size_t smem;
+        cudaGraphExec_t exec;
+    };
+    std::vector<ConsumeGraph> consume_graphs;
     std::vector<kc::JobDesc> jobs;
     std::vector<uint32_t> item_job;
     uint64_t launches = 0;
@@ -554,14 +704,16 @@ kc_status capture_sort_graph(kc_batch_ctx* b) {
     std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     cudaGraph_t g = nullptr;
     KC_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-    const dim3 grid2((unsigned)b->sm_count * 4, 32);
-    cudaMemsetAsync(b->d_hist, 0, b->buckets_cap * 4, b->st);
+    const unsigned grid2 = (unsigned)b->sm_count * 16;  // latency-bound atomics: many threads in flight
+    kc::k_plan_q<<<1, 32, 0, b->st>>>(b->d_desc);
+    kc::k_zero_hist_q<<<(unsigned)b->sm_count * 4, 256, 0, b->st>>>(b->d_desc);
     kc::k_prefix_hist_q<<<grid2, 256, 0, b->st>>>(b->d_desc);
     kc::k_scan_tiles_q<<<(unsigned)b->tiles_cap, 1024, 0, b->st>>>(b->d_desc);
     kc::k_scan_top_q<<<1, 1024, 0, b->st>>>(b->d_desc);
     kc::k_scan_apply_q<<<(unsigned)b->tiles_cap, 1024, 0, b->st>>>(b->d_desc);
     kc::k_scatter_q<<<grid2, 256, 0, b->st>>>(b->d_desc);
-    kc::k_warp_sort_q<<<(unsigned)b->sm_count * 8, 256, 0, b->st>>>(b->d_desc);
+    kc::k_warp_sort_q<<<(unsigned)b->sm_count * 16, 256, 0, b->st>>>(b->d_desc);
+    kc::k_warp_sort_big_q<<<(unsigned)b->sm_count * 2, 256, 0, b->st>>>(b->d_desc);
     cudaError_t e = cudaStreamEndCapture(b->st, &g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(sort)");
     e = cudaGraphInstantiate(&b->sort_graph, g, 0);
@@ -572,6 +724,7 @@ kc_status capture_sort_graph(kc_batch_ctx* b) {
 
 kc_status upload_desc(kc_batch_ctx* b, uint32_t n_jobs, uint32_t n_items, uint64_t n_buckets) {
     kc::BatchDesc d{};
+    d.buckets_cap = b->buckets_cap;
     d.jobs = b->d_jobs;
     d.item_job = b->d_item_job;
     d.counters = b->d_counters;
@@ -613,28 +766,63 @@ void release_work(kc_batch_ctx* b, std::vector<JobWork>& w) {
     }
 }
 
+// prepare: set the kernel's shared-memory limit (before any capture);
+// otherwise launch it.
 template <int NH>
-cudaError_t launch_consume_nh(int n_ctas, size_t smem, const kc::BatchDesc* d, cudaStream_t st) {
-    cudaError_t e = kc::allow_max_dynamic_smem(kc::k_consume_q<NH>);
-    if (e != cudaSuccess) return e;
+cudaError_t launch_consume_nh(bool prepare, int n_ctas, size_t smem, const kc::BatchDesc* d, cudaStream_t st) {
+    if (prepare) return kc::allow_max_dynamic_smem(kc::k_consume_q<NH>);
     kc::k_consume_q<NH><<<n_ctas, kc::kConsumeThreads, smem, st>>>(d);
     return cudaGetLastError();
 }
 
-cudaError_t launch_consume(int nh, int n_ctas, size_t smem, const kc::BatchDesc* d, cudaStream_t st) {
+cudaError_t launch_consume(bool prepare, int nh, int n_ctas, size_t smem, const kc::BatchDesc* d, cudaStream_t st) {
     switch (nh) {
-        case 1: return launch_consume_nh<1>(n_ctas, smem, d, st);
-        case 2: return launch_consume_nh<2>(n_ctas, smem, d, st);
-        case 3: return launch_consume_nh<3>(n_ctas, smem, d, st);
-        case 4: return launch_consume_nh<4>(n_ctas, smem, d, st);
-        case 5: return launch_consume_nh<5>(n_ctas, smem, d, st);
-        case 6: return launch_consume_nh<6>(n_ctas, smem, d, st);
-        case 7: return launch_consume_nh<7>(n_ctas, smem, d, st);
-        case 8: return launch_consume_nh<8>(n_ctas, smem, d, st);
-        case 9: return launch_consume_nh<9>(n_ctas, smem, d, st);
-        case 10: return launch_consume_nh<10>(n_ctas, smem, d, st);
-        default: return launch_consume_nh<0>(n_ctas, smem, d, st);
+        case 1: return launch_consume_nh<1>(prepare, n_ctas, smem, d, st);
+        case 2: return launch_consume_nh<2>(prepare, n_ctas, smem, d, st);
+        case 3: return launch_consume_nh<3>(prepare, n_ctas, smem, d, st);
+        case 4: return launch_consume_nh<4>(prepare, n_ctas, smem, d, st);
+        case 5: return launch_consume_nh<5>(prepare, n_ctas, smem, d, st);
+        case 6: return launch_consume_nh<6>(prepare, n_ctas, smem, d, st);
+        case 7: return launch_consume_nh<7>(prepare, n_ctas, smem, d, st);
+        case 8: return launch_consume_nh<8>(prepare, n_ctas, smem, d, st);
+        case 9: return launch_consume_nh<9>(prepare, n_ctas, smem, d, st);
+        case 10: return launch_consume_nh<10>(prepare, n_ctas, smem, d, st);
+        default: return launch_consume_nh<0>(prepare, n_ctas, smem, d, st);
     }
+}
+
+// The batch's counters reset and its persistent consumer launch, captured
+// once per launch shape (hash count, grid, shared memory); everything else
+// they read comes from the device descriptor.
+kc_status consume_graph(kc_batch_ctx* b, int nh, int n_ctas, size_t smem, cudaGraphExec_t* out) {
+    for (const auto& g : b->consume_graphs)
+        if (g.nh == nh && g.n_ctas == n_ctas && g.smem == smem) {
+            *out = g.exec;
+            return KC_OK;
+        }
+    KC_CUDA(launch_consume(true, nh, n_ctas, smem, b->d_desc, b->st));
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
+    cudaGraph_t g = nullptr;
+    KC_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    kc::k_reset_q<<<1, 256, 0, b->st>>>(b->d_desc);
+    launch_consume(false, nh, n_ctas, smem, b->d_desc, b->st);
+    cudaError_t e = cudaStreamEndCapture(b->st, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(consumer)");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(consumer)");
+    b->consume_graphs.push_back({nh, n_ctas, smem, exec});
+    *out = exec;
+    return KC_OK;
+}
+
+// Bucket bits of a sort of at most n survivors (about 32 a bucket).
+int sort_bits_for(uint64_t n, int key_bits) {
+    int bits = 0;
+    n = std::max<uint64_t>(1, n);
+    while (bits < 24 && bits < key_bits && (n >> bits) > 32) ++bits;
+    return bits;
 }
 
 // Partitions whose shared-memory table overflowed: rebuild their filter
@@ -753,6 +941,7 @@ void kc_batch_destroy_internal(kc_batch_ctx* b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
     if (b->sort_graph) cudaGraphExecDestroy(b->sort_graph);
+    for (auto& g : b->consume_graphs) cudaGraphExecDestroy(g.exec);
     std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
     cudaFree(b->d_desc);
     cudaFree(b->d_flags);
@@ -903,33 +1092,36 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         return s;
     }
     KC_CUDA(cudaMemcpyAsync(b->d_item_job, b->item_job.data(), n_items * 4, cudaMemcpyHostToDevice, st));
-    KC_CUDA(cudaMemsetAsync(b->d_counters, 0, 2 * (size_t)n * 8, st));
-    KC_CUDA(cudaMemsetAsync(b->d_flags, 0, 2 * sizeof(unsigned int), st));
     if ((s = upload_desc(b, (uint32_t)n, n_items, 0)) != KC_OK) {
+        release_work(b, work);
+        return s;
+    }
+    int nh = hs[0]->n_hashes;
+    for (int j = 1; j < n; ++j)
+        if (hs[j]->n_hashes != nh) nh = 0;
+    const int per_sm = std::max(1, std::min(4, b->max_sm / (int)(smem_max + 2048)));
+    const int n_ctas = std::max(1, (int)std::min<uint64_t>(n_items, (uint64_t)b->sm_count * per_sm));
+    cudaGraphExec_t cons = nullptr;
+    if ((s = consume_graph(b, nh, n_ctas, smem_max, &cons)) != KC_OK) {
         release_work(b, work);
         return s;
     }
 
     // consume: one persistent launch over the (job, partition) queue
     cudaEvent_t t0 = timed ? phase_begin(hs[0], st) : nullptr;
-    int nh = hs[0]->n_hashes;
-    for (int j = 1; j < n; ++j)
-        if (hs[j]->n_hashes != nh) nh = 0;
-    const int per_sm = std::max(1, std::min(4, b->max_sm / (int)(smem_max + 2048)));
-    const int n_ctas = std::max(1, (int)std::min<uint64_t>(n_items, (uint64_t)b->sm_count * per_sm));
-    if (launch_consume(nh, n_ctas, smem_max, b->d_desc, st) != cudaSuccess) {
-        cudaGetLastError();
-        release_work(b, work);
-        return fail(KC_ERR_CUDA, "consumer launch");
-    }
+    KC_CUDA(cudaGraphLaunch(cons, st));
     if (timed) phase_end(hs[0], kPass2, t0, st);
-    KC_LAUNCHED("consumer launch");
     std::vector<unsigned long long> cnt(2 * (size_t)n);
     KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
     KC_CUDA(cudaStreamSynchronize(st));
-    for (int j = 0; j < n; ++j) {
-        work[j].h->launches += 1;
-        if (cnt[2 * j + 1]) {
+    for (int j = 0; j < n; ++j) work[j].h->launches += 2;
+
+    // partitions whose table overflowed (rare): counted in global tables
+    bool any_fb = false;
+    for (int j = 0; j < n; ++j) any_fb |= cnt[2 * j + 1] != 0;
+    if (any_fb) {
+        for (int j = 0; j < n; ++j) {
+            if (!cnt[2 * j + 1]) continue;
             t0 = timed ? phase_begin(hs[0], st) : nullptr;
             s = run_fallbacks(b, work[j], (uint32_t)j, (uint32_t)cnt[2 * j + 1]);
             if (timed) phase_end(hs[0], kCompact, t0, st);
@@ -937,73 +1129,67 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
                 release_work(b, work);
                 return s;
             }
-            b->jobs[j].sv_keys = work[j].sv_keys;
-            b->jobs[j].sv_vals = work[j].sv_vals;
-            b->jobs[j].sv_cap = work[j].sv_cap;
+            kc::JobDesc& J = b->jobs[j];
+            J.sv_keys = work[j].sv_keys;
+            J.sv_vals = work[j].sv_vals;
+            J.sv_cap = work[j].sv_cap;
         }
-    }
-    if (n > 0) {
-        bool any_fb = false;
-        for (int j = 0; j < n; ++j) any_fb |= cnt[2 * j + 1] != 0;
-        if (any_fb) {
-            KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
-            for (int j = 0; j < n; ++j) KC_CUDA(cudaMemcpyAsync(&hc[j], hs[j]->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
-            KC_CUDA(cudaStreamSynchronize(st));
-            for (int j = 0; j < n; ++j) {
-                hs[j]->host_ctr = hc[j];
-                if ((s = device_errors(hs[j])) != KC_OK) {
-                    release_work(b, work);
-                    return s;
-                }
+        KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+        for (int j = 0; j < n; ++j) KC_CUDA(cudaMemcpyAsync(&hc[j], hs[j]->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        for (int j = 0; j < n; ++j) {
+            hs[j]->host_ctr = hc[j];
+            if ((s = device_errors(hs[j])) != KC_OK) {
+                release_work(b, work);
+                return s;
             }
         }
     }
 
-    // sort: per job, bucket bits for at most about 32 survivors a bucket
-    uint64_t n_buckets = 0;
+    // sort: result arrays of each job's survivor count (a job's arrays are
+    // kept for its next job when large enough), bucket arrays for as many
+    // buckets as the plan will give; the plan itself runs on the device
+    uint64_t bucket_need = 0;
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
         kc::JobDesc& J = b->jobs[j];
-        const uint64_t nsv = std::min<uint64_t>(cnt[2 * j], work[j].sv_cap);
-        int bits = 0;
-        while (bits < 24 && bits < 2 * h->k && (std::max<uint64_t>(1, nsv) >> bits) > 32) ++bits;
-        J.sort_bits = bits;
-        J.bucket_base = n_buckets;
-        J.n_buckets = 1ull << bits;
-        n_buckets += J.n_buckets;
-        free_result(h);
+        const uint64_t nsv = std::min<uint64_t>(cnt[2 * j], J.sv_cap);
+        bucket_need += 1ull << sort_bits_for(nsv, J.key_bits);
         const uint64_t cap = std::max<uint64_t>(1, nsv);
-        cudaError_t e;
-        if ((e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
-            (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess) {
+        if (!h->res_keys || h->res_cap < cap) {
             free_result(h);
-            release_work(b, work);
-            return cuda_fail(e, "cudaMallocAsync(result)");
+            cudaError_t e;
+            if ((e = cudaMallocAsync(&h->res_keys, cap * 8, st)) != cudaSuccess ||
+                (e = cudaMallocAsync(&h->res_vals, cap * 8, st)) != cudaSuccess) {
+                free_result(h);
+                release_work(b, work);
+                return cuda_fail(e, "cudaMallocAsync(result)");
+            }
+            h->res_cap = cap;
         }
-        h->res_cap = cap;
         h->n_result = nsv;
         J.res_keys = h->res_keys;
         J.res_vals = h->res_vals;
-        J.res_cap = cap;
+        J.res_cap = h->res_cap;
     }
-    if ((s = ensure_buckets(b, n_buckets)) != KC_OK || (s = upload_desc(b, (uint32_t)n, n_items, n_buckets)) != KC_OK) {
-        release_work(b, work);
-        return s;
-    }
-    if (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK) {
+    if ((s = ensure_buckets(b, bucket_need)) != KC_OK || (s = upload_desc(b, (uint32_t)n, n_items, 0)) != KC_OK ||
+        (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK)) {
         release_work(b, work);
         return s;
     }
     t0 = timed ? phase_begin(hs[0], st) : nullptr;
     KC_CUDA(cudaGraphLaunch(b->sort_graph, st));
+    if (timed) phase_end(hs[0], kSort, t0, st);
     unsigned err = 0;
     KC_CUDA(cudaMemcpyAsync(&err, b->d_flags + 1, 4, cudaMemcpyDeviceToHost, st));
     KC_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < n; ++j) work[j].h->launches += 9;
     if (err & kc::DERR_INTERNAL) {
         release_work(b, work);
         for (int j = 0; j < n; ++j) hs[j]->state = State::Poisoned;
         return fail(KC_ERR_INTERNAL, "sort: key outside its bucket range");
     }
+    t0 = timed && (err & (kc::DERR_SORT_MEDIUM | kc::DERR_SORT_BUCKET)) ? phase_begin(hs[0], st) : nullptr;
     if (err & kc::DERR_SORT_MEDIUM) {
         kc::k_medium_sort_q<<<(unsigned)b->sm_count * 4, 256, 0, st>>>(b->d_desc);
         KC_LAUNCHED("batched medium sort launch");
@@ -1012,11 +1198,17 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         for (int j = 0; j < n; ++j) hs[j]->launches += 1;
     }
     if (err & kc::DERR_SORT_BUCKET) {  // rare: buckets above 2048 keys, sorted in global memory
-        std::vector<uint64_t> starts(n_buckets + 1);
-        KC_CUDA(cudaMemcpyAsync(starts.data(), b->d_starts, (n_buckets + 1) * 8, cudaMemcpyDeviceToHost, st));
+        // the plan is on the device: read back the jobs' bucket ranges and the starts
+        std::vector<kc::JobDesc> jd((size_t)n);
+        uint64_t nbk = 0;
+        KC_CUDA(cudaMemcpyAsync(jd.data(), b->d_jobs, n * sizeof(kc::JobDesc), cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaStreamSynchronize(st));
+        for (const auto& J : jd) nbk = std::max<uint64_t>(nbk, J.bucket_base + J.n_buckets);
+        std::vector<uint64_t> starts(nbk + 1);
+        KC_CUDA(cudaMemcpyAsync(starts.data(), b->d_starts, (nbk + 1) * 8, cudaMemcpyDeviceToHost, st));
         KC_CUDA(cudaStreamSynchronize(st));
         for (int j = 0; j < n; ++j) {
-            const kc::JobDesc& J = b->jobs[j];
+            const kc::JobDesc& J = jd[j];
             const uint64_t job0 = starts[J.bucket_base];
             for (uint64_t q = 0; q < J.n_buckets; ++q) {
                 const uint64_t lo = starts[J.bucket_base + q], m = starts[J.bucket_base + q + 1] - lo;
@@ -1028,12 +1220,11 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         }
         KC_LAUNCHED("batched global sort launches");
     }
-    if (timed) phase_end(hs[0], kSort, t0, st);
+    if (t0) phase_end(hs[0], kSort, t0, st);
     release_work(b, work);
     KC_CUDA(cudaStreamSynchronize(st));
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
-        h->launches += 6;
         h->host_ctr.survivors = h->n_result;
         if (!one) {  // the handle's later work is ordered after the batch
             KC_CUDA(cudaEventRecord(h->ev_copy, st));
@@ -1042,7 +1233,7 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         phase_collect(h);
         if (last) h->state = State::Finalized;
     }
-    b->launches += 7;
+    b->launches += 11;
     return KC_OK;
 }
 

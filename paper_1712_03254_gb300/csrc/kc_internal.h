@@ -56,7 +56,7 @@ void launch_scatter(const uint64_t* keys, const uint64_t* vals, DevCounters* ctr
                     cudaStream_t st);
 // Sort every bucket of at most warp_sort_capacity() keys in place, one warp
 // per bucket; larger buckets set DERR_SORT_MEDIUM and are left alone.
-void launch_bucket_sort_warp(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets,
+void launch_bucket_sort_warp(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets, int shift,
                              DevCounters* ctr, const Grid& g, cudaStream_t st);
 int warp_sort_capacity();
 // Sort buckets of warp_sort_capacity()+1 .. bucket_sort_capacity() keys in

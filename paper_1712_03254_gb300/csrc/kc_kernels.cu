@@ -402,9 +402,11 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(uint64_t* __restri
     }
 }
 
+// shift: the keys of a bucket share their bits above `shift` (buckets are
+// key-prefix ranges); buckets of up to 32 keys then sort packed.
 __global__ void __launch_bounds__(256, 2) k_bucket_sort_warp(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
                                                           const uint64_t* __restrict__ starts, uint64_t n_buckets,
-                                                          DevCounters* __restrict__ ctr) {
+                                                          int shift, DevCounters* __restrict__ ctr) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -417,7 +419,9 @@ __global__ void __launch_bounds__(256, 2) k_bucket_sort_warp(uint64_t* __restric
             continue;
         }
         const int n = (int)n64;
-        if (n <= 32) warp_sort_bucket<1>(keys, vals, lo, n, lane);
+        if (n <= 32 && shift <= 59) warp_sort32_packed(keys, vals, lo, n, lane, shift);
+        else if (n <= 64 && shift <= 58) warp_sort64_packed(keys, vals, lo, n, lane, shift);
+        else if (n <= 32) warp_sort_bucket<1>(keys, vals, lo, n, lane);
         else if (n <= 64) warp_sort_bucket<2>(keys, vals, lo, n, lane);
         else if (n <= 128) warp_sort_bucket<4>(keys, vals, lo, n, lane);
         else warp_sort_bucket<8>(keys, vals, lo, n, lane);
@@ -518,14 +522,14 @@ void launch_scatter(const uint64_t* keys, const uint64_t* vals, DevCounters* ctr
 
 int bucket_sort_capacity() { return kSortCap; }
 
-void launch_bucket_sort_warp(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets,
+void launch_bucket_sort_warp(uint64_t* keys, uint64_t* vals, const uint64_t* starts, uint64_t n_buckets, int shift,
                              DevCounters* ctr, const Grid& g, cudaStream_t st) {
     const uint64_t warps = n_buckets;
     unsigned grid = (unsigned)((warps + 7) / 8);
     const unsigned cap = (unsigned)g.sm_count * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    k_bucket_sort_warp<<<grid, 256, 0, st>>>(keys, vals, starts, n_buckets, ctr);
+    k_bucket_sort_warp<<<grid, 256, 0, st>>>(keys, vals, starts, n_buckets, shift, ctr);
 }
 
 int warp_sort_capacity() { return kWarpSortMax; }
