@@ -795,7 +795,12 @@ kc_status kc_reset(kc_handle h) {
         cudaStreamSynchronize(h->copy_stream);
         release_spill(h);
     }
-    KC_CUDA(cudaMemsetAsync(h->bloom, 0, h->bloom_bits / 8, h->stream));
+    // The partition consumer writes back every word of every partition's
+    // filter slice (fallback partitions clear theirs first), so a partitioned
+    // handle that owns every key needs no cleared filter; an owner of a hash
+    // range keeps the other slices at zero.
+    if (h->strategy != KC_STRATEGY_PARTITIONED || h->owner)
+        KC_CUDA(cudaMemsetAsync(h->bloom, 0, h->bloom_bits / 8, h->stream));
     if (h->bloom2) KC_CUDA(cudaMemsetAsync(h->bloom2, 0, h->bloom_bits / 8, h->stream));
     if (h->table) KC_CUDA(cudaMemsetAsync(h->table, 0, h->n_slots * sizeof(kc::Slot), h->stream));
     KC_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(kc::DevCounters), h->stream));
@@ -1013,6 +1018,9 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
     if (counts) {
         if (h->n_samples == 2) {
             KC_CUDA(cudaMemcpyAsync(counts, h->res_vals, h->n_result * 8, cudaMemcpyDefault, st));
+        } else if (is_device_ptr(counts)) {  // narrowed straight into the caller's device buffer
+            kc::launch_counts_narrow(h->res_vals, h->n_result, counts, st);
+            h->launches += 1;
         } else {
             uint32_t* narrow = nullptr;
             KC_CUDA(cudaMallocAsync(&narrow, h->n_result * 4, st));
