@@ -965,7 +965,9 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
                         "plain_k_mers_per_s": round(windows * plain_cap / len(jobs), 1),
                         "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 2),
                         "stage_ms": {x: round(st["mean_" + x + "_ms"], 3)
-                                     for x in ("queue", "ingest", "batch_wait", "finalize")}}
+                                     for x in ("queue", "ingest", "batch_wait", "finalize")},
+                        "per_batch_ms": {x: round(st["mean_batch_" + x + "_ms"], 3)
+                                         for x in ("finalize", "copy", "release")}}
     return out
 
 

@@ -280,6 +280,10 @@ typedef struct kc_server_stats {
      * reads on the device, -> its batch starts, batch start -> result in host
      * memory */
     double mean_queue_ms, mean_ingest_ms, mean_batch_wait_ms, mean_finalize_ms;
+    /* where a finalize thread's time goes, mean per batch: the batched
+     * finalize call, then copying the batch's results to host memory, then
+     * releasing its jobs' handles */
+    double mean_batch_finalize_ms, mean_batch_copy_ms, mean_batch_release_ms;
 } kc_server_stats;
 
 /* Create a server on the current device (max_batch >= 1). */

@@ -107,7 +107,9 @@ class ServerStats(ctypes.Structure):
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("jobs_per_s", ctypes.c_double),
                 ("peak_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
                 ("mean_queue_ms", ctypes.c_double), ("mean_ingest_ms", ctypes.c_double),
-                ("mean_batch_wait_ms", ctypes.c_double), ("mean_finalize_ms", ctypes.c_double)]
+                ("mean_batch_wait_ms", ctypes.c_double), ("mean_finalize_ms", ctypes.c_double),
+                ("mean_batch_finalize_ms", ctypes.c_double), ("mean_batch_copy_ms", ctypes.c_double),
+                ("mean_batch_release_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

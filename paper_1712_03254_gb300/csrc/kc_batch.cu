@@ -1100,7 +1100,9 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     for (int j = 1; j < n; ++j)
         if (hs[j]->n_hashes != nh) nh = 0;
     const int per_sm = std::max(1, std::min(4, b->max_sm / (int)(smem_max + 2048)));
-    const int n_ctas = std::max(1, (int)std::min<uint64_t>(n_items, (uint64_t)b->sm_count * per_sm));
+    // a persistent grid (CTAs without an item exit at once), so the captured
+    // launch depends on the hash count and shared memory alone
+    const int n_ctas = b->sm_count * per_sm;
     cudaGraphExec_t cons = nullptr;
     if ((s = consume_graph(b, nh, n_ctas, smem_max, &cons)) != KC_OK) {
         release_work(b, work);

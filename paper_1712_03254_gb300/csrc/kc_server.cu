@@ -30,7 +30,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/kc.h"
-#include "kc_internal.h"
+#include "kc_ctx.h"
 
 namespace {
 
@@ -138,11 +138,27 @@ struct kc_server_ctx {
     std::vector<std::thread> t_ingest, t_final;
     std::vector<kc_batch> batch;
     int device = 0;
+    // Handles of finished jobs, reset and kept for the next job with the same
+    // parameters (oldest first): creating and destroying a handle per job
+    // costs a stream, events and the filter's allocation.  Their device bytes
+    // count against the budget and the oldest are destroyed to make room.
+    struct IdleHandle {
+        kc_handle h;
+        int k, n_samples, n_hashes;
+        uint32_t min_count;
+        uint64_t bloom_bits;
+        kc_config cfg;
+        uint64_t bytes;
+    };
+    std::deque<IdleHandle> idle;
+    uint64_t idle_bytes = 0;
+    static constexpr size_t kMaxIdle = 32;
     PinnedPool& pool = result_pool();
     // statistics
     std::vector<double> latencies_ms;
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_jobs = 0;
     double sum_stage_ms[4] = {};  // queue, ingest, batch wait, finalize + copy-out of completed jobs
+    double sum_fin_ms[3] = {};    // per batch: batched finalize, copies to host memory, handle release
     Clock::time_point t_first, t_last;
     bool any = false;
 };
@@ -177,10 +193,24 @@ void fail_job(kc_server_ctx* S, const std::shared_ptr<Job>& j, kc_status st) {
     S->failed += 1;
 }
 
+// Destroy idle handles, oldest first, while the admitted jobs and the idle
+// handles together pass the budget (call with S->mu held; the handles are
+// destroyed by the caller, outside the lock).
+void evict_idle(kc_server_ctx* S, std::vector<kc_handle>& out) {
+    while (!S->idle.empty() && S->in_use + S->idle_bytes > S->budget) {
+        out.push_back(S->idle.front().h);
+        S->idle_bytes -= S->idle.front().bytes;
+        S->idle.pop_front();
+    }
+}
+
+bool same_config(const kc_config& a, const kc_config& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+
 void ingest_loop(kc_server_ctx* S) {
     cudaSetDevice(S->device);
     for (;;) {
         std::shared_ptr<Job> j;
+        std::vector<kc_handle> evicted;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_ingest.wait(lk, [&] {
@@ -192,7 +222,9 @@ void ingest_loop(kc_server_ctx* S) {
             S->pending.pop_front();
             S->in_use += j->footprint;  // admitted
             S->peak = std::max(S->peak, S->in_use);
+            evict_idle(S, evicted);
         }
+        for (kc_handle e : evicted) kc_destroy(e);
         j->t_admit = Clock::now();
         const kc_job_spec& s = j->spec;
         kc_config cfg;
@@ -208,7 +240,19 @@ void ingest_loop(kc_server_ctx* S) {
                 cfg = tuned;  // batched finalize needs the partitioned strategy
         }
         cfg.strategy = KC_STRATEGY_PARTITIONED;
-        kc_status st = kc_create_ex(s.k, s.n_samples, s.bloom_bits, s.n_hashes, s.min_count, &cfg, nullptr, &j->h);
+        {  // a finished job's handle with the same parameters, already reset
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (auto it = S->idle.begin(); it != S->idle.end(); ++it)
+                if (it->k == s.k && it->n_samples == s.n_samples && it->n_hashes == s.n_hashes &&
+                    it->min_count == s.min_count && it->bloom_bits == s.bloom_bits && same_config(it->cfg, cfg)) {
+                    j->h = it->h;
+                    S->idle_bytes -= it->bytes;
+                    S->idle.erase(it);
+                    break;
+                }
+        }
+        kc_status st = j->h ? KC_OK
+                            : kc_create_ex(s.k, s.n_samples, s.bloom_bits, s.n_hashes, s.min_count, &cfg, nullptr, &j->h);
         for (int i = 0; st == KC_OK && i < s.n_samples; ++i)
             st = kc_add_reads(j->h, i, s.packed[i], s.offsets[i], s.n_mask[i], s.n_reads[i]);
         std::lock_guard<std::mutex> lk(S->mu);
@@ -244,9 +288,12 @@ void finalize_loop(kc_server_ctx* S, int idx) {
             j->t_fstart = t_start;
         }
         kc_status st = kc_batch_finalize(S->batch[idx], hs.data(), (int)hs.size());
+        const Clock::time_point t_fin = Clock::now();
+        double copy_ms = 0.0, release_ms = 0.0;
         for (auto& j : run) {
             kc_status js = st;
             uint64_t n = 0;
+            const Clock::time_point t_c0 = Clock::now();
             if (js == KC_OK) js = kc_dump(j->h, nullptr, nullptr, 0, &n);
             if (js == KC_OK) {
                 j->keys = static_cast<uint64_t*>(S->pool.get(std::max<uint64_t>(1, n) * 8, &j->keys_class));
@@ -256,12 +303,33 @@ void finalize_loop(kc_server_ctx* S, int idx) {
                 else if (n) js = kc_dump(j->h, j->keys, j->counts, n, &n);
                 j->n_keys = n;
             }
+            const Clock::time_point t_c1 = Clock::now();
+            copy_ms += ms_between(t_c0, t_c1);
+            kc_handle park = nullptr;
             if (js == KC_OK) {
-                kc_destroy(j->h);  // outside the lock: it waits for the job's stream
+                // reset (its grouped hashes and batches freed) and kept for a
+                // later job with the same parameters, or destroyed
+                if (kc_reset(j->h) == KC_OK) park = j->h;
+                else kc_destroy(j->h);
                 j->h = nullptr;
             } else {
                 free_result(S->pool, *j);
             }
+            std::vector<kc_handle> evicted;
+            if (park) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                if (S->idle.size() >= kc_server_ctx::kMaxIdle) {
+                    evicted.push_back(S->idle.front().h);
+                    S->idle_bytes -= S->idle.front().bytes;
+                    S->idle.pop_front();
+                }
+                kc_server_ctx::IdleHandle ih{park, j->spec.k, j->spec.n_samples, j->spec.n_hashes, j->spec.min_count,
+                                             j->spec.bloom_bits, park->cfg, kcapi::held_bytes(park)};
+                S->idle.push_back(ih);
+                S->idle_bytes += ih.bytes;
+            }
+            for (kc_handle e : evicted) kc_destroy(e);
+            release_ms += ms_between(t_c1, Clock::now());
             std::lock_guard<std::mutex> lk(S->mu);
             if (js != KC_OK) {
                 fail_job(S, j, js);
@@ -282,6 +350,9 @@ void finalize_loop(kc_server_ctx* S, int idx) {
             std::lock_guard<std::mutex> lk(S->mu);
             S->batches += 1;
             S->batched_jobs += run.size();
+            S->sum_fin_ms[0] += ms_between(t_start, t_fin);
+            S->sum_fin_ms[1] += copy_ms;
+            S->sum_fin_ms[2] += release_ms;
         }
         S->cv_done.notify_all();
         S->cv_ingest.notify_all();
@@ -431,6 +502,10 @@ kc_status kc_server_stats_get(kc_server S, kc_server_stats* out) {
     out->mean_ingest_ms = S->sum_stage_ms[1] / nc;
     out->mean_batch_wait_ms = S->sum_stage_ms[2] / nc;
     out->mean_finalize_ms = S->sum_stage_ms[3] / nc;
+    const double nbat = S->batches ? (double)S->batches : 1.0;
+    out->mean_batch_finalize_ms = S->sum_fin_ms[0] / nbat;
+    out->mean_batch_copy_ms = S->sum_fin_ms[1] / nbat;
+    out->mean_batch_release_ms = S->sum_fin_ms[2] / nbat;
     return KC_OK;
 }
 
@@ -446,6 +521,7 @@ void kc_server_destroy(kc_server S) {
     for (auto& t : S->t_final) t.join();
     for (auto& d : S->ingested)
         if (d->h) kc_destroy(d->h);
+    for (auto& ih : S->idle) kc_destroy(ih.h);
     for (auto& kv : S->jobs) free_result(S->pool, *kv.second);  // results never collected
     for (kc_batch b : S->batch) kc_batch_destroy(b);
     delete S;
