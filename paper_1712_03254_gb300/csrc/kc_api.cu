@@ -805,6 +805,7 @@ kc_status kc_reset(kc_handle h) {
     if (h->table) KC_CUDA(cudaMemsetAsync(h->table, 0, h->n_slots * sizeof(kc::Slot), h->stream));
     KC_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(kc::DevCounters), h->stream));
     h->bases = 0;
+    h->reads = 0;
     std::memset(&h->host_ctr, 0, sizeof(h->host_ctr));
     for (const auto& m : h->marks) {
         h->ev_pool.push_back(m.a);
@@ -962,6 +963,7 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     }
     h->batches.push_back(b);
     h->bases += b1 - b0;
+    h->reads += n_reads;
     if (any_host) KC_CUDA(cudaEventSynchronize(h->ev_copy));  // caller may reuse its arrays
     return KC_OK;
 }

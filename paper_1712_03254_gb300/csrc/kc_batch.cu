@@ -836,6 +836,12 @@ kc_status run_fallbacks(kc_batch_ctx* b, JobWork& x, uint32_t j, uint32_t n_fail
     KC_CUDA(cudaMemcpyAsync(fl.data(), x.failed, n_failed * 8, cudaMemcpyDeviceToHost, b->st));
     unsigned long long n_sv = 0;
     KC_CUDA(cudaMemcpyAsync(&n_sv, b->d_counters + 2 * j, 8, cudaMemcpyDeviceToHost, b->st));
+    if (x.hs.empty()) {  // sized from the host's counts: the partition starts were not read yet
+        x.hs.resize(nb * (P + 1));
+        for (size_t t = 0; t < nb; ++t)
+            KC_CUDA(cudaMemcpyAsync(x.hs.data() + t * (P + 1), h->batches[t].hstarts, (P + 1) * 8,
+                                    cudaMemcpyDeviceToHost, b->st));
+    }
     KC_CUDA(cudaStreamSynchronize(b->st));
     auto windows_of = [&](uint32_t p) {
         uint64_t w = 0;
@@ -980,22 +986,34 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         }
         work[j].h = h;
     }
-    // partition sizes of every job, and each job's counters (ingest errors)
+    // Partition sizes of every job, and each job's counters (ingest errors):
+    // read back when the batch covers part of a job's partitions (spill
+    // groups, owned ranges, hash ranges of kept reads).  A job counted whole
+    // is sized from the host's counts instead (bases and reads added), so no
+    // host round trip sits between its grouping and its consumer; its ingest
+    // errors are read after the consumer.
     std::vector<kc::DevCounters> hc((size_t)n);
+    bool fast = true;
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
-        const uint64_t P = 1ull << h->part_bits;
-        work[j].hs.resize(h->batches.size() * (P + 1));
-        for (size_t t = 0; t < h->batches.size(); ++t)
-            KC_CUDA(cudaMemcpyAsync(work[j].hs.data() + t * (P + 1), h->batches[t].hstarts, (P + 1) * 8,
-                                    cudaMemcpyDeviceToHost, st));
-        KC_CUDA(cudaMemcpyAsync(&hc[j], h->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
+        fast = fast && part_lo == 0 && part_hi >= (1u << h->part_bits) && !h->owner && !h->deferred;
     }
-    KC_CUDA(cudaStreamSynchronize(st));
-    for (int j = 0; j < n; ++j) {
-        hs[j]->host_ctr = hc[j];
-        kc_status s = device_errors(hs[j]);
-        if (s != KC_OK) return s;
+    if (!fast) {
+        for (int j = 0; j < n; ++j) {
+            kc_handle h = hs[j];
+            const uint64_t P = 1ull << h->part_bits;
+            work[j].hs.resize(h->batches.size() * (P + 1));
+            for (size_t t = 0; t < h->batches.size(); ++t)
+                KC_CUDA(cudaMemcpyAsync(work[j].hs.data() + t * (P + 1), h->batches[t].hstarts, (P + 1) * 8,
+                                        cudaMemcpyDeviceToHost, st));
+            KC_CUDA(cudaMemcpyAsync(&hc[j], h->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
+        }
+        KC_CUDA(cudaStreamSynchronize(st));
+        for (int j = 0; j < n; ++j) {
+            hs[j]->host_ctr = hc[j];
+            kc_status s = device_errors(hs[j]);
+            if (s != KC_OK) return s;
+        }
     }
 
     // per-job consumer setup
@@ -1010,11 +1028,19 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         const uint64_t p_lo = std::max<uint64_t>(std::min<uint64_t>(part_lo, P), h->own_plo);
         const uint64_t p_hi = std::max<uint64_t>(p_lo, std::min<uint64_t>(std::min<uint64_t>(part_hi, P), h->own_phi));
         const size_t nb = h->batches.size();
-        for (uint64_t p = p_lo; p < p_hi; ++p) {
-            uint64_t w = 0;
-            for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
-            x.max_w = std::max(x.max_w, w);
-            x.total_w += w;
+        if (fast) {
+            // windows: at most one per base; about bases - reads (k - 1), spread
+            // evenly over the partitions by the hash
+            const uint64_t est = h->bases > h->reads * (uint64_t)(h->k - 1) ? h->bases - h->reads * (uint64_t)(h->k - 1) : 0;
+            x.total_w = h->bases;
+            x.max_w = est / P + est / P / 16 + 64;
+        } else {
+            for (uint64_t p = p_lo; p < p_hi; ++p) {
+                uint64_t w = 0;
+                for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
+                x.max_w = std::max(x.max_w, w);
+                x.total_w += w;
+            }
         }
         // Shared-memory table: one slot per 8 windows of the largest partition
         // (2^10..2^13 slots); partitions with more candidates split.
@@ -1035,10 +1061,14 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         const int split_max = h->cfg.split_max == KC_SPLIT_NONE ? 0
                               : std::min<int>(h->slice_log2, h->cfg.split_max ? (int)h->cfg.split_max : 6);
         x.sv_cap = 0;
-        for (uint64_t p = p_lo; p < p_hi; ++p) {
-            uint64_t w = 0;
-            for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
-            x.sv_cap += std::min<uint64_t>(1ull << (tl + split_max), w / std::max<uint32_t>(1, h->min_count));
+        if (fast) {  // every survivor has min_count windows, and no partition more than 2^split_max tables
+            x.sv_cap = std::min<uint64_t>((p_hi - p_lo) << (tl + split_max), x.total_w / std::max<uint32_t>(1, h->min_count));
+        } else {
+            for (uint64_t p = p_lo; p < p_hi; ++p) {
+                uint64_t w = 0;
+                for (size_t t = 0; t < nb; ++t) w += x.hs[t * (P + 1) + p + 1] - x.hs[t * (P + 1) + p];
+                x.sv_cap += std::min<uint64_t>(1ull << (tl + split_max), w / std::max<uint32_t>(1, h->min_count));
+            }
         }
         x.sv_cap = std::max<uint64_t>(1, x.sv_cap);
         const size_t meta_bytes = std::max<size_t>(16, nb * 20);
@@ -1115,8 +1145,20 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     if (timed) phase_end(hs[0], kPass2, t0, st);
     std::vector<unsigned long long> cnt(2 * (size_t)n);
     KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    if (fast)
+        for (int j = 0; j < n; ++j) KC_CUDA(cudaMemcpyAsync(&hc[j], hs[j]->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
     KC_CUDA(cudaStreamSynchronize(st));
     for (int j = 0; j < n; ++j) work[j].h->launches += 2;
+    if (fast) {
+        for (int j = 0; j < n; ++j) {
+            hs[j]->host_ctr = hc[j];
+            kc_status s = device_errors(hs[j]);
+            if (s != KC_OK) {
+                release_work(b, work);
+                return s;
+            }
+        }
+    }
 
     // partitions whose table overflowed (rare): counted in global tables
     bool any_fb = false;

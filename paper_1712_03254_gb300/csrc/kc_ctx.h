@@ -97,6 +97,7 @@ struct kc_ctx {
     kc::DevCounters* ctr = nullptr;
     std::vector<kcapi::Batch> batches;
     uint64_t bases = 0;
+    uint64_t reads = 0;  // reads added since create / reset
 
     uint64_t* res_keys = nullptr;
     uint64_t* res_vals = nullptr;
