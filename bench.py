@@ -948,19 +948,25 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
                                     for x in ("queue", "ingest", "batch_wait", "finalize")}},
             "results_equal_alone": same,
         })
-    # saturation: every job submitted at once (one untimed pass first, so the
-    # timed one runs with warm pinned result blocks and captured sort graphs)
+    # saturation: every job submitted at once, each result collected as it
+    # completes, as a client would (collecting returns its pinned block to the
+    # server's pool); one untimed pass first, so the timed one runs with warm
+    # pinned result blocks, captured graphs and recycled handles
     for timed in (False, True):
         srv = kc.KcServer(budget_bytes, max_batch=64)
         start = time.perf_counter()
         ids = [srv.submit(j["k"], j["bloom_bits"], j["n_hashes"], j["min_count"],
                           [(j["packed"], j["offsets"], j["mask"])]) for j in jobs]
-        for i in ids:
-            srv.wait(i, timeout_s=600)
+        sat_same = True
+        for i, jid in enumerate(ids):
+            srv.wait(jid, timeout_s=600)
+            keys, counts = srv.result(jid)
+            sat_same &= _digest(keys, counts) == ref[i]
         span = time.perf_counter() - start
         st = srv.stats()
         srv.close()
     out["saturated"] = {"served_jobs_per_s": round(len(jobs) / span, 2), "plain_jobs_per_s": round(plain_cap, 2),
+                        "results_equal_alone": bool(sat_same),
                         "served_k_mers_per_s": round(windows / span, 1),
                         "plain_k_mers_per_s": round(windows * plain_cap / len(jobs), 1),
                         "p99_ms": round(st["p99_ms"], 3), "mean_batch": round(st["mean_batch"], 2),
