@@ -948,23 +948,37 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
                                     for x in ("queue", "ingest", "batch_wait", "finalize")}},
             "results_equal_alone": same,
         })
-    # saturation: every job submitted at once, each result collected as it
-    # completes, as a client would (collecting returns its pinned block to the
-    # server's pool); one untimed pass first, so the timed one runs with warm
-    # pinned result blocks, captured graphs and recycled handles
+    # saturation: every job submitted at once, each result taken into the
+    # client's memory as soon as it completes by two collector threads (taking
+    # a result returns its pinned block to the server's pool); one untimed
+    # pass first, which also checks every result against the plain run, so
+    # the timed one runs with warm pinned result blocks, captured graphs and
+    # recycled handles
+    sat_same = True
     for timed in (False, True):
         srv = kc.KcServer(budget_bytes, max_batch=64)
         start = time.perf_counter()
         ids = [srv.submit(j["k"], j["bloom_bits"], j["n_hashes"], j["min_count"],
                           [(j["packed"], j["offsets"], j["mask"])]) for j in jobs]
-        sat_same = True
-        for i, jid in enumerate(ids):
-            srv.wait(jid, timeout_s=600)
-            keys, counts = srv.result(jid)
-            sat_same &= _digest(keys, counts) == ref[i]
+        digests = [None] * len(ids)
+
+        def collect(part):
+            for i in part:
+                srv.wait(ids[i], timeout_s=600)
+                keys, counts = srv.result(ids[i])
+                if not timed:
+                    digests[i] = _digest(keys, counts)
+
+        threads = [threading.Thread(target=collect, args=(range(c, len(ids), 2),)) for c in range(2)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
         span = time.perf_counter() - start
         st = srv.stats()
         srv.close()
+        if not timed:
+            sat_same = all(d == r for d, r in zip(digests, ref))
     out["saturated"] = {"served_jobs_per_s": round(len(jobs) / span, 2), "plain_jobs_per_s": round(plain_cap, 2),
                         "results_equal_alone": bool(sat_same),
                         "served_k_mers_per_s": round(windows / span, 1),

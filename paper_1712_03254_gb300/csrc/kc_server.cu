@@ -153,6 +153,17 @@ struct kc_server_ctx {
     std::deque<IdleHandle> idle;
     uint64_t idle_bytes = 0;
     static constexpr size_t kMaxIdle = 32;
+    // finished jobs' handles to reset and keep, and handles to destroy, both
+    // taken by a reaper thread so that neither ingest nor finalize waits for
+    // a handle's reset or teardown
+    struct Parked {
+        kc_handle h;
+        kc_job_spec spec;
+    };
+    std::vector<Parked> to_park;
+    std::vector<kc_handle> graveyard;
+    std::condition_variable cv_reap;
+    std::thread t_reap;
     PinnedPool& pool = result_pool();
     // statistics
     std::vector<double> latencies_ms;
@@ -223,8 +234,11 @@ void ingest_loop(kc_server_ctx* S) {
             S->in_use += j->footprint;  // admitted
             S->peak = std::max(S->peak, S->in_use);
             evict_idle(S, evicted);
+            if (!evicted.empty()) {
+                S->graveyard.insert(S->graveyard.end(), evicted.begin(), evicted.end());
+                S->cv_reap.notify_one();
+            }
         }
-        for (kc_handle e : evicted) kc_destroy(e);
         j->t_admit = Clock::now();
         const kc_job_spec& s = j->spec;
         kc_config cfg;
@@ -305,30 +319,16 @@ void finalize_loop(kc_server_ctx* S, int idx) {
             }
             const Clock::time_point t_c1 = Clock::now();
             copy_ms += ms_between(t_c0, t_c1);
-            kc_handle park = nullptr;
             if (js == KC_OK) {
-                // reset (its grouped hashes and batches freed) and kept for a
-                // later job with the same parameters, or destroyed
-                if (kc_reset(j->h) == KC_OK) park = j->h;
-                else kc_destroy(j->h);
+                // to the reaper: reset (its grouped hashes and batches freed)
+                // and kept for a later job with the same parameters
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->to_park.push_back({j->h, j->spec});
+                S->cv_reap.notify_one();
                 j->h = nullptr;
             } else {
                 free_result(S->pool, *j);
             }
-            std::vector<kc_handle> evicted;
-            if (park) {
-                std::lock_guard<std::mutex> lk(S->mu);
-                if (S->idle.size() >= kc_server_ctx::kMaxIdle) {
-                    evicted.push_back(S->idle.front().h);
-                    S->idle_bytes -= S->idle.front().bytes;
-                    S->idle.pop_front();
-                }
-                kc_server_ctx::IdleHandle ih{park, j->spec.k, j->spec.n_samples, j->spec.n_hashes, j->spec.min_count,
-                                             j->spec.bloom_bits, park->cfg, kcapi::held_bytes(park)};
-                S->idle.push_back(ih);
-                S->idle_bytes += ih.bytes;
-            }
-            for (kc_handle e : evicted) kc_destroy(e);
             release_ms += ms_between(t_c1, Clock::now());
             std::lock_guard<std::mutex> lk(S->mu);
             if (js != KC_OK) {
@@ -356,6 +356,38 @@ void finalize_loop(kc_server_ctx* S, int idx) {
         }
         S->cv_done.notify_all();
         S->cv_ingest.notify_all();
+    }
+}
+
+void reap_loop(kc_server_ctx* S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<kc_handle> dead;
+        std::vector<kc_server_ctx::Parked> park;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_reap.wait(lk, [&] { return S->stop || !S->graveyard.empty() || !S->to_park.empty(); });
+            dead.swap(S->graveyard);
+            park.swap(S->to_park);
+            if (dead.empty() && park.empty() && S->stop) return;
+        }
+        for (auto& p : park) {
+            if (S->stop || kc_reset(p.h) != KC_OK) {
+                dead.push_back(p.h);
+                continue;
+            }
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (S->idle.size() >= kc_server_ctx::kMaxIdle) {
+                dead.push_back(S->idle.front().h);
+                S->idle_bytes -= S->idle.front().bytes;
+                S->idle.pop_front();
+            }
+            kc_server_ctx::IdleHandle ih{p.h, p.spec.k, p.spec.n_samples, p.spec.n_hashes, p.spec.min_count,
+                                         p.spec.bloom_bits, p.h->cfg, kcapi::held_bytes(p.h)};
+            S->idle.push_back(ih);
+            S->idle_bytes += ih.bytes;
+        }
+        for (kc_handle h : dead) kc_destroy(h);
     }
 }
 
@@ -398,6 +430,7 @@ kc_status kc_server_create_ex(uint64_t device_budget_bytes, int max_batch, uint3
     }
     for (int i = 0; i < kIngestThreads; ++i) S->t_ingest.emplace_back(ingest_loop, S);
     for (int i = 0; i < kFinalizeThreads; ++i) S->t_final.emplace_back(finalize_loop, S, i);
+    S->t_reap = std::thread(reap_loop, S);
     *out = S;
     return KC_OK;
 }
@@ -463,19 +496,23 @@ kc_status kc_server_wait(kc_server S, uint64_t job_id, double timeout_s, uint64_
 kc_status kc_server_result(kc_server S, uint64_t job_id, uint64_t* keys, uint32_t* counts, uint64_t capacity,
                            uint64_t* n_out) {
     if (!S) return KC_ERR_ARG;
-    std::lock_guard<std::mutex> lk(S->mu);
-    auto it = S->jobs.find(job_id);
-    if (it == S->jobs.end()) return KC_ERR_ARG;
-    std::shared_ptr<Job> j = it->second;
-    if (!j->done) return KC_ERR_STATE;
-    if (j->status != KC_OK) return j->status;
-    if (n_out) *n_out = j->n_keys;
-    if (!keys) return KC_OK;
-    if (capacity < j->n_keys) return KC_ERR_CAPACITY;
+    std::shared_ptr<Job> j;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->jobs.find(job_id);
+        if (it == S->jobs.end()) return KC_ERR_ARG;
+        j = it->second;
+        if (!j->done) return KC_ERR_STATE;
+        if (j->status != KC_OK) return j->status;
+        if (n_out) *n_out = j->n_keys;
+        if (!keys) return KC_OK;
+        if (capacity < j->n_keys) return KC_ERR_CAPACITY;
+        S->jobs.erase(it);  // the result is handed over: no other call sees the job now
+    }
+    // the copy into the caller's memory runs outside the server's lock
     std::memcpy(keys, j->keys, j->n_keys * 8);
     if (counts) std::memcpy(counts, j->counts, j->n_keys * (size_t)j->spec.n_samples * 4);
     free_result(S->pool, *j);
-    S->jobs.erase(it);  // the result has been handed over
     return KC_OK;
 }
 
@@ -517,8 +554,12 @@ void kc_server_destroy(kc_server S) {
     }
     S->cv_ingest.notify_all();
     S->cv_final.notify_all();
+    S->cv_reap.notify_all();
     for (auto& t : S->t_ingest) t.join();
     for (auto& t : S->t_final) t.join();
+    if (S->t_reap.joinable()) S->t_reap.join();
+    for (kc_handle h : S->graveyard) kc_destroy(h);
+    for (auto& p : S->to_park) kc_destroy(p.h);
     for (auto& d : S->ingested)
         if (d->h) kc_destroy(d->h);
     for (auto& ih : S->idle) kc_destroy(ih.h);
