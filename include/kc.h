@@ -284,6 +284,9 @@ typedef struct kc_server_stats {
      * finalize call, then copying the batch's results to host memory, then
      * releasing its jobs' handles */
     double mean_batch_finalize_ms, mean_batch_copy_ms, mean_batch_release_ms;
+    /* jobs that ran on a finished job's handle (reset and kept for the next
+     * job with the same parameters) instead of a new one */
+    uint64_t reused_handles;
 } kc_server_stats;
 
 /* Create a server on the current device (max_batch >= 1). */

@@ -151,7 +151,7 @@ struct kc_server_ctx {
         uint64_t bytes;
     };
     std::deque<IdleHandle> idle;
-    uint64_t idle_bytes = 0;
+    uint64_t idle_bytes = 0, reused = 0;
     static constexpr size_t kMaxIdle = 32;
     // finished jobs' handles to reset and keep, and handles to destroy, both
     // taken by a reaper thread so that neither ingest nor finalize waits for
@@ -262,6 +262,7 @@ void ingest_loop(kc_server_ctx* S) {
                     j->h = it->h;
                     S->idle_bytes -= it->bytes;
                     S->idle.erase(it);
+                    S->reused += 1;
                     break;
                 }
         }
@@ -543,6 +544,7 @@ kc_status kc_server_stats_get(kc_server S, kc_server_stats* out) {
     out->mean_batch_finalize_ms = S->sum_fin_ms[0] / nbat;
     out->mean_batch_copy_ms = S->sum_fin_ms[1] / nbat;
     out->mean_batch_release_ms = S->sum_fin_ms[2] / nbat;
+    out->reused_handles = S->reused;
     return KC_OK;
 }
 

@@ -122,3 +122,28 @@ def test_failed_job_reports_its_error_and_others_complete(oracle_mod):
     st = srv.stats()
     assert st["failed"] == 1 and st["completed"] == len(good)
     srv.close()
+
+
+def test_reused_handles_give_exact_results(oracle_mod):
+    """Jobs with the same parameters one after another run on the finished
+    jobs' handles (reset and kept by the server); every result still equals
+    the oracle's, whatever the previous job on the handle counted."""
+    base = _jobs(11, 1)[0]
+    jobs = []
+    for i in range(6):  # same k, filter size, hashes and min_count; different reads
+        g = synth.genome(500 + i, 50_000)
+        rs = synth.reads(500 + i, g, 2_000 + 700 * i, 100, 250, 0.005, 0.0005)
+        jobs.append(synth.Workload(f"r{i}", [rs], base.k, 1 << 20, 4, 2))
+    srv = kc.KcServer(device_budget_bytes=8 << 30, max_batch=4)
+    for w in jobs:  # one at a time: each job finds the previous job's handle idle
+        time.sleep(0.05)  # the reaper thread parks the previous job's handle meanwhile
+        jid = srv.submit_workload(w)
+        srv.wait(jid, timeout_s=120)
+        keys, counts = srv.result(jid)
+        o = oracle_mod.count(w)
+        ok, oc = o.result()
+        assert np.array_equal(keys, ok) and np.array_equal(counts, oc)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(jobs)
+    assert st["reused_handles"] >= 1
