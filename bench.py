@@ -987,7 +987,9 @@ def run_served_trace(n_jobs: int, max_reads: int, loads=(0.7, 0.9), budget_bytes
                         "stage_ms": {x: round(st["mean_" + x + "_ms"], 3)
                                      for x in ("queue", "ingest", "batch_wait", "finalize")},
                         "per_batch_ms": {x: round(st["mean_batch_" + x + "_ms"], 3)
-                                         for x in ("finalize", "copy", "release")}}
+                                         for x in ("finalize", "copy", "release")},
+                        "ingest_ms": {x: round(st["mean_ingest_" + x + "_ms"], 3) for x in ("handle", "add")},
+                        "reused_handles": st["reused_handles"]}
     return out
 
 

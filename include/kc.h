@@ -287,6 +287,9 @@ typedef struct kc_server_stats {
     /* jobs that ran on a finished job's handle (reset and kept for the next
      * job with the same parameters) instead of a new one */
     uint64_t reused_handles;
+    /* mean per job of the ingest stage's two parts: getting a handle (a
+     * reused one, or kc_create_ex) and adding its reads (kc_add_reads) */
+    double mean_ingest_handle_ms, mean_ingest_add_ms;
 } kc_server_stats;
 
 /* Create a server on the current device (max_batch >= 1). */

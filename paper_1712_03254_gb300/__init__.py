@@ -109,7 +109,8 @@ class ServerStats(ctypes.Structure):
                 ("mean_queue_ms", ctypes.c_double), ("mean_ingest_ms", ctypes.c_double),
                 ("mean_batch_wait_ms", ctypes.c_double), ("mean_finalize_ms", ctypes.c_double),
                 ("mean_batch_finalize_ms", ctypes.c_double), ("mean_batch_copy_ms", ctypes.c_double),
-                ("mean_batch_release_ms", ctypes.c_double), ("reused_handles", ctypes.c_uint64)]
+                ("mean_batch_release_ms", ctypes.c_double), ("reused_handles", ctypes.c_uint64),
+                ("mean_ingest_handle_ms", ctypes.c_double), ("mean_ingest_add_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -170,6 +170,7 @@ struct kc_server_ctx {
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_jobs = 0;
     double sum_stage_ms[4] = {};  // queue, ingest, batch wait, finalize + copy-out of completed jobs
     double sum_fin_ms[3] = {};    // per batch: batched finalize, copies to host memory, handle release
+    double sum_ingest_ms[2] = {}; // per job: getting a handle, adding its reads
     Clock::time_point t_first, t_last;
     bool any = false;
 };
@@ -215,7 +216,11 @@ void evict_idle(kc_server_ctx* S, std::vector<kc_handle>& out) {
     }
 }
 
-bool same_config(const kc_config& a, const kc_config& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+// Same knobs (the device budget is per job and is set on reuse).
+bool same_config(kc_config a, kc_config b) {
+    a.device_budget = b.device_budget = 0;
+    return std::memcmp(&a, &b, sizeof(a)) == 0;
+}
 
 void ingest_loop(kc_server_ctx* S) {
     cudaSetDevice(S->device);
@@ -254,12 +259,17 @@ void ingest_loop(kc_server_ctx* S) {
                 cfg = tuned;  // batched finalize needs the partitioned strategy
         }
         cfg.strategy = KC_STRATEGY_PARTITIONED;
+        // the job was admitted for its footprint: that is the device memory it
+        // may hold (not the device's free memory, which other jobs and
+        // processes share)
+        cfg.device_budget = j->footprint;
         {  // a finished job's handle with the same parameters, already reset
             std::lock_guard<std::mutex> lk(S->mu);
             for (auto it = S->idle.begin(); it != S->idle.end(); ++it)
                 if (it->k == s.k && it->n_samples == s.n_samples && it->n_hashes == s.n_hashes &&
                     it->min_count == s.min_count && it->bloom_bits == s.bloom_bits && same_config(it->cfg, cfg)) {
                     j->h = it->h;
+                    j->h->cfg.device_budget = cfg.device_budget;
                     S->idle_bytes -= it->bytes;
                     S->idle.erase(it);
                     S->reused += 1;
@@ -268,9 +278,13 @@ void ingest_loop(kc_server_ctx* S) {
         }
         kc_status st = j->h ? KC_OK
                             : kc_create_ex(s.k, s.n_samples, s.bloom_bits, s.n_hashes, s.min_count, &cfg, nullptr, &j->h);
+        const Clock::time_point t_handle = Clock::now();
         for (int i = 0; st == KC_OK && i < s.n_samples; ++i)
             st = kc_add_reads(j->h, i, s.packed[i], s.offsets[i], s.n_mask[i], s.n_reads[i]);
+        const Clock::time_point t_added = Clock::now();
         std::lock_guard<std::mutex> lk(S->mu);
+        S->sum_ingest_ms[0] += ms_between(j->t_admit, t_handle);
+        S->sum_ingest_ms[1] += ms_between(t_handle, t_added);
         if (st != KC_OK) {
             fail_job(S, j, st);
             S->cv_done.notify_all();
@@ -545,6 +559,9 @@ kc_status kc_server_stats_get(kc_server S, kc_server_stats* out) {
     out->mean_batch_copy_ms = S->sum_fin_ms[1] / nbat;
     out->mean_batch_release_ms = S->sum_fin_ms[2] / nbat;
     out->reused_handles = S->reused;
+    const double ns = S->submitted ? (double)(S->completed + S->failed) : 1.0;
+    out->mean_ingest_handle_ms = S->sum_ingest_ms[0] / (ns > 0 ? ns : 1.0);
+    out->mean_ingest_add_ms = S->sum_ingest_ms[1] / (ns > 0 ? ns : 1.0);
     return KC_OK;
 }
 
