@@ -72,6 +72,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kConsumeThreads = 512;
 constexpr int kTile = 4096;
+constexpr uint32_t kChunk = 1u << 31;  // hashes a consumer loop indexes with 32 bits
 
 // NH > 0: every job of the batch sets NH bits per key; NH = 0: per job.
 //
@@ -113,7 +114,6 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
         const uint32_t tmask = T - 1;
         const int S = J.n_samples;
         const int a = J.part_bits;
-        const uint64_t low_mask = (1ull << (64 - a)) - 1ull;
         // the job's fields the inner loops use, in registers
         const int bloom_shift = J.bloom_shift;
         const bool all_cand = J.all_candidates != 0;
@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
             last_ctr = J.ctr;
         }
         const uint64_t hpre = (uint64_t)part << (64 - a);
+        const unsigned long long empty = hpre ^ (1ull << (64 - a));  // a hash of another partition
         int sl = min(hint, J.split_max);  // split level: the partition is taken as 2^sl sub-ranges
         uint32_t sub = 0;  // the sub-range being counted
         bool overflow = false;
@@ -140,41 +141,63 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
             const uint32_t w_lo = sub * w_n;
             const uint32_t smask = (1u << sl) - 1u;
             const int sub_shift = 64 - a - sl;  // sub-range = h bits [sub_shift, 64 - a)
-            const int home_shift = sub_shift - J.table_log2;
+            // a window belongs to the (sub-range of the) partition iff the top
+            // a + sl <= 32 bits of its hash equal those of `range`
+            const uint64_t range = hpre | ((uint64_t)sub << sub_shift);
+            const uint32_t rhi = (uint32_t)(range >> 32), rmask = ~0u << (32 - a - sl);
             uint64_t c_try = 0, k_try = 0;
             for (uint32_t i = threadIdx.x; i < w_n; i += blockDim.x) sb[w_lo + i] = 0ull;
-            for (uint32_t i = threadIdx.x; i < T; i += blockDim.x) sk[i] = 0ull;
+            for (uint32_t i = threadIdx.x; i < T; i += blockDim.x) sk[i] = empty;
             for (uint32_t i = threadIdx.x; i < T * S; i += blockDim.x) sc[i] = 0u;
             if (threadIdx.x == 0) s_fail = 0;
             __syncthreads();
             bool stop = false;
+            // A window of a thread's first 64 iterations over the first batch
+            // that finds or claims its key in the filter pass is counted there
+            // (bit m of `counted` for iteration m); the recount visits only the
+            // other windows.  Each window is counted once, by the pass that
+            // found its key: the table only grows, and the recount sees it whole.
+            uint32_t counted_lo = 0, counted_hi = 0;
             for (int bt = 0; bt < J.n_batches && !stop; ++bt) {
-                const uint64_t* __restrict__ d = J.data[bt];
-                const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
-                // each thread's next hash is in flight while it handles the current one
-                uint64_t hn = lo + threadIdx.x < hi ? __ldcg(d + lo + threadIdx.x) : 0ull;
-                for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                    const uint64_t h = hn;
-                    if (i + blockDim.x < hi) hn = __ldcg(d + i + blockDim.x);  // read again by the recount: keep in L2
-                    if ((uint32_t)(h >> (64 - a)) != part) continue;  // run padding
-                    if (sl && ((uint32_t)(h >> sub_shift) & smask) != sub) continue;
-                    const uint32_t w = (uint32_t)(h >> bloom_shift) & (n_sw - 1);
-                    const uint64_t g = mixer64(h);
-                    const uint64_t pat = NH > 0 ? bloom_pattern_n<(NH > 0 ? NH : 1)>(g) : bloom_pattern_rt(g, J.n_hashes);
-                    const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
-                    if (all_cand || (old & pat) == pat) {
-                        ++c_try;
-                        const int r = smem_claim(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
-                        if (r < 0) {
-                            s_fail = 1;
-                            stop = true;
-                            break;
-                        }
-                        if (r > 0) {
-                            ++k_try;
-                            if (*(volatile int*)&s_fail) {  // another thread overflowed: give up early
+                const uint64_t lo = J.starts[bt][part];
+                const uint64_t n_all = J.starts[bt][part + 1] - lo;
+                uint32_t* const scol = sc + J.samples[bt];  // this batch's count column
+                // 32-bit indices within chunks of 2^31 hashes (one chunk, in practice)
+                for (uint64_t c0 = 0; c0 < n_all && !stop; c0 += kChunk) {
+                    const uint64_t* __restrict__ d = J.data[bt] + lo + c0;
+                    const uint32_t n = (uint32_t)min(n_all - c0, (uint64_t)kChunk);
+                    const bool first = bt == 0 && c0 == 0;
+                    // each thread's next hash is in flight while it handles the current one
+                    uint64_t hn = threadIdx.x < n ? __ldcg(d + threadIdx.x) : 0ull;
+                    uint32_t m = 0;
+                    for (uint32_t t = threadIdx.x; t < n; t += kConsumeThreads, ++m) {
+                        const uint64_t h = hn;
+                        if (t + kConsumeThreads < n) hn = __ldcg(d + t + kConsumeThreads);  // read again by the recount: keep in L2
+                        if ((((uint32_t)(h >> 32)) ^ rhi) & rmask) continue;  // run padding, or another sub-range
+                        const uint32_t w = (uint32_t)(h >> bloom_shift) & (n_sw - 1);
+                        const uint64_t g = mixer64(h);
+                        const uint64_t pat = NH > 0 ? bloom_pattern_n<(NH > 0 ? NH : 1)>(g) : bloom_pattern_rt(g, J.n_hashes);
+                        const unsigned long long old = atomicOr(sb + w, (unsigned long long)pat);
+                        if (all_cand || (old & pat) == pat) {
+                            ++c_try;
+                            uint32_t slot;
+                            const int r = smem_claim(sk, tmask, (uint32_t)h & tmask, h, empty, slot);
+                            if (r < 0) {
+                                s_fail = 1;
                                 stop = true;
                                 break;
+                            }
+                            if (first && m < 64) {
+                                atomicAdd(scol + slot * S, 1u);
+                                if (m < 32) counted_lo |= 1u << m;
+                                else counted_hi |= 1u << (m - 32);
+                            }
+                            if (r > 0) {
+                                ++k_try;
+                                if (*(volatile int*)&s_fail) {  // another thread overflowed: give up early
+                                    stop = true;
+                                    break;
+                                }
                             }
                         }
                     }
@@ -190,23 +213,46 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
                     continue;
                 }
                 overflow = true;
-                h_left = hpre | ((uint64_t)sub << sub_shift);
+                h_left = range;
                 break;
             }
             cand += c_try;
             claimed += k_try;
             for (int bt = 0; bt < J.n_batches; ++bt) {
-                const uint64_t* __restrict__ d = J.data[bt];
-                const int smp = J.samples[bt];
-                const uint64_t lo = J.starts[bt][part], hi = J.starts[bt][part + 1];
-                uint64_t hn = lo + threadIdx.x < hi ? __ldcg(d + lo + threadIdx.x) : 0ull;
-                for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                    const uint64_t h = hn;
-                    if (i + blockDim.x < hi) hn = sl ? __ldcg(d + i + blockDim.x) : __ldcs(d + i + blockDim.x);  // last use unless split
-                    if ((uint32_t)(h >> (64 - a)) != part) continue;
-                    if (sl && ((uint32_t)(h >> sub_shift) & smask) != sub) continue;
-                    const int s = smem_find(sk, tmask, (uint32_t)(h >> home_shift) & tmask, (h & low_mask) + 1ull);
-                    if (s >= 0) atomicAdd(sc + (uint32_t)s * S + smp, 1u);
+                const uint64_t lo = J.starts[bt][part];
+                const uint64_t n_all = J.starts[bt][part + 1] - lo;
+                uint32_t* const scol = sc + J.samples[bt];
+                for (uint64_t c0 = 0; c0 < n_all; c0 += kChunk) {
+                    const uint64_t* __restrict__ d = J.data[bt] + lo + c0;
+                    const uint32_t n = (uint32_t)min(n_all - c0, (uint64_t)kChunk);
+                    uint32_t t0 = threadIdx.x;  // first iteration of the dense loop below
+                    if (bt == 0 && c0 == 0) {
+                        // iterations m < 64 the filter pass did not count, taken
+                        // by their bits; each one's hash is loaded a step ahead
+                        const uint32_t iters = threadIdx.x < n ? (n - 1 - threadIdx.x) / kConsumeThreads + 1 : 0;
+                        const uint32_t mi = iters < 64 ? iters : 64;
+                        const uint64_t in_range = mi == 64 ? ~0ull : (1ull << mi) - 1ull;
+                        uint64_t todo = ~(((uint64_t)counted_hi << 32) | counted_lo) & in_range;
+                        t0 = threadIdx.x + 64u * kConsumeThreads;
+                        uint64_t hn = todo ? __ldcs(d + threadIdx.x + (uint32_t)(__ffsll((long long)todo) - 1) * kConsumeThreads) : 0ull;
+                        while (todo) {
+                            const uint64_t h = hn;
+                            todo &= todo - 1ull;
+                            if (todo) hn = __ldcs(d + threadIdx.x + (uint32_t)(__ffsll((long long)todo) - 1) * kConsumeThreads);
+                            if ((((uint32_t)(h >> 32)) ^ rhi) & rmask) continue;
+                            const int s = smem_find(sk, tmask, (uint32_t)h & tmask, h, empty);
+                            if (s >= 0) atomicAdd(scol + (uint32_t)s * S, 1u);
+                        }
+                    }
+                    if (t0 >= n) continue;
+                    uint64_t hn = __ldcs(d + t0);
+                    for (uint32_t t = t0; t < n; t += kConsumeThreads) {
+                        const uint64_t h = hn;
+                        if (t + kConsumeThreads < n) hn = sl ? __ldcg(d + t + kConsumeThreads) : __ldcs(d + t + kConsumeThreads);  // last use unless split
+                        if ((((uint32_t)(h >> 32)) ^ rhi) & rmask) continue;
+                        const int s = smem_find(sk, tmask, (uint32_t)h & tmask, h, empty);
+                        if (s >= 0) atomicAdd(scol + (uint32_t)s * S, 1u);
+                    }
                 }
             }
             __syncthreads();
@@ -215,7 +261,7 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
                 const unsigned long long k1 = sk[i];
                 uint64_t v = 0;
                 bool keep = false;
-                if (k1 != 0ull) {
+                if (k1 != empty) {
                     const uint32_t c0 = sc[i * S];
                     const uint32_t c1 = S == 2 ? sc[i * S + 1] : 0u;
                     keep = (uint64_t)c0 + c1 >= J.min_count;
@@ -230,7 +276,7 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
                     if (keep) {
                         const uint64_t pos = pos0 + __popc(ballot & lt);
                         if (pos < J.sv_cap) {
-                            J.sv_keys[pos] = unmixer64(hpre | (k1 - 1ull));
+                            J.sv_keys[pos] = unmixer64(k1);
                             J.sv_vals[pos] = v;
                         }
                     }
@@ -1058,8 +1104,10 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         smem_max = std::max(smem_max, smem);
         // survivors: a partition holds at most 2^split_max tables of keys and
         // one key per min_count of its windows
+        // the consumer tells a window's sub-range by the top 32 bits of its hash
         const int split_max = h->cfg.split_max == KC_SPLIT_NONE ? 0
-                              : std::min<int>(h->slice_log2, h->cfg.split_max ? (int)h->cfg.split_max : 6);
+                              : std::min<int>(std::min<int>(h->slice_log2, 32 - h->part_bits),
+                                              h->cfg.split_max ? (int)h->cfg.split_max : 6);
         x.sv_cap = 0;
         if (fast) {  // every survivor has min_count windows, and no partition more than 2^split_max tables
             x.sv_cap = std::min<uint64_t>((p_hi - p_lo) << (tl + split_max), x.total_w / std::max<uint32_t>(1, h->min_count));

@@ -137,17 +137,23 @@ __device__ __forceinline__ void rolling_step(RollingWindow& r, const PassParams&
     r.y <<= 2;
 }
 
+// shl.b32 clamps its shift amount at 32: x << b is 0 for b >= 32.
+__device__ __forceinline__ uint32_t shl_clamped(uint32_t x, uint32_t b) {
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(b));
+    return r;
+}
+
 // Bits of one key in its filter word: bit (g >> 6i) & 63 for i < n_hashes,
-// assembled in two 32-bit halves.
+// assembled in two 32-bit halves (bit b >= 32 is bit b ^ 32 of the high half).
 template <int NH>
 __device__ __forceinline__ uint64_t bloom_pattern_n(uint64_t g) {
     uint32_t lo = 0, hi = 0;
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
         const uint32_t bit = (uint32_t)(g >> (6 * i)) & 63u;
-        const uint32_t m = 1u << (bit & 31u);
-        if (bit & 32u) hi |= m;
-        else lo |= m;
+        lo |= shl_clamped(1u, bit);
+        hi |= shl_clamped(1u, bit ^ 32u);
     }
     return ((uint64_t)hi << 32) | lo;
 }
@@ -363,18 +369,26 @@ __device__ __forceinline__ void warp_sort64_packed(uint64_t* __restrict__ keys, 
 
 constexpr int kProbeLimit = 64;  // shared-memory table probes before a partition falls back
 
-// Shared-memory table: keys[T] hold (h & low_mask) + 1 (0 = empty), counts
-// follow as n_samples uint32 per slot.  Returns 1 = claimed, 0 = present,
-// -1 = no free slot within kProbeLimit probes.
+// Shared-memory table of one partition: keys[T] hold the hashes h of the
+// claimed keys themselves (h determines the key: key = unmixer64(h)), and an
+// empty slot holds `empty`, a hash of another partition that no key of this
+// one can equal.  Counts follow as n_samples uint32 per slot.  Returns 1 =
+// claimed, 0 = present, -1 = no free slot within kProbeLimit probes; `slot`
+// receives the key's slot unless -1 is returned.
 __device__ __forceinline__ int smem_claim(unsigned long long* keys, uint32_t tmask, uint32_t s,
-                                          unsigned long long stored) {
+                                          unsigned long long h, unsigned long long empty, uint32_t& slot) {
     for (int i = 0; i < kProbeLimit; ++i) {
         const unsigned long long cur = keys[s];
-        if (cur == stored) return 0;
-        if (cur == 0ull) {
-            const unsigned long long prev = atomicCAS(&keys[s], 0ull, stored);
-            if (prev == 0ull) return 1;
-            if (prev == stored) return 0;
+        if (cur == h) {
+            slot = s;
+            return 0;
+        }
+        if (cur == empty) {
+            const unsigned long long prev = atomicCAS(&keys[s], empty, h);
+            if (prev == empty || prev == h) {
+                slot = s;
+                return prev == empty ? 1 : 0;
+            }
         }
         s = (s + 1) & tmask;
     }
@@ -382,11 +396,11 @@ __device__ __forceinline__ int smem_claim(unsigned long long* keys, uint32_t tma
 }
 
 __device__ __forceinline__ int smem_find(const unsigned long long* keys, uint32_t tmask, uint32_t s,
-                                         unsigned long long stored) {
+                                         unsigned long long h, unsigned long long empty) {
     for (uint32_t i = 0; i <= tmask; ++i) {
         const unsigned long long cur = keys[s];
-        if (cur == stored) return (int)s;
-        if (cur == 0ull) return -1;
+        if (cur == h) return (int)s;
+        if (cur == empty) return -1;
         s = (s + 1) & tmask;
     }
     return -1;
