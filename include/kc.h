@@ -154,7 +154,16 @@ typedef struct kc_config {
                                      (Section III-D: tables swapped out when they
                                      outgrow memory).  A job whose result would
                                      not fit is spilled the same way.            */
-    uint64_t reserved[1];
+    uint32_t batched_ingest;      /* partitioned: 1 = kc_add_reads stores the reads
+                                     only, and kc_finalize / kc_batch_finalize
+                                     extract and group the windows of every job
+                                     of the batch together: one persistent launch
+                                     over a queue of (batch, unit range) items per
+                                     phase (extraction, bucket offsets, starts,
+                                     run bases, staged scatter) instead of a set
+                                     of launches per kc_add_reads call.  The
+                                     result is the same.                          */
+    uint32_t reserved32;
 } kc_config;
 
 #define KC_SPLIT_NONE 0xffffffffu
@@ -240,13 +249,30 @@ kc_status kc_batch_create(void* stream, kc_batch* out);
  * finalized as by kc_finalize and its stream is ordered after the batch. */
 kc_status kc_batch_finalize(kc_batch b, kc_handle* handles, int n);
 
+/* Batched ingest (kc_config.batched_ingest; Section III-A's pipeline of
+ * transfer and GPU cycles, its kernels over every job of the batch): extract
+ * and group the reads that the n handles' kc_add_reads calls kept, all
+ * together on the batch's stream -- a persistent extraction launch over a
+ * queue of (read batch, unit range) items of every job, one launch each for
+ * the bucket offsets, starts and run bases of all of them, and a persistent
+ * staged-scatter launch over the same items.  Handles without kept reads, or
+ * not partitioned or open, are left alone.  The call does not wait for the
+ * device: each handle's stream is ordered after the work, so a later
+ * kc_finalize / kc_batch_finalize (which runs this step itself for reads
+ * still kept) sees the grouped hashes.  KC_ERR_ARG for a null batch or
+ * handle list, or a handle listed twice. */
+kc_status kc_batch_ingest(kc_batch b, kc_handle* handles, int n);
+
 void kc_batch_destroy(kc_batch b);
 
 /*
  * Job server with continuous batching (host-submitted jobs).  Two ingest
  * threads admit queued jobs in arrival order as soon as their estimated
- * device footprint fits device_budget_bytes and add their reads on their own
- * streams; two finalize threads, each with its own batch object, repeatedly
+ * device footprint fits device_budget_bytes and copy their reads to the
+ * device on their own streams (kc_config.batched_ingest); an extract thread
+ * takes every job copied so far and extracts and groups them together
+ * (kc_batch_ingest, one launch per phase); two finalize threads, each with
+ * its own batch object, repeatedly
  * take every job ingested so far (at most max_batch) as one batch
  * (kc_batch_finalize), copy the results into pinned host blocks (one pool
  * per process, reused across jobs and servers and kept until the process

@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
                 ("strategy", ctypes.c_uint32), ("smem_table_log2", ctypes.c_uint32),
                 ("scatter_mode", ctypes.c_uint32), ("split_max", ctypes.c_uint32), ("prune_chain", ctypes.c_uint32),
                 ("own_bits", ctypes.c_uint32), ("own_lo", ctypes.c_uint32), ("own_hi", ctypes.c_uint32),
-                ("device_budget", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 1)]
+                ("device_budget", ctypes.c_uint64), ("batched_ingest", ctypes.c_uint32),
+                ("reserved32", ctypes.c_uint32)]
 
 
 assert ctypes.sizeof(Config) == 80
@@ -160,6 +161,8 @@ def lib():
             L.kc_batch_create.restype = st
             L.kc_batch_finalize.argtypes = [p, ctypes.POINTER(p), i]
             L.kc_batch_finalize.restype = st
+            L.kc_batch_ingest.argtypes = [p, ctypes.POINTER(p), i]
+            L.kc_batch_ingest.restype = st
             L.kc_batch_destroy.argtypes = [p]
             L.kc_batch_destroy.restype = None
             L.kc_server_create.argtypes = [u64, i, ctypes.POINTER(p)]
@@ -283,7 +286,8 @@ class KmerCounter:
                  table_slots: int = 0, part_bits: int = 0, spill: bool = False, ctas_per_sm: int = 0,
                  timing: bool = False, strategy: str = "auto", smem_table_log2: int = 0, scatter_mode: int = 0,
                  split_max: int = 0, tune_bases: int = 0, prune_chain: bool = False, own_bits: int = 0,
-                 own_lo: int = 0, own_hi: int = 0, device_budget: int = 0, stream=None):
+                 own_lo: int = 0, own_hi: int = 0, device_budget: int = 0, batched_ingest: bool = False,
+                 stream=None):
         L = lib()
         cfg = Config()
         L.kc_default_config(ctypes.byref(cfg))
@@ -311,6 +315,7 @@ class KmerCounter:
         cfg.prune_chain = int(prune_chain)  # the paper's two-filter chain (direct strategy)
         cfg.own_bits, cfg.own_lo, cfg.own_hi = own_bits, own_lo, own_hi  # hash shards [own_lo, own_hi) of 2^own_bits
         cfg.device_budget = device_budget  # bytes; 0: the device's free memory
+        cfg.batched_ingest = 1 if batched_ingest else 0  # extraction and grouping at finalize, batch-wide
         h = ctypes.c_void_p()
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
@@ -474,6 +479,11 @@ class KcBatch:
     def finalize(self, counters):
         arr = (ctypes.c_void_p * len(counters))(*[c._h for c in counters])
         _check(self._L.kc_batch_finalize(self._b, arr, len(counters)), "kc_batch_finalize")
+
+    def ingest(self, counters):
+        """Extract and group the reads the counters kept (batched_ingest), all together (kc_batch_ingest)."""
+        arr = (ctypes.c_void_p * len(counters))(*[c._h for c in counters])
+        _check(self._L.kc_batch_ingest(self._b, arr, len(counters)), "kc_batch_ingest")
 
     def close(self):
         if getattr(self, "_b", None):

@@ -394,6 +394,135 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st,
     return KC_OK;
 }
 
+// Batched ingest: every pending batch of the handles, extracted and grouped
+// together on stream st (which the caller has ordered after each handle's
+// stream).  Items of upi units (at least 2^12, about one per SM over all
+// batches); per batch the histogram rows, segments, linear hashes and run
+// bases live in one scratch block freed after the scatter, the grouped
+// hashes (at most one per base plus run padding of 3 per (item, partition))
+// and partition starts stay with the batch.  Batches of handles with two
+// grouping levels are re-bucketed afterwards (regroup_batch).
+kc_status ingest_pending(kc_handle* hs, int n, cudaStream_t st, int sm_count) {
+    struct Ref {
+        kc_handle h;
+        size_t t;
+    };
+    std::vector<Ref> refs;
+    uint64_t total_units = 0;
+    for (int j = 0; j < n; ++j)
+        for (size_t t = 0; t < hs[j]->batches.size(); ++t)
+            if (hs[j]->batches[t].pending) {
+                refs.push_back({hs[j], t});
+                total_units += hs[j]->batches[t].n_units;
+            }
+    if (refs.empty()) return KC_OK;
+    const uint64_t upi = std::max<uint64_t>(1ull << 12, (total_units + sm_count - 1) / sm_count);
+    std::vector<kc::IngestBatch> ib(refs.size());
+    std::vector<uint32_t> item_batch;
+    std::vector<void*> scratch(refs.size(), nullptr);
+    kc::IngestPlan plan{};
+    bool ranged = false;
+    auto bail = [&](cudaError_t e) {
+        for (size_t i = 0; i < refs.size(); ++i) {
+            if (scratch[i]) cudaFreeAsync(scratch[i], st);
+            Batch& b = refs[i].h->batches[refs[i].t];
+            if (b.hdata) cudaFreeAsync(b.hdata, st);
+            if (b.hstarts) cudaFreeAsync(b.hstarts, st);
+            b.hdata = b.hstarts = nullptr;
+        }
+        return cuda_fail(e, "cudaMallocAsync(batched ingest)");
+    };
+    for (size_t i = 0; i < refs.size(); ++i) {
+        kc_handle h = refs[i].h;
+        Batch& b = h->batches[refs[i].t];
+        kc::IngestBatch& B = ib[i];
+        const uint64_t P = 1ull << h->l1_bits;
+        B.pw = b.pw;
+        B.vw = b.vw;
+        B.n_units = b.n_units;
+        B.p = h->params(b.sample);  // keeps the handle's own hash range
+        ranged |= B.p.h_lo != 0ull || B.p.h_hi != ~0ull;
+        B.a = h->l1_bits;
+        B.item0 = (uint32_t)item_batch.size();
+        B.n_items = (uint32_t)((b.n_units + upi - 1) / upi);
+        B.upi = upi;
+        B.ctr = h->ctr;
+        B.bucket_off = plan.n_buckets;
+        B.rel_off = plan.n_rel;
+        plan.n_buckets += P;
+        plan.n_rel += (uint64_t)B.n_items * P;
+        plan.max_a = std::max(plan.max_a, B.a);
+        item_batch.insert(item_batch.end(), B.n_items, (uint32_t)i);
+        // scratch: counts, relative bases, segments, totals, cursor, linear hashes
+        const uint64_t cells = (uint64_t)B.n_items * P;
+        const uint64_t bytes = cells * 4 + cells * 8 + B.n_items * sizeof(kc::SegDesc) + P * 4 + 8 + b.n_local * 8 + 64;
+        cudaError_t e;
+        if ((e = cudaMallocAsync(&scratch[i], bytes, st)) != cudaSuccess) return bail(e);
+        char* q = static_cast<char*>(scratch[i]);
+        B.rel = reinterpret_cast<uint64_t*>(q);
+        q += cells * 8;
+        B.seg = reinterpret_cast<kc::SegDesc*>(q);
+        q += B.n_items * sizeof(kc::SegDesc);
+        B.lin = reinterpret_cast<uint64_t*>(q);
+        q += b.n_local * 8;
+        B.g_cursor = reinterpret_cast<unsigned long long*>(q);
+        q += 8;
+        B.counts = reinterpret_cast<uint32_t*>(q);
+        q += cells * 4;
+        B.total = reinterpret_cast<uint32_t*>(q);
+        b.hcap = b.n_local + 3 * cells;
+        if ((e = cudaMallocAsync(&b.hstarts, (P + 1) * 8, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, b.hcap) * 8, st)) != cudaSuccess)
+            return bail(e);
+        B.starts = b.hstarts;
+        B.out = b.hdata;
+        KC_CUDA(cudaMemsetAsync(B.g_cursor, 0, 8, st));
+    }
+    plan.n_batches = (uint32_t)refs.size();
+    plan.n_items = (uint32_t)item_batch.size();
+    // the plan, its batches, item map and queue heads in one device block
+    const size_t bytes = sizeof(kc::IngestPlan) + ib.size() * sizeof(kc::IngestBatch) + item_batch.size() * 4 + 16;
+    char* blk = nullptr;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&blk), bytes, st)) != cudaSuccess) return bail(e);
+    kc::IngestPlan* dplan = reinterpret_cast<kc::IngestPlan*>(blk);
+    kc::IngestBatch* dbat = reinterpret_cast<kc::IngestBatch*>(blk + sizeof(kc::IngestPlan));
+    unsigned* dhead = reinterpret_cast<unsigned*>(blk + sizeof(kc::IngestPlan) + ib.size() * sizeof(kc::IngestBatch));
+    uint32_t* ditems = dhead + 4;
+    plan.batches = dbat;
+    plan.item_batch = ditems;
+    plan.head = dhead;
+    KC_CUDA(cudaMemcpyAsync(dbat, ib.data(), ib.size() * sizeof(kc::IngestBatch), cudaMemcpyHostToDevice, st));
+    KC_CUDA(cudaMemcpyAsync(ditems, item_batch.data(), item_batch.size() * 4, cudaMemcpyHostToDevice, st));
+    KC_CUDA(cudaMemsetAsync(dhead, 0, 16, st));
+    KC_CUDA(cudaMemcpyAsync(dplan, &plan, sizeof(plan), cudaMemcpyHostToDevice, st));
+    const bool timed = n == 1;
+    cudaEvent_t t0 = timed ? phase_begin(hs[0], st) : nullptr;
+    kc::launch_ingest(dplan, plan, ranged, sm_count, st);
+    KC_LAUNCHED("batched ingest launches");
+    if (timed) phase_end(hs[0], kPass1, t0, st);
+    cudaFreeAsync(blk, st);
+    for (size_t i = 0; i < refs.size(); ++i) {
+        cudaFreeAsync(scratch[i], st);
+        Batch& b = refs[i].h->batches[refs[i].t];
+        cudaFreeAsync(b.pw, st);  // the hashes replace the reads
+        cudaFreeAsync(b.vw, st);
+        b.pw = b.vw = nullptr;
+        b.pending = false;
+    }
+    for (int j = 0; j < n; ++j) hs[j]->launches += 5;
+    for (const Ref& r : refs) {
+        kc_handle h = r.h;
+        if (h->l1_bits != h->part_bits) {
+            kc_status s = regroup_batch(h, h->batches[r.t], st);
+            if (s != KC_OK) return s;
+        }
+    }
+    return KC_OK;
+}
+
+uint64_t bucket_bytes(kc_handle h, uint64_t n_local);
+
 // Device bytes the handle holds now: filter, table and counters, resident
 // batches (reads and grouped hashes) and its result.
 uint64_t held_bytes(kc_handle h) {
@@ -401,6 +530,7 @@ uint64_t held_bytes(kc_handle h) {
     for (const auto& b : h->batches) {
         if (b.pw) bytes += (2 * b.n_units + 2) * 8 + b.n_units * 8;
         if (b.hdata) bytes += b.hcap * 8 + ((1ull << h->part_bits) + 1) * 8;
+        if (b.pending) bytes += bucket_bytes(h, b.n_local);  // the grouping still to come
     }
     return bytes;
 }
@@ -940,6 +1070,9 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
         // hash range at a time
         b.deferred = true;
         ++h->deferred;
+    } else if (h->cfg.batched_ingest) {
+        b.pending = true;  // extracted and grouped at kc_finalize, with the batch's other jobs
+        b.n_local = n_local;
     } else {
         s = bucket_batch(h, b, n_local, st, h->params(sample), false);
         if (s != KC_OK) {
@@ -955,7 +1088,7 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     cudaFreeAsync(nm, st);
     cudaFreeAsync(bd, st);
     cudaFreeAsync(doff, st);
-    if (h->strategy != KC_STRATEGY_DIRECT && !b.deferred) {
+    if (h->strategy != KC_STRATEGY_DIRECT && !b.deferred && !b.pending) {
         // the hashes replace the reads: nothing rescans them
         cudaFreeAsync(b.pw, st);
         cudaFreeAsync(b.vw, st);

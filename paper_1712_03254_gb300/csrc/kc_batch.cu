@@ -1472,7 +1472,40 @@ kc_status finalize_grouped(kc_batch_ctx* b, kc_handle h) {
     return finish_spill(h);
 }
 
+// The batches kc_add_reads kept for the batched ingest, of every handle of
+// the batch: extracted and grouped on the batch's stream, which waits for each
+// handle's stream first; each handle's stream then waits for the grouping.
+kc_status ingest_batches(kc_batch_ctx* b, kc_handle* hs, int n) {
+    bool any = false;
+    for (int j = 0; j < n; ++j) {
+        kc_handle h = hs[j];
+        if (!h || h->state != State::Open || h->strategy != KC_STRATEGY_PARTITIONED) continue;
+        for (const Batch& bt : h->batches) any |= bt.pending;
+    }
+    if (!any) return KC_OK;
+    std::vector<kc_handle> open;
+    for (int j = 0; j < n; ++j) {
+        kc_handle h = hs[j];
+        if (!h || h->state != State::Open || h->strategy != KC_STRATEGY_PARTITIONED) continue;
+        for (kc_handle o : open)
+            if (o == h) return fail(KC_ERR_ARG, "handle listed twice");
+        open.push_back(h);
+        KC_CUDA(cudaEventRecord(h->ev_main, h->stream));
+        KC_CUDA(cudaStreamWaitEvent(b->st, h->ev_main, 0));
+    }
+    kc_status s = ingest_pending(open.data(), (int)open.size(), b->st, b->sm_count);
+    for (kc_handle h : open) {
+        KC_CUDA(cudaEventRecord(h->ev_main, b->st));
+        KC_CUDA(cudaStreamWaitEvent(h->stream, h->ev_main, 0));
+    }
+    return s;
+}
+
 kc_status kc_batch_finalize_internal(kc_batch_ctx* b, kc_handle* hs, int n) {
+    if (b && hs && n > 0) {
+        kc_status s = ingest_batches(b, hs, n);
+        if (s != KC_OK) return s;
+    }
     if (n == 1 && hs && hs[0] && hs[0]->strategy == KC_STRATEGY_PARTITIONED && hs[0]->state == State::Open) {
         kc_handle h = hs[0];
         if (h->deferred) return finalize_grouped(b, h);
@@ -1508,6 +1541,16 @@ kc_status kc_batch_create(void* stream, kc_batch* out) {
 }
 
 kc_status kc_batch_finalize(kc_batch b, kc_handle* handles, int n) { return kc_batch_finalize_internal(b, handles, n); }
+
+kc_status kc_batch_ingest(kc_batch b, kc_handle* handles, int n) {
+    if (!b || (!handles && n > 0) || n < 0) return fail(KC_ERR_ARG, "null batch or handle list");
+    for (int j = 0; j < n; ++j) {
+        if (!handles[j]) return fail(KC_ERR_ARG, "null handle in batch");
+        for (int i = 0; i < j; ++i)
+            if (handles[i] == handles[j]) return fail(KC_ERR_ARG, "handle listed twice");
+    }
+    return ingest_batches(b, handles, n);
+}
 
 void kc_batch_destroy(kc_batch b) { kc_batch_destroy_internal(b); }
 

@@ -36,6 +36,10 @@ struct Batch {
     // partitioned, over the device budget: the reads are kept (pw, vw) and
     // extracted again at kc_finalize, one hash range at a time
     bool deferred = false;
+    // partitioned, kc_config.batched_ingest: the reads are kept (pw, vw) until
+    // kc_finalize extracts and groups them with the other batches of its batch
+    bool pending = false;
+    uint64_t n_local = 0;  // bases spanned by the batch's units, from its first unit
 };
 
 enum class State { Open, Finalized, Poisoned };
@@ -204,6 +208,9 @@ void free_stems(kc_handle h);
 kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st, const kc::PassParams& p,
                        bool exact);
 uint64_t held_bytes(kc_handle h);
+// Extract and group every pending batch (kc_config.batched_ingest) of the
+// handles on stream st, ordered after each handle's stream by the caller.
+kc_status ingest_pending(kc_handle* hs, int n, cudaStream_t st, int sm_count);
 uint64_t room_bytes(kc_handle h);
 // Sort n (key, value) pairs (keys below 2^key_bits) from tk/tv into out_k/out_v;
 // ctr->survivors holds n on the device; synchronises the stream.

@@ -117,6 +117,47 @@ void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_uni
 // 2^a2; with a1 > 0 only hashes of the segment's level-1 group.
 void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,
                                const uint64_t* base, uint64_t* out, cudaStream_t st);
+// Batched ingest: the read batches of several jobs extracted and grouped by
+// one set of launches.  Each batch is cut into items of whole units; the
+// extraction and the staged scatter are persistent kernels over the item
+// queue, the per-bucket offsets, scans and run bases cover every batch in one
+// launch each.  Per batch: histogram rows and segments of its items, its
+// linear hashes, the runs' relative and absolute bases, its bucket totals and
+// starts (the batch's partition starts) and its grouped hashes.
+struct IngestBatch {
+    const uint64_t* pw;
+    const uint64_t* vw;
+    uint64_t n_units;
+    PassParams p;
+    int a;             // bucket bits (the first grouping level)
+    uint32_t item0;    // first item of the batch in the queue
+    uint32_t n_items;  // items of upi units (the last one shorter)
+    uint64_t upi;
+    uint32_t* counts;   // [n_items][2^a]
+    SegDesc* seg;       // [n_items]
+    uint64_t* lin;      // linear hashes
+    unsigned long long* g_cursor;
+    DevCounters* ctr;
+    uint64_t* rel;      // [n_items][2^a]: run starts, relative, then absolute
+    uint32_t* total;    // [2^a]
+    uint64_t* starts;   // [2^a + 1]
+    uint64_t* out;      // grouped hashes
+    uint64_t bucket_off;  // first (batch, bucket) index of the batch: sum of 2^a over earlier batches
+    uint64_t rel_off;     // first (item, bucket) index: sum of n_items 2^a over earlier batches
+};
+struct IngestPlan {
+    const IngestBatch* batches;
+    const uint32_t* item_batch;  // batch of every item
+    unsigned int* head;          // [0] extraction queue, [1] scatter queue
+    uint32_t n_batches, n_items;
+    uint64_t n_buckets;  // sum of 2^a
+    uint64_t n_rel;      // sum of n_items 2^a
+    int max_a;
+};
+size_t ingest_scatter_smem(int max_a);
+// The five launches; `plan` is on the device, its arrays too.  ranged: some
+// batch keeps only a hash range.
+void launch_ingest(const IngestPlan* plan, const IngestPlan& host_plan, bool ranged, int sm_count, cudaStream_t st);
 // Level-2 re-bucketing of level-1 groups: per-segment counts, per-(group,
 // partition) offsets and totals (padded to 4), absolute run starts.
 void launch_count_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2, uint32_t* counts,

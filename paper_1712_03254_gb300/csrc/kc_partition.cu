@@ -25,6 +25,8 @@
 //                           overflowed: the same steps with the partition's
 //                           filter slice and a table in global memory.
 
+#include <algorithm>
+
 #include "kc_internal.h"
 
 namespace kc {
@@ -214,21 +216,19 @@ __global__ void __launch_bounds__(kStagedThreads) k_bucket_scatter_staged(
 // length is set at the end; the kept total goes to ctr->kept.
 constexpr int kExtractThreads = 1024;
 
+// Units [lo, hi) by one CTA: its histogram row goes to counts[0 .. 2^a) and
+// its segment descriptor to *seg.
 template <bool kRange>
-__global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_t* __restrict__ pw,
-                                                       const uint64_t* __restrict__ vw, uint64_t n_units,
-                                                       uint64_t units_per_cta, PassParams p, int a,
-                                                       uint32_t* __restrict__ counts,
-                                                       unsigned long long* __restrict__ g_cursor,
-                                                       SegDesc* __restrict__ seg, uint64_t* __restrict__ lin,
-                                                       DevCounters* __restrict__ ctr) {
+__device__ __forceinline__ void extract_range(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw,
+                                              uint64_t lo, uint64_t hi, const PassParams& p, int a,
+                                              uint32_t* __restrict__ counts, unsigned long long* __restrict__ g_cursor,
+                                              SegDesc* __restrict__ seg, uint64_t* __restrict__ lin,
+                                              DevCounters* __restrict__ ctr) {
     extern __shared__ uint32_t s_cnt[];
     __shared__ unsigned long long s_base;
     __shared__ unsigned s_pos;
     __shared__ unsigned long long s_warp_tot[kExtractThreads / 32];
     const uint32_t P = 1u << a;
-    const uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
-    const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_cnt[i] = 0;
     // the CTA's window count, from the valid-window bits
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
         for (int w = 0; w < nwarps; ++w) tot += s_warp_tot[w];
         s_base = atomicAdd(g_cursor, tot);
         s_pos = 0;
-        seg[blockIdx.x] = SegDesc{s_base, tot, 0ull, 0ull};
+        *seg = SegDesc{s_base, tot, 0ull, 0ull};
     }
     __syncthreads();
     const uint64_t base = s_base;
@@ -282,11 +282,25 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
         }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[(uint64_t)blockIdx.x * P + i] = s_cnt[i];
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[i] = s_cnt[i];
     if (kRange && threadIdx.x == 0) {
-        seg[blockIdx.x].len = s_pos;
+        seg->len = s_pos;
         if (s_pos) atomicAdd(&ctr->kept, (unsigned long long)s_pos);
     }
+}
+
+template <bool kRange>
+__global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_t* __restrict__ pw,
+                                                       const uint64_t* __restrict__ vw, uint64_t n_units,
+                                                       uint64_t units_per_cta, PassParams p, int a,
+                                                       uint32_t* __restrict__ counts,
+                                                       unsigned long long* __restrict__ g_cursor,
+                                                       SegDesc* __restrict__ seg, uint64_t* __restrict__ lin,
+                                                       DevCounters* __restrict__ ctr) {
+    const uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
+    const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
+    extract_range<kRange>(pw, vw, lo, hi, p, a, counts + ((uint64_t)blockIdx.x << a), g_cursor, seg + blockIdx.x, lin,
+                          ctr);
 }
 
 constexpr int kLinThreads = 1024;
@@ -308,10 +322,9 @@ constexpr uint32_t kRetryCap = 2048;  // hashes one retry list holds
 // rounds.  Hashes failing again go to the front of the other list (at most as
 // many as the list held), new failures to its back, as long as the space the
 // front may still need is left; beyond that a hash stays with its thread.
-__global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64_t* __restrict__ src,
-                                                                    const SegDesc* __restrict__ segs, int a1, int a2,
-                                                                    const uint64_t* __restrict__ base,
-                                                                    uint64_t* __restrict__ out) {
+// Segment sd of src into its runs, one per bucket, starting at base[0 .. 2^a2).
+__device__ __forceinline__ void scatter_segment(const uint64_t* __restrict__ src, const SegDesc sd, int a1, int a2,
+                                                const uint64_t* __restrict__ base, uint64_t* __restrict__ out) {
     extern __shared__ unsigned long long s_stage[];
     __shared__ unsigned s_front[2], s_back[2];  // entries at the front / back of each retry list
     const uint32_t P = 1u << a2;
@@ -319,14 +332,13 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
     uint32_t* fill = reinterpret_cast<uint32_t*>(s_stage + (size_t)D * P);
     uint64_t* cursor = reinterpret_cast<uint64_t*>(fill + P);  // next output position of each run
     uint64_t* retry = cursor + P;                              // two lists of kRetryCap hashes
-    const uint64_t* my_base = base + (uint64_t)blockIdx.x * P;
+    const uint64_t* my_base = base;
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
         fill[i] = 0;
         cursor[i] = __ldg(my_base + i);
     }
     if (threadIdx.x == 0) s_front[0] = s_back[0] = s_front[1] = s_back[1] = 0;
     __syncthreads();
-    const SegDesc sd = segs[blockIdx.x];
     const uint64_t s0 = sd.off, len = sd.len;
     const uint32_t group = (uint32_t)sd.group;
     const int shift = 64 - a1 - a2;
@@ -448,6 +460,13 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64
             for (uint32_t i = whole; i < whole + 4; ++i) dst[i] = i < f ? (uint64_t)s_stage[(size_t)b * D + i] : pad;
         }
     }
+}
+
+__global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64_t* __restrict__ src,
+                                                                    const SegDesc* __restrict__ segs, int a1, int a2,
+                                                                    const uint64_t* __restrict__ base,
+                                                                    uint64_t* __restrict__ out) {
+    scatter_segment(src, segs[blockIdx.x], a1, a2, base + ((uint64_t)blockIdx.x << a2), out);
 }
 
 // Per-segment histogram over the level-2 buckets of a level-1 group's
@@ -618,6 +637,135 @@ __global__ void k_prefix_hist(const uint64_t* __restrict__ keys, DevCounters* __
     }
 }
 
+// ---- batched ingest: the phases over every job's batches -------------------
+
+// Batch of (batch, bucket) index f, of (item, bucket) index r: binary search
+// over the batches' first indices.
+__device__ __forceinline__ uint32_t batch_of_bucket(const IngestPlan* P, uint64_t f) {
+    uint32_t lo = 0, hi = P->n_batches;  // invariant: batches[lo].bucket_off <= f
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (P->batches[mid].bucket_off <= f) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ uint32_t batch_of_rel(const IngestPlan* P, uint64_t r) {
+    uint32_t lo = 0, hi = P->n_batches;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (P->batches[mid].rel_off <= r) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Extraction over the item queue: each CTA takes the next item (a unit range
+// of one batch) and extracts it as a CTA of k_extract_count would.
+template <bool kRange>
+__global__ void __launch_bounds__(kExtractThreads) k_extract_q(const IngestPlan* __restrict__ P) {
+    __shared__ unsigned s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&P->head[0], 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        if (item >= P->n_items) break;
+        const IngestBatch& B = P->batches[P->item_batch[item]];
+        const uint32_t i = item - B.item0;
+        const uint64_t lo = (uint64_t)i * B.upi;
+        const uint64_t hi = lo + B.upi < B.n_units ? lo + B.upi : B.n_units;
+        extract_range<kRange>(B.pw, B.vw, lo, hi, B.p, B.a, B.counts + ((uint64_t)i << B.a), B.g_cursor, B.seg + i,
+                              B.lin, B.ctr);
+        __syncthreads();  // the shared counters are reset by the next item
+    }
+}
+
+// Per (batch, bucket): run starts of the batch's items relative to the
+// bucket's start (counts padded to 4), and the bucket's total.
+__global__ void k_offsets_q(const IngestPlan* __restrict__ P) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < P->n_buckets; f += stride) {
+        const IngestBatch& B = P->batches[batch_of_bucket(P, f)];
+        const uint64_t b = f - B.bucket_off;
+        uint64_t run = 0;
+        for (uint32_t i = 0; i < B.n_items; ++i) {
+            const uint64_t r = ((uint64_t)i << B.a) + b;
+            B.rel[r] = run;
+            run += (B.counts[r] + 3u) & ~3u;
+        }
+        B.total[b] = (uint32_t)run;
+    }
+}
+
+// One CTA per batch: bucket starts = exclusive scan of the totals (2^a <= 4096
+// buckets, four per thread), the sum at starts[2^a].
+__global__ void __launch_bounds__(1024) k_starts_q(const IngestPlan* __restrict__ P) {
+    __shared__ unsigned long long s_w[32];
+    for (uint32_t t = blockIdx.x; t < P->n_batches; t += gridDim.x) {
+        const IngestBatch& B = P->batches[t];
+        const uint32_t n = 1u << B.a;
+        const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+        const uint32_t b0 = threadIdx.x * per;
+        unsigned long long mine = 0;
+        for (uint32_t k = 0; k < per; ++k)
+            if (b0 + k < n) mine += B.total[b0 + k];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        unsigned long long incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const unsigned long long v = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0ull;
+            unsigned long long vi = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, vi, o);
+                if (lane >= o) vi += y;
+            }
+            s_w[lane] = vi - v;
+        }
+        __syncthreads();
+        unsigned long long run = s_w[wid] + incl - mine;
+        for (uint32_t k = 0; k < per; ++k) {
+            if (b0 + k < n) {
+                B.starts[b0 + k] = run;
+                run += B.total[b0 + k];
+            }
+        }
+        if (b0 < n && b0 + per >= n) B.starts[n] = run;
+        __syncthreads();  // s_w is reused by the next batch
+    }
+}
+
+// Per (item, bucket): the run's absolute start.
+__global__ void k_bases_q(const IngestPlan* __restrict__ P) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < P->n_rel; r += stride) {
+        const IngestBatch& B = P->batches[batch_of_rel(P, r)];
+        const uint64_t x = r - B.rel_off;
+        B.rel[x] += B.starts[x & ((1ull << B.a) - 1ull)];
+    }
+}
+
+// Staged scatter over the item queue: each CTA takes the next item's segment.
+__global__ void __launch_bounds__(kLinThreads) k_scatter_q(const IngestPlan* __restrict__ P) {
+    __shared__ unsigned s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&P->head[1], 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        if (item >= P->n_items) break;
+        const IngestBatch& B = P->batches[P->item_batch[item]];
+        const uint32_t i = item - B.item0;
+        scatter_segment(B.lin, B.seg[i], 0, B.a, B.rel + ((uint64_t)i << B.a), B.out);
+        __syncthreads();  // the stages are reset by the next item
+    }
+}
+
 }  // namespace
 
 size_t bucket_pass_smem(int a) { return sizeof(uint32_t) << a; }
@@ -712,6 +860,27 @@ void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_un
         k_bucket_pass<kScatterRegion><<<n_ctas, 512, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, nullptr, base,
                                                                  nullptr, out);
     }
+}
+
+size_t ingest_scatter_smem(int max_a) { return staged_seg_smem(max_a); }
+
+void launch_ingest(const IngestPlan* plan, const IngestPlan& hp, bool ranged, int sm_count, cudaStream_t st) {
+    const size_t esmem = bucket_pass_smem(hp.max_a);
+    const unsigned n_ext = (unsigned)std::min<uint64_t>(hp.n_items, (uint64_t)sm_count * 2);
+    if (ranged) {
+        allow_max_dynamic_smem(k_extract_q<true>);
+        k_extract_q<true><<<n_ext, kExtractThreads, esmem, st>>>(plan);
+    } else {
+        allow_max_dynamic_smem(k_extract_q<false>);
+        k_extract_q<false><<<n_ext, kExtractThreads, esmem, st>>>(plan);
+    }
+    const auto grid_of = [&](uint64_t n) { return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, 4096)); };
+    k_offsets_q<<<grid_of(hp.n_buckets), 256, 0, st>>>(plan);
+    k_starts_q<<<(unsigned)std::min<uint32_t>(hp.n_batches, 1024), 1024, 0, st>>>(plan);
+    k_bases_q<<<grid_of(hp.n_rel), 256, 0, st>>>(plan);
+    const size_t ssmem = ingest_scatter_smem(hp.max_a);
+    allow_max_dynamic_smem(k_scatter_q);
+    k_scatter_q<<<(unsigned)std::min<uint64_t>(hp.n_items, (uint64_t)sm_count), kLinThreads, ssmem, st>>>(plan);
 }
 
 size_t consume_smem(int slice_log2, int table_log2, int n_samples) {

@@ -1,10 +1,15 @@
 // Continuous-batching job server over the C ABI (kc_server_* in include/kc.h).
 //
-// Two host threads drive the GPU:
+// Three kinds of host threads drive the GPU:
 //   ingest    takes queued jobs in arrival order, admits the next one as soon as
 //             its estimated device footprint fits the budget (memory frees up
-//             as jobs finish), creates its handle on its own stream and adds
-//             its reads;
+//             as jobs finish), creates its handle on its own stream and copies
+//             its reads to the device (kc_config.batched_ingest: nothing is
+//             extracted yet);
+//   extract   takes every job copied so far (at most max_batch) and extracts
+//             and groups all their reads together (kc_batch_ingest: one
+//             persistent launch per phase over a queue of (read batch, unit
+//             range) items), without waiting for the device;
 //   finalize  takes every job ingested so far (at most max_batch), finalizes
 //             them together with one kc_batch_finalize (one persistent
 //             consumer launch over all their partitions and one replay of the
@@ -37,6 +42,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int kIngestThreads = 2;
 constexpr int kFinalizeThreads = 2;
+constexpr int kExtractThreads = 2;
 
 struct Job {
     uint64_t id = 0;
@@ -126,9 +132,10 @@ struct kc_server_ctx {
     int max_batch = 64;
     uint32_t flags = 0;
     std::mutex mu;
-    std::condition_variable cv_ingest, cv_final, cv_done;
+    std::condition_variable cv_ingest, cv_extract, cv_final, cv_done;
     std::deque<std::shared_ptr<Job>> pending;   // submitted, not admitted
-    std::deque<std::shared_ptr<Job>> ingested;  // admitted and ingested
+    std::deque<std::shared_ptr<Job>> copied;    // admitted, reads on the device, not extracted
+    std::deque<std::shared_ptr<Job>> ingested;  // admitted and ingested (extracted and grouped)
     std::map<uint64_t, std::shared_ptr<Job>> jobs;
     uint64_t next_id = 1, in_use = 0, peak = 0;
     bool stop = false;
@@ -136,6 +143,8 @@ struct kc_server_ctx {
     // finalize threads, each with its own batch object, so one batch's
     // copy-out overlaps the next batch's kernels
     std::vector<std::thread> t_ingest, t_final;
+    std::vector<std::thread> t_extract;
+    std::vector<kc_batch> extract_batch;
     std::vector<kc_batch> batch;
     int device = 0;
     // Handles of finished jobs, reset and kept for the next job with the same
@@ -263,6 +272,9 @@ void ingest_loop(kc_server_ctx* S) {
         // may hold (not the device's free memory, which other jobs and
         // processes share)
         cfg.device_budget = j->footprint;
+        // reads only at ingest; a batch's jobs are extracted and grouped together
+        // at its finalize, by one launch per phase
+        cfg.batched_ingest = 1;
         {  // a finished job's handle with the same parameters, already reset
             std::lock_guard<std::mutex> lk(S->mu);
             for (auto it = S->idle.begin(); it != S->idle.end(); ++it)
@@ -291,9 +303,41 @@ void ingest_loop(kc_server_ctx* S) {
             S->cv_ingest.notify_all();
             continue;
         }
-        j->t_ingested = Clock::now();
-        S->ingested.push_back(j);
+        S->copied.push_back(j);
+        S->cv_extract.notify_all();
+    }
+}
+
+void extract_loop(kc_server_ctx* S, int idx) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<std::shared_ptr<Job>> run;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_extract.wait(lk, [&] { return S->stop || !S->copied.empty(); });
+            if (S->stop) return;
+            while (!S->copied.empty() && (int)run.size() < S->max_batch) {
+                run.push_back(S->copied.front());
+                S->copied.pop_front();
+            }
+        }
+        std::vector<kc_handle> hs;
+        for (auto& j : run) hs.push_back(j->h);
+        const kc_status st = kc_batch_ingest(S->extract_batch[idx], hs.data(), (int)hs.size());
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto& j : run) {
+            if (st != KC_OK) {
+                fail_job(S, j, st);
+                continue;
+            }
+            j->t_ingested = Clock::now();
+            S->ingested.push_back(j);
+        }
         S->cv_final.notify_all();
+        if (st != KC_OK) {
+            S->cv_done.notify_all();
+            S->cv_ingest.notify_all();
+        }
     }
 }
 
@@ -438,12 +482,19 @@ kc_status kc_server_create_ex(uint64_t device_budget_bytes, int max_batch, uint3
         st = kc_batch_create(nullptr, &b);
         if (st == KC_OK) S->batch.push_back(b);
     }
+    for (int i = 0; st == KC_OK && i < kExtractThreads; ++i) {
+        kc_batch b = nullptr;
+        st = kc_batch_create(nullptr, &b);
+        if (st == KC_OK) S->extract_batch.push_back(b);
+    }
     if (st != KC_OK) {
         for (kc_batch b : S->batch) kc_batch_destroy(b);
+        for (kc_batch b : S->extract_batch) kc_batch_destroy(b);
         delete S;
         return st;
     }
     for (int i = 0; i < kIngestThreads; ++i) S->t_ingest.emplace_back(ingest_loop, S);
+    for (int i = 0; i < kExtractThreads; ++i) S->t_extract.emplace_back(extract_loop, S, i);
     for (int i = 0; i < kFinalizeThreads; ++i) S->t_final.emplace_back(finalize_loop, S, i);
     S->t_reap = std::thread(reap_loop, S);
     *out = S;
@@ -572,18 +623,23 @@ void kc_server_destroy(kc_server S) {
         S->stop = true;
     }
     S->cv_ingest.notify_all();
+    S->cv_extract.notify_all();
     S->cv_final.notify_all();
     S->cv_reap.notify_all();
     for (auto& t : S->t_ingest) t.join();
+    for (auto& t : S->t_extract) t.join();
     for (auto& t : S->t_final) t.join();
     if (S->t_reap.joinable()) S->t_reap.join();
     for (kc_handle h : S->graveyard) kc_destroy(h);
     for (auto& p : S->to_park) kc_destroy(p.h);
+    for (auto& d : S->copied)
+        if (d->h) kc_destroy(d->h);
     for (auto& d : S->ingested)
         if (d->h) kc_destroy(d->h);
     for (auto& ih : S->idle) kc_destroy(ih.h);
     for (auto& kv : S->jobs) free_result(S->pool, *kv.second);  // results never collected
     for (kc_batch b : S->batch) kc_batch_destroy(b);
+    for (kc_batch b : S->extract_batch) kc_batch_destroy(b);
     delete S;
 }
 

@@ -130,3 +130,90 @@ def test_batch_rejects_bad_lists():
     with pytest.raises(kc.KcError) as e:
         b.finalize([c])
     assert e.value.name == "KC_ERR_STATE"
+
+
+def _counter_batches(w, n_batches, **kw):
+    """A counter fed each sample in n_batches kc_add_reads calls."""
+    c = kc.KmerCounter(w.k, len(w.samples), w.bloom_bits, w.n_hashes, w.min_count, strategy="partitioned", **kw)
+    for s, rs in enumerate(w.samples):
+        cuts = np.linspace(0, rs.n_reads, n_batches + 1).astype(int)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            c.add_readset(s, rs.slice(a, b))
+    return c
+
+
+def test_batched_ingest_equals_oracle(oracle_mod):
+    """kc_config.batched_ingest: kc_add_reads keeps the reads and the batch's
+    finalize extracts and groups every job's batches in one launch per phase
+    (mixed k, samples, partition bits -- one job with two grouping levels --
+    and several kc_add_reads calls per sample); each job equals the oracle."""
+    jobs = _jobs(41, 6)
+    kws = [dict(), dict(part_bits=14), dict(part_bits=5), dict(), dict(part_bits=1), dict()]
+    counters = [_counter_batches(w, 1 + i % 3, batched_ingest=True, **kw) for i, (w, kw) in enumerate(zip(jobs, kws))]
+    kc.KcBatch().finalize(counters)
+    for c, w in zip(counters, jobs):
+        o = oracle_mod.count(w)
+        _check(c, o)
+        assert c.stats()["windows"] == o.windows
+
+
+def test_batched_ingest_alone_mixed_and_reused(oracle_mod):
+    """A batched-ingest job finalized alone (kc_finalize), a batch mixing
+    batched-ingest jobs with jobs grouped at kc_add_reads, and a handle reset
+    and reused: all equal the oracle."""
+    jobs = _jobs(43, 5)
+    w = jobs[0]
+    c = _counter_batches(w, 2, batched_ingest=True)
+    c.finalize()
+    _check(c, oracle_mod.count(w))
+    counters = [_counter_batches(x, 2, batched_ingest=(i % 2 == 0)) for i, x in enumerate(jobs)]
+    kc.KcBatch().finalize(counters)
+    for cc, x in zip(counters, jobs):
+        _check(cc, oracle_mod.count(x))
+    # the handle reset and fed again
+    c.reset()
+    for s, rs in enumerate(w.samples):
+        cuts = np.linspace(0, rs.n_reads, 3).astype(int)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            c.add_readset(s, rs.slice(a, b))
+    c.finalize()
+    _check(c, oracle_mod.count(w))
+
+
+def test_batched_ingest_owned_ranges(oracle_mod):
+    """Batched ingest of handles owning hash ranges of the same reads: their
+    merged results equal the oracle's, their filters OR to its filter."""
+    w = _jobs(47, 1)[0]
+    o = oracle_mod.count(w)
+    counters = []
+    for r in range(3):
+        lo, hi = kc.owned_shards(r, 3, 4)
+        counters.append(_counter_batches(w, 2, batched_ingest=True, own_bits=4, own_lo=lo, own_hi=hi))
+    kc.KcBatch().finalize(counters)
+    runs = [c.dump() for c in counters]
+    keys, counts = kc.merge_results(runs, len(w.samples))
+    ok, oc = o.result()
+    assert np.array_equal(keys, ok)
+    assert np.array_equal(counts, oc)
+    bloom = np.zeros_like(o.bloom())
+    for c in counters:
+        bloom |= c.export_bloom()
+    assert np.array_equal(bloom, o.bloom())
+    assert sum(c.stats()["owned_windows"] for c in counters) == o.windows
+
+
+def test_batch_ingest_then_finalize(oracle_mod):
+    """kc_batch_ingest on one batch object groups the kept reads of every
+    job (no wait for the device); a second batch object finalizes them, as
+    the server's extract and finalize threads do."""
+    jobs = _jobs(53, 4)
+    counters = [_counter_batches(w, 2, batched_ingest=True) for w in jobs]
+    ext, fin = kc.KcBatch(), kc.KcBatch()
+    ext.ingest(counters + [_counter_batches(jobs[0], 1)])  # a handle grouped at kc_add_reads is left alone
+    ext.ingest(counters)  # nothing kept any more: no work
+    fin.finalize(counters)
+    for c, w in zip(counters, jobs):
+        _check(c, oracle_mod.count(w))
+    with pytest.raises(kc.KcError) as e:
+        ext.ingest([counters[0], counters[0]])
+    assert e.value.name == "KC_ERR_ARG"
