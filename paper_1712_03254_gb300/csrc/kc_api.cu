@@ -302,7 +302,7 @@ kc_status regroup_batch(kc_handle h, Batch& b, cudaStream_t st) {
     kc::launch_regroup_offsets(counts, dvlo, a1, a2, rel, total, st);
     if ((e = kc::launch_scan(total, P, starts, cursor, st)) != cudaSuccess) return bail(e);
     kc::launch_regroup_base(rel, starts, dsegs, nv, a2, st);
-    kc::launch_scatter_staged_seg(b.hdata, dsegs, (int)nv, a1, a2, rel, out, st);
+    kc::launch_scatter_staged_seg(b.hdata, dsegs, (int)nv, 1, a1, a2, rel, out, st);
     h->launches += 5;
     KC_LAUNCHED("second-level bucketing launches");
     for (void* q : {(void*)counts, (void*)total, (void*)dvlo, (void*)rel, (void*)cursor, (void*)dsegs})
@@ -322,18 +322,33 @@ kc_status regroup_batch(kc_handle h, Batch& b, cudaStream_t st) {
 // windows whose hash lies in [p.h_lo, p.h_hi] are kept.  exact: the grouped
 // hashes get exactly the room they need, read back after the scan (one
 // synchronisation), instead of one slot per base of the batch.
-kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st, const kc::PassParams& p,
-                       bool exact) {
-    const int a = h->l1_bits;
-    const uint64_t P = 1ull << a;
+int scatter_mode_of(kc_handle h) {
     int mode = h->cfg.scatter_mode ? (int)h->cfg.scatter_mode : 4;
     if (h->l1_bits != h->part_bits) mode = 4;  // two levels: staged scatter only
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    const int a = h->l1_bits;
     if (mode >= 3 && std::max(kc::staged_scatter_smem(a), kc::staged_seg_smem(a)) > (size_t)max_optin) mode = 2;
+    return mode;
+}
+
+kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st, const kc::PassParams& p,
+                       bool exact, const ChunkedReads* chunks) {
+    const int a = h->l1_bits;
+    const uint64_t P = 1ull << a;
+    const int mode = scatter_mode_of(h);
+    if (chunks && mode != 4) {  // the other modes extract the whole batch at once: wait for every chunk
+        for (int c = 0; c < chunks->n; ++c) KC_CUDA(cudaStreamWaitEvent(st, chunks->ev[c], 0));
+        kc::launch_build_valid(chunks->nm, chunks->bd, b.n_units, chunks->start_local, chunks->n_local, h->k, b.vw,
+                               h->ctr, h->grid, st);
+        chunks = nullptr;
+    }
     const int max_ctas = h->grid.sm_count * (h->cfg.ctas_per_sm ? (int)h->cfg.ctas_per_sm : 1);
     const uint64_t upc = std::max<uint64_t>(1, (b.n_units + max_ctas - 1) / max_ctas);
+    // extraction CTAs: at most max_ctas over the batch; with chunks, the same
+    // CTAs take a share of every chunk (segment c = its pieces in all chunks)
     const int n_ctas = (int)((b.n_units + upc - 1) / upc);
+    const int n_pieces = chunks ? chunks->n : 1;
     uint32_t *counts = nullptr, *total = nullptr;
     uint64_t *rel = nullptr, *cursor = nullptr, *lin = nullptr, *g_cursor = nullptr;
     kc::SegDesc* seg = nullptr;
@@ -361,10 +376,22 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st,
         (!exact && (e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, b.hcap) * 8, st)) != cudaSuccess))
         return bail(e);
     if (mode == 4 && ((e = cudaMallocAsync(&lin, std::max<uint64_t>(1, n_local) * 8, st)) != cudaSuccess ||
-                      (e = cudaMallocAsync(&seg, (size_t)n_ctas * sizeof(kc::SegDesc), st)) != cudaSuccess ||
+                      (e = cudaMallocAsync(&seg, (size_t)n_ctas * n_pieces * sizeof(kc::SegDesc), st)) != cudaSuccess ||
                       (e = cudaMallocAsync(&g_cursor, 8, st)) != cudaSuccess))
         return bail(e);
-    if (mode == 4) {
+    if (mode == 4 && chunks) {
+        KC_CUDA(cudaMemsetAsync(g_cursor, 0, 8, st));
+        for (int c = 0; c < chunks->n; ++c) {
+            const uint64_t u0 = chunks->u[c], nu = chunks->u[c + 1] - u0;
+            const uint64_t upc_c = std::max<uint64_t>(1, (nu + n_ctas - 1) / n_ctas);
+            KC_CUDA(cudaStreamWaitEvent(st, chunks->ev[c], 0));
+            kc::launch_build_valid_range(chunks->nm, chunks->bd, b.n_units, u0, u0 + nu, chunks->start_local,
+                                         chunks->n_local, h->k, b.vw, h->ctr, h->grid, st);
+            kc::launch_extract_count(b.pw + 2 * u0, b.vw + u0, nu, upc_c, n_ctas, p, a, counts, g_cursor,
+                                     seg + (size_t)c * n_ctas, lin, h->ctr, st, c > 0);
+        }
+        h->launches += 2 * (chunks->n - 1);
+    } else if (mode == 4) {
         KC_CUDA(cudaMemsetAsync(g_cursor, 0, 8, st));
         kc::launch_extract_count(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, counts, g_cursor, seg, lin, h->ctr, st);
     } else {
@@ -380,7 +407,7 @@ kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st,
         if ((e = cudaMallocAsync(&b.hdata, std::max<uint64_t>(1, need) * 8, st)) != cudaSuccess) return bail(e);
     }
     if (mode != 1) kc::launch_bucket_base(rel, b.hstarts, n_ctas, a, st);
-    if (mode == 4) kc::launch_scatter_staged_seg(lin, seg, n_ctas, 0, a, rel, b.hdata, st);
+    if (mode == 4) kc::launch_scatter_staged_seg(lin, seg, n_ctas, n_pieces, 0, a, rel, b.hdata, st);
     else kc::launch_bucket_scatter(b.pw, b.vw, b.n_units, upc, n_ctas, p, a, mode, rel, cursor, b.hdata, st);
     h->launches += mode != 1 ? 5 : 4;
     cudaFreeAsync(counts, st);
@@ -972,10 +999,105 @@ void kc_destroy(kc_handle h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->ev_copy) cudaEventDestroy(h->ev_copy);
     if (h->ev_main) cudaEventDestroy(h->ev_main);
+    for (cudaEvent_t e : h->ev_chunk)
+        if (e) cudaEventDestroy(e);
+    if (h->chk_ctr) cudaFree(h->chk_ctr);
+    if (h->chk_host) cudaFreeHost(h->chk_host);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
+
+}  // extern "C"
+
+namespace kcapi {
+
+// kc_add_reads of host reads in n_chunks chunks (the read store b.pw / b.vw
+// and the scratch nm, bd, doff are allocated on the copy stream; they are
+// freed here, b.pw / b.vw unless kept).  On the copy stream: the offsets,
+// their check (read starts marked into bd, error bits into chk_ctr), then
+// each chunk's packed and N-mask words.  On the handle's stream, after the
+// check: per chunk its valid-window bits and extraction, then the grouping.
+kc_status add_reads_chunked(kc_handle h, Batch& b, int sample, const uint64_t* packed_reads, const uint64_t* offsets,
+                            const uint64_t* n_mask, uint64_t n_reads, uint64_t b0, uint64_t b1, int n_chunks,
+                            uint64_t* nm, uint64_t* bd, uint64_t* doff) {
+    cudaStream_t st = h->stream, cs = h->copy_stream;
+    const uint64_t B = (b0 / 64) * 64;
+    const uint64_t n_local = b1 - B;
+    const uint64_t n_units = b.n_units;
+    const uint64_t n_pwords_src = (n_local + 31) / 32;
+    const uint64_t n_pwords = 2 * n_units + 2;
+    auto release = [&]() {
+        for (void* q : {(void*)b.pw, (void*)b.vw, (void*)nm, (void*)bd, (void*)doff}) cudaFreeAsync(q, cs);
+        b.pw = b.vw = nullptr;
+    };
+    cudaError_t e = cudaSuccess;
+    if (!h->chk_ctr && (e = cudaMalloc(&h->chk_ctr, sizeof(kc::DevCounters))) != cudaSuccess) {
+        release();
+        return cuda_fail(e, "cudaMalloc(offsets check)");
+    }
+    if (!h->chk_host && (e = cudaMallocHost(&h->chk_host, sizeof(unsigned))) != cudaSuccess) {
+        release();
+        return cuda_fail(e, "cudaMallocHost(offsets check)");
+    }
+    for (int c = 0; c <= n_chunks; ++c)
+        if (!h->ev_chunk[c] && (e = cudaEventCreateWithFlags(&h->ev_chunk[c], cudaEventDisableTiming)) != cudaSuccess) {
+            release();
+            return cuda_fail(e, "cudaEventCreate(chunks)");
+        }
+    ChunkedReads ch;
+    ch.n = n_chunks;
+    for (int c = 0; c <= n_chunks; ++c) ch.u[c] = n_units * (uint64_t)c / (uint64_t)n_chunks;
+    for (int c = 0; c < n_chunks; ++c) ch.ev[c] = h->ev_chunk[c];
+    ch.nm = nm;
+    ch.bd = bd;
+    ch.start_local = b0 - B;
+    ch.n_local = n_local;
+    // copy stream: offsets, their check, then the chunks
+    KC_CUDA(cudaMemsetAsync(b.pw + n_pwords_src, 0, (n_pwords - n_pwords_src) * 8, cs));
+    KC_CUDA(cudaMemcpyAsync(doff, offsets, (n_reads + 1) * 8, cudaMemcpyDefault, cs));
+    KC_CUDA(cudaMemsetAsync(h->chk_ctr, 0, sizeof(kc::DevCounters), cs));
+    KC_CUDA(cudaMemsetAsync(bd, 0, n_units * 8, cs));
+    kc::launch_mark_read_starts(doff, n_reads, B, n_local, bd, h->chk_ctr, cs);
+    KC_CUDA(cudaMemcpyAsync(h->chk_host, &h->chk_ctr->err, sizeof(unsigned), cudaMemcpyDeviceToHost, cs));
+    KC_CUDA(cudaEventRecord(h->ev_chunk[n_chunks], cs));  // the check
+    for (int c = 0; c < n_chunks; ++c) {
+        const uint64_t u0 = ch.u[c], u1 = ch.u[c + 1];
+        // the chunk's words and the next unit's first word (its last unit's successor)
+        const uint64_t w0 = 2 * u0, w1 = std::min<uint64_t>(2 * u1 + 1, n_pwords_src);
+        if (w1 > w0) KC_CUDA(cudaMemcpyAsync(b.pw + w0, packed_reads + B / 32 + w0, (w1 - w0) * 8, cudaMemcpyDefault, cs));
+        const uint64_t m1 = std::min<uint64_t>(u1 + 1, n_units);
+        KC_CUDA(cudaMemcpyAsync(nm + u0, n_mask + B / 64 + u0, (m1 - u0) * 8, cudaMemcpyDefault, cs));
+        KC_CUDA(cudaEventRecord(h->ev_chunk[c], cs));
+    }
+    KC_LAUNCHED("offsets check launch");
+    KC_CUDA(cudaEventSynchronize(h->ev_chunk[n_chunks]));
+    if (*h->chk_host & kc::DERR_OFFSETS) {
+        KC_CUDA(cudaStreamSynchronize(cs));  // the caller's arrays are no longer read
+        release();
+        return fail(KC_ERR_ARG, "read offsets decrease");
+    }
+    // handle's stream: the chunks' valid bits and extraction, the grouping
+    KC_CUDA(cudaStreamWaitEvent(st, h->ev_chunk[n_chunks], 0));
+    cudaEvent_t t0 = phase_begin(h);
+    kc_status s = bucket_batch(h, b, n_local, st, h->params(sample), false, &ch);
+    phase_end(h, kPass1, t0);
+    if (s != KC_OK) {
+        KC_CUDA(cudaStreamSynchronize(cs));
+        for (void* q : {(void*)nm, (void*)bd, (void*)doff}) cudaFreeAsync(q, st);
+        return s;
+    }
+    h->launches += 4;
+    KC_LAUNCHED("ingest launches");
+    for (void* q : {(void*)nm, (void*)bd, (void*)doff, (void*)b.pw, (void*)b.vw}) cudaFreeAsync(q, st);
+    b.pw = b.vw = nullptr;  // the hashes replace the reads: nothing rescans them
+    KC_CUDA(cudaEventSynchronize(h->ev_chunk[n_chunks - 1]));  // caller may reuse its arrays
+    return KC_OK;
+}
+
+}  // namespace kcapi
+
+extern "C" {
 
 kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, const uint64_t* offsets,
                        const uint64_t* n_mask, uint64_t n_reads) {
@@ -1034,6 +1156,20 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
         cudaFreeAsync(bd, cs);
         cudaFreeAsync(doff, cs);
         return cuda_fail(e, "cudaMallocAsync(read store)");
+    }
+    // Host reads of a large partitioned batch are copied in chunks, each
+    // chunk's windows extracted as soon as it lands (ChunkedReads); the
+    // offsets go first and are checked on the device before anything touches
+    // the handle.
+    const int n_chunks = (int)std::min<uint64_t>(kMaxChunks, n_units / kChunkUnits);
+    if (!data_dev && !mask_dev && n_chunks >= 2 && h->strategy != KC_STRATEGY_DIRECT && !h->cfg.batched_ingest &&
+        scatter_mode_of(h) == 4 && bucket_bytes(h, n_local) <= room_bytes(h)) {
+        s = add_reads_chunked(h, b, sample, packed_reads, offsets, n_mask, n_reads, b0, b1, n_chunks, nm, bd, doff);
+        if (s != KC_OK) return s;
+        h->batches.push_back(b);
+        h->bases += b1 - b0;
+        h->reads += n_reads;
+        return KC_OK;
     }
     KC_CUDA(cudaMemcpyAsync(b.pw, packed_reads + B / 32, n_pwords_src * 8, cudaMemcpyDefault, cs));
     KC_CUDA(cudaMemsetAsync(b.pw + n_pwords_src, 0, (n_pwords - n_pwords_src) * 8, cs));

@@ -44,6 +44,24 @@ struct Batch {
 
 enum class State { Open, Finalized, Poisoned };
 
+// Host reads copied in chunks by kc_add_reads: chunk c covers units
+// [u[c], u[c + 1]); its packed words (and the next unit's first word) and
+// N-mask words (and the next one) are on the device once ev[c] has completed
+// on the copy stream.  The grouping builds a chunk's valid-window bits and
+// extracts its windows as soon as it lands, so the copies of the later chunks
+// overlap the extraction of the earlier ones (the double-buffered transfer
+// and GPU cycles of Section III-A).
+constexpr int kMaxChunks = 4;
+constexpr uint64_t kChunkUnits = 1ull << 15;  // units per chunk at least (2 Mbases)
+struct ChunkedReads {
+    int n = 0;
+    uint64_t u[kMaxChunks + 1] = {};
+    cudaEvent_t ev[kMaxChunks] = {};
+    const uint64_t* nm = nullptr;  // N-mask words of the batch
+    const uint64_t* bd = nullptr;  // read-start bits of the batch
+    uint64_t start_local = 0, n_local = 0;
+};
+
 // One spilled group of partitions: its sorted survivors in pinned host
 // memory (keys, then packed counts), the swap metadata of the paper's Count
 // unit (partition range, location, number of items).
@@ -87,6 +105,11 @@ struct kc_ctx {
     cudaStream_t stream = nullptr, copy_stream = nullptr;
     bool own_stream = false;
     cudaEvent_t ev_copy = nullptr, ev_main = nullptr;
+    // chunked host copies (kc_add_reads): the offsets check, then one event
+    // per chunk; a device word for the check's error bits and its pinned copy
+    cudaEvent_t ev_chunk[kcapi::kMaxChunks + 1] = {};
+    kc::DevCounters* chk_ctr = nullptr;
+    unsigned* chk_host = nullptr;
     kc::Grid grid;
     int log2_words = 0, log2_slots = 0;
     uint64_t n_slots = 0;
@@ -206,7 +229,10 @@ void free_stems(kc_handle h);
 // Group a batch's window hashes (those in [p.h_lo, p.h_hi]) by partition
 // into b.hdata / b.hstarts; exact: size b.hdata after one read-back.
 kc_status bucket_batch(kc_handle h, Batch& b, uint64_t n_local, cudaStream_t st, const kc::PassParams& p,
-                       bool exact);
+                       bool exact, const ChunkedReads* chunks = nullptr);
+// The ingest scatter mode bucket_batch uses for the handle (kc_config.scatter_mode
+// resolved against the grouping levels and the shared memory).
+int scatter_mode_of(kc_handle h);
 uint64_t held_bytes(kc_handle h);
 // Extract and group every pending batch (kc_config.batched_ingest) of the
 // handles on stream st, ordered after each handle's stream by the caller.

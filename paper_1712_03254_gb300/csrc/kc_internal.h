@@ -32,6 +32,11 @@ void launch_mark_read_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t
                              uint64_t* bd, DevCounters* ctr, cudaStream_t st);
 void launch_build_valid(const uint64_t* nmask, const uint64_t* bd, uint64_t n_vwords, uint64_t start_local,
                         uint64_t n_local, int k, uint64_t* vout, DevCounters* ctr, const Grid& g, cudaStream_t st);
+// The same for words [w_begin, w_end) only (a chunk whose N-mask words up to
+// w_end, inclusive when w_end < n_vwords, are on the device).
+void launch_build_valid_range(const uint64_t* nmask, const uint64_t* bd, uint64_t n_vwords, uint64_t w_begin,
+                              uint64_t w_end, uint64_t start_local, uint64_t n_local, int k, uint64_t* vout,
+                              DevCounters* ctr, const Grid& g, cudaStream_t st);
 
 // Pass 1: filter update, candidates claimed in the table.
 void launch_pass1(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, const PassParams& p, uint64_t* bloom,
@@ -108,14 +113,18 @@ struct SegDesc {
 };
 // mode 4: the extraction pass writes every CTA's hashes to its own segment of
 // a linear array (plus counts); the staged scatter then moves the segments.
+// accumulate: add the CTAs' counts to their rows (a later piece of the same
+// segments, launched with the same number of CTAs).
 // Windows outside [p.h_lo, p.h_hi] are dropped (their number kept goes to
 // ctr->kept when the range is not the whole hash space).
 void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                           int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, SegDesc* seg,
-                          uint64_t* lin, DevCounters* ctr, cudaStream_t st);
-// Staged scatter of segs[c] into its runs: bucket (h >> (64 - a1 - a2)) mod
-// 2^a2; with a1 > 0 only hashes of the segment's level-1 group.
-void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,
+                          uint64_t* lin, DevCounters* ctr, cudaStream_t st,
+                          bool accumulate = false);
+// Staged scatter of segment c into its runs: bucket (h >> (64 - a1 - a2)) mod
+// 2^a2; with a1 > 0 only hashes of the segment's level-1 group.  Segment c
+// comes in n_pieces pieces segs[c], segs[c + n_segs], ...
+void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int n_pieces, int a1, int a2,
                                const uint64_t* base, uint64_t* out, cudaStream_t st);
 // Batched ingest: the read batches of several jobs extracted and grouped by
 // one set of launches.  Each batch is cut into items of whole units; the

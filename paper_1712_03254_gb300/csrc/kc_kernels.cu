@@ -59,12 +59,13 @@ __global__ void k_mark_read_starts(const uint64_t* __restrict__ offsets, uint64_
     }
 }
 
+// Words [w_begin, w_end) of the batch's n_vwords valid-window words.
 __global__ void k_build_valid(const uint64_t* __restrict__ nmask, const uint64_t* __restrict__ bd,
-                              uint64_t n_vwords, uint64_t start_local, uint64_t n_local, int k,
-                              uint64_t* __restrict__ vout, DevCounters* __restrict__ ctr) {
+                              uint64_t n_vwords, uint64_t w_begin, uint64_t w_end, uint64_t start_local,
+                              uint64_t n_local, int k, uint64_t* __restrict__ vout, DevCounters* __restrict__ ctr) {
     unsigned long long local = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_vwords; w += stride) {
+    for (uint64_t w = w_begin + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < w_end; w += stride) {
         const uint64_t n_hi = nmask[w], n_lo = w + 1 < n_vwords ? nmask[w + 1] : 0ull;
         uint64_t bad = cover_pair_hi(n_hi, n_lo, k);
         if (k >= 2) {
@@ -475,8 +476,14 @@ void launch_mark_read_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t
 
 void launch_build_valid(const uint64_t* nmask, const uint64_t* bd, uint64_t n_vwords, uint64_t start_local,
                         uint64_t n_local, int k, uint64_t* vout, DevCounters* ctr, const Grid& g, cudaStream_t st) {
-    k_build_valid<<<grid_for(n_vwords, 256, g.sm_count * 8), 256, 0, st>>>(nmask, bd, n_vwords, start_local,
-                                                                            n_local, k, vout, ctr);
+    launch_build_valid_range(nmask, bd, n_vwords, 0, n_vwords, start_local, n_local, k, vout, ctr, g, st);
+}
+
+void launch_build_valid_range(const uint64_t* nmask, const uint64_t* bd, uint64_t n_vwords, uint64_t w_begin,
+                              uint64_t w_end, uint64_t start_local, uint64_t n_local, int k, uint64_t* vout,
+                              DevCounters* ctr, const Grid& g, cudaStream_t st) {
+    k_build_valid<<<grid_for(w_end - w_begin, 256, g.sm_count * 8), 256, 0, st>>>(nmask, bd, n_vwords, w_begin, w_end,
+                                                                                   start_local, n_local, k, vout, ctr);
 }
 
 void launch_pass1(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, const PassParams& p, uint64_t* bloom,

@@ -216,14 +216,15 @@ __global__ void __launch_bounds__(kStagedThreads) k_bucket_scatter_staged(
 // length is set at the end; the kept total goes to ctr->kept.
 constexpr int kExtractThreads = 1024;
 
-// Units [lo, hi) by one CTA: its histogram row goes to counts[0 .. 2^a) and
-// its segment descriptor to *seg.
+// Units [lo, hi) by one CTA: its histogram row goes to counts[0 .. 2^a)
+// (added to it with accumulate: a later piece of the same segment) and its
+// segment (piece) descriptor to *seg.
 template <bool kRange>
 __device__ __forceinline__ void extract_range(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw,
                                               uint64_t lo, uint64_t hi, const PassParams& p, int a,
                                               uint32_t* __restrict__ counts, unsigned long long* __restrict__ g_cursor,
                                               SegDesc* __restrict__ seg, uint64_t* __restrict__ lin,
-                                              DevCounters* __restrict__ ctr) {
+                                              DevCounters* __restrict__ ctr, bool accumulate = false) {
     extern __shared__ uint32_t s_cnt[];
     __shared__ unsigned long long s_base;
     __shared__ unsigned s_pos;
@@ -282,7 +283,7 @@ __device__ __forceinline__ void extract_range(const uint64_t* __restrict__ pw, c
         }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[i] = s_cnt[i];
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) counts[i] = (accumulate ? counts[i] : 0u) + s_cnt[i];
     if (kRange && threadIdx.x == 0) {
         seg->len = s_pos;
         if (s_pos) atomicAdd(&ctr->kept, (unsigned long long)s_pos);
@@ -296,11 +297,12 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
                                                        uint32_t* __restrict__ counts,
                                                        unsigned long long* __restrict__ g_cursor,
                                                        SegDesc* __restrict__ seg, uint64_t* __restrict__ lin,
-                                                       DevCounters* __restrict__ ctr) {
-    const uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
+                                                       DevCounters* __restrict__ ctr, int accumulate) {
+    uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
+    if (lo > n_units) lo = n_units;  // a CTA past the end: an empty piece
     const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
     extract_range<kRange>(pw, vw, lo, hi, p, a, counts + ((uint64_t)blockIdx.x << a), g_cursor, seg + blockIdx.x, lin,
-                          ctr);
+                          ctr, accumulate != 0);
 }
 
 constexpr int kLinThreads = 1024;
@@ -323,7 +325,10 @@ constexpr uint32_t kRetryCap = 2048;  // hashes one retry list holds
 // many as the list held), new failures to its back, as long as the space the
 // front may still need is left; beyond that a hash stays with its thread.
 // Segment sd of src into its runs, one per bucket, starting at base[0 .. 2^a2).
-__device__ __forceinline__ void scatter_segment(const uint64_t* __restrict__ src, const SegDesc sd, int a1, int a2,
+// The segment may come in pieces (pieces[0], pieces[stride], ... of the same
+// group), taken one after the other into the same runs.
+__device__ __forceinline__ void scatter_segment(const uint64_t* __restrict__ src, const SegDesc* __restrict__ pieces,
+                                                int n_pieces, size_t stride, int a1, int a2,
                                                 const uint64_t* __restrict__ base, uint64_t* __restrict__ out) {
     extern __shared__ unsigned long long s_stage[];
     __shared__ unsigned s_front[2], s_back[2];  // entries at the front / back of each retry list
@@ -339,116 +344,120 @@ __device__ __forceinline__ void scatter_segment(const uint64_t* __restrict__ src
     }
     if (threadIdx.x == 0) s_front[0] = s_back[0] = s_front[1] = s_back[1] = 0;
     __syncthreads();
-    const uint64_t s0 = sd.off, len = sd.len;
-    const uint32_t group = (uint32_t)sd.group;
+    const uint32_t group = (uint32_t)pieces[0].group;
     const int shift = 64 - a1 - a2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    // thread t owns elements t, t + nt, t + 2 nt, ... of the segment, in order;
-    // the next rows are always in flight while the current ones are staged
-    uint64_t next = threadIdx.x;
-    uint64_t ph[kLinPerThread], nx[kLinPerThread];
-    uint32_t pend = 0;  // bit e: ph[e] still to be staged
-    uint32_t nval = 0;  // bit e: nx[e] loaded, not yet taken
-#pragma unroll
-    for (int e = 0; e < kLinPerThread; ++e) {
-        if (next < len) {
-            nx[e] = __ldcg(src + s0 + next);
-            nval |= 1u << e;
-        }
-        next += blockDim.x;
-    }
     int par = 0;  // retry list read this round
-    for (;;) {
-        const unsigned n_front = min(s_front[par], kRetryCap), n_back = min(s_back[par], kRetryCap);
-        const unsigned n_in = n_front + n_back;
-        const uint64_t* rin = retry + (size_t)par * kRetryCap;
-        uint64_t* rout = retry + (size_t)(par ^ 1) * kRetryCap;
-        // the retry list first: a failure goes to the front of the other list
-        for (unsigned i = threadIdx.x; i < n_in; i += blockDim.x) {
-            const uint64_t h = rin[i < n_front ? i : kRetryCap - 1 - (i - n_front)];
-            const uint32_t b = (uint32_t)(h >> shift) & (P - 1);
-            const uint32_t pos = atomicAdd(&fill[b], 1u);
-            if (pos < D) s_stage[(size_t)b * D + pos] = h;
-            else rout[atomicAdd(&s_front[par ^ 1], 1u)] = h;  // at most n_in of these
-        }
-        // Warp-uniform: a warp takes its next rows only when none of its lanes
-        // still holds a pending hash, so every load stays coalesced.
-        if (__all_sync(kFull, pend == 0)) {
-#pragma unroll
-            for (int e = 0; e < kLinPerThread; ++e) {
-                ph[e] = nx[e];
-                if (((nval >> e) & 1u) && (a1 == 0 || (uint32_t)(ph[e] >> (64 - a1)) == group)) pend |= 1u << e;
-            }
-            nval = 0;
-#pragma unroll
-            for (int e = 0; e < kLinPerThread; ++e) {
-                if (next < len) {
-                    nx[e] = __ldcg(src + s0 + next);
-                    nval |= 1u << e;
-                }
-                // the rows after these start their way into L2 now
-                const uint64_t ahead = next + kLinPerThread * blockDim.x;
-                if (ahead < len) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + s0 + ahead));
-                next += blockDim.x;
-            }
-        }
-#pragma unroll
+    for (int pc = 0; pc < n_pieces; ++pc) {
+        // a piece ends with every hash staged or flushed: the stages go on
+        const SegDesc sd = pieces[(size_t)pc * stride];
+        const uint64_t s0 = sd.off, len = sd.len;
+        // thread t owns elements t, t + nt, t + 2 nt, ... of the segment, in order;
+        // the next rows are always in flight while the current ones are staged
+        uint64_t next = threadIdx.x;
+        uint64_t ph[kLinPerThread], nx[kLinPerThread];
+        uint32_t pend = 0;  // bit e: ph[e] still to be staged
+        uint32_t nval = 0;  // bit e: nx[e] loaded, not yet taken
+    #pragma unroll
         for (int e = 0; e < kLinPerThread; ++e) {
-            if (pend & (1u << e)) {
-                const uint64_t h = ph[e];
+            if (next < len) {
+                nx[e] = __ldcg(src + s0 + next);
+                nval |= 1u << e;
+            }
+            next += blockDim.x;
+        }
+        for (;;) {
+            const unsigned n_front = min(s_front[par], kRetryCap), n_back = min(s_back[par], kRetryCap);
+            const unsigned n_in = n_front + n_back;
+            const uint64_t* rin = retry + (size_t)par * kRetryCap;
+            uint64_t* rout = retry + (size_t)(par ^ 1) * kRetryCap;
+            // the retry list first: a failure goes to the front of the other list
+            for (unsigned i = threadIdx.x; i < n_in; i += blockDim.x) {
+                const uint64_t h = rin[i < n_front ? i : kRetryCap - 1 - (i - n_front)];
                 const uint32_t b = (uint32_t)(h >> shift) & (P - 1);
                 const uint32_t pos = atomicAdd(&fill[b], 1u);
-                if (pos < D) {
-                    s_stage[(size_t)b * D + pos] = h;
-                    pend &= ~(1u << e);
-                } else {
-                    // the back of the other list, leaving the n_in entries the
-                    // front may take; past that the hash stays and retries
-                    const unsigned k = atomicAdd(&s_back[par ^ 1], 1u);
-                    if (k < kRetryCap - n_in) {
-                        rout[kRetryCap - 1 - k] = h;
+                if (pos < D) s_stage[(size_t)b * D + pos] = h;
+                else rout[atomicAdd(&s_front[par ^ 1], 1u)] = h;  // at most n_in of these
+            }
+            // Warp-uniform: a warp takes its next rows only when none of its lanes
+            // still holds a pending hash, so every load stays coalesced.
+            if (__all_sync(kFull, pend == 0)) {
+    #pragma unroll
+                for (int e = 0; e < kLinPerThread; ++e) {
+                    ph[e] = nx[e];
+                    if (((nval >> e) & 1u) && (a1 == 0 || (uint32_t)(ph[e] >> (64 - a1)) == group)) pend |= 1u << e;
+                }
+                nval = 0;
+    #pragma unroll
+                for (int e = 0; e < kLinPerThread; ++e) {
+                    if (next < len) {
+                        nx[e] = __ldcg(src + s0 + next);
+                        nval |= 1u << e;
+                    }
+                    // the rows after these start their way into L2 now
+                    const uint64_t ahead = next + kLinPerThread * blockDim.x;
+                    if (ahead < len) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + s0 + ahead));
+                    next += blockDim.x;
+                }
+            }
+    #pragma unroll
+            for (int e = 0; e < kLinPerThread; ++e) {
+                if (pend & (1u << e)) {
+                    const uint64_t h = ph[e];
+                    const uint32_t b = (uint32_t)(h >> shift) & (P - 1);
+                    const uint32_t pos = atomicAdd(&fill[b], 1u);
+                    if (pos < D) {
+                        s_stage[(size_t)b * D + pos] = h;
                         pend &= ~(1u << e);
                     } else {
-                        atomicSub(&s_back[par ^ 1], 1u);
+                        // the back of the other list, leaving the n_in entries the
+                        // front may take; past that the hash stays and retries
+                        const unsigned k = atomicAdd(&s_back[par ^ 1], 1u);
+                        if (k < kRetryCap - n_in) {
+                            rout[kRetryCap - 1 - k] = h;
+                            pend &= ~(1u << e);
+                        } else {
+                            atomicSub(&s_back[par ^ 1], 1u);
+                        }
                     }
                 }
             }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_front[par] = s_back[par] = 0;  // read by every thread above
-        if (D == 4) {
-            // shallow stages (many buckets): a thread per bucket, one sector
-            for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
-                if (fill[b] >= 4) {
-                    const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
-                    ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + cursor[b]);
-                    dst[0] = sp[0];
-                    dst[1] = sp[1];
-                    cursor[b] += 4;
-                    fill[b] = 0;
+            __syncthreads();
+            if (threadIdx.x == 0) s_front[par] = s_back[par] = 0;  // read by every thread above
+            if (D == 4) {
+                // shallow stages (many buckets): a thread per bucket, one sector
+                for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
+                    if (fill[b] >= 4) {
+                        const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(s_stage + (size_t)b * 4);
+                        ulonglong2* dst = reinterpret_cast<ulonglong2*>(out + cursor[b]);
+                        dst[0] = sp[0];
+                        dst[1] = sp[1];
+                        cursor[b] += 4;
+                        fill[b] = 0;
+                    }
+                }
+            } else {
+                // deep stages (few buckets): a warp per bucket writes its whole
+                // sectors, then keeps the 0..3 entries left over at the front
+                for (uint32_t b = wid; b < P; b += nwarps) {
+                    const uint32_t f = min(fill[b], D);
+                    const uint32_t whole = f & ~3u;
+                    unsigned long long* st = s_stage + (size_t)b * D;
+                    uint64_t* dst = out + cursor[b];
+                    for (uint32_t i = lane * 2; i < whole; i += 64)
+                        *reinterpret_cast<ulonglong2*>(dst + i) = *reinterpret_cast<const ulonglong2*>(st + i);
+                    __syncwarp();
+                    if (lane == 0) {
+                        for (uint32_t i = whole; i < f; ++i) st[i - whole] = st[i];
+                        cursor[b] += whole;
+                        fill[b] = f - whole;  // hashes beyond D went to the retry list
+                    }
+                    __syncwarp();
                 }
             }
-        } else {
-            // deep stages (few buckets): a warp per bucket writes its whole
-            // sectors, then keeps the 0..3 entries left over at the front
-            for (uint32_t b = wid; b < P; b += nwarps) {
-                const uint32_t f = min(fill[b], D);
-                const uint32_t whole = f & ~3u;
-                unsigned long long* st = s_stage + (size_t)b * D;
-                uint64_t* dst = out + cursor[b];
-                for (uint32_t i = lane * 2; i < whole; i += 64)
-                    *reinterpret_cast<ulonglong2*>(dst + i) = *reinterpret_cast<const ulonglong2*>(st + i);
-                __syncwarp();
-                if (lane == 0) {
-                    for (uint32_t i = whole; i < f; ++i) st[i - whole] = st[i];
-                    cursor[b] += whole;
-                    fill[b] = f - whole;  // hashes beyond D went to the retry list
-                }
-                __syncwarp();
-            }
+            par ^= 1;
+            if (!__syncthreads_or(pend != 0 || nval != 0 || s_front[par] != 0 || s_back[par] != 0)) break;
         }
-        par ^= 1;
-        if (!__syncthreads_or(pend != 0 || nval != 0 || s_front[par] != 0 || s_back[par] != 0)) break;
     }
     for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
         const uint32_t f = min(fill[b], D);
@@ -462,11 +471,13 @@ __device__ __forceinline__ void scatter_segment(const uint64_t* __restrict__ src
     }
 }
 
+// CTA c: segment c, in n_pieces pieces segs[c], segs[c + gridDim.x], ...
 __global__ void __launch_bounds__(kLinThreads) k_scatter_staged_seg(const uint64_t* __restrict__ src,
-                                                                    const SegDesc* __restrict__ segs, int a1, int a2,
+                                                                    const SegDesc* __restrict__ segs, int n_pieces,
+                                                                    int a1, int a2,
                                                                     const uint64_t* __restrict__ base,
                                                                     uint64_t* __restrict__ out) {
-    scatter_segment(src, segs[blockIdx.x], a1, a2, base + ((uint64_t)blockIdx.x << a2), out);
+    scatter_segment(src, segs + blockIdx.x, n_pieces, gridDim.x, a1, a2, base + ((uint64_t)blockIdx.x << a2), out);
 }
 
 // Per-segment histogram over the level-2 buckets of a level-1 group's
@@ -761,7 +772,7 @@ __global__ void __launch_bounds__(kLinThreads) k_scatter_q(const IngestPlan* __r
         if (item >= P->n_items) break;
         const IngestBatch& B = P->batches[P->item_batch[item]];
         const uint32_t i = item - B.item0;
-        scatter_segment(B.lin, B.seg[i], 0, B.a, B.rel + ((uint64_t)i << B.a), B.out);
+        scatter_segment(B.lin, B.seg + i, 1, 0, 0, B.a, B.rel + ((uint64_t)i << B.a), B.out);
         __syncthreads();  // the stages are reset by the next item
     }
 }
@@ -783,17 +794,17 @@ void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_unit
 
 void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                           int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, SegDesc* seg,
-                          uint64_t* lin, DevCounters* ctr, cudaStream_t st) {
+                          uint64_t* lin, DevCounters* ctr, cudaStream_t st, bool accumulate) {
     const size_t smem = bucket_pass_smem(a);
     unsigned long long* cur = reinterpret_cast<unsigned long long*>(g_cursor);
     if (p.h_lo == 0ull && p.h_hi == ~0ull) {
         allow_max_dynamic_smem(k_extract_count<false>);
         k_extract_count<false><<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
-                                                                      cur, seg, lin, ctr);
+                                                                      cur, seg, lin, ctr, accumulate ? 1 : 0);
     } else {
         allow_max_dynamic_smem(k_extract_count<true>);
         k_extract_count<true><<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
-                                                                     cur, seg, lin, ctr);
+                                                                     cur, seg, lin, ctr, accumulate ? 1 : 0);
     }
 }
 
@@ -803,11 +814,11 @@ size_t staged_seg_smem(int a) {
            2 * kRetryCap * sizeof(uint64_t);
 }
 
-void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2,
+void launch_scatter_staged_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int n_pieces, int a1, int a2,
                                const uint64_t* base, uint64_t* out, cudaStream_t st) {
     const size_t smem = staged_seg_smem(a2);
     allow_max_dynamic_smem(k_scatter_staged_seg);
-    k_scatter_staged_seg<<<n_segs, kLinThreads, smem, st>>>(src, segs, a1, a2, base, out);
+    k_scatter_staged_seg<<<n_segs, kLinThreads, smem, st>>>(src, segs, n_pieces, a1, a2, base, out);
 }
 
 void launch_count_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2, uint32_t* counts,

@@ -461,3 +461,50 @@ def test_spill_to_host_merges_runs(oracle_mod, part_bits, spill):
         c.add_readset(s_i, rs)
     c.finalize()
     assert_same_result(c, o)
+
+
+def test_chunked_host_copies_equal_oracle(oracle_mod):
+    """Host reads of at least 2 x 2^15 units (64 bases each) are copied in
+    chunks, each chunk's windows extracted as soon as it lands, the offsets
+    checked on the device first: the result and filter equal the oracle's
+    and those of the same reads given from device memory, with several calls
+    and two samples; decreasing offsets are still rejected by the call and
+    leave the handle usable."""
+    torch = pytest.importorskip("torch")
+    g = synth.genome(61, 400_000)
+    rs = synth.reads(61, g, 60_000, 100, 160, 0.01, 0.001)  # about 7.8 Mbases: 3 or 4 chunks
+    rs2 = synth.reads(62, g, 45_000, 100, 160, 0.01, 0.001)
+    w = synth.Workload("chunked", [rs, rs2], k=25, bloom_bits=1 << 24, n_hashes=4, min_count=2)
+    o = oracle_mod.count(w)
+    ok, oc = o.result()
+    c = kc.KmerCounter(w.k, 2, w.bloom_bits, w.n_hashes, w.min_count, strategy="partitioned")
+    c.add_readset(0, rs)
+    c.add_readset(1, rs2.slice(0, 20_000))  # below the chunked size: one copy
+    c.add_readset(1, rs2.slice(20_000, 45_000))
+    c.finalize()
+    gk, gc = c.dump()
+    assert np.array_equal(gk, ok) and np.array_equal(gc, oc)
+    assert np.array_equal(c.export_bloom(), o.bloom())
+    assert c.stats()["windows"] == o.windows
+    # the same reads from device memory (one copy, no chunks)
+    d = kc.KmerCounter(w.k, 2, w.bloom_bits, w.n_hashes, w.min_count, strategy="partitioned")
+    for s, r in enumerate((rs, rs2)):
+        packed, mask = kc.pack_ascii(r.ascii)
+        offs = np.ascontiguousarray(r.offsets, dtype=np.uint64)
+        d.add_reads(s, *(torch.from_numpy(a.view(np.int64)).cuda() for a in (packed, offs, mask)))
+    d.finalize()
+    dk, dc = d.dump()
+    assert np.array_equal(dk, gk) and np.array_equal(dc, gc)
+    # decreasing offsets: rejected, nothing added, the handle goes on
+    c.reset()
+    packed, mask = kc.pack_ascii(rs.ascii)
+    bad = np.ascontiguousarray(rs.offsets, dtype=np.uint64).copy()
+    bad[30_000] = bad[30_001] + 5
+    with pytest.raises(kc.KcError) as e:
+        c.add_reads(0, packed, bad, mask)
+    assert e.value.name == "KC_ERR_ARG"
+    c.add_readset(0, rs)
+    c.add_readset(1, rs2)
+    c.finalize()
+    gk2, gc2 = c.dump()
+    assert np.array_equal(gk2, ok) and np.array_equal(gc2, oc)
