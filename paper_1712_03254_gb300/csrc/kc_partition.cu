@@ -674,7 +674,7 @@ __device__ __forceinline__ uint32_t batch_of_rel(const IngestPlan* P, uint64_t r
 // Extraction over the item queue: each CTA takes the next item (a unit range
 // of one batch) and extracts it as a CTA of k_extract_count would.
 template <bool kRange>
-__global__ void __launch_bounds__(kExtractThreads) k_extract_q(const IngestPlan* __restrict__ P) {
+__global__ void __launch_bounds__(kExtractThreads) k_ingest_extract(const IngestPlan* __restrict__ P) {
     __shared__ unsigned s_item;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&P->head[0], 1u);
@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_q(const IngestPlan*
 
 // Per (batch, bucket): run starts of the batch's items relative to the
 // bucket's start (counts padded to 4), and the bucket's total.
-__global__ void k_offsets_q(const IngestPlan* __restrict__ P) {
+__global__ void k_ingest_offsets(const IngestPlan* __restrict__ P) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < P->n_buckets; f += stride) {
         const IngestBatch& B = P->batches[batch_of_bucket(P, f)];
@@ -710,7 +710,7 @@ __global__ void k_offsets_q(const IngestPlan* __restrict__ P) {
 
 // One CTA per batch: bucket starts = exclusive scan of the totals (2^a <= 4096
 // buckets, four per thread), the sum at starts[2^a].
-__global__ void __launch_bounds__(1024) k_starts_q(const IngestPlan* __restrict__ P) {
+__global__ void __launch_bounds__(1024) k_ingest_starts(const IngestPlan* __restrict__ P) {
     __shared__ unsigned long long s_w[32];
     for (uint32_t t = blockIdx.x; t < P->n_batches; t += gridDim.x) {
         const IngestBatch& B = P->batches[t];
@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(1024) k_starts_q(const IngestPlan* __restrict_
 }
 
 // Per (item, bucket): the run's absolute start.
-__global__ void k_bases_q(const IngestPlan* __restrict__ P) {
+__global__ void k_ingest_bases(const IngestPlan* __restrict__ P) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < P->n_rel; r += stride) {
         const IngestBatch& B = P->batches[batch_of_rel(P, r)];
@@ -763,7 +763,7 @@ __global__ void k_bases_q(const IngestPlan* __restrict__ P) {
 }
 
 // Staged scatter over the item queue: each CTA takes the next item's segment.
-__global__ void __launch_bounds__(kLinThreads) k_scatter_q(const IngestPlan* __restrict__ P) {
+__global__ void __launch_bounds__(kLinThreads) k_ingest_scatter(const IngestPlan* __restrict__ P) {
     __shared__ unsigned s_item;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&P->head[1], 1u);
@@ -879,19 +879,19 @@ void launch_ingest(const IngestPlan* plan, const IngestPlan& hp, bool ranged, in
     const size_t esmem = bucket_pass_smem(hp.max_a);
     const unsigned n_ext = (unsigned)std::min<uint64_t>(hp.n_items, (uint64_t)sm_count * 2);
     if (ranged) {
-        allow_max_dynamic_smem(k_extract_q<true>);
-        k_extract_q<true><<<n_ext, kExtractThreads, esmem, st>>>(plan);
+        allow_max_dynamic_smem(k_ingest_extract<true>);
+        k_ingest_extract<true><<<n_ext, kExtractThreads, esmem, st>>>(plan);
     } else {
-        allow_max_dynamic_smem(k_extract_q<false>);
-        k_extract_q<false><<<n_ext, kExtractThreads, esmem, st>>>(plan);
+        allow_max_dynamic_smem(k_ingest_extract<false>);
+        k_ingest_extract<false><<<n_ext, kExtractThreads, esmem, st>>>(plan);
     }
     const auto grid_of = [&](uint64_t n) { return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, 4096)); };
-    k_offsets_q<<<grid_of(hp.n_buckets), 256, 0, st>>>(plan);
-    k_starts_q<<<(unsigned)std::min<uint32_t>(hp.n_batches, 1024), 1024, 0, st>>>(plan);
-    k_bases_q<<<grid_of(hp.n_rel), 256, 0, st>>>(plan);
+    k_ingest_offsets<<<grid_of(hp.n_buckets), 256, 0, st>>>(plan);
+    k_ingest_starts<<<(unsigned)std::min<uint32_t>(hp.n_batches, 1024), 1024, 0, st>>>(plan);
+    k_ingest_bases<<<grid_of(hp.n_rel), 256, 0, st>>>(plan);
     const size_t ssmem = ingest_scatter_smem(hp.max_a);
-    allow_max_dynamic_smem(k_scatter_q);
-    k_scatter_q<<<(unsigned)std::min<uint64_t>(hp.n_items, (uint64_t)sm_count), kLinThreads, ssmem, st>>>(plan);
+    allow_max_dynamic_smem(k_ingest_scatter);
+    k_ingest_scatter<<<(unsigned)std::min<uint64_t>(hp.n_items, (uint64_t)sm_count), kLinThreads, ssmem, st>>>(plan);
 }
 
 size_t consume_smem(int slice_log2, int table_log2, int n_samples) {
