@@ -448,7 +448,7 @@ kc_status ingest_pending(kc_handle* hs, int n, cudaStream_t st, int sm_count) {
     std::vector<uint32_t> item_batch;
     std::vector<void*> scratch(refs.size(), nullptr);
     kc::IngestPlan plan{};
-    bool ranged = false;
+    bool ranged = false, all_k31 = true;
     auto bail = [&](cudaError_t e) {
         for (size_t i = 0; i < refs.size(); ++i) {
             if (scratch[i]) cudaFreeAsync(scratch[i], st);
@@ -469,6 +469,7 @@ kc_status ingest_pending(kc_handle* hs, int n, cudaStream_t st, int sm_count) {
         B.n_units = b.n_units;
         B.p = h->params(b.sample);  // keeps the handle's own hash range
         ranged |= B.p.h_lo != 0ull || B.p.h_hi != ~0ull;
+        all_k31 &= h->k == 31;
         B.a = h->l1_bits;
         B.item0 = (uint32_t)item_batch.size();
         B.n_items = (uint32_t)((b.n_units + upi - 1) / upi);
@@ -525,7 +526,7 @@ kc_status ingest_pending(kc_handle* hs, int n, cudaStream_t st, int sm_count) {
     KC_CUDA(cudaMemcpyAsync(dplan, &plan, sizeof(plan), cudaMemcpyHostToDevice, st));
     const bool timed = n == 1;
     cudaEvent_t t0 = timed ? phase_begin(hs[0], st) : nullptr;
-    kc::launch_ingest(dplan, plan, ranged, sm_count, st);
+    kc::launch_ingest(dplan, plan, ranged, all_k31, sm_count, st);
     KC_LAUNCHED("batched ingest launches");
     if (timed) phase_end(hs[0], kPass1, t0, st);
     cudaFreeAsync(blk, st);

@@ -137,6 +137,17 @@ __device__ __forceinline__ void rolling_step(RollingWindow& r, const PassParams&
     r.y <<= 2;
 }
 
+// rolling_step with k = K a compile-time constant (every shift an immediate).
+template <int K>
+__device__ __forceinline__ void rolling_step_k(RollingWindow& r) {
+    constexpr uint64_t kmask = K >= 32 ? ~0ull : (1ull << (2 * K)) - 1ull;
+    const uint64_t b = r.x >> 62;
+    r.fwd = ((r.fwd << 2) | b) & kmask;
+    r.rc = (r.rc >> 2) | ((b ^ 3ull) << (2 * K - 2));
+    r.x = (r.x << 2) | (r.y >> 62);
+    r.y <<= 2;
+}
+
 // shl.b32 clamps its shift amount at 32: x << b is 0 for b >= 32.
 __device__ __forceinline__ uint32_t shl_clamped(uint32_t x, uint32_t b) {
     uint32_t r;

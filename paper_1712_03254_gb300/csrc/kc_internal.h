@@ -165,8 +165,9 @@ struct IngestPlan {
 };
 size_t ingest_scatter_smem(int max_a);
 // The five launches; `plan` is on the device, its arrays too.  ranged: some
-// batch keeps only a hash range.
-void launch_ingest(const IngestPlan* plan, const IngestPlan& host_plan, bool ranged, int sm_count, cudaStream_t st);
+// batch keeps only a hash range; all_k31: every batch has k = 31.
+void launch_ingest(const IngestPlan* plan, const IngestPlan& host_plan, bool ranged, bool all_k31, int sm_count,
+                   cudaStream_t st);
 // Level-2 re-bucketing of level-1 groups: per-segment counts, per-(group,
 // partition) offsets and totals (padded to 4), absolute run starts.
 void launch_count_seg(const uint64_t* src, const SegDesc* segs, int n_segs, int a1, int a2, uint32_t* counts,

@@ -218,8 +218,9 @@ constexpr int kExtractThreads = 1024;
 
 // Units [lo, hi) by one CTA: its histogram row goes to counts[0 .. 2^a)
 // (added to it with accumulate: a later piece of the same segment) and its
-// segment (piece) descriptor to *seg.
-template <bool kRange>
+// segment (piece) descriptor to *seg.  K > 0: k = K known at compile time
+// (every shift of the rolling codes a constant); K = 0: k from p.
+template <bool kRange, int K>
 __device__ __forceinline__ void extract_range(const uint64_t* __restrict__ pw, const uint64_t* __restrict__ vw,
                                               uint64_t lo, uint64_t hi, const PassParams& p, int a,
                                               uint32_t* __restrict__ counts, unsigned long long* __restrict__ g_cursor,
@@ -247,6 +248,7 @@ __device__ __forceinline__ void extract_range(const uint64_t* __restrict__ pw, c
     }
     __syncthreads();
     const uint64_t base = s_base;
+    const int hist_shift = 32 - a;  // a <= 20: the partition is the top a bits of h's high word
     const unsigned lt = (1u << lane) - 1u;
     for (uint64_t g = lo + (uint64_t)wid * 32; g < hi; g += (uint64_t)nwarps * 32) {
         const UnitWords uw = load_unit(pw, vw, g + lane, hi, lane);
@@ -263,14 +265,16 @@ __device__ __forceinline__ void extract_range(const uint64_t* __restrict__ pw, c
         }
         // every lane walks the 64 window starts of its unit with rolling codes
         RollingWindow rw = rolling_start(uw.w0, uw.w1, uw.w2, p);
+        uint64_t vbits = vm;  // window start j's bit at the top at step j
 #pragma unroll 4
         for (int j = 0; j < 64; ++j) {
-            bool has = (vm >> (63 - j)) & 1ull;
+            bool has = (int64_t)vbits < 0;
+            vbits <<= 1;
             uint64_t h = 0;
             if (has) {
                 h = mixer64(rw.fwd < rw.rc ? rw.fwd : rw.rc);
                 if (kRange) has = h >= p.h_lo && h <= p.h_hi;
-                if (has) atomicAdd(&s_cnt[(uint32_t)(h >> (64 - a))], 1u);
+                if (has) atomicAdd(&s_cnt[(uint32_t)(h >> 32) >> hist_shift], 1u);
             }
             const unsigned ballot = __ballot_sync(kFull, has);
             if (kRange && ballot) {  // warp-uniform: positions for this step's kept windows
@@ -279,7 +283,8 @@ __device__ __forceinline__ void extract_range(const uint64_t* __restrict__ pw, c
             }
             if (has) lin[base + wb + __popc(ballot & lt)] = h;
             if (!kRange) wb += __popc(ballot);
-            rolling_step(rw, p);
+            if (K > 0) rolling_step_k<(K > 0 ? K : 1)>(rw);
+            else rolling_step(rw, p);
         }
     }
     __syncthreads();
@@ -290,7 +295,7 @@ __device__ __forceinline__ void extract_range(const uint64_t* __restrict__ pw, c
     }
 }
 
-template <bool kRange>
+template <bool kRange, int K>
 __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_t* __restrict__ pw,
                                                        const uint64_t* __restrict__ vw, uint64_t n_units,
                                                        uint64_t units_per_cta, PassParams p, int a,
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
     uint64_t lo = (uint64_t)blockIdx.x * units_per_cta;
     if (lo > n_units) lo = n_units;  // a CTA past the end: an empty piece
     const uint64_t hi = lo + units_per_cta < n_units ? lo + units_per_cta : n_units;
-    extract_range<kRange>(pw, vw, lo, hi, p, a, counts + ((uint64_t)blockIdx.x << a), g_cursor, seg + blockIdx.x, lin,
+    extract_range<kRange, K>(pw, vw, lo, hi, p, a, counts + ((uint64_t)blockIdx.x << a), g_cursor, seg + blockIdx.x, lin,
                           ctr, accumulate != 0);
 }
 
@@ -673,7 +678,7 @@ __device__ __forceinline__ uint32_t batch_of_rel(const IngestPlan* P, uint64_t r
 
 // Extraction over the item queue: each CTA takes the next item (a unit range
 // of one batch) and extracts it as a CTA of k_extract_count would.
-template <bool kRange>
+template <bool kRange, int K>
 __global__ void __launch_bounds__(kExtractThreads) k_ingest_extract(const IngestPlan* __restrict__ P) {
     __shared__ unsigned s_item;
     for (;;) {
@@ -685,7 +690,7 @@ __global__ void __launch_bounds__(kExtractThreads) k_ingest_extract(const Ingest
         const uint32_t i = item - B.item0;
         const uint64_t lo = (uint64_t)i * B.upi;
         const uint64_t hi = lo + B.upi < B.n_units ? lo + B.upi : B.n_units;
-        extract_range<kRange>(B.pw, B.vw, lo, hi, B.p, B.a, B.counts + ((uint64_t)i << B.a), B.g_cursor, B.seg + i,
+        extract_range<kRange, K>(B.pw, B.vw, lo, hi, B.p, B.a, B.counts + ((uint64_t)i << B.a), B.g_cursor, B.seg + i,
                               B.lin, B.ctr);
         __syncthreads();  // the shared counters are reset by the next item
     }
@@ -792,20 +797,32 @@ void launch_bucket_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_unit
                                                            nullptr, nullptr);
 }
 
+// k = 31 (the longest k, the one the paper's configurations use) gets the
+// kernel with constant shifts
+template <bool kRange>
+static void extract_count_k(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
+                            int n_ctas, const PassParams& p, int a, uint32_t* counts, unsigned long long* cur,
+                            SegDesc* seg, uint64_t* lin, DevCounters* ctr, cudaStream_t st, bool accumulate) {
+    const size_t smem = bucket_pass_smem(a);
+    if (p.k == 31) {
+        allow_max_dynamic_smem(k_extract_count<kRange, 31>);
+        k_extract_count<kRange, 31><<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a,
+                                                                           counts, cur, seg, lin, ctr, accumulate);
+    } else {
+        allow_max_dynamic_smem(k_extract_count<kRange, 0>);
+        k_extract_count<kRange, 0><<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
+                                                                          cur, seg, lin, ctr, accumulate);
+    }
+}
+
 void launch_extract_count(const uint64_t* pw, const uint64_t* vw, uint64_t n_units, uint64_t units_per_cta,
                           int n_ctas, const PassParams& p, int a, uint32_t* counts, uint64_t* g_cursor, SegDesc* seg,
                           uint64_t* lin, DevCounters* ctr, cudaStream_t st, bool accumulate) {
-    const size_t smem = bucket_pass_smem(a);
     unsigned long long* cur = reinterpret_cast<unsigned long long*>(g_cursor);
-    if (p.h_lo == 0ull && p.h_hi == ~0ull) {
-        allow_max_dynamic_smem(k_extract_count<false>);
-        k_extract_count<false><<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
-                                                                      cur, seg, lin, ctr, accumulate ? 1 : 0);
-    } else {
-        allow_max_dynamic_smem(k_extract_count<true>);
-        k_extract_count<true><<<n_ctas, kExtractThreads, smem, st>>>(pw, vw, n_units, units_per_cta, p, a, counts,
-                                                                     cur, seg, lin, ctr, accumulate ? 1 : 0);
-    }
+    if (p.h_lo == 0ull && p.h_hi == ~0ull)
+        extract_count_k<false>(pw, vw, n_units, units_per_cta, n_ctas, p, a, counts, cur, seg, lin, ctr, st, accumulate);
+    else
+        extract_count_k<true>(pw, vw, n_units, units_per_cta, n_ctas, p, a, counts, cur, seg, lin, ctr, st, accumulate);
 }
 
 // stage, fill count and 64-bit output cursor per bucket, then the two retry lists
@@ -875,15 +892,20 @@ void launch_bucket_scatter(const uint64_t* pw, const uint64_t* vw, uint64_t n_un
 
 size_t ingest_scatter_smem(int max_a) { return staged_seg_smem(max_a); }
 
-void launch_ingest(const IngestPlan* plan, const IngestPlan& hp, bool ranged, int sm_count, cudaStream_t st) {
+void launch_ingest(const IngestPlan* plan, const IngestPlan& hp, bool ranged, bool all_k31, int sm_count,
+                   cudaStream_t st) {
     const size_t esmem = bucket_pass_smem(hp.max_a);
     const unsigned n_ext = (unsigned)std::min<uint64_t>(hp.n_items, (uint64_t)sm_count * 2);
+    const auto ext = [&](auto kern) {
+        allow_max_dynamic_smem(kern);
+        kern<<<n_ext, kExtractThreads, esmem, st>>>(plan);
+    };
     if (ranged) {
-        allow_max_dynamic_smem(k_ingest_extract<true>);
-        k_ingest_extract<true><<<n_ext, kExtractThreads, esmem, st>>>(plan);
+        if (all_k31) ext(k_ingest_extract<true, 31>);
+        else ext(k_ingest_extract<true, 0>);
     } else {
-        allow_max_dynamic_smem(k_ingest_extract<false>);
-        k_ingest_extract<false><<<n_ext, kExtractThreads, esmem, st>>>(plan);
+        if (all_k31) ext(k_ingest_extract<false, 31>);
+        else ext(k_ingest_extract<false, 0>);
     }
     const auto grid_of = [&](uint64_t n) { return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, 4096)); };
     k_ingest_offsets<<<grid_of(hp.n_buckets), 256, 0, st>>>(plan);
