@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(kExtractThreads) k_extract_count(const uint64_
 constexpr int kLinThreads = 1024;
 constexpr int kLinPerThread = 4;
 constexpr uint32_t kRetryCap = 2048;  // hashes one retry list holds
+constexpr uint32_t kPieceMax = 1u << 31;  // hashes a scatter loop indexes with 32 bits
 
 // Staged scatter of hashes already in memory.  CTA c moves segment c
 // (seg[c] = {offset into src, length, group}) into its padded runs, 4 hashes
@@ -350,23 +351,27 @@ __device__ __forceinline__ void scatter_segment(const uint64_t* __restrict__ src
     if (threadIdx.x == 0) s_front[0] = s_back[0] = s_front[1] = s_back[1] = 0;
     __syncthreads();
     const uint32_t group = (uint32_t)pieces[0].group;
-    const int shift = 64 - a1 - a2;
+    // a1 + a2 <= 20: bucket and group are bits of h's high word
+    const int shift = 32 - a1 - a2, gshift = 32 - a1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     int par = 0;  // retry list read this round
-    for (int pc = 0; pc < n_pieces; ++pc) {
-        // a piece ends with every hash staged or flushed: the stages go on
+    for (int pc = 0; pc < n_pieces; ++pc)
+    for (uint64_t c0 = 0; c0 < pieces[(size_t)pc * stride].len; c0 += kPieceMax) {
+        // a piece (at most kPieceMax hashes of it, 32-bit indices) ends with
+        // every hash staged or flushed: the stages go on
         const SegDesc sd = pieces[(size_t)pc * stride];
-        const uint64_t s0 = sd.off, len = sd.len;
+        const uint64_t* __restrict__ in = src + sd.off + c0;
+        const uint32_t len = (uint32_t)min(sd.len - c0, (uint64_t)kPieceMax);
         // thread t owns elements t, t + nt, t + 2 nt, ... of the segment, in order;
         // the next rows are always in flight while the current ones are staged
-        uint64_t next = threadIdx.x;
+        uint32_t next = threadIdx.x;
         uint64_t ph[kLinPerThread], nx[kLinPerThread];
         uint32_t pend = 0;  // bit e: ph[e] still to be staged
         uint32_t nval = 0;  // bit e: nx[e] loaded, not yet taken
-    #pragma unroll
+#pragma unroll
         for (int e = 0; e < kLinPerThread; ++e) {
             if (next < len) {
-                nx[e] = __ldcg(src + s0 + next);
+                nx[e] = __ldcg(in + next);
                 nval |= 1u << e;
             }
             next += blockDim.x;
@@ -379,7 +384,7 @@ __device__ __forceinline__ void scatter_segment(const uint64_t* __restrict__ src
             // the retry list first: a failure goes to the front of the other list
             for (unsigned i = threadIdx.x; i < n_in; i += blockDim.x) {
                 const uint64_t h = rin[i < n_front ? i : kRetryCap - 1 - (i - n_front)];
-                const uint32_t b = (uint32_t)(h >> shift) & (P - 1);
+                const uint32_t b = ((uint32_t)(h >> 32) >> shift) & (P - 1);
                 const uint32_t pos = atomicAdd(&fill[b], 1u);
                 if (pos < D) s_stage[(size_t)b * D + pos] = h;
                 else rout[atomicAdd(&s_front[par ^ 1], 1u)] = h;  // at most n_in of these
@@ -387,29 +392,29 @@ __device__ __forceinline__ void scatter_segment(const uint64_t* __restrict__ src
             // Warp-uniform: a warp takes its next rows only when none of its lanes
             // still holds a pending hash, so every load stays coalesced.
             if (__all_sync(kFull, pend == 0)) {
-    #pragma unroll
+#pragma unroll
                 for (int e = 0; e < kLinPerThread; ++e) {
                     ph[e] = nx[e];
-                    if (((nval >> e) & 1u) && (a1 == 0 || (uint32_t)(ph[e] >> (64 - a1)) == group)) pend |= 1u << e;
+                    if (((nval >> e) & 1u) && (a1 == 0 || ((uint32_t)(ph[e] >> 32) >> gshift) == group)) pend |= 1u << e;
                 }
                 nval = 0;
-    #pragma unroll
+#pragma unroll
                 for (int e = 0; e < kLinPerThread; ++e) {
                     if (next < len) {
-                        nx[e] = __ldcg(src + s0 + next);
+                        nx[e] = __ldcg(in + next);
                         nval |= 1u << e;
                     }
                     // the rows after these start their way into L2 now
-                    const uint64_t ahead = next + kLinPerThread * blockDim.x;
-                    if (ahead < len) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + s0 + ahead));
+                    const uint32_t ahead = next + kLinPerThread * blockDim.x;
+                    if (ahead < len) asm volatile("prefetch.global.L2 [%0];" ::"l"(in + ahead));
                     next += blockDim.x;
                 }
             }
-    #pragma unroll
+#pragma unroll
             for (int e = 0; e < kLinPerThread; ++e) {
                 if (pend & (1u << e)) {
                     const uint64_t h = ph[e];
-                    const uint32_t b = (uint32_t)(h >> shift) & (P - 1);
+                    const uint32_t b = ((uint32_t)(h >> 32) >> shift) & (P - 1);
                     const uint32_t pos = atomicAdd(&fill[b], 1u);
                     if (pos < D) {
                         s_stage[(size_t)b * D + pos] = h;
