@@ -992,6 +992,7 @@ void kc_destroy(kc_handle h) {
         if (h->bloom2) cudaFreeAsync(h->bloom2, h->stream);
         if (h->table) cudaFreeAsync(h->table, h->stream);
         if (h->ctr) cudaFreeAsync(h->ctr, h->stream);
+        if (h->chk_ctr) cudaFreeAsync(h->chk_ctr, h->copy_stream);
     }
     for (const auto& m : h->marks) {
         cudaEventDestroy(m.a);
@@ -1002,8 +1003,10 @@ void kc_destroy(kc_handle h) {
     if (h->ev_main) cudaEventDestroy(h->ev_main);
     for (cudaEvent_t e : h->ev_chunk)
         if (e) cudaEventDestroy(e);
-    if (h->chk_ctr) cudaFree(h->chk_ctr);
-    if (h->chk_host) cudaFreeHost(h->chk_host);
+    if (h->chk_host) {
+        std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
+        cudaFreeHost(h->chk_host);
+    }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -1033,13 +1036,18 @@ kc_status add_reads_chunked(kc_handle h, Batch& b, int sample, const uint64_t* p
         b.pw = b.vw = nullptr;
     };
     cudaError_t e = cudaSuccess;
-    if (!h->chk_ctr && (e = cudaMalloc(&h->chk_ctr, sizeof(kc::DevCounters))) != cudaSuccess) {
+    // the check's device counters (stream-ordered on the copy stream) and the
+    // pinned word its error bits come back to, both kept with the handle
+    if (!h->chk_ctr && (e = cudaMallocAsync(&h->chk_ctr, sizeof(kc::DevCounters), cs)) != cudaSuccess) {
         release();
-        return cuda_fail(e, "cudaMalloc(offsets check)");
+        return cuda_fail(e, "cudaMallocAsync(offsets check)");
     }
-    if (!h->chk_host && (e = cudaMallocHost(&h->chk_host, sizeof(unsigned))) != cudaSuccess) {
-        release();
-        return cuda_fail(e, "cudaMallocHost(offsets check)");
+    if (!h->chk_host) {
+        std::lock_guard<std::mutex> lk(kc::sync_api_mutex());  // pinning may synchronise the device
+        if ((e = cudaMallocHost(&h->chk_host, sizeof(unsigned))) != cudaSuccess) {
+            release();
+            return cuda_fail(e, "cudaMallocHost(offsets check)");
+        }
     }
     for (int c = 0; c <= n_chunks; ++c)
         if (!h->ev_chunk[c] && (e = cudaEventCreateWithFlags(&h->ev_chunk[c], cudaEventDisableTiming)) != cudaSuccess) {

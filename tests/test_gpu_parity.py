@@ -508,3 +508,28 @@ def test_chunked_host_copies_equal_oracle(oracle_mod):
     c.finalize()
     gk2, gc2 = c.dump()
     assert np.array_equal(gk2, ok) and np.array_equal(gc2, oc)
+
+
+def test_chunked_host_copies_owned_two_levels(oracle_mod):
+    """Chunked host copies with k = 31 (the compile-time-k extraction), two
+    grouping levels (14 partition bits) and hash-range owners (the ranged
+    extraction adding to its rows chunk by chunk): the owners' merged result
+    and OR-ed filters equal the oracle's."""
+    g = synth.genome(71, 300_000)
+    rs = synth.reads(71, g, 50_000, 120, 160, 0.01, 0.001)  # about 7 Mbases: chunked
+    w = synth.Workload("chunked-owned", [rs], k=31, bloom_bits=1 << 26, n_hashes=4, min_count=2)
+    o = oracle_mod.count(w)
+    ok, oc = o.result()
+    runs, bloom = [], np.zeros_like(o.bloom())
+    for r in range(2):
+        lo, hi = kc.owned_shards(r, 2, 3)
+        c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, strategy="partitioned", part_bits=14,
+                           own_bits=3, own_lo=lo, own_hi=hi)
+        c.add_readset(0, rs)
+        c.finalize()
+        runs.append(c.dump())
+        bloom |= c.export_bloom()
+        c.close()
+    keys, counts = kc.merge_results(runs, 1)
+    assert np.array_equal(keys, ok) and np.array_equal(counts, oc)
+    assert np.array_equal(bloom, o.bloom())
