@@ -423,12 +423,18 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
 
 /*
  * Add n_reads reads of one sample (0 <= sample < n_samples) in the packed
- * format above.  The library copies what it needs before returning, so the
- * caller may reuse its arrays at once; device work continues asynchronously
- * on the handle's stream.  Reads shorter than k add no windows.  Offsets that
- * decrease give KC_ERR_ARG (checked on the host for host offsets, on the
- * device for device offsets, where the error surfaces at kc_finalize).
- * Not allowed after kc_finalize (KC_ERR_STATE).
+ * format above.  The library copies what it needs: host arrays before
+ * returning, so the caller may reuse them at once; device arrays on the
+ * handle's stream, in order after the work already queued there, so the
+ * caller may reuse them once its own work is ordered after that stream
+ * (kc_finalize returns after it).  Device work continues asynchronously on
+ * the handle's stream.  Host reads of at least 2 x 2^15 units (64 bases
+ * each) are copied in up to four chunks, each extracted as it lands (Section
+ * III-A's overlapped transfer and GPU cycles).  Reads shorter than k add no
+ * windows.  Offsets that decrease give KC_ERR_ARG (checked before the call
+ * returns for host reads -- on the host, or for the chunked copies on the
+ * device -- and on the device for device reads, where the error surfaces at
+ * kc_finalize).  Not allowed after kc_finalize (KC_ERR_STATE).
  */
 kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, const uint64_t* offsets,
                        const uint64_t* n_mask, uint64_t n_reads);
