@@ -321,10 +321,15 @@ __global__ void k_plan_q(BatchDesc* __restrict__ D) {
     JobDesc* jobs = const_cast<JobDesc*>(D->jobs);
     uint64_t total = 0, flat = 0;
     int packable = 1;
+    bool short_arrays = false;
     for (uint32_t j = 0; j < D->n_jobs; ++j) {
         JobDesc& J = jobs[j];
         uint64_t nsv = D->counters[2 * j];
         if (nsv > J.sv_cap) nsv = J.sv_cap;
+        if (nsv > J.res_cap) {  // result arrays too short (a sort run ahead of the count): sort nothing
+            short_arrays = true;
+            nsv = 0;
+        }
         J.flat_base = flat;
         flat += nsv;
         if (nsv < 1) nsv = 1;
@@ -338,7 +343,7 @@ __global__ void k_plan_q(BatchDesc* __restrict__ D) {
     }
     D->all_packable = packable;
     D->n_flat = flat;
-    *D->err = 0u;
+    *D->err = short_arrays ? DERR_INTERNAL : 0u;
     if (total > D->buckets_cap) {
         atomicOr(D->err, DERR_INTERNAL);
         total = 0;
@@ -1170,6 +1175,28 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         return s;
     }
     KC_CUDA(cudaMemcpyAsync(b->d_item_job, b->item_job.data(), n_items * 4, cudaMemcpyHostToDevice, st));
+    // Whole jobs whose handles still hold result arrays from their last job:
+    // the sort graph runs right behind the consumer into those arrays, with
+    // bucket arrays for that many survivors, and one host round trip checks
+    // both (no partition left to the fallback, every job's survivors within
+    // its arrays); otherwise the sort runs again after the fallbacks, into
+    // arrays of the right size.
+    bool spec = fast;
+    for (int j = 0; j < n && spec; ++j) spec = hs[j]->res_keys != nullptr && hs[j]->res_cap > 0;
+    if (spec) {
+        uint64_t need = 0;
+        for (int j = 0; j < n; ++j) {
+            kc::JobDesc& J = b->jobs[j];
+            need += 1ull << sort_bits_for(std::min<uint64_t>(hs[j]->res_cap, J.sv_cap), J.key_bits);
+            J.res_keys = hs[j]->res_keys;
+            J.res_vals = hs[j]->res_vals;
+            J.res_cap = hs[j]->res_cap;
+        }
+        if ((s = ensure_buckets(b, need)) != KC_OK || (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK)) {
+            release_work(b, work);
+            return s;
+        }
+    }
     if ((s = upload_desc(b, (uint32_t)n, n_items, 0)) != KC_OK) {
         release_work(b, work);
         return s;
@@ -1191,12 +1218,19 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     cudaEvent_t t0 = timed ? phase_begin(hs[0], st) : nullptr;
     KC_CUDA(cudaGraphLaunch(cons, st));
     if (timed) phase_end(hs[0], kPass2, t0, st);
+    unsigned err = 0;
+    if (spec) {
+        t0 = timed ? phase_begin(hs[0], st) : nullptr;
+        KC_CUDA(cudaGraphLaunch(b->sort_graph, st));
+        if (timed) phase_end(hs[0], kSort, t0, st);
+        KC_CUDA(cudaMemcpyAsync(&err, b->d_flags + 1, 4, cudaMemcpyDeviceToHost, st));
+    }
     std::vector<unsigned long long> cnt(2 * (size_t)n);
     KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
     if (fast)
         for (int j = 0; j < n; ++j) KC_CUDA(cudaMemcpyAsync(&hc[j], hs[j]->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
     KC_CUDA(cudaStreamSynchronize(st));
-    for (int j = 0; j < n; ++j) work[j].h->launches += 2;
+    for (int j = 0; j < n; ++j) work[j].h->launches += spec ? 11 : 2;
     if (fast) {
         for (int j = 0; j < n; ++j) {
             hs[j]->host_ctr = hc[j];
@@ -1211,6 +1245,10 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     // partitions whose table overflowed (rare): counted in global tables
     bool any_fb = false;
     for (int j = 0; j < n; ++j) any_fb |= cnt[2 * j + 1] != 0;
+    bool sorted = spec && !any_fb && !(err & kc::DERR_INTERNAL);
+    for (int j = 0; j < n && sorted; ++j) sorted = std::min<uint64_t>(cnt[2 * j], b->jobs[j].sv_cap) <= hs[j]->res_cap;
+    if (sorted)
+        for (int j = 0; j < n; ++j) hs[j]->n_result = std::min<uint64_t>(cnt[2 * j], b->jobs[j].sv_cap);
     if (any_fb) {
         for (int j = 0; j < n; ++j) {
             if (!cnt[2 * j + 1]) continue;
@@ -1241,6 +1279,7 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     // sort: result arrays of each job's survivor count (a job's arrays are
     // kept for its next job when large enough), bucket arrays for as many
     // buckets as the plan will give; the plan itself runs on the device
+    if (!sorted) {
     uint64_t bucket_need = 0;
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
@@ -1272,10 +1311,10 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     t0 = timed ? phase_begin(hs[0], st) : nullptr;
     KC_CUDA(cudaGraphLaunch(b->sort_graph, st));
     if (timed) phase_end(hs[0], kSort, t0, st);
-    unsigned err = 0;
     KC_CUDA(cudaMemcpyAsync(&err, b->d_flags + 1, 4, cudaMemcpyDeviceToHost, st));
     KC_CUDA(cudaStreamSynchronize(st));
     for (int j = 0; j < n; ++j) work[j].h->launches += 9;
+    }  // !sorted
     if (err & kc::DERR_INTERNAL) {
         release_work(b, work);
         for (int j = 0; j < n; ++j) hs[j]->state = State::Poisoned;
