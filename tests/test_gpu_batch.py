@@ -217,3 +217,32 @@ def test_batch_ingest_then_finalize(oracle_mod):
     with pytest.raises(kc.KcError) as e:
         ext.ingest([counters[0], counters[0]])
     assert e.value.name == "KC_ERR_ARG"
+
+
+def test_kept_result_arrays_too_short_or_fallback(oracle_mod):
+    """A handle keeps its result arrays across kc_reset, and the next job's
+    sort runs right behind its consumer into them: a larger job finds them
+    too short and is sorted again into larger ones; a job whose partitions
+    overflow their tables (1024 slots) falls back after the early sort; a
+    smaller job fits.  Every result equals the oracle's."""
+    g = synth.genome(81, 150_000)
+    small = synth.reads(81, g, 2_000, 100, 150, 0.01, 0.001)
+    big = synth.reads(82, g, 20_000, 100, 150, 0.01, 0.001)
+    ws = [synth.Workload(n, [r], k=25, bloom_bits=1 << 22, n_hashes=4, min_count=2)
+          for n, r in (("small", small), ("big", big), ("small-again", small))]
+    c = kc.KmerCounter(25, 1, 1 << 22, 4, 2, strategy="partitioned")
+    for w in ws:
+        c.reset()
+        c.add_readset(0, w.samples[0])
+        c.finalize()
+        _check(c, oracle_mod.count(w))
+    # 2^18-bit filters in 4 partitions (slices of 1024 words), 1024-slot tables, no splits
+    wf = [synth.Workload(n, [r], k=25, bloom_bits=1 << 18, n_hashes=4, min_count=2)
+          for n, r in (("small", small), ("big", big))]
+    d = kc.KmerCounter(25, 1, 1 << 18, 4, 2, strategy="partitioned", part_bits=2, smem_table_log2=10, split_max=-1)
+    for w in wf:
+        d.reset()
+        d.add_readset(0, w.samples[0])
+        d.finalize()
+        _check(d, oracle_mod.count(w))
+    assert d.stats()["fallback_partitions"] > 0
