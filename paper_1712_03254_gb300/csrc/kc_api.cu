@@ -57,6 +57,18 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Memory the handle's kernels may read in place: device memory of its own
+// device, or managed memory (another GPU's memory is copied instead).
+bool is_local_device_ptr(const void* p, int device) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice && a.device == device) || a.type == cudaMemoryTypeManaged;
+}
+
 
 
 }  // namespace kcapi
@@ -1153,12 +1165,25 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     // inputs are copied on the handle's stream, after the work queued there.
     const bool any_host = !(data_dev && mask_dev && off_dev);
     cudaStream_t cs = any_host ? h->copy_stream : st;
+    // Host reads of a large partitioned batch are copied in chunks, each
+    // chunk's windows extracted as soon as it lands (ChunkedReads); the
+    // offsets go first and are checked on the device before anything touches
+    // the handle.
+    const int n_chunks = (int)std::min<uint64_t>(kMaxChunks, n_units / kChunkUnits);
+    const bool chunked = !data_dev && !mask_dev && n_chunks >= 2 && h->strategy != KC_STRATEGY_DIRECT &&
+                         !h->cfg.batched_ingest && scatter_mode_of(h) == 4 && bucket_bytes(h, n_local) <= room_bytes(h);
+    // The N mask and offsets serve this call's kernels only: device ones are
+    // read where they are (in stream order), host ones copied.  The packed
+    // words are always copied: the store is padded for the kernels' loads and
+    // may outlive the call.
+    const bool own_nm = chunked || !is_local_device_ptr(n_mask, h->device);
+    const bool own_off = chunked || !is_local_device_ptr(offsets, h->device);
     cudaError_t e;
     if ((e = cudaMallocAsync(&b.pw, n_pwords * 8, cs)) != cudaSuccess ||
         (e = cudaMallocAsync(&b.vw, n_units * 8, cs)) != cudaSuccess ||
-        (e = cudaMallocAsync(&nm, n_units * 8, cs)) != cudaSuccess ||
+        (own_nm && (e = cudaMallocAsync(&nm, n_units * 8, cs)) != cudaSuccess) ||
         (e = cudaMallocAsync(&bd, n_units * 8, cs)) != cudaSuccess ||
-        (e = cudaMallocAsync(&doff, (n_reads + 1) * 8, cs)) != cudaSuccess) {
+        (own_off && (e = cudaMallocAsync(&doff, (n_reads + 1) * 8, cs)) != cudaSuccess)) {
         cudaFreeAsync(b.pw, cs);
         cudaFreeAsync(b.vw, cs);
         cudaFreeAsync(nm, cs);
@@ -1166,13 +1191,7 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
         cudaFreeAsync(doff, cs);
         return cuda_fail(e, "cudaMallocAsync(read store)");
     }
-    // Host reads of a large partitioned batch are copied in chunks, each
-    // chunk's windows extracted as soon as it lands (ChunkedReads); the
-    // offsets go first and are checked on the device before anything touches
-    // the handle.
-    const int n_chunks = (int)std::min<uint64_t>(kMaxChunks, n_units / kChunkUnits);
-    if (!data_dev && !mask_dev && n_chunks >= 2 && h->strategy != KC_STRATEGY_DIRECT && !h->cfg.batched_ingest &&
-        scatter_mode_of(h) == 4 && bucket_bytes(h, n_local) <= room_bytes(h)) {
+    if (chunked) {
         s = add_reads_chunked(h, b, sample, packed_reads, offsets, n_mask, n_reads, b0, b1, n_chunks, nm, bd, doff);
         if (s != KC_OK) return s;
         h->batches.push_back(b);
@@ -1182,8 +1201,10 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     }
     KC_CUDA(cudaMemcpyAsync(b.pw, packed_reads + B / 32, n_pwords_src * 8, cudaMemcpyDefault, cs));
     KC_CUDA(cudaMemsetAsync(b.pw + n_pwords_src, 0, (n_pwords - n_pwords_src) * 8, cs));
-    KC_CUDA(cudaMemcpyAsync(nm, n_mask + B / 64, n_units * 8, cudaMemcpyDefault, cs));
-    KC_CUDA(cudaMemcpyAsync(doff, offsets, (n_reads + 1) * 8, cudaMemcpyDefault, cs));
+    if (own_nm) KC_CUDA(cudaMemcpyAsync(nm, n_mask + B / 64, n_units * 8, cudaMemcpyDefault, cs));
+    if (own_off) KC_CUDA(cudaMemcpyAsync(doff, offsets, (n_reads + 1) * 8, cudaMemcpyDefault, cs));
+    const uint64_t* nm_in = own_nm ? nm : n_mask + B / 64;
+    const uint64_t* off_in = own_off ? doff : offsets;
     if (!off_dev) {
         bool decreasing = false;
         for (uint64_t r = 0; r < n_reads && !decreasing; ++r) decreasing = offsets[r + 1] < offsets[r];
@@ -1199,8 +1220,8 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     }
     cudaEvent_t t0 = phase_begin(h);
     KC_CUDA(cudaMemsetAsync(bd, 0, n_units * 8, st));
-    kc::launch_mark_read_starts(doff, n_reads, B, n_local, bd, h->ctr, st);
-    kc::launch_build_valid(nm, bd, n_units, b0 - B, n_local, h->k, b.vw, h->ctr, h->grid, st);
+    kc::launch_mark_read_starts(off_in, n_reads, B, n_local, bd, h->ctr, st);
+    kc::launch_build_valid(nm_in, bd, n_units, b0 - B, n_local, h->k, b.vw, h->ctr, h->grid, st);
     phase_end(h, kIngest, t0);
     t0 = phase_begin(h);
     if (h->strategy == KC_STRATEGY_DIRECT) {
