@@ -1015,9 +1015,9 @@ void kc_destroy(kc_handle h) {
     if (h->ev_main) cudaEventDestroy(h->ev_main);
     for (cudaEvent_t e : h->ev_chunk)
         if (e) cudaEventDestroy(e);
-    if (h->chk_host) {
+    if (h->pinned) {
         std::lock_guard<std::mutex> lk(kc::sync_api_mutex());
-        cudaFreeHost(h->chk_host);
+        cudaFreeHost(h->pinned);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -1027,6 +1027,13 @@ void kc_destroy(kc_handle h) {
 }  // extern "C"
 
 namespace kcapi {
+
+// The handle's pinned readback words (8), allocated at first use.
+cudaError_t pinned_words(kc_handle h) {
+    if (h->pinned) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());  // pinning may synchronise the device
+    return cudaMallocHost(&h->pinned, 8 * sizeof(uint64_t));
+}
 
 // kc_add_reads of host reads in n_chunks chunks (the read store b.pw / b.vw
 // and the scratch nm, bd, doff are allocated on the copy stream; they are
@@ -1054,13 +1061,11 @@ kc_status add_reads_chunked(kc_handle h, Batch& b, int sample, const uint64_t* p
         release();
         return cuda_fail(e, "cudaMallocAsync(offsets check)");
     }
-    if (!h->chk_host) {
-        std::lock_guard<std::mutex> lk(kc::sync_api_mutex());  // pinning may synchronise the device
-        if ((e = cudaMallocHost(&h->chk_host, sizeof(unsigned))) != cudaSuccess) {
-            release();
-            return cuda_fail(e, "cudaMallocHost(offsets check)");
-        }
+    if ((e = pinned_words(h)) != cudaSuccess) {
+        release();
+        return cuda_fail(e, "cudaMallocHost(offsets check)");
     }
+    unsigned* chk_host = reinterpret_cast<unsigned*>(h->pinned);
     for (int c = 0; c <= n_chunks; ++c)
         if (!h->ev_chunk[c] && (e = cudaEventCreateWithFlags(&h->ev_chunk[c], cudaEventDisableTiming)) != cudaSuccess) {
             release();
@@ -1080,7 +1085,7 @@ kc_status add_reads_chunked(kc_handle h, Batch& b, int sample, const uint64_t* p
     KC_CUDA(cudaMemsetAsync(h->chk_ctr, 0, sizeof(kc::DevCounters), cs));
     KC_CUDA(cudaMemsetAsync(bd, 0, n_units * 8, cs));
     kc::launch_mark_read_starts(doff, n_reads, B, n_local, bd, h->chk_ctr, cs);
-    KC_CUDA(cudaMemcpyAsync(h->chk_host, &h->chk_ctr->err, sizeof(unsigned), cudaMemcpyDeviceToHost, cs));
+    KC_CUDA(cudaMemcpyAsync(chk_host, &h->chk_ctr->err, sizeof(unsigned), cudaMemcpyDeviceToHost, cs));
     KC_CUDA(cudaEventRecord(h->ev_chunk[n_chunks], cs));  // the check
     for (int c = 0; c < n_chunks; ++c) {
         const uint64_t u0 = ch.u[c], u1 = ch.u[c + 1];
@@ -1093,7 +1098,7 @@ kc_status add_reads_chunked(kc_handle h, Batch& b, int sample, const uint64_t* p
     }
     KC_LAUNCHED("offsets check launch");
     KC_CUDA(cudaEventSynchronize(h->ev_chunk[n_chunks]));
-    if (*h->chk_host & kc::DERR_OFFSETS) {
+    if (*chk_host & kc::DERR_OFFSETS) {
         KC_CUDA(cudaStreamSynchronize(cs));  // the caller's arrays are no longer read
         release();
         return fail(KC_ERR_ARG, "read offsets decrease");
@@ -1132,12 +1137,12 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     const bool off_dev = is_device_ptr(offsets);
     uint64_t b0, b1;
     if (off_dev) {
-        uint64_t ends[2];
-        KC_CUDA(cudaMemcpyAsync(&ends[0], offsets, 8, cudaMemcpyDeviceToHost, h->stream));
-        KC_CUDA(cudaMemcpyAsync(&ends[1], offsets + n_reads, 8, cudaMemcpyDeviceToHost, h->stream));
+        KC_CUDA(pinned_words(h));
+        KC_CUDA(cudaMemcpyAsync(h->pinned + 1, offsets, 8, cudaMemcpyDeviceToHost, h->stream));
+        KC_CUDA(cudaMemcpyAsync(h->pinned + 2, offsets + n_reads, 8, cudaMemcpyDeviceToHost, h->stream));
         KC_CUDA(cudaStreamSynchronize(h->stream));
-        b0 = ends[0];
-        b1 = ends[1];
+        b0 = h->pinned[1];
+        b1 = h->pinned[2];
     } else {
         // the full check of host offsets runs below, while the copies are in flight
         b0 = offsets[0];

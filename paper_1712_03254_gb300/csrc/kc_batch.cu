@@ -688,6 +688,10 @@ struct kc_batch_ctx {
     std::vector<kc::JobDesc> jobs;
     std::vector<uint32_t> item_job;
     uint64_t launches = 0;
+    // pinned host memory the finalize reads its counters back into (so the
+    // copies queue behind the kernels and one synchronisation waits for all)
+    unsigned char* h_read = nullptr;
+    size_t h_read_jobs = 0;
 };
 
 namespace {
@@ -722,6 +726,20 @@ kc_status ensure_jobs(kc_batch_ctx* b, size_t n_jobs, size_t n_items) {
     kc_status s = grow(b->d_item_job, cap, n_items);
     b->items_cap = cap;
     return s;
+}
+
+// Readback area for n jobs: the error word, then 2 n queue counters, then n
+// device-counter blocks.
+kc_status ensure_readback(kc_batch_ctx* b, size_t n) {
+    if (n <= b->h_read_jobs) return KC_OK;
+    const size_t m = std::max<size_t>(n, 2 * b->h_read_jobs);
+    std::lock_guard<std::mutex> lk(kc::sync_api_mutex());  // pinning may synchronise the device
+    if (b->h_read) cudaFreeHost(b->h_read);
+    b->h_read = nullptr;
+    b->h_read_jobs = 0;
+    KC_CUDA(cudaMallocHost(&b->h_read, 64 + m * (16 + sizeof(kc::DevCounters))));
+    b->h_read_jobs = m;
+    return KC_OK;
 }
 
 kc_status ensure_buckets(kc_batch_ctx* b, uint64_t n_buckets) {
@@ -1009,6 +1027,7 @@ void kc_batch_destroy_internal(kc_batch_ctx* b) {
     cudaFree(b->d_starts);
     cudaFree(b->d_cursor);
     cudaFree(b->d_tiles);
+    if (b->h_read) cudaFreeHost(b->h_read);
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
     delete b;
 }
@@ -1043,7 +1062,11 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     // is sized from the host's counts instead (bases and reads added), so no
     // host round trip sits between its grouping and its consumer; its ingest
     // errors are read after the consumer.
-    std::vector<kc::DevCounters> hc((size_t)n);
+    kc_status rs = ensure_readback(b, (size_t)n);
+    if (rs != KC_OK) return rs;
+    unsigned& err = *reinterpret_cast<unsigned*>(b->h_read);
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(b->h_read + 64);
+    kc::DevCounters* hc = reinterpret_cast<kc::DevCounters*>(b->h_read + 64 + 16 * (size_t)n);
     bool fast = true;
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
@@ -1218,15 +1241,14 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     cudaEvent_t t0 = timed ? phase_begin(hs[0], st) : nullptr;
     KC_CUDA(cudaGraphLaunch(cons, st));
     if (timed) phase_end(hs[0], kPass2, t0, st);
-    unsigned err = 0;
+    err = 0;
     if (spec) {
         t0 = timed ? phase_begin(hs[0], st) : nullptr;
         KC_CUDA(cudaGraphLaunch(b->sort_graph, st));
         if (timed) phase_end(hs[0], kSort, t0, st);
         KC_CUDA(cudaMemcpyAsync(&err, b->d_flags + 1, 4, cudaMemcpyDeviceToHost, st));
     }
-    std::vector<unsigned long long> cnt(2 * (size_t)n);
-    KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    KC_CUDA(cudaMemcpyAsync(cnt, b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
     if (fast)
         for (int j = 0; j < n; ++j) KC_CUDA(cudaMemcpyAsync(&hc[j], hs[j]->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
     KC_CUDA(cudaStreamSynchronize(st));
@@ -1264,7 +1286,7 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
             J.sv_vals = work[j].sv_vals;
             J.sv_cap = work[j].sv_cap;
         }
-        KC_CUDA(cudaMemcpyAsync(cnt.data(), b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+        KC_CUDA(cudaMemcpyAsync(cnt, b->d_counters, 2 * (size_t)n * 8, cudaMemcpyDeviceToHost, st));
         for (int j = 0; j < n; ++j) KC_CUDA(cudaMemcpyAsync(&hc[j], hs[j]->ctr, sizeof(kc::DevCounters), cudaMemcpyDeviceToHost, st));
         KC_CUDA(cudaStreamSynchronize(st));
         for (int j = 0; j < n; ++j) {

@@ -109,7 +109,9 @@ struct kc_ctx {
     // per chunk; a device word for the check's error bits and its pinned copy
     cudaEvent_t ev_chunk[kcapi::kMaxChunks + 1] = {};
     kc::DevCounters* chk_ctr = nullptr;
-    unsigned* chk_host = nullptr;
+    // pinned host words small readbacks land in ([0] the offsets check's
+    // error bits, [1..2] the first and last offset of device offsets)
+    uint64_t* pinned = nullptr;
     kc::Grid grid;
     int log2_words = 0, log2_slots = 0;
     uint64_t n_slots = 0;
