@@ -1041,7 +1041,7 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     std::vector<JobWork> work((size_t)n);
     const bool one = n == 1 && hs[0]->stream == st;  // no cross-stream ordering needed
     const bool timed = n == 1;                         // phase times go to the only handle
-    // order the batch after every handle's queued work
+    bool fast = true;  // every job whole: sized from host counts (below)
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
         if (!h) return fail(KC_ERR_ARG, "null handle in batch");
@@ -1050,11 +1050,23 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         if (h->strategy != KC_STRATEGY_PARTITIONED) return fail(KC_ERR_ARG, "batched finalize needs the partitioned strategy");
         for (int i = 0; i < j; ++i)
             if (hs[i] == h) return fail(KC_ERR_ARG, "handle listed twice");
-        if (!one) {
-            KC_CUDA(cudaEventRecord(h->ev_main, h->stream));
-            KC_CUDA(cudaStreamWaitEvent(st, h->ev_main, 0));
-        }
         work[j].h = h;
+        fast = fast && part_lo == 0 && part_hi >= (1u << h->part_bits) && !h->owner && !h->deferred;
+    }
+    // order the batch after every handle's queued work: at once when the
+    // setup reads the grouping back, else just before the consumer, so the
+    // setup's uploads queue while the handles' grouping still runs
+    const auto order_after_handles = [&]() -> kc_status {
+        if (!one)
+            for (int j = 0; j < n; ++j) {
+                KC_CUDA(cudaEventRecord(hs[j]->ev_main, hs[j]->stream));
+                KC_CUDA(cudaStreamWaitEvent(st, hs[j]->ev_main, 0));
+            }
+        return KC_OK;
+    };
+    if (!fast) {
+        kc_status os = order_after_handles();
+        if (os != KC_OK) return os;
     }
     // Partition sizes of every job, and each job's counters (ingest errors):
     // read back when the batch covers part of a job's partitions (spill
@@ -1067,11 +1079,6 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     unsigned& err = *reinterpret_cast<unsigned*>(b->h_read);
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(b->h_read + 64);
     kc::DevCounters* hc = reinterpret_cast<kc::DevCounters*>(b->h_read + 64 + 16 * (size_t)n);
-    bool fast = true;
-    for (int j = 0; j < n; ++j) {
-        kc_handle h = hs[j];
-        fast = fast && part_lo == 0 && part_hi >= (1u << h->part_bits) && !h->owner && !h->deferred;
-    }
     if (!fast) {
         for (int j = 0; j < n; ++j) {
             kc_handle h = hs[j];
@@ -1237,6 +1244,10 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         return s;
     }
 
+    if (fast && (s = order_after_handles()) != KC_OK) {
+        release_work(b, work);
+        return s;
+    }
     // consume: one persistent launch over the (job, partition) queue
     cudaEvent_t t0 = timed ? phase_begin(hs[0], st) : nullptr;
     KC_CUDA(cudaGraphLaunch(cons, st));
