@@ -1110,7 +1110,8 @@ kc_status add_reads_chunked(kc_handle h, Batch& b, int sample, const uint64_t* p
     phase_end(h, kPass1, t0);
     if (s != KC_OK) {
         KC_CUDA(cudaStreamSynchronize(cs));
-        for (void* q : {(void*)nm, (void*)bd, (void*)doff}) cudaFreeAsync(q, st);
+        for (void* q : {(void*)nm, (void*)bd, (void*)doff, (void*)b.pw, (void*)b.vw}) cudaFreeAsync(q, st);
+        b.pw = b.vw = nullptr;
         return s;
     }
     h->launches += 4;
@@ -1247,9 +1248,8 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     } else {
         s = bucket_batch(h, b, n_local, st, h->params(sample), false);
         if (s != KC_OK) {
-            cudaFreeAsync(nm, st);
-            cudaFreeAsync(bd, st);
-            cudaFreeAsync(doff, st);
+            for (void* q : {(void*)nm, (void*)bd, (void*)doff, (void*)b.pw, (void*)b.vw}) cudaFreeAsync(q, st);
+            if (any_host) cudaEventSynchronize(h->ev_copy);  // the caller's arrays are no longer read
             return s;
         }
         h->launches += 2;
