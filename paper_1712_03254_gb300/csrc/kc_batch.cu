@@ -46,6 +46,12 @@ struct JobDesc {
     uint64_t* res_vals;
     uint64_t res_cap;
     uint64_t flat_base;  // this job's first survivor in the batch's survivors, in job order (set by the plan)
+    // survivors histogrammed by the consumer itself (the sort's bucket bits
+    // fixed before it runs): fixed_bits >= 0, hist_job = the job's first
+    // bucket counter, hist_shift = key_bits - fixed_bits; else fixed_bits = -1
+    int fixed_bits;
+    int hist_shift;
+    uint32_t* hist_job;
 };
 
 struct BatchDesc {
@@ -65,6 +71,7 @@ struct BatchDesc {
     uint64_t buckets_cap;  // room of hist / starts / cursor
     int all_packable;      // set by the plan: every job's small buckets sort packed (k_warp_sort_q)
     uint64_t n_flat;       // set by the plan: survivors of all jobs
+    int hist_early;        // the consumer has histogrammed the survivors: the sort does not
 };
 
 namespace {
@@ -276,8 +283,10 @@ __global__ void __launch_bounds__(kConsumeThreads, 2) k_consume_q(const BatchDes
                     if (keep) {
                         const uint64_t pos = pos0 + __popc(ballot & lt);
                         if (pos < J.sv_cap) {
-                            J.sv_keys[pos] = unmixer64(k1);
+                            const uint64_t key = unmixer64(k1);
+                            J.sv_keys[pos] = key;
                             J.sv_vals[pos] = v;
+                            if (J.hist_job) atomicAdd(J.hist_job + (key >> J.hist_shift), 1u);
                         }
                     }
                 }
@@ -334,7 +343,9 @@ __global__ void k_plan_q(BatchDesc* __restrict__ D) {
         flat += nsv;
         if (nsv < 1) nsv = 1;
         int bits = 0;
-        while (bits < 24 && bits < J.key_bits && (nsv >> bits) > 32) ++bits;
+        if (J.fixed_bits >= 0) bits = J.fixed_bits;  // the consumer's histogram has these buckets
+        else
+            while (bits < 24 && bits < J.key_bits && (nsv >> bits) > 32) ++bits;
         J.sort_bits = bits;
         J.bucket_base = total;
         J.n_buckets = 1ull << bits;
@@ -342,16 +353,20 @@ __global__ void k_plan_q(BatchDesc* __restrict__ D) {
         if (J.key_bits - bits > 58) packable = 0;
     }
     D->all_packable = packable;
-    D->n_flat = flat;
+    // short result arrays: no bucket and no survivor is sorted at all (a
+    // histogram the consumer took may count that job's survivors), and the
+    // host sorts again into larger arrays
+    D->n_flat = short_arrays ? 0 : flat;
     *D->err = short_arrays ? DERR_INTERNAL : 0u;
     if (total > D->buckets_cap) {
         atomicOr(D->err, DERR_INTERNAL);
         total = 0;
     }
-    D->n_buckets = total;
+    D->n_buckets = short_arrays ? 0 : total;
 }
 
 __global__ void k_zero_hist_q(const BatchDesc* __restrict__ D) {
+    if (D->hist_early) return;  // counted by the consumer
     const uint64_t n = D->n_buckets;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) D->hist[i] = 0u;
@@ -403,6 +418,7 @@ struct SurvivorJob {
 // The survivors of all jobs as one flat range: every thread takes survivors
 // across job boundaries, so one job or many keep the whole grid busy.
 __global__ void k_prefix_hist_q(const BatchDesc* __restrict__ D) {
+    if (D->hist_early) return;  // counted by the consumer
     const uint64_t n = D->n_flat;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -791,8 +807,9 @@ kc_status capture_sort_graph(kc_batch_ctx* b) {
     return KC_OK;
 }
 
-kc_status upload_desc(kc_batch_ctx* b, uint32_t n_jobs, uint32_t n_items, uint64_t n_buckets) {
+kc_status upload_desc(kc_batch_ctx* b, uint32_t n_jobs, uint32_t n_items, uint64_t n_buckets, int hist_early = 0) {
     kc::BatchDesc d{};
+    d.hist_early = hist_early;
     d.buckets_cap = b->buckets_cap;
     d.jobs = b->d_jobs;
     d.item_job = b->d_item_job;
@@ -1184,6 +1201,8 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         J.key_bits = 2 * h->k;
         J.min_count = h->min_count;
         J.split_max = split_max;
+        J.fixed_bits = -1;  // the plan chooses the bucket bits (unless set below)
+        J.hist_job = nullptr;
         J.n_batches = (int)nb;
         J.item_base = (uint32_t)b->item_job.size();
         J.part_base = (uint32_t)p_lo;
@@ -1211,23 +1230,34 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     // both (no partition left to the fallback, every job's survivors within
     // its arrays); otherwise the sort runs again after the fallbacks, into
     // arrays of the right size.
+    // The bucket bits are then fixed in advance (for the kept arrays' size),
+    // so the consumer histograms the survivors as it writes them and the sort
+    // graph skips its histogram pass.
     bool spec = fast;
     for (int j = 0; j < n && spec; ++j) spec = hs[j]->res_keys != nullptr && hs[j]->res_cap > 0;
+    uint64_t spec_buckets = 0;
     if (spec) {
-        uint64_t need = 0;
         for (int j = 0; j < n; ++j) {
             kc::JobDesc& J = b->jobs[j];
-            need += 1ull << sort_bits_for(std::min<uint64_t>(hs[j]->res_cap, J.sv_cap), J.key_bits);
+            J.fixed_bits = sort_bits_for(std::min<uint64_t>(hs[j]->res_cap, J.sv_cap), J.key_bits);
+            J.hist_shift = J.key_bits - J.fixed_bits;
+            spec_buckets += 1ull << J.fixed_bits;
             J.res_keys = hs[j]->res_keys;
             J.res_vals = hs[j]->res_vals;
             J.res_cap = hs[j]->res_cap;
         }
-        if ((s = ensure_buckets(b, need)) != KC_OK || (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK)) {
+        if ((s = ensure_buckets(b, spec_buckets)) != KC_OK || (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK)) {
             release_work(b, work);
             return s;
         }
+        uint64_t first = 0;  // the plan gives the jobs their buckets in this order
+        for (int j = 0; j < n; ++j) {
+            b->jobs[j].hist_job = b->d_hist + first;
+            first += 1ull << b->jobs[j].fixed_bits;
+        }
+        KC_CUDA(cudaMemsetAsync(b->d_hist, 0, spec_buckets * 4, st));
     }
-    if ((s = upload_desc(b, (uint32_t)n, n_items, 0)) != KC_OK) {
+    if ((s = upload_desc(b, (uint32_t)n, n_items, 0, spec ? 1 : 0)) != KC_OK) {
         release_work(b, work);
         return s;
     }
@@ -1313,6 +1343,10 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
     // kept for its next job when large enough), bucket arrays for as many
     // buckets as the plan will give; the plan itself runs on the device
     if (!sorted) {
+    for (int j = 0; j < n; ++j) {  // the plan chooses the bits and the sort histograms again
+        b->jobs[j].fixed_bits = -1;
+        b->jobs[j].hist_job = nullptr;
+    }
     uint64_t bucket_need = 0;
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
