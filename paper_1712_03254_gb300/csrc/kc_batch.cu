@@ -72,6 +72,10 @@ struct BatchDesc {
     int all_packable;      // set by the plan: every job's small buckets sort packed (k_warp_sort_q)
     uint64_t n_flat;       // set by the plan: survivors of all jobs
     int hist_early;        // the consumer has histogrammed the survivors: the sort does not
+    // the survivors scattered into their buckets, (key, value) side by side in
+    // the flat bucket order of all jobs; the bucket sorts write the results
+    ulonglong2* pairs;
+    uint64_t pairs_cap;
 };
 
 namespace {
@@ -534,13 +538,12 @@ __global__ void k_scatter_q(const BatchDesc* __restrict__ D) {
             atomicOr(D->err, DERR_INTERNAL);
             continue;
         }
-        const uint64_t pos = atomicAdd(reinterpret_cast<unsigned long long*>(D->cursor) + S.bucket_base + b, 1ull) - job0;
-        if (pos >= S.res_cap) {
+        const uint64_t gpos = atomicAdd(reinterpret_cast<unsigned long long*>(D->cursor) + S.bucket_base + b, 1ull);
+        if (gpos - job0 >= S.res_cap || gpos >= D->pairs_cap) {
             atomicOr(D->err, DERR_INTERNAL);
             continue;
         }
-        S.res_keys[pos] = key;
-        S.res_vals[pos] = val;
+        D->pairs[gpos] = make_ulonglong2(key, val);  // one 16-byte store
     }
 }
 
@@ -566,15 +569,46 @@ __global__ void __launch_bounds__(256, 6) k_warp_sort_q(const BatchDesc* __restr
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nb = D->n_buckets;
-    if (!D->all_packable) return;  // every bucket goes to k_warp_sort_big_q
+    const bool packable = D->all_packable != 0;
     for (uint64_t fb = warp; fb < nb; fb += n_warps) {
-        const uint64_t n64 = D->starts[fb + 1] - D->starts[fb];
-        if (n64 <= 1 || n64 > 64) continue;  // larger ones: k_warp_sort_big_q
+        const uint64_t g0 = D->starts[fb], n64 = D->starts[fb + 1] - g0;
+        if (n64 == 0) continue;
         const JobDesc& J = D->jobs[job_of_bucket(D, fb)];
+        const uint64_t lo = g0 - D->starts[J.bucket_base];
+        const ulonglong2* __restrict__ src = D->pairs + g0;
+        if (!packable || n64 == 1 || n64 > 64) {
+            // one key, or sorted later in place (k_warp_sort_big_q): the pairs
+            // into the result arrays as they are
+            for (uint64_t i = lane; i < n64; i += 32) {
+                const ulonglong2 q = src[i];
+                J.res_keys[lo + i] = q.x;
+                J.res_vals[lo + i] = q.y;
+            }
+            continue;
+        }
         const int shift = J.key_bits - J.sort_bits;  // the bucket's keys share the bits above shift (<= 58)
-        const uint64_t lo = D->starts[fb] - D->starts[J.bucket_base];
-        if (n64 <= 32) warp_sort32_packed(J.res_keys, J.res_vals, lo, (int)n64, lane, shift);
-        else warp_sort64_packed(J.res_keys, J.res_vals, lo, (int)n64, lane, shift);
+        if (n64 <= 32) {
+            const bool in = lane < (int)n64;
+            const ulonglong2 q = in ? src[lane] : make_ulonglong2(0ull, 0ull);
+            uint64_t k = q.x, v = q.y;
+            warp_sort32_core(k, v, in, lane, shift);
+            if (in) {
+                J.res_keys[lo + lane] = k;
+                J.res_vals[lo + lane] = v;
+            }
+        } else {
+            const bool in1 = 32 + lane < (int)n64;
+            const ulonglong2 q0 = src[lane];
+            const ulonglong2 q1 = in1 ? src[32 + lane] : make_ulonglong2(0ull, 0ull);
+            uint64_t k0 = q0.x, v0 = q0.y, k1 = q1.x, v1 = q1.y;
+            warp_sort64_core(k0, v0, k1, v1, true, in1, lane, shift);
+            J.res_keys[lo + lane] = k0;
+            J.res_vals[lo + lane] = v0;
+            if (in1) {
+                J.res_keys[lo + 32 + lane] = k1;
+                J.res_vals[lo + 32 + lane] = v1;
+            }
+        }
     }
 }
 
@@ -708,6 +742,9 @@ struct kc_batch_ctx {
     // copies queue behind the kernels and one synchronisation waits for all)
     unsigned char* h_read = nullptr;
     size_t h_read_jobs = 0;
+    // the scattered survivors of a batch, (key, value) pairs
+    ulonglong2* d_pairs = nullptr;
+    size_t pairs_cap = 0;
 };
 
 namespace {
@@ -810,6 +847,8 @@ kc_status capture_sort_graph(kc_batch_ctx* b) {
 kc_status upload_desc(kc_batch_ctx* b, uint32_t n_jobs, uint32_t n_items, uint64_t n_buckets, int hist_early = 0) {
     kc::BatchDesc d{};
     d.hist_early = hist_early;
+    d.pairs = b->d_pairs;
+    d.pairs_cap = b->pairs_cap;
     d.buckets_cap = b->buckets_cap;
     d.jobs = b->d_jobs;
     d.item_job = b->d_item_job;
@@ -1045,6 +1084,7 @@ void kc_batch_destroy_internal(kc_batch_ctx* b) {
     cudaFree(b->d_cursor);
     cudaFree(b->d_tiles);
     if (b->h_read) cudaFreeHost(b->h_read);
+    cudaFree(b->d_pairs);
     if (b->own_stream && b->st) cudaStreamDestroy(b->st);
     delete b;
 }
@@ -1246,7 +1286,10 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
             J.res_vals = hs[j]->res_vals;
             J.res_cap = hs[j]->res_cap;
         }
-        if ((s = ensure_buckets(b, spec_buckets)) != KC_OK || (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK)) {
+        uint64_t spec_pairs = 0;
+        for (int j = 0; j < n; ++j) spec_pairs += hs[j]->res_cap;
+        if ((s = ensure_buckets(b, spec_buckets)) != KC_OK || (s = grow(b->d_pairs, b->pairs_cap, spec_pairs)) != KC_OK ||
+            (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK)) {
             release_work(b, work);
             return s;
         }
@@ -1347,12 +1390,13 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         b->jobs[j].fixed_bits = -1;
         b->jobs[j].hist_job = nullptr;
     }
-    uint64_t bucket_need = 0;
+    uint64_t bucket_need = 0, pairs_need = 0;
     for (int j = 0; j < n; ++j) {
         kc_handle h = hs[j];
         kc::JobDesc& J = b->jobs[j];
         const uint64_t nsv = std::min<uint64_t>(cnt[2 * j], J.sv_cap);
         bucket_need += 1ull << sort_bits_for(nsv, J.key_bits);
+        pairs_need += nsv;
         const uint64_t cap = std::max<uint64_t>(1, nsv);
         if (!h->res_keys || h->res_cap < cap) {
             free_result(h);
@@ -1370,7 +1414,9 @@ kc_status finalize_core(kc_batch_ctx* b, kc_handle* hs, int n, uint32_t part_lo,
         J.res_vals = h->res_vals;
         J.res_cap = h->res_cap;
     }
-    if ((s = ensure_buckets(b, bucket_need)) != KC_OK || (s = upload_desc(b, (uint32_t)n, n_items, 0)) != KC_OK ||
+    if ((s = ensure_buckets(b, bucket_need)) != KC_OK ||
+        (s = grow(b->d_pairs, b->pairs_cap, std::max<uint64_t>(1, pairs_need))) != KC_OK ||
+        (s = upload_desc(b, (uint32_t)n, n_items, 0)) != KC_OK ||
         (!b->sort_graph && (s = capture_sort_graph(b)) != KC_OK)) {
         release_work(b, work);
         return s;

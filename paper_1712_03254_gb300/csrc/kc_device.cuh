@@ -302,17 +302,14 @@ __device__ __forceinline__ void warp_sort_bucket(uint64_t* __restrict__ keys, ui
 }
 
 // Warp sort of a bucket of n <= 32 (key, value) pairs whose keys all share
-// the bits above bit `shift` (shift <= 59: the bucket is a key-prefix range).
-// Each lane packs its key's low `shift` bits with its lane index into one
-// word, the bitonic network exchanges that single word (the lane index
-// breaks ties between equal keys), and each value then follows its key
-// through the lane index.  Lanes >= n hold ~0, which sorts last (a packed word equals
-// ~0 only at lane 31, i.e. when n = 32 and no lane is empty).
-__device__ __forceinline__ void warp_sort32_packed(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
-                                                   uint64_t lo, int n, int lane, int shift) {
-    const bool in = lane < n;
-    const uint64_t k = in ? keys[lo + lane] : 0ull;
-    const uint64_t v = in ? vals[lo + lane] : 0ull;
+// the bits above bit `shift` (shift <= 59: the bucket is a key-prefix range),
+// one pair per lane (k, v; in = lane < n).  Each lane packs its key's low
+// `shift` bits with its lane index into one word, the bitonic network
+// exchanges that single word (the lane index breaks ties between equal keys),
+// and each value then follows its key through the lane index.  Lanes >= n
+// hold ~0, which sorts last (a packed word equals ~0 only at lane 31, i.e.
+// when n = 32 and no lane is empty).  On return lane i holds the i-th pair.
+__device__ __forceinline__ void warp_sort32_core(uint64_t& k, uint64_t& v, bool in, int lane, int shift) {
     const uint64_t low_mask = (1ull << shift) - 1ull;
     uint64_t p = in ? (((k & low_mask) << 5) | (uint64_t)lane) : ~0ull;
 #pragma unroll
@@ -326,22 +323,29 @@ __device__ __forceinline__ void warp_sort32_packed(uint64_t* __restrict__ keys, 
             p = take ? o : p;
         }
     }
-    const uint64_t vs = __shfl_sync(0xffffffffu, v, (int)(p & 31ull));
+    v = __shfl_sync(0xffffffffu, v, (int)(p & 31ull));
+    k = (k & ~low_mask) | (p >> 5);
+}
+
+__device__ __forceinline__ void warp_sort32_packed(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
+                                                   uint64_t lo, int n, int lane, int shift) {
+    const bool in = lane < n;
+    uint64_t k = in ? keys[lo + lane] : 0ull;
+    uint64_t v = in ? vals[lo + lane] : 0ull;
+    warp_sort32_core(k, v, in, lane, shift);
     if (in) {
-        keys[lo + lane] = (k & ~low_mask) | (p >> 5);
-        vals[lo + lane] = vs;
+        keys[lo + lane] = k;
+        vals[lo + lane] = v;
     }
 }
 
 // The same for 33..64 pairs (shift <= 58): two packed words per lane, element
-// i = 32 r + lane in register r; 6 index bits.  Compare-exchanges across the
-// two registers of a lane (stride 32) need no shuffle.
-__device__ __forceinline__ void warp_sort64_packed(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
-                                                   uint64_t lo, int n, int lane, int shift) {
+// i = 32 r + lane in register r (k0, v0: element lane; k1, v1: element 32 +
+// lane; n > 32, so lane 0 holds a key); 6 index bits.  Compare-exchanges
+// across the two registers of a lane (stride 32) need no shuffle.
+__device__ __forceinline__ void warp_sort64_core(uint64_t& k0, uint64_t& v0, uint64_t& k1, uint64_t& v1, bool in0,
+                                                 bool in1, int lane, int shift) {
     const uint64_t low_mask = (1ull << shift) - 1ull;
-    const bool in0 = lane < n, in1 = 32 + lane < n;
-    const uint64_t k0 = in0 ? keys[lo + lane] : 0ull, v0 = in0 ? vals[lo + lane] : 0ull;
-    const uint64_t k1 = in1 ? keys[lo + 32 + lane] : 0ull, v1 = in1 ? vals[lo + 32 + lane] : 0ull;
     uint64_t p0 = in0 ? (((k0 & low_mask) << 6) | (uint64_t)lane) : ~0ull;
     uint64_t p1 = in1 ? (((k1 & low_mask) << 6) | (uint64_t)(32 + lane)) : ~0ull;
 #pragma unroll
@@ -367,14 +371,26 @@ __device__ __forceinline__ void warp_sort64_packed(uint64_t* __restrict__ keys, 
     const int i0 = (int)(p0 & 63ull), i1 = (int)(p1 & 63ull);
     const uint64_t a0 = __shfl_sync(0xffffffffu, v0, i0 & 31), b0 = __shfl_sync(0xffffffffu, v1, i0 & 31);
     const uint64_t a1 = __shfl_sync(0xffffffffu, v0, i1 & 31), b1 = __shfl_sync(0xffffffffu, v1, i1 & 31);
-    const uint64_t prefix = __shfl_sync(0xffffffffu, k0, 0) & ~low_mask;  // lane 0 holds a key: n > 32
+    const uint64_t prefix = __shfl_sync(0xffffffffu, k0, 0) & ~low_mask;
+    k0 = prefix | (p0 >> 6);
+    v0 = (i0 >> 5) ? b0 : a0;
+    k1 = prefix | (p1 >> 6);
+    v1 = (i1 >> 5) ? b1 : a1;
+}
+
+__device__ __forceinline__ void warp_sort64_packed(uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
+                                                   uint64_t lo, int n, int lane, int shift) {
+    const bool in0 = lane < n, in1 = 32 + lane < n;
+    uint64_t k0 = in0 ? keys[lo + lane] : 0ull, v0 = in0 ? vals[lo + lane] : 0ull;
+    uint64_t k1 = in1 ? keys[lo + 32 + lane] : 0ull, v1 = in1 ? vals[lo + 32 + lane] : 0ull;
+    warp_sort64_core(k0, v0, k1, v1, in0, in1, lane, shift);
     if (in0) {
-        keys[lo + lane] = prefix | (p0 >> 6);
-        vals[lo + lane] = (i0 >> 5) ? b0 : a0;
+        keys[lo + lane] = k0;
+        vals[lo + lane] = v0;
     }
     if (in1) {
-        keys[lo + 32 + lane] = prefix | (p1 >> 6);
-        vals[lo + 32 + lane] = (i1 >> 5) ? b1 : a1;
+        keys[lo + 32 + lane] = k1;
+        vals[lo + 32 + lane] = v1;
     }
 }
 
