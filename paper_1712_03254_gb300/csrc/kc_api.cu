@@ -57,6 +57,20 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Pinned host memory the device can write (its device-side address in *dev):
+// a kernel writes such memory directly, over the host link.
+bool host_mapped(const void* p, void** dev) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dev = a.devicePointer;
+    return true;
+}
+
 // Memory the handle's kernels may read in place: device memory of its own
 // device, or managed memory (another GPU's memory is copied instead).
 bool is_local_device_ptr(const void* p, int device) {
@@ -1320,8 +1334,19 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
         if (dev_k || dev_c) KC_CUDA(cudaStreamSynchronize(st));  // the staging buffers go out of scope
         return KC_OK;
     }
+    // pinned host counts of one sample: narrowed straight into them by a
+    // kernel on the copy stream (over the host link), while the keys' copy
+    // runs on the handle's stream
+    void* dc = nullptr;
+    const bool counts_mapped = counts && h->n_samples == 1 && !is_device_ptr(counts) && host_mapped(counts, &dc);
+    if (counts_mapped) {
+        KC_CUDA(cudaEventRecord(h->ev_copy, st));
+        KC_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_copy, 0));
+        kc::launch_counts_narrow(h->res_vals, h->n_result, static_cast<uint32_t*>(dc), h->copy_stream);
+        h->launches += 1;
+    }
     KC_CUDA(cudaMemcpyAsync(keys, h->res_keys, h->n_result * 8, cudaMemcpyDefault, st));
-    if (counts) {
+    if (counts && !counts_mapped) {
         if (h->n_samples == 2) {
             KC_CUDA(cudaMemcpyAsync(counts, h->res_vals, h->n_result * 8, cudaMemcpyDefault, st));
         } else if (is_device_ptr(counts)) {  // narrowed straight into the caller's device buffer
@@ -1336,7 +1361,9 @@ kc_status kc_dump(kc_handle h, uint64_t* keys, uint32_t* counts, uint64_t capaci
             cudaFreeAsync(narrow, st);
         }
     }
+    KC_LAUNCHED("dump launches");
     KC_CUDA(cudaStreamSynchronize(st));
+    if (counts_mapped) KC_CUDA(cudaStreamSynchronize(h->copy_stream));
     return KC_OK;
 }
 

@@ -533,3 +533,30 @@ def test_chunked_host_copies_owned_two_levels(oracle_mod):
     keys, counts = kc.merge_results(runs, 1)
     assert np.array_equal(keys, ok) and np.array_equal(counts, oc)
     assert np.array_equal(bloom, o.bloom())
+
+
+def test_dump_into_pinned_host_buffers(oracle_mod):
+    """kc_dump into pinned host buffers (the counts narrowed straight into
+    them by a kernel while the keys are copied) gives the oracle's result;
+    one sample and two."""
+    torch = pytest.importorskip("torch")
+    w = synth.tiny(scale=0.5)
+    o = oracle_mod.count(w)
+    ok, oc = o.result()
+    c = gpu_count(w, strategy="partitioned")
+    n = c.result_size()
+    keys = torch.empty(n, dtype=torch.int64).pin_memory()
+    counts = torch.empty((n, 1), dtype=torch.int32).pin_memory()
+    c.dump(keys, counts)
+    assert np.array_equal(keys.numpy().view(np.uint64), ok)
+    assert np.array_equal(counts.numpy().view(np.uint32), oc)
+    w2 = synth.paired(scale=0.002)
+    o2 = oracle_mod.count(w2)
+    c2 = gpu_count(w2, strategy="partitioned")
+    n2 = c2.result_size()
+    k2 = torch.empty(n2, dtype=torch.int64).pin_memory()
+    n2c = torch.empty((n2, 2), dtype=torch.int32).pin_memory()
+    c2.dump(k2, n2c)
+    ok2, oc2 = o2.result()
+    assert np.array_equal(k2.numpy().view(np.uint64), ok2)
+    assert np.array_equal(n2c.numpy().view(np.uint32), oc2)
