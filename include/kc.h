@@ -200,8 +200,9 @@ typedef struct kc_stats {
     uint64_t launches;        /* kernels launched since create / reset           */
     /* Device time per phase since create / reset, from CUDA events on the
      * handle's stream (zero unless kc_config.timing = 1; complete after
-     * kc_finalize): ingest = read-start and valid-window bits; sort = key-
-     * prefix bucketing and bucket sorts.  DIRECT: pass1 = filter update and
+     * kc_finalize): ingest = read-start and valid-window bits (host reads
+     * copied in chunks: their valid bits are built with each chunk's
+     * extraction, inside pass1); sort = key-prefix bucketing and bucket sorts.  DIRECT: pass1 = filter update and
      * candidate claims, pass2 = exact recount, compact = survivor compaction.
      * PARTITIONED: pass1 = hash bucketing (count and scatter), pass2 = the
      * shared-memory partition consumer (filter, claims, recount, compaction),
