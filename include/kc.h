@@ -629,9 +629,9 @@ const char* kc_status_string(kc_status s);
  * KC_NOALLOC_MAX_BASES bases from offsets[0] rounded down to a multiple of 64
  * to offsets[n_reads]; larger sets give KC_ERR_CAPACITY.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture.  All calls
- * share the array and each clears the parts that must start at zero, so calls
- * whose device work overlaps (other streams or host threads) race: order them.
+ * device current).  All calls share the array and each clears the parts that
+ * must start at zero, so calls whose device work overlaps (other streams or
+ * host threads) race: order them.
  * Errors are reported by the status and kc_last_error().
  */
 #define KC_NOALLOC_MAX_BASES (1ull << 23)
