@@ -1050,8 +1050,8 @@ cudaError_t pinned_words(kc_handle h) {
 }
 
 // kc_add_reads of host reads in n_chunks chunks (the read store b.pw / b.vw
-// and the scratch nm, bd, doff are allocated on the copy stream; they are
-// freed here, b.pw / b.vw unless kept).  On the copy stream: the offsets,
+// and the scratch nm, bd, doff are allocated on the copy stream; all are
+// freed here, the grouped hashes replacing the reads).  On the copy stream: the offsets,
 // their check (read starts marked into bd, error bits into chk_ctr), then
 // each chunk's packed and N-mask words.  On the handle's stream, after the
 // check: per chunk its valid-window bits and extraction, then the grouping.
