@@ -810,6 +810,39 @@ kc_status resort_spilled(kc_handle h) {
     return KC_OK;
 }
 
+// 2^pb partitions: the grouping levels, the filter slice of a partition and
+// an owner's partition range follow.
+void set_partitions(kc_handle h, int pb) {
+    h->part_bits = pb;
+    h->l1_bits = pb <= 12 ? pb : pb - 12;
+    h->slice_log2 = h->log2_words - pb;
+    h->own_plo = 0;
+    h->own_phi = h->strategy == KC_STRATEGY_PARTITIONED ? (1u << pb) : 0u;
+    if (h->owner) {
+        const int ob = (int)h->cfg.own_bits;
+        const uint64_t hi = h->cfg.own_hi ? h->cfg.own_hi : (1ull << ob);
+        h->own_plo = h->cfg.own_lo << (pb - ob);
+        h->own_phi = (uint32_t)(hi << (pb - ob));
+    }
+}
+
+// Partition bits chosen by the library (kc_config.part_bits = 0): at the
+// first kc_add_reads after create / reset, enough partitions, up to 2^12 (one
+// grouping level), for at most kWindowsPerPartition windows each, estimated
+// as bases - reads * (k - 1) of this call; never fewer than the filter's own
+// (slices of 4096 words).  The consumer counts a partition's windows in one
+// pass over its hashes while they number at most its threads * 64, and a
+// partition of fewer windows holds fewer keys in its shared-memory table.
+void choose_partitions(kc_handle h, uint64_t bases, uint64_t n_reads) {
+    if (!h->auto_part || !h->batches.empty()) return;
+    const uint64_t edge = n_reads * (uint64_t)(h->k - 1);
+    const uint64_t est = bases > edge ? bases - edge : 0;
+    int want = 0;
+    while (want < 12 && (est >> want) > kWindowsPerPartition) ++want;
+    const int pb = std::max(h->base_part_bits, std::min(want, h->log2_words));
+    if (pb != h->part_bits) set_partitions(h, pb);
+}
+
 }  // namespace kcapi
 
 using namespace kcapi;
@@ -906,21 +939,17 @@ kc_status kc_create_ex(int k, int n_samples, uint64_t bloom_bits, int n_hashes, 
     h->cfg = c;
     h->log2_words = log2_exact(bloom_bits / 64);
     h->strategy = strategy;
-    h->part_bits = pb;
-    h->l1_bits = pb <= 12 ? pb : pb - 12;
-    h->slice_log2 = lw - pb;
     if (strategy == KC_STRATEGY_PARTITIONED) slots = 0;
-    h->own_plo = 0;
-    h->own_phi = strategy == KC_STRATEGY_PARTITIONED ? (1u << pb) : 0u;
     if (c.own_bits) {
         const int ob = (int)c.own_bits;
         const uint64_t hi = c.own_hi ? c.own_hi : (1ull << ob);
         h->owner = true;
         h->own_h_lo = (uint64_t)c.own_lo << (64 - ob);
         h->own_h_hi = (hi << (64 - ob)) - 1ull;  // hi = 2^ob wraps to 0, giving ~0
-        h->own_plo = c.own_lo << (pb - ob);
-        h->own_phi = (uint32_t)(hi << (pb - ob));
     }
+    set_partitions(h, pb);
+    h->auto_part = strategy == KC_STRATEGY_PARTITIONED && c.part_bits == 0;
+    h->base_part_bits = pb;
     h->n_slots = slots;
     h->log2_slots = slots ? log2_exact(slots) : 0;
 
@@ -1166,6 +1195,7 @@ kc_status kc_add_reads(kc_handle h, int sample, const uint64_t* packed_reads, co
     if (b1 < b0) return fail(KC_ERR_ARG, "read offsets decrease");
     if (b1 == b0) return KC_OK;
     if (!packed_reads || !n_mask) return fail(KC_ERR_ARG, "packed_reads or n_mask is null");
+    choose_partitions(h, b1 - b0, n_reads);
 
     const uint64_t B = (b0 / 64) * 64;
     const uint64_t n_local = b1 - B;

@@ -44,6 +44,11 @@ struct Batch {
 
 enum class State { Open, Finalized, Poisoned };
 
+// Windows per partition the library's own choice of partition bits aims at:
+// the partition consumer's threads (512) times the 64 iterations of each
+// thread whose windows it counts in its filter pass.
+constexpr uint64_t kWindowsPerPartition = 32768;
+
 // Host reads copied in chunks by kc_add_reads: chunk c covers units
 // [u[c], u[c + 1]); its packed words (and the next unit's first word) and
 // N-mask words (and the next one) are on the device once ev[c] has completed
@@ -119,6 +124,11 @@ struct kc_ctx {
     int part_bits = 0;   // partitioned: 2^part_bits partitions
     int l1_bits = 0;     // partitioned: bits of the first grouping at ingest (= part_bits up to 12)
     int slice_log2 = 0;  // partitioned: filter words per partition
+    // partitioned, kc_config.part_bits = 0: the partition bits of the filter
+    // alone (slices of 4096 words), raised at the first kc_add_reads after
+    // create / reset for the windows it brings (kcapi::choose_partitions)
+    bool auto_part = false;
+    int base_part_bits = 0;
 
     uint64_t* bloom = nullptr;
     uint64_t* bloom2 = nullptr;  // the Prune chain's second filter (kc_config.prune_chain)

@@ -73,6 +73,20 @@ def _owners_parity(w, o, n_owners, own_bits, **kw):
 
 
 @pytest.mark.parametrize("n_owners", [2, 4])
+def test_owners_with_library_partition_bits(oracle_mod, n_owners):
+    """Owners of 2^2 shards whose partitions the library raises from 4 to 64
+    at their first kc_add_reads (a 2^20-bit filter, tiny's 1.4 M windows):
+    each owner's partition range follows, and the merge is the oracle's."""
+    w = synth.tiny()
+    w.bloom_bits = 1 << 20
+    o = oracle_mod.count(w)
+    c = _count(w, own_bits=2, own_lo=0, own_hi=1)
+    assert c.stats()["partitions"] == 64
+    c.close()
+    _owners_parity(w, o, n_owners, own_bits=2)
+
+
+@pytest.mark.parametrize("n_owners", [2, 4])
 def test_owners_merge_to_the_oracle_tiny(oracle_mod, n_owners):
     w = synth.tiny(scale=0.5)
     o = oracle_mod.count(w)

@@ -269,6 +269,58 @@ def test_errors_are_reported_not_faulted(oracle_mod):
     assert e.value.name == "KC_ERR_CAPACITY"
 
 
+def library_part_bits(bloom_bits, bases, reads, k):
+    """The partition bits the library picks when kc_config.part_bits is 0, as
+    include/kc.h states the rule: slices of 4096 filter words, or more
+    partitions, up to 2^12, for at most 32768 windows (bases - reads * (k - 1))
+    each."""
+    lw = (bloom_bits // 64).bit_length() - 1
+    base = min(20, max(1, lw - 12))
+    est = max(0, bases - reads * (k - 1))
+    want = 0
+    while want < 12 and (est >> want) > 32768:
+        want += 1
+    return max(base, min(want, lw))
+
+
+def test_library_partition_bits_follow_the_windows(oracle_mod):
+    """part_bits left to the library: a 2^20-bit filter alone gives 4
+    partitions of 4096 words, but tiny's 1.4 M windows take 64 partitions of at
+    most 32768 windows, which the first kc_add_reads sets; after a reset a job
+    of 1,000 reads is back at 4.  Both results and filters are the oracle's."""
+    w = synth.tiny()
+    w.bloom_bits = 1 << 20
+    rs = w.samples[0]
+    o = oracle_mod.count(w)
+    c = kc.KmerCounter(w.k, 1, w.bloom_bits, w.n_hashes, w.min_count, strategy="partitioned")
+    assert c.stats()["partitions"] == 4
+    c.add_readset(0, rs)
+    c.finalize()
+    pb = library_part_bits(w.bloom_bits, rs.n_bases, rs.n_reads, w.k)
+    assert pb == 6
+    assert c.stats()["partitions"] == 1 << pb
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    small = synth.Workload("tiny_1000", [rs.slice(0, 1000)], k=w.k, bloom_bits=w.bloom_bits, n_hashes=w.n_hashes,
+                           min_count=w.min_count)
+    o2 = oracle_mod.count(small)
+    c.reset()
+    c.add_readset(0, small.samples[0])
+    c.finalize()
+    assert c.stats()["partitions"] == 4
+    assert_same_result(c, o2)
+    assert_same_bloom(c, o2)
+    # the first call decides: a second one adds to the partitions already chosen
+    c.reset()
+    c.add_readset(0, rs.slice(0, 1000))
+    c.add_readset(0, rs.slice(1000, rs.n_reads))
+    c.finalize()
+    assert c.stats()["partitions"] == 4
+    assert_same_result(c, o)
+    assert_same_bloom(c, o)
+    c.close()
+
+
 def test_partition_fallback_matches(oracle_mod):
     """With splitting switched off, two partitions with 1024-slot shared-memory
     tables cannot hold tiny's candidates: every partition takes the
