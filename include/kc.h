@@ -89,10 +89,11 @@ typedef struct kc_config {
                                      partitions (1..20; above 12 the hashes are
                                      grouped in two levels).  0: chosen by the
                                      library -- filter slices of 4096 words, or
-                                     more partitions (at most 2^12) when the
-                                     first kc_add_reads after create / reset
-                                     brings more than 32768 windows (bases -
-                                     reads * (k - 1)) per partition             */
+                                     more partitions (at most 2^12, slices of at
+                                     least 8 words) when the first kc_add_reads
+                                     after create / reset brings more than 32768
+                                     windows (bases - reads * (k - 1)) per
+                                     partition                                  */
     uint64_t table_slots;         /* direct: open-addressing slots (power of two)
                                      of the global table                            */
     uint32_t spill;               /* partitioned: kc_finalize takes 64 groups of

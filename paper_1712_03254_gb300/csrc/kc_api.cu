@@ -828,18 +828,19 @@ void set_partitions(kc_handle h, int pb) {
 
 // Partition bits chosen by the library (kc_config.part_bits = 0): at the
 // first kc_add_reads after create / reset, enough partitions, up to 2^12 (one
-// grouping level), for at most kWindowsPerPartition windows each, estimated
-// as bases - reads * (k - 1) of this call; never fewer than the filter's own
-// (slices of 4096 words).  The consumer counts a partition's windows in one
-// pass over its hashes while they number at most its threads * 64, and a
-// partition of fewer windows holds fewer keys in its shared-memory table.
+// grouping level) and filter slices of at least 8 words, for at most
+// kWindowsPerPartition windows each, estimated as bases - reads * (k - 1) of
+// this call; never fewer than the filter's own (slices of 4096 words).  The
+// consumer counts a partition's windows in one pass over its hashes while
+// they number at most its threads * 64, and a partition of fewer windows
+// holds fewer keys in its shared-memory table.
 void choose_partitions(kc_handle h, uint64_t bases, uint64_t n_reads) {
     if (!h->auto_part || !h->batches.empty()) return;
     const uint64_t edge = n_reads * (uint64_t)(h->k - 1);
     const uint64_t est = bases > edge ? bases - edge : 0;
     int want = 0;
     while (want < 12 && (est >> want) > kWindowsPerPartition) ++want;
-    const int pb = std::max(h->base_part_bits, std::min(want, h->log2_words));
+    const int pb = std::max(h->base_part_bits, std::min(want, h->log2_words - 3));
     if (pb != h->part_bits) set_partitions(h, pb);
 }
 

@@ -272,15 +272,15 @@ def test_errors_are_reported_not_faulted(oracle_mod):
 def library_part_bits(bloom_bits, bases, reads, k):
     """The partition bits the library picks when kc_config.part_bits is 0, as
     include/kc.h states the rule: slices of 4096 filter words, or more
-    partitions, up to 2^12, for at most 32768 windows (bases - reads * (k - 1))
-    each."""
+    partitions, up to 2^12 and slices of at least 8 words, for at most 32768
+    windows (bases - reads * (k - 1)) each."""
     lw = (bloom_bits // 64).bit_length() - 1
     base = min(20, max(1, lw - 12))
     est = max(0, bases - reads * (k - 1))
     want = 0
     while want < 12 and (est >> want) > 32768:
         want += 1
-    return max(base, min(want, lw))
+    return max(base, min(want, lw - 3))
 
 
 def test_library_partition_bits_follow_the_windows(oracle_mod):
